@@ -1,0 +1,111 @@
+"""Pins of the top-k / Long-Axis-Split oracle (Sec. 2.2, Alg. 1-2)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+import synth
+from oracle import densify as od
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "las_worked_example.json")
+
+
+def _one(g, i):
+    return {k: (v[i:i + 1] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
+
+
+def test_worked_example_with_paper_constants():
+    ex = json.load(open(GOLDEN))
+    p = ex["params"]
+    # the paper's constants, Sec. 2.2 after Alg. 1
+    assert p == {"k_off": 0.5, "long_factor": 0.5, "other_factor": 0.85, "beta": 0.6}
+    assert od.PAPER_PRESET == p
+    gs = ex["gaussians"]
+    g = {"means": np.array([x["mean"] for x in gs]),
+         "log_scales": np.log(np.array([x["scale"] for x in gs])),
+         "quats": np.array([x["quat_wxyz"] for x in gs]),
+         "opacity_logits": np.array([math.log(x["opacity"] / (1 - x["opacity"])) for x in gs]),
+         "sh": np.zeros((len(gs), 1, 3)), "sh_degree": 0}
+    out = od.las_split(g, np.ones(len(gs), bool), **p)
+    n = len(gs)
+    for i, x in enumerate(gs):
+        assert int(np.argmax(g["log_scales"][i])) == x["expected_long_axis"]
+        for slot, key in ((i, "expected_child0_mean"), (n + i, "expected_child1_mean")):
+            np.testing.assert_allclose(out["means"][slot], x[key], rtol=0, atol=1e-15)
+            np.testing.assert_allclose(np.exp(out["log_scales"][slot]), x["expected_scale"], rtol=1e-14)
+            np.testing.assert_allclose(1 / (1 + np.exp(-out["opacity_logits"][slot])),
+                                       x["expected_opacity"], rtol=1e-14)
+            np.testing.assert_array_equal(out["quats"][slot], g["quats"][i])
+
+
+@pytest.mark.parametrize("preset", ["paper", "config"])
+def test_children_symmetric_and_offset_along_long_axis(preset):
+    p = od.PAPER_PRESET if preset == "paper" else od.CONFIG_PRESET
+    g = synth.gaussians(300, 3, seed=11)
+    g["quats"] = g["quats"] * np.random.default_rng(1).uniform(0.5, 2.0, (300, 1)).astype(np.float32)
+    mask = np.zeros(300, bool)
+    mask[::3] = True
+    out = od.las_split(g, mask, **p)
+    sel = np.nonzero(mask)[0]
+    n = 300
+    rot = Rotation.from_quat(g["quats"].astype(np.float64), scalar_first=True).as_matrix()
+    for rank, i in enumerate(sel):
+        c0, c1 = out["means"][i], out["means"][n + rank]
+        mu = g["means"][i].astype(np.float64)
+        np.testing.assert_allclose(0.5 * (c0 + c1), mu, atol=1e-15)
+        s = g["log_scales"][i].astype(np.float64)
+        l = int(np.argmax(s))
+        d = 0.5 * (c0 - c1)
+        assert abs(np.linalg.norm(d) - p["k_off"] * math.exp(s[l])) < 1e-14
+        # Alg. 2's column read equals R (off e_l) with R from scipy
+        e = np.zeros(3)
+        e[l] = p["k_off"] * math.exp(s[l])
+        np.testing.assert_allclose(d, rot[i] @ e, atol=1e-14)
+        ds = out["log_scales"][i] - s
+        for a in range(3):
+            want = math.log(p["long_factor"] if a == l else p["other_factor"])
+            assert abs(ds[a] - want) < 1e-14
+        sig_new = 1 / (1 + math.exp(-out["opacity_logits"][i]))
+        sig_old = 1 / (1 + math.exp(-float(g["opacity_logits"][i])))
+        assert abs(sig_new - p["beta"] * sig_old) < 1e-14
+        np.testing.assert_array_equal(out["sh"][n + rank], g["sh"][i])
+        np.testing.assert_array_equal(out["quats"][n + rank], g["quats"][i])
+    untouched = ~mask
+    np.testing.assert_array_equal(out["means"][:n][untouched], g["means"][untouched])
+    np.testing.assert_array_equal(out["log_scales"][:n][untouched], g["log_scales"][untouched])
+
+
+def test_config_preset_changes_only_the_long_axis():
+    g = synth.gaussians(50, 0, seed=2)
+    out = od.las_split(g, np.ones(50, bool), **od.CONFIG_PRESET)
+    for i in range(50):
+        s = g["log_scales"][i].astype(np.float64)
+        l = int(np.argmax(s))
+        changed = np.nonzero(out["log_scales"][i] != s)[0]
+        assert list(changed) == [l]
+
+
+def test_long_axis_ties_go_to_lowest_index():
+    g = {"means": np.zeros((1, 3)), "log_scales": np.array([[-2.0, -1.0, -1.0]]),
+         "quats": np.array([[1.0, 0, 0, 0]]), "opacity_logits": np.zeros(1),
+         "sh": np.zeros((1, 1, 3)), "sh_degree": 0}
+    out = od.las_split(g, np.ones(1, bool), **od.CONFIG_PRESET)
+    np.testing.assert_allclose(out["means"][0], [0, math.exp(-1.0), 0], atol=1e-15)
+
+
+def test_topk_ties_lowest_index_and_brute_force():
+    s = np.array([0.5, 0.9, 0.5, 0.1, 0.9, 0.5, 0.7], dtype=np.float32)
+    m = od.topk_mask(s, 4)
+    # 0.9 (1, 4), 0.7 (6), then the lowest-index 0.5 (0)
+    assert list(np.nonzero(m)[0]) == [0, 1, 4, 6]
+    rng = np.random.default_rng(0)
+    for trial in range(20):
+        n = int(rng.integers(1, 200))
+        s = rng.integers(0, 10, n).astype(np.float32)
+        k = int(rng.integers(0, n + 1))
+        ref = sorted(range(n), key=lambda i: (-float(s[i]), i))[:k]
+        assert set(np.nonzero(od.topk_mask(s, k))[0]) == set(ref)
+        assert od.topk_mask(s, k).sum() == k
