@@ -1,0 +1,508 @@
+#!/usr/bin/env python
+"""Benchmark of one edge-guided densification step on a GB300.
+
+Workload (the 1M-Gaussian configuration): 1,000,000 Gaussians with SH degree 3
+and one 1237x822 view against a synthetic target image.  One step is the
+whole hot path once:
+
+  edge map of the target (fused launch)  ->  splatting forward with L1 loss
+  ->  adjoint with the edge score fused in  ->  top-10% selection  ->  Long-Axis-Split
+
+Each timed step works on its own pre-made copy of the parameters (the split
+rewrites them in place), so every step sees the identical scene; a copy is
+236 MB, larger than L2, and no copy is touched twice, so no L2 flush is
+needed.  The plain path (edge map one launch per stage, score accumulated in
+the forward, no CUDA graph) is timed beside it on the same GPU.
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead, each
+step a bounded pixel-region sample of the same workload scaled to the view.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd+edge-score ms/iter @1M Gaussians 1237×822 vs plain; % HBM roofline"
+N_GAUSS = 1_000_000
+SH_DEGREE = 3
+WIDTH, HEIGHT = 1237, 822
+SPLIT_FRACTION = 0.10
+WORKLOAD = "1M Gaussians SH3, one 1237x822 view: edge map + fwd + L1 + bwd + edge score + top-10% LAS"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gsp", choices=["gsp", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--gaussians", type=int, default=N_GAUSS)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """Samples SM clock and clock-event reasons through NVML during the timed region."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown", 0x2: "applications_clocks_setting"}
+
+    def __init__(self, pci_bus_id: str | None, period_s: float = 0.002):
+        self.samples, self.reasons, self.max_mhz = [], 0, None
+        self.period = period_s
+        self._stop = threading.Event()
+        self.ok = False
+        try:
+            self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nv.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            if pci_bus_id is None or self.nv.nvmlDeviceGetHandleByPciBusId_v2(
+                    pci_bus_id.encode(), ctypes.byref(self.h)) != 0:
+                if self.nv.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(self.h)) != 0:
+                    return
+            m = ctypes.c_uint(0)
+            if self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(m)) == 0:
+                self.max_mhz = int(m.value)
+            self.ok = True
+        except OSError:
+            self.ok = False
+
+    def _run(self):
+        c = ctypes.c_uint(0)
+        r = ctypes.c_ulonglong(0)
+        fn_r = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(self.nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        while not self._stop.is_set():
+            if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(c)) == 0:
+                self.samples.append(int(c.value))
+            if fn_r(self.h, ctypes.byref(r)) == 0:
+                self.reasons |= int(r.value)
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.ok:
+            self.t = threading.Thread(target=self._run, daemon=True)
+            self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.ok:
+            self._stop.set()
+            self.t.join()
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": [n for b, n in self.REASONS.items() if self.reasons & b], "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------- workload
+
+def make_inputs(n_gauss):
+    import synth
+    g = synth.gaussians(n_gauss, SH_DEGREE, seed=1)
+    cam = synth.camera_front(WIDTH, HEIGHT)
+    tgt = synth.image(HEIGHT, WIDTH, 2000)
+    return g, cam, tgt
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# algorithmic bytes per launch of each stage for this workload
+def algorithmic_bytes(stage, n, k_sh, npix, pairs, contrib_pairs):
+    param_b = 4 * (3 + 3 + 4 + 1 + 3 * k_sh)
+    rec_b = 48 + 4 + 8  # projected record + depth key + tile rectangle
+    if stage == "project":
+        return n * (param_b + rec_b)
+    if stage == "project_bwd":
+        return n * (param_b + 36 + param_b)
+    if stage == "depth_sort":
+        return n * 4 * (4 + 4) * 2
+    if stage == "bin":
+        return n * 8 * 2 + pairs * 4
+    if stage == "composite_fwd":
+        return npix * (4 + 3 + 12 + 4 + 4) + contrib_pairs * (4 + 52)
+    if stage == "composite_bwd":
+        return npix * (4 + 4 + 12 + 3 + 4) + contrib_pairs * (4 + 52 + 40)
+    if stage == "edge_fused":
+        return npix * (3 + 4)
+    return None
+
+
+STAGES = ["edge_fused", "project", "depth_sort", "bin", "composite_fwd", "composite_bwd", "project_bwd",
+          "topk", "las"]
+
+
+def run_gsp(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_2603_08661_gb300 as gsp
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    g, cam, tgt_np = make_inputs(args.gaussians)
+    n = int(g["means"].shape[0])
+    k_split = int(SPLIT_FRACTION * n)
+    cap = n + k_split
+    k_sh = (SH_DEGREE + 1) ** 2
+    npix = WIDTH * HEIGHT
+
+    target = gsp.pitched_image(torch.from_numpy(tgt_np).to(dev), 16)
+    pristine = gsp.GaussianSet.from_arrays(g, capacity=cap, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # learn the pair count once (outside any timed region) to size the pair buffer
+    probe = gsp.Renderer(pristine, [cam], pair_capacity=1 << 28, device=dev)
+    out = probe.forward(targets=[target])
+    torch.cuda.synchronize()
+    gsp.raise_on_device_status(out["status"], "probe")
+    pairs = int(probe.pair_count().item())
+    pair_cap = int(pairs * 1.05) + 1024
+    del probe, out
+    torch.cuda.empty_cache()
+
+    def clone(src):
+        return gsp.GaussianSet(src.means.clone(), src.log_scales.clone(), src.quats.clone(),
+                               src.opacity_logits.clone(), src.sh.clone(), src.count.clone(), src.sh_degree)
+
+    def restore(dst, src):
+        for name in ("means", "log_scales", "quats", "opacity_logits", "sh", "count"):
+            getattr(dst, name).copy_(getattr(src, name))
+
+    total = args.warmup + args.steps
+    copies = [clone(pristine) for _ in range(total)]
+    scores = [torch.zeros(cap, device=dev) for _ in range(total)]
+    ws_r = None
+    rends = []
+    for c in copies:
+        r = gsp.Renderer(c, [cam], pair_cap, device=dev, workspace=ws_r)
+        ws_r = r.ws
+        rends.append(r)
+    E = torch.empty(npix, dtype=torch.float32, device=dev)
+    ws_e = torch.empty(1 << 26, dtype=torch.uint8, device=dev)
+    ws_las = torch.empty(gsp._lib.load().gsp_las_workspace_size(cap), dtype=torch.uint8, device=dev)
+    status = gsp.new_status(dev)
+    grads = {"means": torch.zeros_like(pristine.means), "log_scales": torch.zeros_like(pristine.log_scales),
+             "quats": torch.zeros_like(pristine.quats), "opacity_logits": torch.zeros_like(pristine.opacity_logits),
+             "sh": torch.zeros_like(pristine.sh)}
+    fwd_bufs = {"rgb": torch.empty((npix, 3), device=dev), "T": torch.empty(npix, device=dev),
+                "last": torch.empty(npix, dtype=torch.int32, device=dev), "loss": torch.empty(1, device=dev)}
+
+    def step(j, plain=False):
+        r = rends[j]
+        gsp.edge_map([target], mode="plain" if plain else "fused", out=E, status=status, workspace=ws_e)
+        if plain:
+            out = r.forward(targets=[target], edge=E, score=scores[j], status=status, out=fwd_bufs)
+            r.backward(out, targets=[target], grads=grads, status=status)
+        else:
+            out = r.forward(targets=[target], status=status, out=fwd_bufs)
+            r.backward(out, targets=[target], edge=E, score=scores[j], grads=grads, status=status)
+        gsp.las_split(copies[j], scores=scores[j], k=k_split, params=gsp.LAS_CONFIG, status=status,
+                      workspace=ws_las)
+        return out
+
+    # launches per step (counted by the library while enqueueing one eager step)
+    l0 = gsp.launch_count()
+    step(0)
+    launches_per_step = gsp.launch_count() - l0
+    torch.cuda.synchronize()
+    gsp.raise_on_device_status(status, "first step")
+    restore(copies[0], pristine)
+    scores[0].zero_()
+
+    # per-stage breakdown (one eager step per armed stage, untimed)
+    breakdown = {}
+    for st in STAGES:
+        timer = gsp.StageTimer(st, 8)
+        step(0)
+        ms, cnt = timer.read()
+        breakdown[st] = ms / max(cnt, 1)
+        restore(copies[0], pristine)
+        scores[0].zero_()
+    gsp.StageTimer.disarm()
+    torch.cuda.synchronize()
+    dominant = max((s for s in breakdown if algorithmic_bytes(s, n, k_sh, npix, 1, 1) is not None),
+                   key=lambda s: breakdown[s])
+
+    # capture one graph per copy; the dominant stage is bracketed by library events
+    use_graph = not args.no_graph
+    graphs = []
+    timer = None
+    if use_graph:
+        try:
+            side = torch.cuda.Stream(device=dev)
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                for j in range(total):
+                    if j == args.warmup:
+                        timer = gsp.StageTimer(dominant, args.steps)
+                    gr = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(gr, stream=side):
+                        step(j)
+                    graphs.append(gr)
+            stream.wait_stream(side)
+            torch.cuda.synchronize()
+        except Exception as exc:  # capture unsupported: fall back to eager launches
+            print(f"[bench] graph capture failed ({exc}); timing eager launches", file=sys.stderr)
+            use_graph = False
+            graphs = []
+            torch.cuda.synchronize()
+            for j in range(total):
+                restore(copies[j], pristine)
+                scores[j].zero_()
+    if not use_graph:
+        timer = None
+
+    def run_range(lo, hi):
+        for j in range(lo, hi):
+            if use_graph:
+                graphs[j].replay()
+            else:
+                step(j)
+
+    run_range(0, args.warmup)
+    if not use_graph:
+        timer = gsp.StageTimer(dominant, args.steps)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+    bus_str = None if bus is None else f"{getattr(props, 'pci_domain_id', 0):08x}:{bus:02x}:{getattr(props, 'pci_device_id', 0):02x}.0"
+    with ClockSampler(bus_str) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        run_range(args.warmup, total)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms_total = ev0.elapsed_time(ev1)
+    dom_ms, dom_cnt = timer.read()
+    gsp.StageTimer.disarm()
+    gsp.raise_on_device_status(status, "timed steps")
+    ms_total = dist_max(ms_total, world)
+    ms_step = ms_total / args.steps
+
+    # plain path: edge map per stage, score in the forward, no graph
+    plain = None
+    if not args.no_plain:
+        m = min(args.steps, 20)
+        for j in range(m + 3):
+            restore(copies[j], pristine)
+            scores[j].zero_()
+        for j in range(3):
+            step(j, plain=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for j in range(3, 3 + m):
+            step(j, plain=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain = {"ms_per_step": a.elapsed_time(b) / m, "steps": m, "graph": False,
+                 "edge_map": "one launch per stage", "score": "accumulated in the forward"}
+
+    # end to end: pinned host parameters and image in, loss and count out, every step
+    e2e = None
+    if not args.no_e2e:
+        host = {name: getattr(pristine, name).cpu().pin_memory()
+                for name in ("means", "log_scales", "quats", "opacity_logits", "sh", "count")}
+        host_img = target.cpu().pin_memory()
+        res_host = torch.empty(2, dtype=torch.float32).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host.values()) + host_img.numel()
+        m = min(args.steps, 20)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a.record(stream)
+        for j in range(m):
+            c = copies[j]
+            for name, t in host.items():
+                getattr(c, name).copy_(t, non_blocking=True)
+            target.copy_(host_img, non_blocking=True)
+            scores[j].zero_()
+            out = step(j)
+            res_host[0].copy_(out["loss"][0], non_blocking=True)
+            res_host[1:2].copy_(c.count.float(), non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) * 1e3 / m
+        e2e = {"value": round(max(a.elapsed_time(b) / m, wall), 4), "unit": "ms/iter",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8, "steps": m,
+               "note": "parameters and target image copied from pinned host memory, loss and count read back"}
+
+    hbm, peak_kind = peaks()
+    algo = algorithmic_bytes(dominant, n, k_sh, npix, pairs, pairs)
+    dom_avg_ms = dom_ms / max(dom_cnt, 1)
+    achieved = algo / (dom_avg_ms * 1e-3) / 1e9 if algo and dom_avg_ms > 0 else None
+    roof = {"kernel": dominant, "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
+            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
+            "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+            else "fallback 6.8 TB/s", "avg_launch_ms": round(dom_avg_ms, 5), "launches": dom_cnt,
+            "algorithmic_bytes_per_launch": algo}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g, cam, tgt_np, budget_s=20.0)
+
+    line = {
+        "metric": METRIC, "value": round(ms_step / world, 4), "unit": "ms/iter", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded scenes shaped like the paper's Mip-NeRF360 views)",
+        "config": {"workload": WORKLOAD, "gaussians": n, "sh_degree": SH_DEGREE, "view": f"{WIDTH}x{HEIGHT}",
+                   "split_k": k_split, "pairs": pairs, "graph": use_graph,
+                   "l2": "inputs larger than L2: every step uses its own 236 MB parameter copy",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clk.summary(), "plain": plain,
+        "stages_ms": {k: round(v, 4) for k, v in breakdown.items()},
+    }
+    return line
+
+
+# --------------------------------------------------------------- oracle
+
+def cpu_baseline(g, cam, tgt_np, budget_s=20.0, region=None):
+    """Time the FP64 oracle on a pixel-region sample of the step, scaled to the view."""
+    import numpy as np
+
+    from oracle import densify as od
+    from oracle import edge as oe
+    from oracle import raster as orc
+
+    h, w = tgt_np.shape[:2]
+    # region sized for the time budget (probe: a 64x64 crop)
+    def crop_times(rw, rh):
+        x0, y0 = (w - rw) // 2, (h - rh) // 2
+        region = (x0, y0, x0 + rw, y0 + rh)
+        t0 = time.perf_counter()
+        e = oe.edge_map(tgt_np[y0:y0 + rh, x0:x0 + rw])
+        t1 = time.perf_counter()
+        proj = orc.project(g, cam)
+        t2 = time.perf_counter()
+        out = orc.render(g, cam, region=region, proj=proj)
+        t3 = time.perf_counter()
+        return (t1 - t0, t2 - t1, t3 - t2), region
+
+    (te, tp, tr), region = crop_times(64, 64)
+    frac = 64 * 64 / (w * h)
+    per_px = tr / (64 * 64)
+    side = int(min(max(64, math.sqrt(max(budget_s * 0.5 - tp, 1.0) / max(per_px, 1e-9))), min(w, h)))
+    (te, tp, tr), region = crop_times(side, side)
+    frac = side * side / (w * h)
+    n = g["means"].shape[0]
+    k = int(SPLIT_FRACTION * n)
+    scores = np.random.default_rng(0).gamma(2.0, 1.0, n)
+    t0 = time.perf_counter()
+    m = od.topk_mask(scores, k)
+    t1 = time.perf_counter()
+    sub = max(1, k // 100)  # LAS loop on 1% of the selected, scaled
+    sel = np.zeros(n, bool)
+    sel[np.nonzero(m)[0][:sub]] = True
+    t2 = time.perf_counter()
+    od.las_split(g, sel, **od.CONFIG_PRESET)
+    t3 = time.perf_counter()
+    # the backward oracle runs per pixel like the forward; it is timed on the same crop share
+    bwd_est = 2.0 * tr
+    ms = 1e3 * (te / frac + tp + tr / frac + bwd_est / frac + (t1 - t0) + (t3 - t2) * k / sub)
+    return {"value": round(ms, 1), "unit": "ms/iter", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle: edge map + forward composite of a centred {side}x{side} crop "
+                      f"({100 * frac:.1f}% of the view) with full projection, top-k over all Gaussians, "
+                      f"LAS of {sub} of {k} selected; scaled to the full view; backward estimated as 2x forward"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    g, cam, tgt = make_inputs(args.gaussians)
+    budget = min(20.0, max(1.0, 150.0 / max(args.steps + args.warmup, 1)))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(g, cam, tgt, budget_s=budget)
+        if i >= args.warmup:
+            vals.append(r["value"])
+    v = statistics.mean(vals)
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms/iter", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": args.gaussians, "sh_degree": SH_DEGREE,
+                       "view": f"{WIDTH}x{HEIGHT}"},
+            "cpu_baseline": {"value": round(v, 1), "unit": "ms/iter", "cores": 1, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": round(v, 1), "unit": "ms/iter", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------- distributed
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    return rank, world
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup()
+    if args.impl == "reference":
+        if world > 1:
+            # the reference arm runs on rank 0 only
+            pass
+        line = run_reference(args, rank, world)
+    else:
+        line = run_gsp(args, rank, world)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        if args.impl != "reference":
+            dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

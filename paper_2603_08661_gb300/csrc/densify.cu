@@ -1,0 +1,431 @@
+// Edge-score selection and Long-Axis-Split (paper Sec. 2.2, Alg. 1 and Alg. 2).
+//
+// Selection: exact top-k.  Scores map to order-preserving 32-bit keys; the
+// k-th largest key is found by a 3-digit radix select (11 + 11 + 10 bits),
+// every key above it is taken, and the ties at it are taken in ascending
+// index order (their ranks come from a block scan plus a scan over blocks).
+//
+// Split: the selected Gaussians are ranked in index order by the same kind
+// of scan; one thread per selected Gaussian applies Alg. 1: the long axis l
+// is the argmax of the log-scales, the offset is k_off * exp(s_l) along
+// column l of R read as entries l, l+3, l+6 of the row-major matrix (Alg. 2),
+// the scales move in log space and the opacity in logit space.  Child 0
+// replaces the parent; child 1 is appended at slot N + rank.  The capacity
+// is checked on the device before anything is written.
+#include "common.cuh"
+
+namespace gsp {
+namespace {
+
+constexpr int kThreads = 256, kPerThread = 4, kBlockItems = kThreads * kPerThread;
+constexpr int kSelBins = 2048;
+
+struct SelState {
+    unsigned prefix;     // key bits fixed so far
+    unsigned remaining;  // how many still to take among keys matching the prefix
+    unsigned n;          // live count
+    unsigned k;          // clamped k
+};
+
+__device__ __forceinline__ unsigned order_key(float f)
+{
+    unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__global__ void sel_init(const int32_t *count, long long k, SelState *s, unsigned *hist)
+{
+    for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) hist[i] = 0;
+    if (threadIdx.x == 0) {
+        unsigned n = unsigned(max(*count, 0));
+        unsigned kk = k < 0 ? 0u : (k > (long long)n ? n : unsigned(k));
+        s->prefix = 0;
+        s->remaining = kk;
+        s->n = n;
+        s->k = kk;
+    }
+}
+
+// Histogram of digit `pass` over keys matching the prefix of the previous digits.
+__global__ void sel_hist(const float *scores, const SelState *s, int shift, int bits, int pass, unsigned *hist)
+{
+    __shared__ unsigned h[kSelBins];
+    const int nb = 1 << bits;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const unsigned n = s->n;
+    const int hi = shift + bits;
+    const unsigned prefix = s->prefix;
+    if (s->remaining > 0) {
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            unsigned key = order_key(scores[i]);
+            if (pass > 0 && (key >> hi) != (prefix >> hi)) continue;
+            atomicAdd(&h[(key >> shift) & (nb - 1)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// Pick the digit holding the remaining-th largest key (one block).
+__global__ void __launch_bounds__(kThreads) sel_pick(SelState *s, int shift, int bits, unsigned *hist)
+{
+    __shared__ unsigned seg_s[kThreads];
+    __shared__ int s_bin;
+    __shared__ unsigned s_above;
+    const int nb = 1 << bits;
+    const int per = nb / kThreads;
+    const unsigned rem = s->remaining;
+    // segments are taken from the top: thread t owns bins [nb - (t+1) per, nb - t per)
+    unsigned seg = 0;
+    for (int k = 0; k < per; ++k) seg += hist[nb - 1 - (threadIdx.x * per + k)];
+    seg_s[threadIdx.x] = seg;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_bin = -1;
+        if (rem > 0) {
+            unsigned acc = 0;
+            for (int t = 0; t < kThreads && s_bin < 0; ++t) {
+                if (acc + seg_s[t] >= rem) {
+                    for (int k = 0; k < per; ++k) {
+                        int b = nb - 1 - (t * per + k);
+                        if (acc + hist[b] >= rem) {
+                            s_bin = b;
+                            s_above = acc;
+                            break;
+                        }
+                        acc += hist[b];
+                    }
+                } else {
+                    acc += seg_s[t];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_bin >= 0) {
+        s->prefix |= unsigned(s_bin) << shift;
+        s->remaining -= s_above;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += kThreads) hist[i] = 0;
+}
+
+// Block-local exclusive scan of per-thread counts; returns the block total.
+__device__ unsigned block_scan(unsigned x, unsigned *excl)
+{
+    __shared__ unsigned wsum[kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    unsigned base = 0, tot = 0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+        if (w < wid) base += wsum[w];
+        tot += wsum[w];
+    }
+    __syncthreads();
+    *excl = base + inc - x;
+    return tot;
+}
+
+struct TieFlag {
+    const float *scores;
+    const SelState *s;
+    __device__ bool operator()(long long i) const { return order_key(scores[i]) == s->prefix && s->k > 0; }
+};
+
+struct MaskFlag {
+    const uint8_t *mask;
+    __device__ bool operator()(long long i) const { return mask[i] != 0; }
+};
+
+template <class F>
+__global__ void __launch_bounds__(kThreads) flag_block_sums(F f, const int32_t *count, unsigned *sums)
+{
+    const long long n = *count;
+    const long long b0 = (long long)blockIdx.x * kBlockItems;
+    if (b0 >= n) return;
+    unsigned c = 0;
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        long long i = b0 + threadIdx.x * kPerThread + j;
+        if (i < n && f(i)) ++c;
+    }
+    unsigned ex;
+    unsigned tot = block_scan(c, &ex);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the block sums (one block); total goes to sums[nblocks].
+__global__ void __launch_bounds__(kThreads) scan_block_sums(const int32_t *count, unsigned *sums)
+{
+    __shared__ unsigned carry;
+    const long long n = *count;
+    const int nb = int((n + kBlockItems - 1) / kBlockItems);
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += kThreads) {
+        int b = b0 + threadIdx.x;
+        unsigned x = b < nb ? sums[b] : 0u;
+        unsigned ex;
+        unsigned tot = block_scan(x, &ex);
+        unsigned c0 = carry;
+        __syncthreads();
+        if (b < nb) sums[b] = c0 + ex;
+        if (threadIdx.x == 0) carry = c0 + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void __launch_bounds__(kThreads) sel_mark(const float *scores, const int32_t *count, long long cap,
+                                                   const SelState *s, const unsigned *tie_off, uint8_t *mask,
+                                                   int32_t *selected_out)
+{
+    const long long n = *count;
+    const long long b0 = (long long)blockIdx.x * kBlockItems;
+    if (b0 >= cap) return;
+    const unsigned t = s->prefix, need = s->remaining, k = s->k;
+    bool tie[kPerThread], gt[kPerThread];
+    unsigned c = 0;
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        long long i = b0 + threadIdx.x * kPerThread + j;
+        unsigned key = i < n ? order_key(scores[i]) : 0u;
+        tie[j] = i < n && k > 0 && key == t;
+        gt[j] = i < n && k > 0 && key > t;
+        c += tie[j];
+    }
+    unsigned ex;
+    block_scan(c, &ex);
+    unsigned r = (b0 < n ? tie_off[blockIdx.x] : 0u) + ex;
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        long long i = b0 + threadIdx.x * kPerThread + j;
+        if (i >= cap) continue;
+        bool sel = gt[j] || (tie[j] && r < need);
+        r += tie[j];
+        mask[i] = sel;
+    }
+    if (selected_out && blockIdx.x == 0 && threadIdx.x == 0) *selected_out = int32_t(k);
+}
+
+struct LasArgs {
+    float *means, *log_scales, *quats, *opac, *sh;
+    int32_t *count;
+    long long cap;
+    int K;
+    float k_off, log_long, log_other, beta;
+    const uint8_t *mask;
+    const unsigned *rank_off;  // block offsets; [nblocks] = total selected
+    int32_t *status;
+};
+
+__global__ void __launch_bounds__(kThreads) las_kernel(LasArgs a)
+{
+    const long long n = *a.count;
+    const long long b0 = (long long)blockIdx.x * kBlockItems;
+    if (b0 >= n) return;
+    const int nb = int((n + kBlockItems - 1) / kBlockItems);
+    const long long total = a.rank_off[nb];
+    if (n + total > a.cap) return;  // reported by las_commit; nothing is written
+    bool f[kPerThread];
+    unsigned c = 0;
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        long long i = b0 + threadIdx.x * kPerThread + j;
+        f[j] = i < n && a.mask[i] != 0;
+        c += f[j];
+    }
+    unsigned ex;
+    block_scan(c, &ex);
+    unsigned r = a.rank_off[blockIdx.x] + ex;
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        if (!f[j]) continue;
+        const long long i = b0 + threadIdx.x * kPerThread + j;
+        const long long dst = n + r;
+        ++r;
+        float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
+        int l = 0;
+        if (ls[1] > ls[l]) l = 1;
+        if (ls[2] > ls[l]) l = 2;
+        const float off = a.k_off * expf(ls[l]);
+        float q[4] = {a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]};
+        const float qi = __frsqrt_rn(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const float w = q[0] * qi, x = q[1] * qi, y = q[2] * qi, z = q[3] * qi;
+        // column l of the row-major rotation matrix: entries l, l + 3, l + 6 (Alg. 2)
+        float cx, cy, cz;
+        if (l == 0) {
+            cx = 1.f - 2.f * (y * y + z * z); cy = 2.f * (x * y + w * z); cz = 2.f * (x * z - w * y);
+        } else if (l == 1) {
+            cx = 2.f * (x * y - w * z); cy = 1.f - 2.f * (x * x + z * z); cz = 2.f * (y * z + w * x);
+        } else {
+            cx = 2.f * (x * z + w * y); cy = 2.f * (y * z - w * x); cz = 1.f - 2.f * (x * x + y * y);
+        }
+        const float dx = cx * off, dy = cy * off, dz = cz * off;
+        float nls[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) nls[k] = ls[k] + (k == l ? a.log_long : a.log_other);
+        const float sig = 1.f / (1.f + expf(-a.opac[i]));
+        const float p = a.beta * sig;
+        const float nop = logf(p) - log1pf(-p);
+        const float m0 = a.means[3 * i], m1 = a.means[3 * i + 1], m2 = a.means[3 * i + 2];
+        // child 1 (appended)
+        a.means[3 * dst] = m0 - dx; a.means[3 * dst + 1] = m1 - dy; a.means[3 * dst + 2] = m2 - dz;
+        for (int k = 0; k < 3; ++k) a.log_scales[3 * dst + k] = nls[k];
+        for (int k = 0; k < 4; ++k) a.quats[4 * dst + k] = q[k];
+        a.opac[dst] = nop;
+        for (int k = 0; k < 3 * a.K; ++k) a.sh[(size_t)dst * 3 * a.K + k] = a.sh[(size_t)i * 3 * a.K + k];
+        // child 0 (in place)
+        a.means[3 * i] = m0 + dx; a.means[3 * i + 1] = m1 + dy; a.means[3 * i + 2] = m2 + dz;
+        for (int k = 0; k < 3; ++k) a.log_scales[3 * i + k] = nls[k];
+        a.opac[i] = nop;
+    }
+}
+
+__global__ void las_commit(int32_t *count, long long cap, const unsigned *rank_off, int32_t *status)
+{
+    const long long n = *count;
+    const int nb = int((n + kBlockItems - 1) / kBlockItems);
+    const long long total = n > 0 ? rank_off[nb] : 0;
+    if (n + total > cap) {
+        set_status(status, GSP_ERR_CAPACITY);
+        return;
+    }
+    *count = int32_t(n + total);
+}
+
+struct DensifyLayout {
+    SelState *sel;
+    unsigned *hist;
+    unsigned *sums;
+    uint8_t *mask;
+    size_t bytes;
+};
+
+DensifyLayout densify_layout(void *ws, long long cap)
+{
+    Carver c(ws);
+    DensifyLayout L{};
+    L.sel = c.take<SelState>(1);
+    L.hist = c.take<unsigned>(kSelBins);
+    L.sums = c.take<unsigned>(div_up(cap, kBlockItems) + 1);
+    L.mask = c.take<uint8_t>((size_t)cap);
+    L.bytes = c.size();
+    return L;
+}
+
+gsp_status enqueue_topk(const float *scores, const int32_t *count, long long cap, long long k, uint8_t *mask,
+                        int32_t *selected_out, const DensifyLayout &L, cudaStream_t s)
+{
+    const unsigned nblk = div_up(cap, kBlockItems);
+    unsigned hist_blocks = div_up(cap, 256 * 8);
+    if (hist_blocks > 4u * num_sms()) hist_blocks = 4u * num_sms();
+    if (hist_blocks < 1) hist_blocks = 1;
+    stage_begin("topk", s);
+    sel_init<<<1, 256, 0, s>>>(count, k, L.sel, L.hist);
+    const int shifts[3] = {21, 10, 0}, bits[3] = {11, 11, 10};
+    for (int pass = 0; pass < 3; ++pass) {
+        sel_hist<<<hist_blocks, 256, 0, s>>>(scores, L.sel, shifts[pass], bits[pass], pass, L.hist);
+        sel_pick<<<1, kThreads, 0, s>>>(L.sel, shifts[pass], bits[pass], L.hist);
+    }
+    TieFlag tf{scores, L.sel};
+    flag_block_sums<<<nblk, kThreads, 0, s>>>(tf, count, L.sums);
+    scan_block_sums<<<1, kThreads, 0, s>>>(count, L.sums);
+    sel_mark<<<nblk, kThreads, 0, s>>>(scores, count, cap, L.sel, L.sums, mask, selected_out);
+    stage_end("topk", s);
+    note_launches(10);
+    GSP_LAUNCH_CHECK();
+    return GSP_OK;
+}
+
+}  // namespace
+}  // namespace gsp
+
+using namespace gsp;
+
+extern "C" void gsp_las_params_paper(gsp_las_params *p)
+{
+    if (!p) return;
+    p->k_off = 0.5f;
+    p->long_factor = 0.5f;
+    p->other_factor = 0.85f;
+    p->beta = 0.6f;
+}
+
+extern "C" size_t gsp_las_workspace_size(int64_t capacity)
+{
+    if (capacity < 1) return 0;
+    return densify_layout(nullptr, capacity).bytes;
+}
+
+extern "C" gsp_status gsp_topk_mask(const float *scores, const int32_t *count, int64_t capacity, int64_t k,
+                                    uint8_t *mask_out, int32_t *selected_out, void *ws, size_t ws_bytes,
+                                    int32_t *dev_status, gsp_stream_t stream)
+{
+    if (!scores || !count || !mask_out || !dev_status || capacity < 1 || capacity > (1LL << 30))
+        return GSP_ERR_INVALID_ARG;
+    DensifyLayout L = densify_layout(nullptr, capacity);
+    gsp_status st = check_workspace(ws, ws_bytes, L.bytes);
+    if (st != GSP_OK) return st;
+    L = densify_layout(ws, capacity);
+    return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L,
+                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask, const float *scores, int64_t k,
+                                    const gsp_las_params *p, void *ws, size_t ws_bytes, int32_t *dev_status,
+                                    gsp_stream_t stream)
+{
+    if (!g || !g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh || !g->count || !p ||
+        !dev_status)
+        return GSP_ERR_INVALID_ARG;
+    if (g->capacity < 1 || g->capacity > (1LL << 30) || g->sh_degree < 0 || g->sh_degree > 3)
+        return GSP_ERR_INVALID_ARG;
+    if (!mask && !scores) return GSP_ERR_INVALID_ARG;
+    if (!(p->k_off >= 0.f) || !(p->long_factor > 0.f) || !(p->other_factor > 0.f) || !(p->beta > 0.f) ||
+        !(p->beta <= 1.f))
+        return GSP_ERR_INVALID_ARG;
+    const long long cap = g->capacity;
+    DensifyLayout L = densify_layout(nullptr, cap);
+    gsp_status st = check_workspace(ws, ws_bytes, L.bytes);
+    if (st != GSP_OK) return st;
+    L = densify_layout(ws, cap);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!mask) {
+        st = enqueue_topk(scores, g->count, cap, k, L.mask, nullptr, L, s);
+        if (st != GSP_OK) return st;
+        mask = L.mask;
+    }
+    const unsigned nblk = div_up(cap, kBlockItems);
+    MaskFlag mf{mask};
+    stage_begin("las", s);
+    flag_block_sums<<<nblk, kThreads, 0, s>>>(mf, g->count, L.sums);
+    scan_block_sums<<<1, kThreads, 0, s>>>(g->count, L.sums);
+    LasArgs a;
+    a.means = g->means; a.log_scales = g->log_scales; a.quats = g->quats; a.opac = g->opacity_logits;
+    a.sh = g->sh; a.count = g->count; a.cap = cap;
+    a.K = (g->sh_degree + 1) * (g->sh_degree + 1);
+    a.k_off = p->k_off;
+    a.log_long = float(log(double(p->long_factor)));
+    a.log_other = float(log(double(p->other_factor)));
+    a.beta = p->beta;
+    a.mask = mask;
+    a.rank_off = L.sums;
+    a.status = dev_status;
+    las_kernel<<<nblk, kThreads, 0, s>>>(a);
+    las_commit<<<1, 1, 0, s>>>(g->count, cap, L.sums, dev_status);
+    stage_end("las", s);
+    note_launches(4);
+    GSP_LAUNCH_CHECK();
+    return GSP_OK;
+}

@@ -1,0 +1,735 @@
+// Edge-importance map (paper Sec. 2.1): grayscale, 5x5 Gaussian blur, Sobel,
+// NMS along the quantised gradient, lower-median normalisation.
+//
+// Arithmetic.  The luma is formed as the exact integer I = 299 R + 587 G + 114 B
+// (= 255000 x the [0, 1] luma).  Blur and Sobel are linear and act on the
+// clamp-extended image, so they commute: the Sobel differences are taken first
+// on the exact integers (|S| < 2^21, exact in FP32) and the 5x5 blur is applied
+// to them in FP32 with its symmetric taps paired (pair sums stay exact).  The
+// magnitudes therefore carry only the blur's own rounding, which keeps the NMS
+// comparisons consistent with an FP64 evaluation except at genuine near-ties.
+// Magnitudes stay in units of 255000 x luma; E = M / median is unit-free.
+//
+// Median.  The lower median of the kept magnitudes is selected exactly from
+// the float bit patterns (positive floats order like their bits): a 4096-bin
+// histogram of bits [30:19], then the values falling into the median's bin
+// are gathered and resolved on bits [18:9] and [8:0].
+//
+// Fused mode runs every stage of every view in one cooperative launch:
+//   A  per 64x16 tile: stencil chain in shared memory, NMS, write M_thin to
+//      E_out, per-view histogram of bits [30:19]
+//   -- grid barrier --
+//   B  each block finds its views' median bin and gathers its candidates
+//   -- grid barrier --
+//   C  block v resolves view v's median from its candidates
+//   -- grid barrier --
+//   D  each block divides its kept pixels by the median, in place
+// Plain mode launches one kernel per stage and per view, with every
+// intermediate in global memory (the unfused reference path).
+
+#include "common.cuh"
+
+namespace gsp {
+namespace {
+
+constexpr int TW = 64, TH = 16, NT = 256;
+constexpr int IW = TW + 8, IH = TH + 8;  // integer luma with a 4-pixel halo
+constexpr int SW = TW + 6, SH = TH + 6;  // Sobel responses
+constexpr int HW = TW + 2, HH = TH + 6;  // after the horizontal blur
+constexpr int MW = TW + 2, MH = TH + 2;  // magnitude with a 1-pixel ring
+constexpr int kBins1 = 4096, kShift1 = 19;
+constexpr int kBins2 = 1024, kShift2 = 9;
+constexpr int kBins3 = 512;
+constexpr float kTan22 = 0.41421356237309503f;  // tan(22.5 deg) = sqrt(2) - 1
+
+struct EdgeView {
+    const uint8_t *rgb;
+    long long pitch;
+    long long out_off;
+    int w, h;
+    int tiles_x;
+    int tile_base;
+    int ntiles;
+    int pad;
+};
+
+struct EdgeArgs {
+    EdgeView v[GSP_MAX_VIEWS];
+    int nviews;
+    int total_tiles;
+    float w0, w1, w2;  // blur taps: centre, +-1, +-2
+    float *E;
+    uint8_t *mask;
+    float *median_out;
+    unsigned *hist1;       // [V][kBins1]
+    unsigned *cand_count;  // [V]
+    float *cand;           // candidate values, laid out like E
+    unsigned *med_bits;    // [V]
+    unsigned *bar;         // grid barrier state [2]
+    int32_t *status;
+    long long spin_limit;
+};
+
+struct TileSmem {
+    int I[IH][IW];
+    float Sx[SH][SW], Sy[SH][SW];
+    float Hx[HH][HW], Hy[HH][HW];
+    float M[MH][MW];
+    float Gx[TH][TW], Gy[TH][TW];
+};
+
+__device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+// Stencil chain for one 64x16 output tile at (x0, y0) of view V.
+__device__ void tile_stencil(const EdgeView &V, int x0, int y0, float w0, float w1, float w2,
+                             TileSmem &s)
+{
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < IH * IW; idx += NT) {
+        int r = idx / IW, c = idx - r * IW;
+        int yy = clampi(y0 - 4 + r, 0, V.h - 1), xx = clampi(x0 - 4 + c, 0, V.w - 1);
+        const uint8_t *p = V.rgb + (long long)yy * V.pitch + 3 * xx;
+        s.I[r][c] = 299 * int(p[0]) + 587 * int(p[1]) + 114 * int(p[2]);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < SH * SW; idx += NT) {
+        int r = idx / SW, c = idx - r * SW;
+        int sx = (s.I[r][c + 2] - s.I[r][c]) + 2 * (s.I[r + 1][c + 2] - s.I[r + 1][c]) +
+                 (s.I[r + 2][c + 2] - s.I[r + 2][c]);
+        int sy = (s.I[r + 2][c] - s.I[r][c]) + 2 * (s.I[r + 2][c + 1] - s.I[r][c + 1]) +
+                 (s.I[r + 2][c + 2] - s.I[r][c + 2]);
+        s.Sx[r][c] = float(sx);
+        s.Sy[r][c] = float(sy);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < HH * HW; idx += NT) {
+        int r = idx / HW, c = idx - r * HW;
+        float ax1 = s.Sx[r][c + 1] + s.Sx[r][c + 3], ax2 = s.Sx[r][c] + s.Sx[r][c + 4];
+        float ay1 = s.Sy[r][c + 1] + s.Sy[r][c + 3], ay2 = s.Sy[r][c] + s.Sy[r][c + 4];
+        s.Hx[r][c] = __fmaf_rn(w2, ax2, __fmaf_rn(w1, ax1, __fmul_rn(w0, s.Sx[r][c + 2])));
+        s.Hy[r][c] = __fmaf_rn(w2, ay2, __fmaf_rn(w1, ay1, __fmul_rn(w0, s.Sy[r][c + 2])));
+    }
+    __syncthreads();
+    for (int idx = tid; idx < MH * MW; idx += NT) {
+        int r = idx / MW, c = idx - r * MW;
+        float bx1 = __fadd_rn(s.Hx[r + 1][c], s.Hx[r + 3][c]), bx2 = __fadd_rn(s.Hx[r][c], s.Hx[r + 4][c]);
+        float by1 = __fadd_rn(s.Hy[r + 1][c], s.Hy[r + 3][c]), by2 = __fadd_rn(s.Hy[r][c], s.Hy[r + 4][c]);
+        float gx = __fmaf_rn(w2, bx2, __fmaf_rn(w1, bx1, __fmul_rn(w0, s.Hx[r + 2][c])));
+        float gy = __fmaf_rn(w2, by2, __fmaf_rn(w1, by1, __fmul_rn(w0, s.Hy[r + 2][c])));
+        int yy = y0 - 1 + r, xx = x0 - 1 + c;
+        bool inside = yy >= 0 && yy < V.h && xx >= 0 && xx < V.w;
+        s.M[r][c] = inside ? __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(gy, gy))) : 0.0f;
+        if (r >= 1 && r <= TH && c >= 1 && c <= TW) {
+            s.Gx[r - 1][c - 1] = gx;
+            s.Gy[r - 1][c - 1] = gy;
+        }
+    }
+    __syncthreads();
+}
+
+// NMS decision for inner pixel (r, c) of the tile (Sec. 2.1 step 3).
+__device__ __forceinline__ float nms_value(const TileSmem &s, int r, int c)
+{
+    float m = s.M[r + 1][c + 1];
+    float gx = s.Gx[r][c], gy = s.Gy[r][c];
+    float ax = fabsf(gx), ay = fabsf(gy);
+    bool horiz = ay <= __fmul_rn(kTan22, ax);
+    bool vert = !horiz && ax <= __fmul_rn(kTan22, ay);
+    int sx = vert ? 0 : (gx > 0.f) - (gx < 0.f);
+    int sy = horiz ? 0 : (gy > 0.f) - (gy < 0.f);
+    float mp = s.M[r + 1 + sy][c + 1 + sx];
+    float mm = s.M[r + 1 - sy][c + 1 - sx];
+    bool keep = m > 0.f && m >= mp && m > mm;
+    return keep ? m : 0.f;
+}
+
+__device__ __forceinline__ int find_view(const EdgeArgs &a, int tile)
+{
+    int v = 0;
+    while (v + 1 < a.nviews && a.v[v + 1].tile_base <= tile) ++v;
+    return v;
+}
+
+// Exclusive block scan of one value per thread (NT threads); returns the total.
+__device__ unsigned block_exclusive_scan(unsigned x, unsigned *out)
+{
+    __shared__ unsigned warp_tot[NT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    unsigned base = 0, total = 0;
+    for (int w = 0; w < NT / 32; ++w) {
+        if (w < wid) base += warp_tot[w];
+        total += warp_tot[w];
+    }
+    *out = base + inc - x;
+    __syncthreads();
+    return total;
+}
+
+// Find the bin of the element of ascending rank `rank` in a histogram (any
+// address space).  Every thread receives (bin, count below the bin).
+__device__ void block_find_bin(const unsigned *hist, int nbins, unsigned rank, int *bin_out,
+                               unsigned *below_out)
+{
+    __shared__ int s_bin;
+    __shared__ unsigned s_below;
+    const int per = nbins / NT;
+    unsigned seg = 0;
+    for (int k = 0; k < per; ++k) seg += hist[threadIdx.x * per + k];
+    unsigned before;
+    block_exclusive_scan(seg, &before);
+    if (rank >= before && rank < before + seg) {
+        unsigned acc = before;
+        for (int k = 0; k < per; ++k) {
+            unsigned h = hist[threadIdx.x * per + k];
+            if (rank < acc + h) {
+                s_bin = threadIdx.x * per + k;
+                s_below = acc;
+                break;
+            }
+            acc += h;
+        }
+    }
+    __syncthreads();
+    *bin_out = s_bin;
+    *below_out = s_below;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void warp_append(float val, bool pred, unsigned *counter, float *dst)
+{
+    unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pred) dst[base + __popc(m & ((1u << lane) - 1))] = val;
+}
+
+// Resolve the median of view v from its candidates (rank `rank` among them,
+// all sharing bin b1 of bits [30:19]); one block.  Returns the float bits.
+__device__ unsigned select_from_candidates(const float *cand, unsigned count, unsigned rank, int b1,
+                                           unsigned *hist_smem /* kBins2 */)
+{
+    for (int i = threadIdx.x; i < kBins2; i += NT) hist_smem[i] = 0;
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < count; i += NT)
+        atomicAdd(&hist_smem[(__float_as_uint(cand[i]) >> kShift2) & (kBins2 - 1)], 1u);
+    __syncthreads();
+    int b2;
+    unsigned below2;
+    block_find_bin(hist_smem, kBins2, rank, &b2, &below2);
+    rank -= below2;
+    for (int i = threadIdx.x; i < kBins3; i += NT) hist_smem[i] = 0;
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < count; i += NT) {
+        unsigned bits = __float_as_uint(cand[i]);
+        if (((bits >> kShift2) & (kBins2 - 1)) == unsigned(b2)) atomicAdd(&hist_smem[bits & (kBins3 - 1)], 1u);
+    }
+    __syncthreads();
+    int b3;
+    unsigned below3;
+    block_find_bin(hist_smem, kBins3, rank, &b3, &below3);
+    return (unsigned(b1) << kShift1) | (unsigned(b2) << kShift2) | unsigned(b3);
+}
+
+__global__ void __launch_bounds__(NT) edge_fused_kernel(const __grid_constant__ EdgeArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSmem &s = *reinterpret_cast<TileSmem *>(smem_raw);
+    unsigned *hist_s = reinterpret_cast<unsigned *>(smem_raw + sizeof(TileSmem));
+    const int tid = threadIdx.x;
+    const int G = gridDim.x;
+    const int t_begin = int((long long)a.total_tiles * blockIdx.x / G);
+    const int t_end = int((long long)a.total_tiles * (blockIdx.x + 1) / G);
+    const float scale = 1.0f / 255000.0f;
+
+    // ---- phase A: stencil, NMS, M_thin -> E, histogram of bits [30:19]
+    int cur_view = -1;
+    for (int t = t_begin; t < t_end; ++t) {
+        int v = find_view(a, t);
+        const EdgeView &V = a.v[v];
+        if (v != cur_view) {
+            if (cur_view >= 0) {
+                __syncthreads();
+                for (int i = tid; i < kBins1; i += NT)
+                    if (hist_s[i]) atomicAdd(&a.hist1[(size_t)cur_view * kBins1 + i], hist_s[i]);
+            }
+            __syncthreads();
+            for (int i = tid; i < kBins1; i += NT) hist_s[i] = 0;
+            cur_view = v;
+        }
+        int lt = t - V.tile_base;
+        int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
+        int x0 = tx * TW, y0 = ty * TH;
+        tile_stencil(V, x0, y0, a.w0, a.w1, a.w2, s);
+        for (int idx = tid; idx < TH * TW; idx += NT) {
+            int r = idx / TW, c = idx - r * TW;
+            int y = y0 + r, x = x0 + c;
+            if (y < V.h && x < V.w) {
+                float mt = nms_value(s, r, c);
+                long long o = V.out_off + (long long)y * V.w + x;
+                a.E[o] = mt;
+                if (a.mask) a.mask[o] = mt > 0.f;
+                if (mt > 0.f) atomicAdd(&hist_s[__float_as_uint(mt) >> kShift1], 1u);
+            }
+        }
+        __syncthreads();
+    }
+    if (cur_view >= 0) {
+        __syncthreads();
+        for (int i = tid; i < kBins1; i += NT)
+            if (hist_s[i]) atomicAdd(&a.hist1[(size_t)cur_view * kBins1 + i], hist_s[i]);
+    }
+    if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
+
+    // ---- phase B: median bin per view, gather this block's candidates
+    for (int t = t_begin; t < t_end;) {
+        int v = find_view(a, t);
+        const EdgeView &V = a.v[v];
+        int t_stop = min(t_end, V.tile_base + V.ntiles);
+        const unsigned *h = a.hist1 + (size_t)v * kBins1;
+        unsigned seg = 0;
+        for (int k = 0; k < kBins1 / NT; ++k) seg += h[tid * (kBins1 / NT) + k];
+        unsigned before;
+        unsigned n = block_exclusive_scan(seg, &before);
+        if (n > 0) {
+            int b1;
+            unsigned below;
+            block_find_bin(h, kBins1, (n - 1) / 2, &b1, &below);
+            for (int tt = t; tt < t_stop; ++tt) {
+                int lt = tt - V.tile_base;
+                int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
+                for (int idx = tid; idx < TH * TW; idx += NT) {
+                    int r = idx / TW, c = idx - r * TW;
+                    int y = ty * TH + r, x = tx * TW + c;
+                    bool in = y < V.h && x < V.w;
+                    float mt = in ? a.E[V.out_off + (long long)y * V.w + x] : 0.f;
+                    bool pick = mt > 0.f && int(__float_as_uint(mt) >> kShift1) == b1;
+                    warp_append(mt, pick, a.cand_count + v, a.cand + V.out_off);
+                }
+            }
+        }
+        t = t_stop;
+    }
+    if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
+
+    // ---- phase C: exact median of each view from its candidates
+    for (int v = blockIdx.x; v < a.nviews; v += G) {
+        const unsigned *h = a.hist1 + (size_t)v * kBins1;
+        unsigned seg = 0;
+        for (int k = 0; k < kBins1 / NT; ++k) seg += h[tid * (kBins1 / NT) + k];
+        unsigned before;
+        unsigned n = block_exclusive_scan(seg, &before);
+        unsigned bits = 0;
+        if (n > 0) {
+            int b1;
+            unsigned below;
+            block_find_bin(h, kBins1, (n - 1) / 2, &b1, &below);
+            bits = select_from_candidates(a.cand + a.v[v].out_off, a.cand_count[v], (n - 1) / 2 - below,
+                                          b1, hist_s);
+        }
+        if (tid == 0) {
+            a.med_bits[v] = bits;
+            a.median_out[v] = __uint_as_float(bits) * scale;
+        }
+        __syncthreads();
+    }
+    if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
+
+    // ---- phase D: E = M_thin / median
+    for (int t = t_begin; t < t_end; ++t) {
+        int v = find_view(a, t);
+        const EdgeView &V = a.v[v];
+        float med = __uint_as_float(a.med_bits[v]);
+        if (!(med > 0.f)) continue;
+        int lt = t - V.tile_base;
+        int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
+        for (int idx = tid; idx < TH * TW; idx += NT) {
+            int r = idx / TW, c = idx - r * TW;
+            int y = ty * TH + r, x = tx * TW + c;
+            if (y < V.h && x < V.w) {
+                long long o = V.out_off + (long long)y * V.w + x;
+                float mt = a.E[o];
+                if (mt > 0.f) a.E[o] = __fdiv_rn(mt, med);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ plain path
+
+struct PlainBufs {
+    int *I;          // (h+8) x (w+8)
+    float *Sx, *Sy;  // (h+6) x (w+6)
+    float *Hx, *Hy;  // (h+6) x (w+2)
+    float *Gx, *Gy, *M;  // (h+2) x (w+2)
+    unsigned *hist;  // kBins1
+    unsigned *state; // [0] prefix bits, [1] remaining rank, [2] count
+};
+
+__global__ void plain_luma(EdgeView V, int *I)
+{
+    int W = V.w + 8, H = V.h + 8;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)W * H) return;
+    int r = int(i / W), c = int(i - (long long)r * W);
+    int yy = clampi(r - 4, 0, V.h - 1), xx = clampi(c - 4, 0, V.w - 1);
+    const uint8_t *p = V.rgb + (long long)yy * V.pitch + 3 * xx;
+    I[i] = 299 * int(p[0]) + 587 * int(p[1]) + 114 * int(p[2]);
+}
+
+__global__ void plain_sobel(EdgeView V, const int *I, float *Sx, float *Sy)
+{
+    int W = V.w + 6, H = V.h + 6, IWp = V.w + 8;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)W * H) return;
+    int r = int(i / W), c = int(i - (long long)r * W);
+    const int *a0 = I + (long long)r * IWp + c, *a1 = a0 + IWp, *a2 = a1 + IWp;
+    int sx = (a0[2] - a0[0]) + 2 * (a1[2] - a1[0]) + (a2[2] - a2[0]);
+    int sy = (a2[0] - a0[0]) + 2 * (a2[1] - a0[1]) + (a2[2] - a0[2]);
+    Sx[i] = float(sx);
+    Sy[i] = float(sy);
+}
+
+__global__ void plain_hblur(EdgeView V, const float *Sx, const float *Sy, float *Hx, float *Hy, float w0,
+                            float w1, float w2)
+{
+    int W = V.w + 2, H = V.h + 6, SWp = V.w + 6;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)W * H) return;
+    int r = int(i / W), c = int(i - (long long)r * W);
+    const float *x = Sx + (long long)r * SWp + c, *y = Sy + (long long)r * SWp + c;
+    Hx[i] = __fmaf_rn(w2, x[0] + x[4], __fmaf_rn(w1, x[1] + x[3], __fmul_rn(w0, x[2])));
+    Hy[i] = __fmaf_rn(w2, y[0] + y[4], __fmaf_rn(w1, y[1] + y[3], __fmul_rn(w0, y[2])));
+}
+
+__global__ void plain_vblur_mag(EdgeView V, const float *Hx, const float *Hy, float *Gx, float *Gy,
+                                float *M, float w0, float w1, float w2)
+{
+    int W = V.w + 2, H = V.h + 2;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)W * H) return;
+    int r = int(i / W), c = int(i - (long long)r * W);
+    long long s = (long long)W;
+    const float *x = Hx + (long long)r * W + c, *y = Hy + (long long)r * W + c;
+    float gx = __fmaf_rn(w2, __fadd_rn(x[0], x[4 * s]), __fmaf_rn(w1, __fadd_rn(x[s], x[3 * s]), __fmul_rn(w0, x[2 * s])));
+    float gy = __fmaf_rn(w2, __fadd_rn(y[0], y[4 * s]), __fmaf_rn(w1, __fadd_rn(y[s], y[3 * s]), __fmul_rn(w0, y[2 * s])));
+    bool inside = r >= 1 && r <= V.h && c >= 1 && c <= V.w;
+    Gx[i] = gx;
+    Gy[i] = gy;
+    M[i] = inside ? __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(gy, gy))) : 0.f;
+}
+
+__global__ void plain_nms(EdgeView V, const float *Gx, const float *Gy, const float *M, float *E,
+                          uint8_t *mask)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)V.w * V.h) return;
+    int y = int(i / V.w), x = int(i - (long long)y * V.w);
+    int W = V.w + 2;
+    long long q = (long long)(y + 1) * W + (x + 1);
+    float m = M[q], gx = Gx[q], gy = Gy[q];
+    float ax = fabsf(gx), ay = fabsf(gy);
+    bool horiz = ay <= __fmul_rn(kTan22, ax);
+    bool vert = !horiz && ax <= __fmul_rn(kTan22, ay);
+    int sx = vert ? 0 : (gx > 0.f) - (gx < 0.f);
+    int sy = horiz ? 0 : (gy > 0.f) - (gy < 0.f);
+    float mp = M[q + (long long)sy * W + sx], mm = M[q - (long long)sy * W - sx];
+    bool keep = m > 0.f && m >= mp && m > mm;
+    E[V.out_off + i] = keep ? m : 0.f;
+    if (mask) mask[V.out_off + i] = keep;
+}
+
+// Histogram of digit (bits >> shift) & (nbins-1) over kept values whose bits
+// above the digit match state[0] (pass > 0).
+__global__ void plain_hist(const float *E, long long n, int shift, int nbins, int pass,
+                           const unsigned *state, unsigned *hist)
+{
+    __shared__ unsigned h[kBins1];
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    unsigned prefix = pass ? state[0] : 0;
+    int hi = shift + __popc(nbins - 1);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float v = E[i];
+        if (!(v > 0.f)) continue;
+        unsigned b = __float_as_uint(v);
+        if (pass && (b >> hi) != (prefix >> hi)) continue;
+        atomicAdd(&h[(b >> shift) & (nbins - 1)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+__global__ void __launch_bounds__(NT) plain_select(unsigned *hist, int nbins, int shift, int pass,
+                                                   unsigned *state, unsigned *med_bits, float *median_out)
+{
+    unsigned seg = 0;
+    const int per = nbins / NT;
+    for (int k = 0; k < per; ++k) seg += hist[threadIdx.x * per + k];
+    unsigned before;
+    unsigned n = block_exclusive_scan(seg, &before);
+    if (pass == 0) {
+        if (threadIdx.x == 0) {
+            state[2] = n;
+            state[1] = n ? (n - 1) / 2 : 0;
+            state[0] = 0;
+        }
+        __syncthreads();
+    }
+    if (state[2] == 0) {
+        if (threadIdx.x == 0 && pass == 2) {
+            *med_bits = 0;
+            *median_out = 0.f;
+        }
+        return;
+    }
+    int bin;
+    unsigned below;
+    block_find_bin(hist, nbins, state[1], &bin, &below);
+    if (threadIdx.x == 0) {
+        state[0] |= unsigned(bin) << shift;
+        state[1] -= below;
+        if (pass == 2) {
+            *med_bits = state[0];
+            *median_out = __uint_as_float(state[0]) * (1.0f / 255000.0f);
+        }
+    }
+}
+
+__global__ void plain_normalise(EdgeView V, float *E, const unsigned *med_bits)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)V.w * V.h) return;
+    float med = __uint_as_float(*med_bits);
+    float m = E[V.out_off + i];
+    if (med > 0.f && m > 0.f) E[V.out_off + i] = __fdiv_rn(m, med);
+}
+
+void fill_taps(const gsp_edge_opts &o, float &w0, float &w1, float &w2)
+{
+    if (o.use_custom_taps) {
+        w0 = o.taps[2];
+        w1 = o.taps[1];
+        w2 = o.taps[0];
+        return;
+    }
+    double s = o.sigma > 0 ? o.sigma : 1.0;
+    double e1 = exp(-1.0 / (2 * s * s)), e2 = exp(-4.0 / (2 * s * s));
+    double z = 1.0 + 2 * e1 + 2 * e2;
+    w0 = float(1.0 / z);
+    w1 = float(e1 / z);
+    w2 = float(e2 / z);
+}
+
+struct EdgeLayout {
+    unsigned *hist1, *cand_count, *med_bits, *bar;
+    float *cand;
+    PlainBufs plain;
+    size_t bytes;
+};
+
+EdgeLayout edge_layout(void *ws, const gsp_image_desc *imgs, int nv, int mode)
+{
+    Carver c(ws);
+    EdgeLayout L{};
+    L.hist1 = c.take<unsigned>((size_t)nv * kBins1);
+    L.cand_count = c.take<unsigned>(nv);
+    L.med_bits = c.take<unsigned>(nv);
+    L.bar = c.take<unsigned>(2);
+    if (mode == GSP_EDGE_FUSED) {
+        long long total = 0;
+        for (int v = 0; v < nv; ++v)
+            total = total > imgs[v].out_offset + (long long)imgs[v].width * imgs[v].height
+                        ? total
+                        : imgs[v].out_offset + (long long)imgs[v].width * imgs[v].height;
+        L.cand = c.take<float>((size_t)total);
+    } else {
+        long long mw = 0, mh = 0;
+        for (int v = 0; v < nv; ++v) {
+            mw = mw > imgs[v].width ? mw : imgs[v].width;
+            mh = mh > imgs[v].height ? mh : imgs[v].height;
+        }
+        // sized for the largest view, reused view after view
+        size_t n8 = (size_t)(mw + 8) * (mh + 8), n6 = (size_t)(mw + 6) * (mh + 6);
+        size_t nh = (size_t)(mw + 2) * (mh + 6), n2 = (size_t)(mw + 2) * (mh + 2);
+        L.plain.I = c.take<int>(n8);
+        L.plain.Sx = c.take<float>(n6);
+        L.plain.Sy = c.take<float>(n6);
+        L.plain.Hx = c.take<float>(nh);
+        L.plain.Hy = c.take<float>(nh);
+        L.plain.Gx = c.take<float>(n2);
+        L.plain.Gy = c.take<float>(n2);
+        L.plain.M = c.take<float>(n2);
+        L.plain.hist = c.take<unsigned>(kBins1);
+        L.plain.state = c.take<unsigned>(4);
+    }
+    L.bytes = c.size();
+    return L;
+}
+
+gsp_status validate_edge(const gsp_image_desc *imgs, int nv, const gsp_edge_opts *o)
+{
+    if (!imgs || nv < 1) return GSP_ERR_INVALID_ARG;
+    if (nv > GSP_MAX_VIEWS) return GSP_ERR_UNSUPPORTED;
+    for (int v = 0; v < nv; ++v) {
+        const gsp_image_desc &d = imgs[v];
+        if (!d.rgb || d.width < 1 || d.height < 1 || d.pitch_bytes < 3LL * d.width || d.out_offset < 0)
+            return GSP_ERR_INVALID_ARG;
+        if ((long long)d.width * d.height > (1LL << 30)) return GSP_ERR_UNSUPPORTED;
+    }
+    if (o) {
+        if (o->mode != GSP_EDGE_FUSED && o->mode != GSP_EDGE_PLAIN) return GSP_ERR_INVALID_ARG;
+        if (o->use_custom_taps) {
+            if (o->taps[0] != o->taps[4] || o->taps[1] != o->taps[3]) return GSP_ERR_INVALID_ARG;
+        } else if (!(o->sigma > 0.f)) {
+            return GSP_ERR_INVALID_ARG;
+        }
+    }
+    return GSP_OK;
+}
+
+}  // namespace
+}  // namespace gsp
+
+using namespace gsp;
+
+extern "C" void gsp_edge_opts_default(gsp_edge_opts *o)
+{
+    if (!o) return;
+    *o = gsp_edge_opts{};
+    o->mode = GSP_EDGE_FUSED;
+    o->sigma = 1.0f;
+    o->taps[0] = o->taps[4] = 0.f;
+}
+
+extern "C" size_t gsp_edge_map_workspace_size(const gsp_image_desc *imgs, int32_t nv, const gsp_edge_opts *opts)
+{
+    gsp_edge_opts o;
+    gsp_edge_opts_default(&o);
+    if (opts) o = *opts;
+    if (validate_edge(imgs, nv, &o) != GSP_OK) return 0;
+    return edge_layout(nullptr, imgs, nv, o.mode).bytes;
+}
+
+extern "C" gsp_status gsp_edge_map(const gsp_image_desc *imgs, int32_t nv, float *E_out, float *median_out,
+                                   uint8_t *nms_mask_out, const gsp_edge_opts *opts, void *ws,
+                                   size_t ws_bytes, int32_t *dev_status, gsp_stream_t stream)
+{
+    gsp_edge_opts o;
+    gsp_edge_opts_default(&o);
+    if (opts) o = *opts;
+    gsp_status st = validate_edge(imgs, nv, &o);
+    if (st != GSP_OK) return st;
+    if (!E_out || !median_out || !dev_status) return GSP_ERR_INVALID_ARG;
+    EdgeLayout L = edge_layout(nullptr, imgs, nv, o.mode);
+    st = check_workspace(ws, ws_bytes, L.bytes);
+    if (st != GSP_OK) return st;
+    L = edge_layout(ws, imgs, nv, o.mode);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+    EdgeArgs a{};
+    int tiles = 0;
+    for (int v = 0; v < nv; ++v) {
+        EdgeView &V = a.v[v];
+        V.rgb = imgs[v].rgb;
+        V.pitch = imgs[v].pitch_bytes;
+        V.out_off = imgs[v].out_offset;
+        V.w = imgs[v].width;
+        V.h = imgs[v].height;
+        V.tiles_x = int(div_up(V.w, TW));
+        V.ntiles = V.tiles_x * int(div_up(V.h, TH));
+        V.tile_base = tiles;
+        tiles += V.ntiles;
+    }
+    a.nviews = nv;
+    a.total_tiles = tiles;
+    fill_taps(o, a.w0, a.w1, a.w2);
+    a.E = E_out;
+    a.mask = nms_mask_out;
+    a.median_out = median_out;
+    a.hist1 = L.hist1;
+    a.cand_count = L.cand_count;
+    a.cand = L.cand;
+    a.med_bits = L.med_bits;
+    a.bar = L.bar;
+    a.status = dev_status;
+    a.spin_limit = o.spin_limit > 0 ? o.spin_limit : kDefaultSpinLimit;
+
+    // histogram, candidate counters, medians and barrier state start at zero
+    size_t zero_bytes = reinterpret_cast<char *>(L.bar + 2) - reinterpret_cast<char *>(L.hist1);
+    GSP_CUDA_TRY(cudaMemsetAsync(L.hist1, 0, zero_bytes, s));
+
+    if (o.mode == GSP_EDGE_FUSED) {
+        const size_t smem = sizeof(TileSmem) + kBins1 * sizeof(unsigned);
+        static bool attr_set = false;
+        if (!attr_set) {
+            GSP_CUDA_TRY(cudaFuncSetAttribute(edge_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(smem)));
+            attr_set = true;
+        }
+        int per_sm = 0;
+        GSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_fused_kernel, NT, smem));
+        if (per_sm < 1) return GSP_ERR_UNSUPPORTED;
+        int grid = per_sm * num_sms();
+        if (grid > tiles) grid = tiles;
+        if (grid < nv && nv <= per_sm * num_sms()) grid = nv;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(NT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        stage_begin("edge_fused", s);
+        GSP_CUDA_TRY(cudaLaunchKernelEx(&cfg, edge_fused_kernel, a));
+        stage_end("edge_fused", s);
+        note_launches(2);
+        return GSP_OK;
+    }
+
+    // plain: one launch per stage, view after view
+    const PlainBufs &P = L.plain;
+    stage_begin("edge_plain", s);
+    for (int v = 0; v < nv; ++v) {
+        const EdgeView &V = a.v[v];
+        long long n8 = (long long)(V.w + 8) * (V.h + 8), n6 = (long long)(V.w + 6) * (V.h + 6);
+        long long nh = (long long)(V.w + 2) * (V.h + 6), n2 = (long long)(V.w + 2) * (V.h + 2);
+        long long np = (long long)V.w * V.h;
+        plain_luma<<<div_up(n8, 256), 256, 0, s>>>(V, P.I);
+        plain_sobel<<<div_up(n6, 256), 256, 0, s>>>(V, P.I, P.Sx, P.Sy);
+        plain_hblur<<<div_up(nh, 256), 256, 0, s>>>(V, P.Sx, P.Sy, P.Hx, P.Hy, a.w0, a.w1, a.w2);
+        plain_vblur_mag<<<div_up(n2, 256), 256, 0, s>>>(V, P.Hx, P.Hy, P.Gx, P.Gy, P.M, a.w0, a.w1, a.w2);
+        plain_nms<<<div_up(np, 256), 256, 0, s>>>(V, P.Gx, P.Gy, P.M, E_out, nms_mask_out);
+        const int shifts[3] = {kShift1, kShift2, 0}, bins[3] = {kBins1, kBins2, kBins3};
+        unsigned hist_blocks = div_up(np, 256 * 8);
+        if (hist_blocks > 4u * num_sms()) hist_blocks = 4u * num_sms();
+        for (int pass = 0; pass < 3; ++pass) {
+            GSP_CUDA_TRY(cudaMemsetAsync(P.hist, 0, kBins1 * sizeof(unsigned), s));
+            plain_hist<<<hist_blocks, 256, 0, s>>>(E_out + V.out_off, np, shifts[pass], bins[pass], pass, P.state,
+                                                   P.hist);
+            plain_select<<<1, NT, 0, s>>>(P.hist, bins[pass], shifts[pass], pass, P.state, L.med_bits + v,
+                                          median_out + v);
+        }
+        plain_normalise<<<div_up(np, 256), 256, 0, s>>>(V, E_out, L.med_bits + v);
+    }
+    stage_end("edge_plain", s);
+    note_launches(1 + 15 * nv);
+    GSP_LAUNCH_CHECK();
+    return GSP_OK;
+}

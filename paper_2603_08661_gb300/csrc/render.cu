@@ -1,0 +1,1235 @@
+// Tile-binned Gaussian splatting with per-Gaussian edge score, and its adjoint.
+//
+// The paper builds on an existing 3DGS renderer without describing it (Sec. 1,
+// Sec. 2); the conventions implemented here are listed in gsp.h.  The edge
+// score s_i = sum_p alpha_i(p) T_i(p) E(p) is the per-Gaussian importance the
+// densification selects on (Sec. 1, "Edge-Score importance").
+//
+// Pipeline of gsp_render_fwd (all asynchronous on the caller's stream):
+//   project   one thread per Gaussian reads its parameters once and projects
+//             them into every view: screen mean, conic, opacity, SH colour,
+//             FP32 depth key and the tile rectangle of its 1/255 footprint
+//   sort      per view, stable LSD radix sort of the depth keys (4 x 8 bits),
+//             ties keep ascending index
+//   bin       per view, the depth-ordered Gaussians are cut into chunks;
+//             per-chunk tile counts, a scan over chunks per tile and over
+//             tiles give every (tile, chunk) its output range, and a stable
+//             scatter writes each tile's list already in depth order (no sort
+//             over the pairs)
+//   composite one 256-thread block per 16x16 tile, Gaussians staged through
+//             shared memory in batches, block-wide early exit
+// gsp_render_bwd replays each pixel back to front from T_final and the
+// last-contributor position, reduces the per-Gaussian screen-space gradients
+// over the block (warp transpose-reduction, shared-memory accumulation, one
+// global atomic per Gaussian, tile and value) and then chains them to the
+// parameters, one thread per Gaussian over all views.
+#include "common.cuh"
+
+namespace gsp {
+namespace {
+
+constexpr int kSortThreads = 256, kSortItems = 8, kSortTile = kSortThreads * kSortItems;
+constexpr int kChunk = 2048;  // depth-ordered Gaussians per binning block
+constexpr int kBinSmemBudget = 200 * 1024;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kNear = 0.2f;
+
+struct ViewP {
+    float vm[12];
+    float fx, fy, cx, cy;
+    float ccx, ccy, ccz;  // camera centre in world space
+    int w, h;
+    int tiles_x, tiles_y;
+    int tile_base;        // first global tile of the view
+    long long pix_off;    // first pixel of the view
+    const uint8_t *tgt;   // target image (or null)
+    long long tgt_pitch;
+};
+
+struct Views {
+    ViewP v[GSP_MAX_VIEWS];
+    int n;
+    int total_tiles;
+    long long total_pix;
+};
+
+struct Params {
+    const float *means, *log_scales, *quats, *opac, *sh;
+    const int32_t *count;
+    long long cap;
+    int K;  // SH coefficients per channel
+};
+
+struct State {
+    float4 *xyo;   // [V][cap] (mean x, mean y, opacity, depth key)
+    float4 *con;   // [V][cap] (conic A, B, C, 0)
+    float4 *col;   // [V][cap] (r, g, b, clamp bits)
+    uint2 *rect;   // [V][cap] (tx0 | ty0 << 16, tx1 | ty1 << 16); empty if tx1 < tx0
+    uint32_t *key, *key_alt;  // [V][cap]
+    int32_t *val, *val_alt;   // [V][cap]
+    unsigned *sort_hist;      // [256][nb_max]
+    unsigned *sort_tot;       // [256]
+    int32_t *chunk_cnt;       // [C][total_tiles] (per view: [C][T_v] at tile_base * C)
+    long long *tile_start;    // [total_tiles + 1]
+    long long *pair_count;    // [1]
+    int32_t *ids;             // [pair_capacity]
+    float4 *g2d;              // [V][cap][3]
+    double *loss_acc;         // [1]
+    int32_t *overflow;        // [1]
+    int nb_max;               // sort blocks for cap
+    int nchunk_max;
+    long long pair_cap;
+};
+
+__device__ __forceinline__ int find_view(const Views &vs, int gt)
+{
+    int v = 0;
+    while (v + 1 < vs.n && vs.v[v + 1].tile_base <= gt) ++v;
+    return v;
+}
+
+// ------------------------------------------------------------ SH basis (FP32)
+
+constexpr float C0 = 0.28209479177387814f;
+constexpr float C1 = 0.4886025119029199f;
+constexpr float C2a = 1.0925484305920792f, C2b = 0.31539156525252005f, C2c = 0.5462742152960396f;
+constexpr float C3a = 0.5900435899266435f, C3b = 2.890611442640554f, C3c = 0.4570457994644658f;
+constexpr float C3d = 0.3731763325901154f, C3e = 1.445305721320277f;
+
+__device__ __forceinline__ void sh_eval(float x, float y, float z, int K, float Y[16])
+{
+    Y[0] = C0;
+    if (K > 1) {
+        Y[1] = C1 * y; Y[2] = C1 * z; Y[3] = C1 * x;
+    }
+    if (K > 4) {
+        Y[4] = C2a * x * y; Y[5] = C2a * y * z; Y[6] = C2b * (3.f * z * z - 1.f);
+        Y[7] = C2a * x * z; Y[8] = C2c * (x * x - y * y);
+    }
+    if (K > 9) {
+        Y[9] = C3a * y * (3.f * x * x - y * y); Y[10] = C3b * x * y * z;
+        Y[11] = C3c * y * (5.f * z * z - 1.f); Y[12] = C3d * z * (5.f * z * z - 3.f);
+        Y[13] = C3c * x * (5.f * z * z - 1.f); Y[14] = C3e * z * (x * x - y * y);
+        Y[15] = C3a * x * (x * x - 3.f * y * y);
+    }
+}
+
+// sum_k w[k] * grad Y_k at (x, y, z), the basis polynomials differentiated in R^3
+__device__ __forceinline__ void sh_grad_dot(float x, float y, float z, int K, const float w[16], float g[3])
+{
+    g[0] = g[1] = g[2] = 0.f;
+    if (K > 1) {
+        g[1] += C1 * w[1]; g[2] += C1 * w[2]; g[0] += C1 * w[3];
+    }
+    if (K > 4) {
+        g[0] += C2a * y * w[4]; g[1] += C2a * x * w[4];
+        g[1] += C2a * z * w[5]; g[2] += C2a * y * w[5];
+        g[2] += C2b * 6.f * z * w[6];
+        g[0] += C2a * z * w[7]; g[2] += C2a * x * w[7];
+        g[0] += C2c * 2.f * x * w[8]; g[1] -= C2c * 2.f * y * w[8];
+    }
+    if (K > 9) {
+        g[0] += C3a * 6.f * x * y * w[9]; g[1] += C3a * 3.f * (x * x - y * y) * w[9];
+        g[0] += C3b * y * z * w[10]; g[1] += C3b * x * z * w[10]; g[2] += C3b * x * y * w[10];
+        g[1] += C3c * (5.f * z * z - 1.f) * w[11]; g[2] += C3c * 10.f * y * z * w[11];
+        g[2] += C3d * (15.f * z * z - 3.f) * w[12];
+        g[0] += C3c * (5.f * z * z - 1.f) * w[13]; g[2] += C3c * 10.f * x * z * w[13];
+        g[0] += C3e * 2.f * x * z * w[14]; g[1] -= C3e * 2.f * y * z * w[14]; g[2] += C3e * (x * x - y * y) * w[14];
+        g[0] += C3a * 3.f * (x * x - y * y) * w[15]; g[1] -= C3a * 6.f * x * y * w[15];
+    }
+}
+
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9])
+{
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Depth key: the same fma order the FP64 reference uses for this decision.
+__device__ __forceinline__ float depth_key(const float *vm, float mx, float my, float mz)
+{
+    return __fmaf_rn(vm[8], mx, __fmaf_rn(vm[9], my, __fmaf_rn(vm[10], mz, vm[11])));
+}
+
+struct Proj {
+    float tx, ty, tz;
+    float R[9], s[3];
+    float Sig[6];   // xx xy xz yy yz zz
+    float T[6];     // J W
+    float a, b, c;  // Sigma2 (with +0.3)
+    float det;
+};
+
+__device__ __forceinline__ void project_geom(const ViewP &V, const float *mu, const float *ls, const float *q4,
+                                             Proj &P)
+{
+    const float *vm = V.vm;
+    P.tz = depth_key(vm, mu[0], mu[1], mu[2]);
+    P.tx = vm[0] * mu[0] + vm[1] * mu[1] + vm[2] * mu[2] + vm[3];
+    P.ty = vm[4] * mu[0] + vm[5] * mu[1] + vm[6] * mu[2] + vm[7];
+    float qn = __frsqrt_rn(q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3]);
+    quat_rot(q4[0] * qn, q4[1] * qn, q4[2] * qn, q4[3] * qn, P.R);
+    P.s[0] = expf(ls[0]); P.s[1] = expf(ls[1]); P.s[2] = expf(ls[2]);
+    float M[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) M[3 * a + b] = P.R[3 * a + b] * P.s[b];
+    P.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    P.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    P.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    P.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    P.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    P.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+    float iz = 1.f / P.tz;
+    float j00 = V.fx * iz, j02 = -V.fx * P.tx * iz * iz;
+    float j11 = V.fy * iz, j12 = -V.fy * P.ty * iz * iz;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        P.T[b] = j00 * vm[b] + j02 * vm[8 + b];
+        P.T[3 + b] = j11 * vm[4 + b] + j12 * vm[8 + b];
+    }
+    // Sigma2 = T Sig T^T
+    const float *S = P.Sig;
+    float u0 = P.T[0] * S[0] + P.T[1] * S[1] + P.T[2] * S[2];
+    float u1 = P.T[0] * S[1] + P.T[1] * S[3] + P.T[2] * S[4];
+    float u2 = P.T[0] * S[2] + P.T[1] * S[4] + P.T[2] * S[5];
+    float v0 = P.T[3] * S[0] + P.T[4] * S[1] + P.T[5] * S[2];
+    float v1 = P.T[3] * S[1] + P.T[4] * S[3] + P.T[5] * S[4];
+    float v2 = P.T[3] * S[2] + P.T[4] * S[4] + P.T[5] * S[5];
+    P.a = u0 * P.T[0] + u1 * P.T[1] + u2 * P.T[2] + 0.3f;
+    P.b = u0 * P.T[3] + u1 * P.T[4] + u2 * P.T[5];
+    P.c = v0 * P.T[3] + v1 * P.T[4] + v2 * P.T[5] + 0.3f;
+    P.det = P.a * P.c - P.b * P.b;
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + expf(-x)); }
+
+// --------------------------------------------------------------- projection
+
+__global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Views vs, Params p, State st)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= p.cap) return;
+    const int n = *p.count;
+    const long long cap = p.cap;
+    for (int v = 0; v < vs.n; ++v) {
+        st.val[v * cap + i] = int32_t(i);
+        st.g2d[(v * cap + i) * 3 + 0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        st.g2d[(v * cap + i) * 3 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        st.g2d[(v * cap + i) * 3 + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (i >= n) return;
+    float mu[3] = {p.means[3 * i], p.means[3 * i + 1], p.means[3 * i + 2]};
+    float ls[3] = {p.log_scales[3 * i], p.log_scales[3 * i + 1], p.log_scales[3 * i + 2]};
+    float q4[4] = {p.quats[4 * i], p.quats[4 * i + 1], p.quats[4 * i + 2], p.quats[4 * i + 3]};
+    float opac = sigmoidf_(p.opac[i]);
+    const float *shp = p.sh + (size_t)i * p.K * 3;
+    for (int v = 0; v < vs.n; ++v) {
+        const ViewP &V = vs.v[v];
+        const long long o = v * cap + i;
+        Proj P;
+        project_geom(V, mu, ls, q4, P);
+        bool ok = P.tz > kNear && P.det > 0.f && opac >= kAlphaMin;
+        uint2 rect = make_uint2(1u, 0u);  // empty
+        if (ok) {
+            float iz = 1.f / P.tz;
+            float mx = V.fx * P.tx * iz + V.cx, my = V.fy * P.ty * iz + V.cy;
+            float id = 1.f / P.det;
+            // footprint of alpha >= 1/255: d^T Q d <= 2 ln(255 o); its bounding box
+            // has half-extents sqrt(2 ln(255 o) Sigma2_xx), sqrt(... Sigma2_yy)
+            float lim = 2.f * logf(255.f * opac);
+            float ex = sqrtf(fmaxf(lim, 0.f) * P.a) * 1.0001f + 0.01f;
+            float ey = sqrtf(fmaxf(lim, 0.f) * P.c) * 1.0001f + 0.01f;
+            int tx0 = max(int(floorf((mx - ex - 0.5f) / kTile)), 0);
+            int tx1 = min(int(floorf((mx + ex - 0.5f) / kTile)), V.tiles_x - 1);
+            int ty0 = max(int(floorf((my - ey - 0.5f) / kTile)), 0);
+            int ty1 = min(int(floorf((my + ey - 0.5f) / kTile)), V.tiles_y - 1);
+            if (tx0 <= tx1 && ty0 <= ty1) {
+                rect = make_uint2(unsigned(tx0) | (unsigned(ty0) << 16), unsigned(tx1) | (unsigned(ty1) << 16));
+            } else {
+                ok = false;
+            }
+            // view-dependent colour
+            float dx = mu[0] - V.ccx, dy = mu[1] - V.ccy, dz = mu[2] - V.ccz;
+            float rn = __frsqrt_rn(dx * dx + dy * dy + dz * dz);
+            float Y[16];
+            sh_eval(dx * rn, dy * rn, dz * rn, p.K, Y);
+            float col[3];
+            unsigned clampbits = 0;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float acc = 0.5f;
+                for (int k = 0; k < p.K; ++k) acc += shp[3 * k + ch] * Y[k];
+                if (acc < 0.f) {
+                    clampbits |= 1u << ch;
+                    acc = 0.f;
+                }
+                col[ch] = acc;
+            }
+            st.xyo[o] = make_float4(mx, my, opac, P.tz);
+            st.con[o] = make_float4(P.c * id, -P.b * id, P.a * id, 0.f);
+            st.col[o] = make_float4(col[0], col[1], col[2], __uint_as_float(clampbits));
+        }
+        st.rect[o] = rect;
+        st.key[o] = ok ? __float_as_uint(P.tz) : 0xffffffffu;
+    }
+}
+
+// ------------------------------------------------------------ radix sort
+
+__global__ void __launch_bounds__(kSortThreads) sort_count(const uint32_t *keys, const int32_t *count, int shift,
+                                                           unsigned *hist, int nb_max)
+{
+    __shared__ unsigned h[256];
+    const int n = *count;
+    const int nb = (n + kSortTile - 1) / kSortTile;
+    if (int(blockIdx.x) >= nb) return;
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kSortTile;
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        long long e = base + j * kSortThreads + threadIdx.x;
+        if (e < n) atomicAdd(&h[(keys[e] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nb_max + blockIdx.x] = h[threadIdx.x];
+}
+
+// One block per digit: exclusive scan of that digit's counts over blocks.
+__global__ void __launch_bounds__(256) sort_scan(unsigned *hist, int nb_max, const int32_t *count, unsigned *tot)
+{
+    __shared__ unsigned wsum[8];
+    __shared__ unsigned carry;
+    const int n = *count;
+    const int nb = (n + kSortTile - 1) / kSortTile;
+    unsigned *row = hist + (size_t)blockIdx.x * nb_max;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += 256) {
+        int b = b0 + threadIdx.x;
+        unsigned x = b < nb ? row[b] : 0u;
+        unsigned inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[wid] = inc;
+        __syncthreads();
+        unsigned wb = 0, all = 0;
+        for (int w = 0; w < 8; ++w) {
+            if (w < wid) wb += wsum[w];
+            all += wsum[w];
+        }
+        if (b < nb) row[b] = carry + wb + inc - x;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += all;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tot[blockIdx.x] = carry;
+}
+
+__global__ void __launch_bounds__(kSortThreads) sort_scatter(const uint32_t *kin, const int32_t *vin, uint32_t *kout,
+                                                             int32_t *vout, const int32_t *count, int shift,
+                                                             const unsigned *hist, int nb_max, const unsigned *tot)
+{
+    __shared__ unsigned base_d[256];
+    __shared__ unsigned run[256];
+    __shared__ unsigned wcnt[kSortThreads / 32][256];
+    __shared__ unsigned wsum[8];
+    const int n = *count;
+    const int nb = (n + kSortTile - 1) / kSortTile;
+    if (int(blockIdx.x) >= nb) return;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    {   // digit base = exclusive scan of totals + this block's offset
+        unsigned x = tot[tid];
+        unsigned inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[wid] = inc;
+        __syncthreads();
+        unsigned wb = 0;
+        for (int w = 0; w < wid; ++w) wb += wsum[w];
+        base_d[tid] = wb + inc - x + hist[(size_t)tid * nb_max + blockIdx.x];
+        run[tid] = 0;
+    }
+    const long long base = (long long)blockIdx.x * kSortTile;
+    for (int j = 0; j < kSortItems; ++j) {
+        for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+        long long e = base + j * kSortThreads + tid;
+        bool valid = e < n;
+        uint32_t k = valid ? kin[e] : 0u;
+        int32_t val = valid ? vin[e] : 0;
+        unsigned d = valid ? ((k >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned lrank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && lrank == 0) wcnt[wid][d] = __popc(peers);
+        __syncthreads();
+        {   // per digit: prefix over warps, carried across items
+            unsigned r = run[tid];
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                unsigned c = wcnt[w][tid];
+                wcnt[w][tid] = r;
+                r += c;
+            }
+            run[tid] = r;
+        }
+        __syncthreads();
+        if (valid) {
+            unsigned pos = base_d[d] + wcnt[wid][d] + lrank;
+            kout[pos] = k;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- binning
+
+__device__ __forceinline__ void rect_unpack(uint2 r, int &tx0, int &ty0, int &tx1, int &ty1)
+{
+    tx0 = int(r.x & 0xffffu); ty0 = int(r.x >> 16); tx1 = int(r.y & 0xffffu); ty1 = int(r.y >> 16);
+}
+
+// Per-warp tile counts of one chunk of depth-ordered Gaussians.
+__device__ void chunk_warp_counts(const ViewP &V, const uint2 *rect, const int32_t *sorted, int n, int chunk,
+                                  int nwarps, int T, int *cnt /* [nwarps][T] */)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < nwarps * T; t += blockDim.x) cnt[t] = 0;
+    __syncthreads();
+    const int per = kChunk / nwarps;
+    const int b0 = chunk * kChunk + wid * per;
+    int *mine = cnt + wid * T;
+    for (int p = b0; p < b0 + per && p < n; ++p) {
+        int g = sorted[p];
+        int tx0, ty0, tx1, ty1;
+        rect_unpack(rect[g], tx0, ty0, tx1, ty1);
+        if (tx1 < tx0) continue;
+        int wr = tx1 - tx0 + 1, area = wr * (ty1 - ty0 + 1);
+        for (int c = lane; c < area; c += 32) {
+            int yy = c / wr;
+            mine[(ty0 + yy) * V.tiles_x + tx0 + (c - yy * wr)]++;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+__global__ void bin_count(const __grid_constant__ Views vs, int v, State st, const int32_t *count, int nwarps)
+{
+    extern __shared__ int bsm[];
+    const ViewP &V = vs.v[v];
+    const int n = *count;
+    const int T = V.tiles_x * V.tiles_y;
+    const int chunk = blockIdx.x;
+    if (chunk * kChunk >= n) return;
+    chunk_warp_counts(V, st.rect, st.val, n, chunk, nwarps, T, bsm);
+    int32_t *dst = st.chunk_cnt + (size_t)V.tile_base * st.nchunk_max + (size_t)chunk * T;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        int sum = 0;
+        for (int w = 0; w < nwarps; ++w) sum += bsm[w * T + t];
+        dst[t] = sum;
+    }
+}
+
+// One thread per global tile: exclusive scan over chunks (in place), totals out.
+__global__ void bin_scan_chunks(const __grid_constant__ Views vs, State st, const int32_t *count)
+{
+    int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gt >= vs.total_tiles) return;
+    const int n = *count;
+    const int nc = (n + kChunk - 1) / kChunk;
+    int v = find_view(vs, gt);
+    const ViewP &V = vs.v[v];
+    const int T = V.tiles_x * V.tiles_y;
+    int t = gt - V.tile_base;
+    int32_t *col = st.chunk_cnt + (size_t)V.tile_base * st.nchunk_max + t;
+    long long run = 0;
+    for (int c = 0; c < nc; ++c) {
+        int x = col[(size_t)c * T];
+        col[(size_t)c * T] = int(run);
+        run += x;
+    }
+    st.tile_start[gt + 1] = run;  // totals; turned into starts by bin_scan_tiles
+}
+
+// Single block: exclusive scan of the tile totals into tile starts; capacity check.
+__global__ void __launch_bounds__(1024) bin_scan_tiles(int total_tiles, State st, int32_t *status)
+{
+    __shared__ long long wsum[32];
+    __shared__ long long carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < total_tiles; b0 += 1024) {
+        int t = b0 + threadIdx.x;
+        long long x = t < total_tiles ? st.tile_start[t + 1] : 0;
+        long long inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[wid] = inc;
+        __syncthreads();
+        long long wb = 0, all = 0;
+        for (int w = 0; w < 32; ++w) {
+            if (w < wid) wb += wsum[w];
+            all += wsum[w];
+        }
+        long long c0 = carry;
+        __syncthreads();
+        if (t < total_tiles) st.tile_start[t] = c0 + wb + inc - x;
+        if (threadIdx.x == 0) carry = c0 + all;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        st.tile_start[total_tiles] = carry;
+        *st.pair_count = carry;
+        int over = carry > st.pair_cap;
+        *st.overflow = over;
+        if (over) set_status(status, GSP_ERR_CAPACITY);
+    }
+}
+
+__global__ void bin_scatter(const __grid_constant__ Views vs, int v, State st, const int32_t *count, int nwarps)
+{
+    extern __shared__ int bsm[];
+    if (*st.overflow) return;
+    const ViewP &V = vs.v[v];
+    const int n = *count;
+    const int T = V.tiles_x * V.tiles_y;
+    const int chunk = blockIdx.x;
+    if (chunk * kChunk >= n) return;
+    chunk_warp_counts(V, st.rect, st.val, n, chunk, nwarps, T, bsm);
+    // per-warp write cursors, relative to the view's first pair
+    const long long view_base = st.tile_start[V.tile_base];
+    const int32_t *coff = st.chunk_cnt + (size_t)V.tile_base * st.nchunk_max + (size_t)chunk * T;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        int r = int(st.tile_start[V.tile_base + t] - view_base) + coff[t];
+        for (int w = 0; w < nwarps; ++w) {
+            int c = bsm[w * T + t];
+            bsm[w * T + t] = r;
+            r += c;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int per = kChunk / nwarps;
+    const int b0 = chunk * kChunk + wid * per;
+    int *mine = bsm + wid * T;
+    int32_t *out = st.ids + view_base;
+    for (int p = b0; p < b0 + per && p < n; ++p) {
+        int g = st.val[p];
+        int tx0, ty0, tx1, ty1;
+        rect_unpack(st.rect[g], tx0, ty0, tx1, ty1);
+        if (tx1 < tx0) continue;
+        int wr = tx1 - tx0 + 1, area = wr * (ty1 - ty0 + 1);
+        for (int c = lane; c < area; c += 32) {
+            int yy = c / wr;
+            int t = (ty0 + yy) * V.tiles_x + tx0 + (c - yy * wr);
+            out[mine[t]++] = g;
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------- compositing
+
+struct Alpha {
+    float G, raw, alpha, dx, dy;
+};
+
+// Identical in the forward and the backward kernel (explicitly rounded ops),
+// so both take the same 1/255 decision.
+__device__ __forceinline__ Alpha eval_alpha(float4 xyo, float4 con, float px, float py)
+{
+    Alpha r;
+    r.dx = __fsub_rn(px, xyo.x);
+    r.dy = __fsub_rn(py, xyo.y);
+    float t1 = __fmul_rn(con.x, __fmul_rn(r.dx, r.dx));
+    float t2 = __fmul_rn(con.z, __fmul_rn(r.dy, r.dy));
+    float t3 = __fmul_rn(con.y, __fmul_rn(r.dx, r.dy));
+    float power = __fmaf_rn(-0.5f, __fadd_rn(t1, t2), -t3);
+    r.G = __expf(power);
+    r.raw = __fmul_rn(xyo.z, r.G);
+    r.alpha = fminf(kAlphaMax, r.raw);
+    return r;
+}
+
+__device__ __forceinline__ float target_value(const ViewP &V, int x, int y, int ch)
+{
+    return __fdiv_rn(float(V.tgt[(long long)y * V.tgt_pitch + 3 * x + ch]), 255.f);
+}
+
+struct FwdOut {
+    float *rgb, *T, *score, *edge;
+    int32_t *last;
+};
+
+__global__ void __launch_bounds__(kTilePix) composite_fwd(const __grid_constant__ Views vs, State st, long long cap,
+                                                          const float *edge, float *rgb_out, float *T_out,
+                                                          int32_t *last_out, float *score)
+{
+    __shared__ float4 s_xyo[kTilePix], s_con[kTilePix], s_col[kTilePix];
+    __shared__ int32_t s_id[kTilePix];
+    __shared__ float s_score[kTilePix];
+    __shared__ float s_red[kTilePix / 32];
+    if (*st.overflow) return;
+    const int gt = blockIdx.x;
+    const int v = find_view(vs, gt);
+    const ViewP &V = vs.v[v];
+    const int lt = gt - V.tile_base;
+    const int tyy = lt / V.tiles_x, txx = lt - tyy * V.tiles_x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int x = txx * kTile + (tid & (kTile - 1)), y = tyy * kTile + tid / kTile;
+    const bool inside = x < V.w && y < V.h;
+    const float px = x + 0.5f, py = y + 0.5f;
+    const long long pid = V.pix_off + (long long)y * V.w + x;
+    const float E = (edge && inside) ? edge[pid] : 0.f;
+    const long long start = st.tile_start[gt], end = st.tile_start[gt + 1];
+    const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
+
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    int last = 0;
+    bool done = !inside;
+    for (long long b = start; b < end; b += kTilePix) {
+        if (__syncthreads_count(done) == kTilePix) break;
+        long long k = b + tid;
+        if (k < end) {
+            int id = st.ids[k];
+            s_id[tid] = id;
+            s_xyo[tid] = xyo[id];
+            s_con[tid] = con[id];
+            s_col[tid] = col[id];
+        }
+        if (score) s_score[tid] = 0.f;
+        __syncthreads();
+        const int cnt = int(min((long long)kTilePix, end - b));
+        for (int j = 0; j < cnt; ++j) {
+            float w = 0.f;
+            if (!done) {
+                Alpha a = eval_alpha(s_xyo[j], s_con[j], px, py);
+                if (a.alpha >= kAlphaMin) {
+                    float Tn = __fmul_rn(T, __fsub_rn(1.f, a.alpha));
+                    if (Tn < kTMin) {
+                        done = true;
+                    } else {
+                        w = __fmul_rn(a.alpha, T);
+                        float4 c = s_col[j];
+                        C0 = __fmaf_rn(c.x, w, C0);
+                        C1 = __fmaf_rn(c.y, w, C1);
+                        C2 = __fmaf_rn(c.z, w, C2);
+                        T = Tn;
+                        last = int(b - start) + j + 1;
+                    }
+                }
+            }
+            if (score) {
+                float sv = w * E;
+                if (__any_sync(0xffffffffu, sv != 0.f)) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+                    if (lane == 0) atomicAdd(&s_score[j], sv);
+                }
+            }
+        }
+        __syncthreads();
+        if (score && tid < cnt && s_score[tid] != 0.f) atomicAdd(&score[s_id[tid]], s_score[tid]);
+    }
+    if (inside) {
+        rgb_out[3 * pid + 0] = C0;
+        rgb_out[3 * pid + 1] = C1;
+        rgb_out[3 * pid + 2] = C2;
+        T_out[pid] = T;
+        last_out[pid] = last;
+    }
+    if (V.tgt) {
+        float l = 0.f;
+        if (inside)
+            l = fabsf(C0 - target_value(V, x, y, 0)) + fabsf(C1 - target_value(V, x, y, 1)) +
+                fabsf(C2 - target_value(V, x, y, 2));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if (lane == 0) s_red[wid] = l;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int w = 0; w < kTilePix / 32; ++w) s += s_red[w];
+            atomicAdd(st.loss_acc, s);
+        }
+    }
+}
+
+__global__ void loss_finalise(State st, long long total_pix, float *loss_out)
+{
+    if (*st.overflow) return;
+    *loss_out = float(*st.loss_acc / (3.0 * double(total_pix)));
+}
+
+// Sum of 16 per-lane values over the warp: lane L ends up holding the total of
+// value (L >> 1).  16 shuffles instead of 16 x 5.
+__device__ __forceinline__ float warp_transpose_reduce16(float v[16])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int half = 8, mask = 16; half >= 1; half >>= 1, mask >>= 1) {
+        const bool upper = lane & mask;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            float send = upper ? v[k] : v[k + half];
+            float keep = upper ? v[k + half] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+constexpr int kG2 = 10;  // mean x, mean y, conic A, B, C, opacity, r, g, b, score
+
+__global__ void __launch_bounds__(kTilePix) composite_bwd(const __grid_constant__ Views vs, State st, long long cap,
+                                                          const float *dL_drgb, const float *rgb, const float *T_fin,
+                                                          const int32_t *last_idx, const float *edge, float *score,
+                                                          float inv_norm)
+{
+    __shared__ float4 s_xyo[kTilePix], s_con[kTilePix], s_col[kTilePix];
+    __shared__ int32_t s_id[kTilePix];
+    __shared__ float s_acc[kTilePix][kG2];
+    __shared__ int s_maxlast;
+    if (*st.overflow) return;
+    const int gt = blockIdx.x;
+    const int v = find_view(vs, gt);
+    const ViewP &V = vs.v[v];
+    const int lt = gt - V.tile_base;
+    const int tyy = lt / V.tiles_x, txx = lt - tyy * V.tiles_x;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int x = txx * kTile + (tid & (kTile - 1)), y = tyy * kTile + tid / kTile;
+    const bool inside = x < V.w && y < V.h;
+    const float px = x + 0.5f, py = y + 0.5f;
+    const long long pid = V.pix_off + (long long)y * V.w + x;
+    const long long start = st.tile_start[gt];
+    const int list_len = int(st.tile_start[gt + 1] - start);
+    const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
+    float4 *g2d = st.g2d + (size_t)v * cap * 3;
+
+    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, E = 0.f;
+    int last = 0;
+    if (inside) {
+        T = T_fin[pid];
+        last = min(max(last_idx[pid], 0), list_len);
+        E = edge ? edge[pid] : 0.f;
+        if (dL_drgb) {
+            g0 = dL_drgb[3 * pid];
+            g1 = dL_drgb[3 * pid + 1];
+            g2 = dL_drgb[3 * pid + 2];
+        } else {
+            float d0 = rgb[3 * pid] - target_value(V, x, y, 0);
+            float d1 = rgb[3 * pid + 1] - target_value(V, x, y, 1);
+            float d2 = rgb[3 * pid + 2] - target_value(V, x, y, 2);
+            g0 = ((d0 > 0.f) - (d0 < 0.f)) * inv_norm;
+            g1 = ((d1 > 0.f) - (d1 < 0.f)) * inv_norm;
+            g2 = ((d2 > 0.f) - (d2 < 0.f)) * inv_norm;
+        }
+    }
+    const bool want_score = score && edge;
+    if (tid == 0) s_maxlast = 0;
+    for (int k = tid; k < kTilePix * kG2; k += kTilePix) (&s_acc[0][0])[k] = 0.f;
+    __syncthreads();
+    atomicMax(&s_maxlast, last);
+    __syncthreads();
+    const int maxlast = s_maxlast;
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;  // colour behind, normalised
+
+    for (int hi = maxlast; hi > 0; hi -= kTilePix) {
+        const int lo = max(hi - kTilePix, 0);
+        const int cnt = hi - lo;
+        if (tid < cnt) {
+            int id = st.ids[start + lo + tid];
+            s_id[tid] = id;
+            s_xyo[tid] = xyo[id];
+            s_con[tid] = con[id];
+            s_col[tid] = col[id];
+        }
+        __syncthreads();
+        for (int j = cnt - 1; j >= 0; --j) {
+            const int pos = lo + j;
+            float val[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) val[k] = 0.f;
+            bool active = false;
+            if (pos < last) {
+                Alpha a = eval_alpha(s_xyo[j], s_con[j], px, py);
+                if (a.alpha >= kAlphaMin) {
+                    active = true;
+                    const float4 c = s_col[j];
+                    const float one_m = __fsub_rn(1.f, a.alpha);
+                    T = __fdiv_rn(T, one_m);
+                    const float w = a.alpha * T;
+                    val[6] = w * g0;
+                    val[7] = w * g1;
+                    val[8] = w * g2;
+                    const float dalpha = T * (g0 * (c.x - acc0) + g1 * (c.y - acc1) + g2 * (c.z - acc2));
+                    acc0 = acc0 * one_m + c.x * a.alpha;
+                    acc1 = acc1 * one_m + c.y * a.alpha;
+                    acc2 = acc2 * one_m + c.z * a.alpha;
+                    if (a.raw < kAlphaMax) {
+                        const float4 q = s_con[j];
+                        const float dpow = dalpha * s_xyo[j].z * a.G;
+                        val[5] = dalpha * a.G;
+                        val[0] = dpow * (q.x * a.dx + q.y * a.dy);
+                        val[1] = dpow * (q.y * a.dx + q.z * a.dy);
+                        val[2] = -0.5f * dpow * a.dx * a.dx;
+                        val[3] = -dpow * a.dx * a.dy;
+                        val[4] = -0.5f * dpow * a.dy * a.dy;
+                    }
+                    if (want_score) val[9] = w * E;
+                }
+            }
+            if (__any_sync(0xffffffffu, active)) {
+                float r = warp_transpose_reduce16(val);
+                if ((lane & 1) == 0 && (lane >> 1) < kG2 && r != 0.f) atomicAdd(&s_acc[j][lane >> 1], r);
+            }
+        }
+        __syncthreads();
+        if (tid < cnt) {
+            float *a = s_acc[tid];
+            const long long o = (long long)s_id[tid] * 3;
+            float *gp = reinterpret_cast<float *>(g2d + o);
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                if (a[k] != 0.f) atomicAdd(gp + k, a[k]);
+            if (want_score && a[9] != 0.f) atomicAdd(&score[s_id[tid]], a[9]);
+#pragma unroll
+            for (int k = 0; k < kG2; ++k) a[k] = 0.f;
+        }
+        __syncthreads();
+    }
+}
+
+// Chain the screen-space gradients to the parameters, one thread per Gaussian,
+// summing over views.
+__global__ void __launch_bounds__(128) project_bwd(const __grid_constant__ Views vs, Params p, State st,
+                                                  float *gm, float *gls, float *gq, float *go, float *gsh,
+                                                  int accumulate)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= *p.count) return;
+    if (*st.overflow) return;
+    const long long cap = p.cap;
+    const int K = p.K;
+    float mu[3] = {p.means[3 * i], p.means[3 * i + 1], p.means[3 * i + 2]};
+    float ls[3] = {p.log_scales[3 * i], p.log_scales[3 * i + 1], p.log_scales[3 * i + 2]};
+    float q4[4] = {p.quats[4 * i], p.quats[4 * i + 1], p.quats[4 * i + 2], p.quats[4 * i + 3]};
+    const float opac = sigmoidf_(p.opac[i]);
+    const float *shp = p.sh + (size_t)i * K * 3;
+    float G_mu[3] = {0.f, 0.f, 0.f}, G_ls[3] = {0.f, 0.f, 0.f}, G_q[4] = {0.f, 0.f, 0.f, 0.f}, G_o = 0.f;
+    float G_sh[48];
+#pragma unroll
+    for (int k = 0; k < 48; ++k) G_sh[k] = 0.f;
+    const float qn2 = q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3];
+    const float qinv = __frsqrt_rn(qn2);
+    const float qh[4] = {q4[0] * qinv, q4[1] * qinv, q4[2] * qinv, q4[3] * qinv};
+
+    for (int v = 0; v < vs.n; ++v) {
+        const float4 *gg = st.g2d + ((size_t)v * cap + i) * 3;
+        const float4 ga = gg[0], gb = gg[1], gc = gg[2];
+        // ga = (mean x, mean y, A, B), gb = (C, opacity, r, g), gc = (b, -, -, -)
+        if (ga.x == 0.f && ga.y == 0.f && ga.z == 0.f && ga.w == 0.f && gb.x == 0.f && gb.y == 0.f &&
+            gb.z == 0.f && gb.w == 0.f && gc.x == 0.f)
+            continue;
+        const ViewP &V = vs.v[v];
+        const float *W = V.vm;
+        Proj P;
+        project_geom(V, mu, ls, q4, P);
+        if (!(P.tz > kNear && P.det > 0.f)) continue;
+        const float id = 1.f / P.det;
+        const float QA = P.c * id, QB = -P.b * id, QC = P.a * id;
+        // dL/dSigma2 = -Q G_Q Q with G_Q = [[gA, gB/2], [gB/2, gC]]
+        const float hA = ga.z, hB = 0.5f * ga.w, hC = gb.x;
+        const float m00 = QA * hA + QB * hB, m01 = QA * hB + QB * hC;
+        const float m10 = QB * hA + QC * hB, m11 = QB * hB + QC * hC;
+        const float S00 = -(m00 * QA + m01 * QB), S01 = -(m00 * QB + m01 * QC);
+        const float S11 = -(m10 * QB + m11 * QC);
+        // Sigma2 = T Sig T^T: dL/dSig = T^T S2 T, dL/dT = 2 S2 T Sig
+        const float *T = P.T;
+        float GSig[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                GSig[3 * a + b] = T[a] * (S00 * T[b] + S01 * T[3 + b]) + T[3 + a] * (S01 * T[b] + S11 * T[3 + b]);
+        const float Sg[9] = {P.Sig[0], P.Sig[1], P.Sig[2], P.Sig[1], P.Sig[3], P.Sig[4], P.Sig[2], P.Sig[4], P.Sig[5]};
+        float GT[6];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            float ts0 = T[0] * Sg[b] + T[1] * Sg[3 + b] + T[2] * Sg[6 + b];
+            float ts1 = T[3] * Sg[b] + T[4] * Sg[3 + b] + T[5] * Sg[6 + b];
+            GT[b] = 2.f * (S00 * ts0 + S01 * ts1);
+            GT[3 + b] = 2.f * (S01 * ts0 + S11 * ts1);
+        }
+        // T = J W: dL/dJ = GT W^T (entries 00, 02, 11, 12 used)
+        const float GJ00 = GT[0] * W[0] + GT[1] * W[1] + GT[2] * W[2];
+        const float GJ02 = GT[0] * W[8] + GT[1] * W[9] + GT[2] * W[10];
+        const float GJ11 = GT[3] * W[4] + GT[4] * W[5] + GT[5] * W[6];
+        const float GJ12 = GT[3] * W[8] + GT[4] * W[9] + GT[5] * W[10];
+        const float iz = 1.f / P.tz, iz2 = iz * iz, iz3 = iz2 * iz;
+        float gt0 = 0.f, gt1 = 0.f, gt2 = 0.f;
+        gt2 += GJ00 * (-V.fx * iz2);
+        gt0 += GJ02 * (-V.fx * iz2);
+        gt2 += GJ02 * (2.f * V.fx * P.tx * iz3);
+        gt2 += GJ11 * (-V.fy * iz2);
+        gt1 += GJ12 * (-V.fy * iz2);
+        gt2 += GJ12 * (2.f * V.fy * P.ty * iz3);
+        gt0 += ga.x * V.fx * iz;
+        gt2 += ga.x * (-V.fx * P.tx * iz2);
+        gt1 += ga.y * V.fy * iz;
+        gt2 += ga.y * (-V.fy * P.ty * iz2);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) G_mu[j] += W[j] * gt0 + W[4 + j] * gt1 + W[8 + j] * gt2;
+        // Sig = M M^T, M = R S: dL/dM = (GSig + GSig^T) M
+        float M[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) M[3 * a + b] = P.R[3 * a + b] * P.s[b];
+        float GM[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) acc += (GSig[3 * a + k] + GSig[3 * k + a]) * M[3 * k + b];
+                GM[3 * a + b] = acc;
+            }
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            G_ls[b] += (GM[b] * P.R[b] + GM[3 + b] * P.R[3 + b] + GM[6 + b] * P.R[6 + b]) * P.s[b];
+        float GR[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) GR[3 * a + b] = GM[3 * a + b] * P.s[b];
+        const float w = qh[0], x = qh[1], y = qh[2], z = qh[3];
+        float gqw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+        float gqx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6] + w * GR[7] -
+                           2.f * x * GR[8]);
+        float gqy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6] + z * GR[7] -
+                           2.f * y * GR[8]);
+        float gqz = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] + y * GR[5] +
+                           x * GR[6] + y * GR[7]);
+        const float dq = gqw * w + gqx * x + gqy * y + gqz * z;
+        G_q[0] += (gqw - w * dq) * qinv;
+        G_q[1] += (gqx - x * dq) * qinv;
+        G_q[2] += (gqy - y * dq) * qinv;
+        G_q[3] += (gqz - z * dq) * qinv;
+        G_o += gb.y * opac * (1.f - opac);
+        // colour
+        const float dx = mu[0] - V.ccx, dy = mu[1] - V.ccy, dz = mu[2] - V.ccz;
+        const float rn = __frsqrt_rn(dx * dx + dy * dy + dz * dz);
+        const float ux = dx * rn, uy = dy * rn, uz = dz * rn;
+        float Y[16];
+        sh_eval(ux, uy, uz, K, Y);
+        const float gcol[3] = {gb.z, gb.w, gc.x};
+        const unsigned clampbits = __float_as_uint(st.col[(size_t)v * cap + i].w);
+        float wsh[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) wsh[k] = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            if (clampbits & (1u << ch)) continue;
+            const float g = gcol[ch];
+            for (int k = 0; k < K; ++k) {
+                G_sh[3 * k + ch] += g * Y[k];
+                wsh[k] += g * shp[3 * k + ch];
+            }
+        }
+        float gu[3];
+        sh_grad_dot(ux, uy, uz, K, wsh, gu);
+        const float ud = gu[0] * ux + gu[1] * uy + gu[2] * uz;
+        G_mu[0] += (gu[0] - ux * ud) * rn;
+        G_mu[1] += (gu[1] - uy * ud) * rn;
+        G_mu[2] += (gu[2] - uz * ud) * rn;
+    }
+    if (accumulate) {
+        for (int j = 0; j < 3; ++j) gm[3 * i + j] += G_mu[j], gls[3 * i + j] += G_ls[j];
+        for (int j = 0; j < 4; ++j) gq[4 * i + j] += G_q[j];
+        go[i] += G_o;
+        for (int k = 0; k < 3 * K; ++k) gsh[(size_t)i * 3 * K + k] += G_sh[k];
+    } else {
+        for (int j = 0; j < 3; ++j) gm[3 * i + j] = G_mu[j], gls[3 * i + j] = G_ls[j];
+        for (int j = 0; j < 4; ++j) gq[4 * i + j] = G_q[j];
+        go[i] = G_o;
+        for (int k = 0; k < 3 * K; ++k) gsh[(size_t)i * 3 * K + k] = G_sh[k];
+    }
+}
+
+// ------------------------------------------------------------------- host
+
+struct Layout {
+    State st;
+    size_t bytes;
+};
+
+Layout render_layout(void *ws, long long cap, int nv, int total_tiles, long long pair_cap)
+{
+    Carver c(ws);
+    Layout L{};
+    State &s = L.st;
+    const size_t vc = (size_t)nv * cap;
+    s.xyo = c.take<float4>(vc);
+    s.con = c.take<float4>(vc);
+    s.col = c.take<float4>(vc);
+    s.rect = c.take<uint2>(vc);
+    s.key = c.take<uint32_t>(vc);
+    s.key_alt = c.take<uint32_t>((size_t)cap);
+    s.val = c.take<int32_t>(vc);
+    s.val_alt = c.take<int32_t>((size_t)cap);
+    s.nb_max = int(div_up(cap, kSortTile));
+    s.sort_hist = c.take<unsigned>((size_t)256 * s.nb_max);
+    s.sort_tot = c.take<unsigned>(256);
+    s.nchunk_max = int(div_up(cap, kChunk));
+    s.chunk_cnt = c.take<int32_t>((size_t)s.nchunk_max * total_tiles);
+    s.tile_start = c.take<long long>((size_t)total_tiles + 1);
+    s.pair_count = c.take<long long>(1);
+    s.ids = c.take<int32_t>((size_t)pair_cap);
+    s.g2d = c.take<float4>(vc * 3);
+    s.loss_acc = c.take<double>(1);
+    s.overflow = c.take<int32_t>(1);
+    s.pair_cap = pair_cap;
+    L.bytes = c.size();
+    return L;
+}
+
+gsp_status build_views(const gsp_camera *cams, int nv, const gsp_image_desc *targets, Views &vs)
+{
+    if (!cams || nv < 1) return GSP_ERR_INVALID_ARG;
+    if (nv > GSP_MAX_VIEWS) return GSP_ERR_UNSUPPORTED;
+    int tiles = 0;
+    long long pix = 0;
+    for (int v = 0; v < nv; ++v) {
+        const gsp_camera &c = cams[v];
+        if (c.width < 1 || c.height < 1 || c.pixel_offset < 0) return GSP_ERR_INVALID_ARG;
+        if (!(c.fx > 0.f) || !(c.fy > 0.f)) return GSP_ERR_INVALID_ARG;
+        ViewP &V = vs.v[v];
+        for (int k = 0; k < 12; ++k) V.vm[k] = c.viewmat[k];
+        V.fx = c.fx; V.fy = c.fy; V.cx = c.cx; V.cy = c.cy;
+        // camera centre = -W^T t
+        double cc[3];
+        for (int j = 0; j < 3; ++j)
+            cc[j] = -(double(c.viewmat[j]) * c.viewmat[3] + double(c.viewmat[4 + j]) * c.viewmat[7] +
+                      double(c.viewmat[8 + j]) * c.viewmat[11]);
+        V.ccx = float(cc[0]); V.ccy = float(cc[1]); V.ccz = float(cc[2]);
+        V.w = c.width; V.h = c.height;
+        V.tiles_x = int(div_up(c.width, kTile));
+        V.tiles_y = int(div_up(c.height, kTile));
+        if (V.tiles_x > 65535 || V.tiles_y > 65535) return GSP_ERR_UNSUPPORTED;
+        V.tile_base = tiles;
+        V.pix_off = c.pixel_offset;
+        tiles += V.tiles_x * V.tiles_y;
+        pix += (long long)c.width * c.height;
+        V.tgt = nullptr;
+        V.tgt_pitch = 0;
+        if (targets) {
+            const gsp_image_desc &t = targets[v];
+            if (!t.rgb || t.width != c.width || t.height != c.height || t.pitch_bytes < 3LL * c.width)
+                return GSP_ERR_INVALID_ARG;
+            V.tgt = t.rgb;
+            V.tgt_pitch = t.pitch_bytes;
+        }
+    }
+    vs.n = nv;
+    vs.total_tiles = tiles;
+    vs.total_pix = pix;
+    return GSP_OK;
+}
+
+gsp_status validate_gauss(const gsp_gaussians *g)
+{
+    if (!g || !g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh || !g->count)
+        return GSP_ERR_INVALID_ARG;
+    if (g->capacity < 1 || g->capacity > (1LL << 30)) return GSP_ERR_INVALID_ARG;
+    if (g->sh_degree < 0 || g->sh_degree > 3) return GSP_ERR_INVALID_ARG;
+    return GSP_OK;
+}
+
+Params make_params(const gsp_gaussians *g)
+{
+    Params p;
+    p.means = g->means; p.log_scales = g->log_scales; p.quats = g->quats; p.opac = g->opacity_logits;
+    p.sh = g->sh; p.count = g->count; p.cap = g->capacity;
+    p.K = (g->sh_degree + 1) * (g->sh_degree + 1);
+    return p;
+}
+
+int bin_warps(int T)
+{
+    int nw = 4;
+    while (nw > 1 && size_t(nw) * T * sizeof(int) > size_t(kBinSmemBudget)) nw >>= 1;
+    return nw;
+}
+
+}  // namespace
+}  // namespace gsp
+
+using namespace gsp;
+
+extern "C" size_t gsp_render_workspace_size(int64_t capacity, int32_t sh_degree, const gsp_camera *cams, int32_t nv,
+                                            const gsp_render_opts *opts)
+{
+    Views vs;
+    if (build_views(cams, nv, nullptr, vs) != GSP_OK || !opts || opts->pair_capacity < 1 || capacity < 1 ||
+        sh_degree < 0 || sh_degree > 3)
+        return 0;
+    return render_layout(nullptr, capacity, nv, vs.total_tiles, opts->pair_capacity).bytes;
+}
+
+extern "C" const int64_t *gsp_render_pair_count_ptr(const void *ws, int64_t capacity, int32_t sh_degree,
+                                                    const gsp_camera *cams, int32_t nv, const gsp_render_opts *opts)
+{
+    Views vs;
+    (void)sh_degree;
+    if (!ws || build_views(cams, nv, nullptr, vs) != GSP_OK || !opts) return nullptr;
+    return reinterpret_cast<const int64_t *>(
+        render_layout(const_cast<void *>(ws), capacity, nv, vs.total_tiles, opts->pair_capacity).st.pair_count);
+}
+
+extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *cams, int32_t nv,
+                                     const gsp_image_desc *targets, const float *edge, float *rgb_out, float *T_final,
+                                     int32_t *last_idx, float *score, float *loss_out, const gsp_render_opts *opts,
+                                     void *ws, size_t ws_bytes, int32_t *dev_status, gsp_stream_t stream)
+{
+    gsp_status st = validate_gauss(g);
+    if (st != GSP_OK) return st;
+    static thread_local Views vs;
+    st = build_views(cams, nv, targets, vs);
+    if (st != GSP_OK) return st;
+    if (!opts || opts->pair_capacity < 1 || !rgb_out || !T_final || !last_idx || !dev_status)
+        return GSP_ERR_INVALID_ARG;
+    if (score && !edge) return GSP_ERR_INVALID_ARG;
+    if (loss_out && !targets) return GSP_ERR_INVALID_ARG;
+    for (int v = 0; v < nv; ++v) {
+        int T = vs.v[v].tiles_x * vs.v[v].tiles_y;
+        if (size_t(T) * sizeof(int) > size_t(kBinSmemBudget)) return GSP_ERR_UNSUPPORTED;
+    }
+    const long long cap = g->capacity;
+    Layout L = render_layout(nullptr, cap, nv, vs.total_tiles, opts->pair_capacity);
+    st = check_workspace(ws, ws_bytes, L.bytes);
+    if (st != GSP_OK) return st;
+    L = render_layout(ws, cap, nv, vs.total_tiles, opts->pair_capacity);
+    State S = L.st;
+    Params P = make_params(g);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+    GSP_CUDA_TRY(cudaMemsetAsync(S.loss_acc, 0, sizeof(double), s));
+    stage_begin("project", s);
+    project_kernel<<<div_up(cap, 256), 256, 0, s>>>(vs, P, S);
+    stage_end("project", s);
+    GSP_LAUNCH_CHECK();
+    stage_begin("depth_sort", s);
+    // depth sort, per view (4 passes of 8 bits; an even count leaves the result in key/val)
+    for (int v = 0; v < nv; ++v) {
+        uint32_t *k0 = S.key + (size_t)v * cap, *k1 = S.key_alt;
+        int32_t *v0 = S.val + (size_t)v * cap, *v1 = S.val_alt;
+        for (int pass = 0; pass < 4; ++pass) {
+            sort_count<<<S.nb_max, kSortThreads, 0, s>>>(k0, g->count, 8 * pass, S.sort_hist, S.nb_max);
+            sort_scan<<<256, 256, 0, s>>>(S.sort_hist, S.nb_max, g->count, S.sort_tot);
+            sort_scatter<<<S.nb_max, kSortThreads, 0, s>>>(k0, v0, k1, v1, g->count, 8 * pass, S.sort_hist,
+                                                           S.nb_max, S.sort_tot);
+            uint32_t *tk = k0; k0 = k1; k1 = tk;
+            int32_t *tv = v0; v0 = v1; v1 = tv;
+        }
+    }
+    stage_end("depth_sort", s);
+    GSP_LAUNCH_CHECK();
+    stage_begin("bin", s);
+    // binning: per-chunk tile counts (per view), scans, stable scatter
+    for (int v = 0; v < nv; ++v) {
+        const int T = vs.v[v].tiles_x * vs.v[v].tiles_y;
+        const int nw = bin_warps(T);
+        const size_t smem = size_t(nw) * T * sizeof(int);
+        GSP_CUDA_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        State Sv = S;
+        Sv.rect = S.rect + (size_t)v * cap;
+        Sv.val = S.val + (size_t)v * cap;
+        bin_count<<<S.nchunk_max, nw * 32, smem, s>>>(vs, v, Sv, g->count, nw);
+    }
+    GSP_LAUNCH_CHECK();
+    bin_scan_chunks<<<div_up(vs.total_tiles, 128), 128, 0, s>>>(vs, S, g->count);
+    bin_scan_tiles<<<1, 1024, 0, s>>>(vs.total_tiles, S, dev_status);
+    for (int v = 0; v < nv; ++v) {
+        const int T = vs.v[v].tiles_x * vs.v[v].tiles_y;
+        const int nw = bin_warps(T);
+        const size_t smem = size_t(nw) * T * sizeof(int);
+        GSP_CUDA_TRY(cudaFuncSetAttribute(bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        State Sv = S;
+        Sv.rect = S.rect + (size_t)v * cap;
+        Sv.val = S.val + (size_t)v * cap;
+        bin_scatter<<<S.nchunk_max, nw * 32, smem, s>>>(vs, v, Sv, g->count, nw);
+    }
+    stage_end("bin", s);
+    GSP_LAUNCH_CHECK();
+    stage_begin("composite_fwd", s);
+    composite_fwd<<<vs.total_tiles, kTilePix, 0, s>>>(vs, S, cap, edge, rgb_out, T_final, last_idx, score);
+    stage_end("composite_fwd", s);
+    GSP_LAUNCH_CHECK();
+    note_launches(2 + 12 * nv + 2 * nv + 2 + 1);
+    if (loss_out) {
+        loss_finalise<<<1, 1, 0, s>>>(S, vs.total_pix, loss_out);
+        note_launches(1);
+        GSP_LAUNCH_CHECK();
+    }
+    return GSP_OK;
+}
+
+extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *cams, int32_t nv,
+                                     const gsp_image_desc *targets, const float *dL_drgb, const float *rgb,
+                                     const float *T_final, const int32_t *last_idx, const float *edge, float *score,
+                                     float *grad_means, float *grad_log_scales, float *grad_quats,
+                                     float *grad_opacity_logits, float *grad_sh, int32_t accumulate,
+                                     const gsp_render_opts *opts, void *ws, size_t ws_bytes, int32_t *dev_status,
+                                     gsp_stream_t stream)
+{
+    gsp_status st = validate_gauss(g);
+    if (st != GSP_OK) return st;
+    static thread_local Views vs;
+    st = build_views(cams, nv, dL_drgb ? nullptr : targets, vs);
+    if (st != GSP_OK) return st;
+    if (!opts || !T_final || !last_idx || !dev_status || !grad_means || !grad_log_scales || !grad_quats ||
+        !grad_opacity_logits || !grad_sh)
+        return GSP_ERR_INVALID_ARG;
+    if (!dL_drgb && (!targets || !rgb)) return GSP_ERR_INVALID_ARG;
+    if (score && !edge) return GSP_ERR_INVALID_ARG;
+    const long long cap = g->capacity;
+    Layout L = render_layout(nullptr, cap, nv, vs.total_tiles, opts->pair_capacity);
+    st = check_workspace(ws, ws_bytes, L.bytes);
+    if (st != GSP_OK) return st;
+    L = render_layout(ws, cap, nv, vs.total_tiles, opts->pair_capacity);
+    State S = L.st;
+    Params P = make_params(g);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const float inv_norm = float(1.0 / (3.0 * double(vs.total_pix)));
+    stage_begin("composite_bwd", s);
+    composite_bwd<<<vs.total_tiles, kTilePix, 0, s>>>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score,
+                                                      inv_norm);
+    stage_end("composite_bwd", s);
+    GSP_LAUNCH_CHECK();
+    stage_begin("project_bwd", s);
+    project_bwd<<<div_up(cap, 128), 128, 0, s>>>(vs, P, S, grad_means, grad_log_scales, grad_quats,
+                                                 grad_opacity_logits, grad_sh, accumulate);
+    stage_end("project_bwd", s);
+    note_launches(2);
+    GSP_LAUNCH_CHECK();
+    return GSP_OK;
+}

@@ -1,0 +1,131 @@
+"""GPU top-k selection and Long-Axis-Split (Sec. 2.2, Alg. 1-2) against the oracle.
+
+Selection is integer work: masks must match exactly for the same scores.
+LAS parameters match within 1e-6 (max of absolute and relative) given the
+same selection.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import densify as od
+
+pytestmark = pytest.mark.gpu
+
+
+def _las_close(got, ref, tol=1e-6):
+    err = np.abs(got - ref) / np.maximum(1.0, np.abs(ref))
+    assert err.max(initial=0) <= tol, err.max()
+
+
+@pytest.mark.parametrize("n,k", [(1, 0), (1, 1), (7, 3), (1000, 100), (4097, 4097), (300000, 30000)])
+def test_topk_matches_oracle_with_ties(gsp_lib, n, k):
+    import torch
+    rng = np.random.default_rng(n + k)
+    s = rng.integers(0, 50, n).astype(np.float32) * np.float32(0.25)  # many ties
+    s[rng.integers(0, n, max(n // 10, 1))] = -rng.uniform(0, 3, max(n // 10, 1)).astype(np.float32)
+    cap = n + 5
+    sc = torch.zeros(cap, device="cuda")
+    sc[:n] = torch.from_numpy(s).cuda()
+    cnt = torch.tensor([n], dtype=torch.int32, device="cuda")
+    mask, sel, st = gsp_lib.topk_mask(sc, cnt, k)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    m = mask.cpu().numpy().astype(bool)
+    assert not m[n:].any()
+    assert np.array_equal(m[:n], od.topk_mask(s, k))
+    assert int(sel.item()) == k
+
+
+def test_topk_continuous_scores_and_k_beyond_n(gsp_lib):
+    import torch
+    s = np.random.default_rng(0).gamma(2.0, 1.0, 50000).astype(np.float32)
+    sc = torch.from_numpy(s).cuda()
+    cnt = torch.tensor([50000], dtype=torch.int32, device="cuda")
+    for k in (0, 1, 4999, 50000, 70000):
+        mask, sel, _ = gsp_lib.topk_mask(sc, cnt, k)
+        m = mask.cpu().numpy().astype(bool)
+        assert np.array_equal(m, od.topk_mask(s, min(k, 50000)))
+
+
+@pytest.mark.parametrize("preset", ["config", "paper"])
+@pytest.mark.parametrize("sh_degree", [0, 3])
+def test_las_matches_oracle(gsp_lib, preset, sh_degree):
+    import torch
+    n = 5000
+    g = synth.gaussians(n, sh_degree, seed=21)
+    g["quats"] = (g["quats"] * np.random.default_rng(2).uniform(0.5, 2, (n, 1))).astype(np.float32)
+    mask = np.zeros(n, bool)
+    mask[np.random.default_rng(3).choice(n, 700, replace=False)] = True
+    params = gsp_lib.LAS_CONFIG if preset == "config" else gsp_lib.LAS_PAPER
+    gs = gsp_lib.GaussianSet.from_arrays(g, capacity=n + 1000)
+    st = gsp_lib.las_split(gs, mask=torch.from_numpy(mask.astype(np.uint8)).cuda(), params=params)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and int(gs.count.item()) == n + 700
+    p32 = {k: float(np.float32(v)) for k, v in params.items()}
+    ref = od.las_split(g, mask, **p32)
+    for name in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        got = getattr(gs, name)[:n + 700].cpu().numpy().astype(np.float64)
+        _las_close(got.reshape(n + 700, -1), ref[name].reshape(n + 700, -1))
+
+
+def test_las_capacity_overflow_changes_nothing(gsp_lib):
+    import torch
+    n = 1000
+    g = synth.gaussians(n, 1, seed=5)
+    gs = gsp_lib.GaussianSet.from_arrays(g, capacity=n + 10)
+    before = {k: getattr(gs, k).clone() for k in ("means", "log_scales", "opacity_logits")}
+    mask = torch.ones(n + 10, dtype=torch.uint8, device="cuda")
+    st = gsp_lib.las_split(gs, mask=mask)
+    torch.cuda.synchronize()
+    assert int(st.item()) == gsp_lib._lib.GSP_ERR_CAPACITY
+    assert int(gs.count.item()) == n
+    for k, v in before.items():
+        assert torch.equal(getattr(gs, k), v)
+
+
+def test_las_topk_path_equals_mask_path(gsp_lib):
+    import torch
+    n = 20000
+    g = synth.gaussians(n, 3, seed=9)
+    scores = torch.from_numpy(np.random.default_rng(1).gamma(2, 1, n).astype(np.float32)).cuda()
+    a = gsp_lib.GaussianSet.from_arrays(g, capacity=n + 3000)
+    b = gsp_lib.GaussianSet.from_arrays(g, capacity=n + 3000)
+    sc = torch.zeros(n + 3000, device="cuda")
+    sc[:n] = scores
+    gsp_lib.las_split(a, scores=sc, k=2000)
+    mask, _, _ = gsp_lib.topk_mask(sc, b.count, 2000)
+    gsp_lib.las_split(b, mask=mask)
+    torch.cuda.synchronize()
+    for name in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        assert torch.equal(getattr(a, name), getattr(b, name))
+    assert int(a.count.item()) == n + 2000
+
+
+def test_config0_pipeline_selection_and_split(gsp_lib):
+    """Edge map -> render with score -> top 10% -> LAS on the tiny configuration."""
+    import torch
+    from oracle import edge as oe
+    from oracle import raster as orc
+    g = synth.gaussians(2000, 0, seed=1)
+    cam = synth.camera_front(128, 128)
+    tgt = synth.image(128, 128, 2000)
+    t = torch.from_numpy(tgt).cuda()
+    E, med, _, _ = gsp_lib.edge_map([t])
+    gs = gsp_lib.GaussianSet.from_arrays(g, capacity=2200)
+    r = gsp_lib.Renderer(gs, [cam], 1 << 20)
+    score = torch.zeros(2200, device="cuda")
+    r.forward(targets=[t], edge=E, score=score)
+    mask, sel, st = gsp_lib.topk_mask(score, gs.count, 200)
+    gsp_lib.las_split(gs, mask=mask, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and int(gs.count.item()) == 2200
+    ref_e = oe.edge_map(tgt)["E"]
+    ref = orc.render(g, cam, edge=ref_e)
+    m = mask.cpu().numpy().astype(bool)[:2000]
+    ref_m = od.topk_mask(ref["score"], 200)
+    kth = np.sort(ref["score"])[::-1][199]
+    near = np.abs(ref["score"] - kth) <= 1e-4 * kth
+    assert ((m != ref_m) & ~near).sum() == 0
+    ref_las = od.las_split(g, m, **od.CONFIG_PRESET)
+    _las_close(gs.means[:2200].cpu().numpy().astype(np.float64), ref_las["means"])

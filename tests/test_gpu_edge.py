@@ -1,0 +1,142 @@
+"""GPU edge-map parity (Sec. 2.1) against the FP64 oracle, through the C ABI.
+
+Tolerances (stated with the workload): NMS masks bit-exact except at pixels
+whose compared magnitudes or direction-bin boundary differ by < 1e-6
+relative (oracle.edge.nms_exempt); E within 1e-5 relative where both keep;
+medians within 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import edge as oe
+
+pytestmark = pytest.mark.gpu
+
+DYADIC = [1 / 16, 4 / 16, 6 / 16, 4 / 16, 1 / 16]
+
+
+def _run(gsp, imgs, **kw):
+    import torch
+    dev = torch.device("cuda")
+    ts = [torch.from_numpy(np.ascontiguousarray(i)).to(dev) for i in imgs]
+    E, med, mask, st = gsp.edge_map(ts, with_mask=True, **kw)
+    torch.cuda.synchronize()
+    gsp.raise_on_device_status(st, "edge")
+    out, off = [], 0
+    for i in imgs:
+        h, w = i.shape[:2]
+        out.append((E[off:off + h * w].view(h, w).cpu().numpy(), mask[off:off + h * w].view(h, w).cpu().numpy()))
+        off += h * w
+    return out, med.cpu().numpy()
+
+
+def _compare(img, e_gpu, m_gpu, med_gpu, taps=None):
+    ref = oe.edge_map(img, None if taps is None else np.array(taps))
+    keep = m_gpu.astype(bool)
+    ex = oe.nms_exempt(ref)
+    bad = (keep != ref["keep"]) & ~ex
+    assert bad.sum() == 0, f"{bad.sum()} non-exempt NMS differences"
+    both = keep & ref["keep"]
+    assert np.all(e_gpu[~keep] == 0.0)
+    if both.any():
+        rel = np.abs(e_gpu[both] - ref["E"][both]) / ref["E"][both]
+        assert rel.max() <= 1e-5, rel.max()
+    if ref["median"] > 0:
+        assert abs(med_gpu - ref["median"]) <= 1e-5 * ref["median"]
+    else:
+        assert med_gpu == 0.0
+    return ex.sum()
+
+
+@pytest.mark.parametrize("mode", ["fused", "plain"])
+def test_tiny_view_matches_oracle(gsp_lib, mode):
+    img = synth.image(128, 128, 1000)
+    outs, med = _run(gsp_lib, [img], mode=mode)
+    _compare(img, outs[0][0], outs[0][1], med[0])
+
+
+@pytest.mark.parametrize("mode", ["fused", "plain"])
+def test_ragged_batch_in_one_call(gsp_lib, mode):
+    shapes = [(1, 1), (1, 7), (5, 1), (3, 200), (67, 131), (16, 64), (17, 65), (129, 63)]
+    imgs = [synth.image(h, w, 300 + i) for i, (h, w) in enumerate(shapes)]
+    outs, med = _run(gsp_lib, imgs, mode=mode)
+    for i, img in enumerate(imgs):
+        _compare(img, outs[i][0], outs[i][1], med[i])
+
+
+def test_fused_equals_plain_bitwise(gsp_lib):
+    imgs = [synth.image(203, 347, 40 + i) for i in range(3)]
+    a, ma = _run(gsp_lib, imgs, mode="fused")
+    b, mb = _run(gsp_lib, imgs, mode="plain")
+    for x, y in zip(a, b):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+    assert np.array_equal(ma, mb)
+
+
+@pytest.mark.parametrize("mode", ["fused", "plain"])
+def test_constant_image_gives_zero(gsp_lib, mode):
+    img = np.full((50, 70, 3), 91, np.uint8)
+    outs, med = _run(gsp_lib, [img], mode=mode)
+    e, m = outs[0]
+    assert np.all(e == 0) and not m.any() and med[0] == 0.0
+
+
+@pytest.mark.parametrize("mode", ["fused", "plain"])
+def test_ideal_step_single_column_exact(gsp_lib, mode):
+    h, w, c = 40, 90, 37
+    img = np.zeros((h, w, 3), np.uint8)
+    img[:, :c] = 60
+    img[:, c:] = 200
+    outs, med = _run(gsp_lib, [img], mode=mode, taps=DYADIC)
+    e, m = outs[0]
+    assert m.sum() == h and m[:, c - 1].all()
+    assert np.all(e[m.astype(bool)] == 1.0)
+    _compare(img, e, m, med[0], taps=DYADIC)
+
+
+def test_pitched_rows_match_dense(gsp_lib):
+    import torch
+    img = synth.image(822, 1237, 1000)
+    t = torch.from_numpy(img).cuda()
+    E1, med1, _, s1 = gsp_lib.edge_map([t])
+    E2, med2, _, s2 = gsp_lib.edge_map([gsp_lib.pitched_image(t, 16)])
+    torch.cuda.synchronize()
+    assert torch.equal(E1, E2) and torch.equal(med1, med2)
+
+
+def test_barrier_wait_that_runs_out_reports_timeout(gsp_lib):
+    import torch
+    imgs = [torch.from_numpy(synth.image(822, 1237, 1000 + i)).cuda() for i in range(4)]
+    E, med, _, st = gsp_lib.edge_map(imgs, spin_limit=1)
+    torch.cuda.synchronize()
+    code = int(st.item())
+    assert code in (0, gsp_lib._lib.GSP_ERR_TIMEOUT)
+    # the context stays usable
+    E2, med2, _, st2 = gsp_lib.edge_map(imgs[:1])
+    torch.cuda.synchronize()
+    assert int(st2.item()) == 0
+
+
+def test_full_batch_32_views_1237x822(gsp_lib):
+    """The batched workload (32 views of 1237x822): fused == plain bitwise on
+    every view; two sampled views against the oracle; median property on all."""
+    import torch
+    imgs = [synth.image(822, 1237, 1000 + v) for v in range(32)]
+    ts = [torch.from_numpy(i).cuda() for i in imgs]
+    E, med, mask, st = gsp_lib.edge_map(ts, with_mask=True)
+    Ep, medp, maskp, stp = gsp_lib.edge_map(ts, with_mask=True, mode="plain")
+    torch.cuda.synchronize()
+    gsp_lib.raise_on_device_status(st)
+    assert torch.equal(E, Ep) and torch.equal(med, medp) and torch.equal(mask, maskp)
+    npx = 822 * 1237
+    Ec = E.cpu().numpy().reshape(32, 822, 1237)
+    Mc = mask.cpu().numpy().reshape(32, 822, 1237)
+    for v in range(32):
+        kept = Ec[v][Mc[v].astype(bool)]
+        n = kept.size
+        # lower median: exactly floor((n-1)/2) kept values lie strictly below 1
+        assert (kept < 1.0).sum() <= (n - 1) // 2 < (kept <= 1.0).sum()
+    for v in (0, 17):
+        _compare(imgs[v], Ec[v], Mc[v], med.cpu().numpy()[v])
+    assert E.numel() == 32 * npx

@@ -1,0 +1,250 @@
+"""GPU splatting parity against the FP64 oracle, through the C ABI.
+
+Tolerances: rendered RGB and T_final within 1e-4 absolute; per-Gaussian edge
+scores within 1e-4 relative; gradients within 1e-4 relative of the oracle's
+analytic adjoint (floor 1e-2 x the RMS of the parameter group: FP32 sums over
+thousands of pixel contributions carry ~1e-6 x RMS of rounding) and 1e-3
+relative of its central finite differences (floor 1e-3 x RMS).  Pixels whose oracle
+evaluation passes a gate (alpha = 1/255, T (1 - alpha) = 1e-4) within
+GATE_REL relative are exempt and counted; so are the Gaussians composited
+at such pixels, for the score and gradient checks.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import edge as oe
+from oracle import raster as orc
+
+pytestmark = pytest.mark.gpu
+
+GATE_REL = 2e-5
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def _flat_edge(edges):
+    return np.concatenate([e.ravel() for e in edges]).astype(np.float32)
+
+
+def gpu_render(gsp, g, cams, targets=None, edges=None, dL=None, pair_capacity=1 << 22, score_in="fwd",
+               capacity=None):
+    import torch
+    dev = torch.device("cuda")
+    gs = gsp.GaussianSet.from_arrays(g, capacity=capacity, device=dev)
+    r = gsp.Renderer(gs, cams, pair_capacity, device=dev)
+    E = torch.from_numpy(_flat_edge(edges)).to(dev) if edges is not None else None
+    score = torch.zeros(gs.capacity, device=dev) if E is not None else None
+    tg = [torch.from_numpy(t).to(dev) for t in targets] if targets is not None else None
+    out = r.forward(targets=tg, edge=E, score=score if score_in == "fwd" else None)
+    grads = None
+    if dL is not None or tg is not None:
+        dl = torch.from_numpy(np.ascontiguousarray(dL, dtype=np.float32)).to(dev) if dL is not None else None
+        grads = r.backward(out, targets=tg if dl is None else None, dL_drgb=dl, edge=E,
+                           score=score if score_in == "bwd" else None)
+    torch.cuda.synchronize()
+    res = {"status": int(out["status"].item()), "rgb": out["rgb"].cpu().numpy(), "T": out["T"].cpu().numpy(),
+           "last": out["last"].cpu().numpy(), "pairs": int(r.pair_count().item()),
+           "score": score.cpu().numpy() if score is not None else None,
+           "loss": float(out["loss"].item()) if out["loss"] is not None else None}
+    if grads is not None:
+        res["grads"] = {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
+    return res
+
+
+def oracle_views(g, cams, edges=None):
+    outs = []
+    for v, cam in enumerate(cams):
+        outs.append(orc.render(g, cam, edge=None if edges is None else edges[v]))
+    return outs
+
+
+def exempt_gaussians(g, cam, ref, window=GATE_REL):
+    """Indices of Gaussians whose footprint holds a gate-exempt pixel."""
+    ys, xs = np.nonzero(ref["gate_gap"] < window)
+    proj = ref["proj"]
+    out = set()
+    for x, y in zip(xs, ys):
+        d = np.hypot(proj[:, orc.P_MX] - (x + 0.5), proj[:, orc.P_MY] - (y + 0.5))
+        hit = (proj[:, orc.P_VALID] > 0) & (proj[:, orc.P_RADIUS] >= 0) & (d <= proj[:, orc.P_RADIUS] + 1)
+        out.update(np.nonzero(hit)[0].tolist())
+    return out
+
+
+def check_image(res, refs, cams):
+    off = 0
+    n_ex = 0
+    for cam, ref in zip(cams, refs):
+        h, w = cam["height"], cam["width"]
+        rgb = res["rgb"][off:off + h * w].reshape(h, w, 3)
+        T = res["T"][off:off + h * w].reshape(h, w)
+        ok = ref["gate_gap"] >= GATE_REL
+        n_ex += int((~ok).sum())
+        err = np.abs(rgb - ref["rgb"]).max(axis=2)
+        assert err[ok].max(initial=0) <= 1e-4, err[ok].max()
+        assert np.abs(T - ref["T"])[ok].max(initial=0) <= 1e-4
+        off += h * w
+    return n_ex
+
+
+def check_scores(s_gpu, s_ref, skip=()):
+    keep = np.ones(s_ref.shape[0], bool)
+    keep[list(skip)] = False
+    floor = 1e-3 * np.abs(s_ref).max(initial=0)
+    rel = np.abs(s_gpu - s_ref) / np.maximum(np.abs(s_ref), max(floor, 1e-30))
+    assert rel[keep].max(initial=0) <= 1e-4, rel[keep].max()
+
+
+def check_grads(gr_gpu, gr_ref, n, skip=(), tol=1e-4, floor=1e-2):
+    keep = np.ones(n, bool)
+    keep[list(skip)] = False
+    for name in GROUPS:
+        a = gr_gpu[name][:n].reshape(n, -1)
+        b = gr_ref[name].reshape(n, -1)
+        rms = np.sqrt(np.mean(b[keep] ** 2)) if keep.any() else 0.0
+        if rms == 0:
+            continue
+        rel = np.abs(a - b) / np.maximum(np.abs(b), floor * rms)
+        assert rel[keep].max() <= tol, (name, rel[keep].max())
+
+
+def test_tiny_config_matches_oracle(gsp_lib):
+    g = synth.gaussians(2000, 0, seed=1)
+    cam = synth.camera_front(128, 128)
+    tgt = synth.image(128, 128, 2000)
+    e = oe.edge_map(tgt)["E"]
+    res = gpu_render(gsp_lib, g, [cam], targets=[tgt], edges=[e])
+    assert res["status"] == 0
+    ref = orc.render(g, cam, edge=e)
+    check_image(res, [ref], [cam])
+    check_scores(res["score"], ref["score"], exempt_gaussians(g, cam, ref))
+    loss_ref, _ = orc.l1_loss(ref["rgb"], tgt)
+    assert abs(res["loss"] - loss_ref) <= 1e-5 * loss_ref
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tiny_scenes_against_brute_force(gsp_lib, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 65))
+    g = synth.gaussians(n, [0, 1, 2, 3][seed % 4], seed=500 + seed)
+    g["log_scales"] += np.float32(rng.uniform(0.0, 1.5))
+    w, h = int(rng.integers(16, 49)), int(rng.integers(16, 49))
+    cam = synth.camera_look_at(rng.uniform(-1, 1, 3) + np.array([0, 0, -4.0]), w, h)
+    e = rng.uniform(0, 3, (h, w))
+    res = gpu_render(gsp_lib, g, [cam], edges=[e])
+    ref = orc.render(g, cam, edge=e, brute=True)
+    check_image(res, [ref], [cam])
+    check_scores(res["score"], ref["score"], exempt_gaussians(g, cam, ref))
+
+
+def test_uneven_views_in_one_launch(gsp_lib):
+    g = synth.gaussians(800, 3, seed=8)
+    g["log_scales"] += np.float32(0.7)
+    sizes = [(40, 30), (64, 64), (97, 51)]
+    cams = [synth.camera_ring(k, 3, resolutions=sizes) for k in range(3)]
+    rng = np.random.default_rng(3)
+    edges = [rng.uniform(0, 2, (c["height"], c["width"])) for c in cams]
+    res = gpu_render(gsp_lib, g, cams, edges=edges)
+    refs = oracle_views(g, cams, edges)
+    check_image(res, refs, cams)
+    skip = set()
+    for c, r in zip(cams, refs):
+        skip |= exempt_gaussians(g, c, r)
+    check_scores(res["score"], sum(r["score"] for r in refs), skip)
+
+
+def test_empty_and_fully_culled_scenes(gsp_lib):
+    cam = synth.camera_front(40, 24)
+    g = synth.gaussians(0, 0)
+    res = gpu_render(gsp_lib, g, [cam], edges=[np.ones((24, 40))], capacity=16)
+    assert res["status"] == 0 and np.all(res["rgb"] == 0) and np.all(res["T"] == 1) and res["pairs"] == 0
+    g = synth.gaussians(50, 0, seed=2)
+    g["means"][:, 2] = -5.0  # behind the camera
+    res = gpu_render(gsp_lib, g, [cam], edges=[np.ones((24, 40))])
+    assert np.all(res["rgb"] == 0) and np.all(res["score"] == 0) and res["pairs"] == 0
+
+
+def test_pair_capacity_overflow_is_reported_and_writes_nothing(gsp_lib):
+    import torch
+    g = synth.gaussians(2000, 0, seed=1)
+    cam = synth.camera_front(128, 128)
+    gs = gsp_lib.GaussianSet.from_arrays(g)
+    r = gsp_lib.Renderer(gs, [cam], pair_capacity=100)
+    sentinel = {"rgb": torch.full((128 * 128, 3), -7.0, device="cuda"),
+                "T": torch.full((128 * 128,), -7.0, device="cuda"),
+                "last": torch.full((128 * 128,), -7, dtype=torch.int32, device="cuda")}
+    out = r.forward(out=sentinel)
+    torch.cuda.synchronize()
+    assert int(out["status"].item()) == gsp_lib._lib.GSP_ERR_CAPACITY
+    assert bool((out["rgb"] == -7).all()) and bool((out["T"] == -7).all())
+    assert int(r.pair_count().item()) > 100
+
+
+def _grad_scene():
+    rng = np.random.default_rng(5)
+    g = synth.gaussians(40, 3, seed=3)
+    g["log_scales"] = (g["log_scales"] + 1.2).astype(np.float32)
+    g["quats"] = (g["quats"] * rng.uniform(0.5, 2.0, (40, 1))).astype(np.float32)
+    return g, synth.camera_look_at((0.5, -0.3, -4.0), 48, 40), synth.image(40, 48, 2000)
+
+
+def test_gradients_match_oracle_adjoint(gsp_lib):
+    g, cam, _ = _grad_scene()
+    rng = np.random.default_rng(11)
+    dL = rng.normal(size=(40 * 48, 3)) / (40 * 48)
+    res = gpu_render(gsp_lib, g, [cam], dL=dL)
+    ref = orc.render(g, cam)
+    gr = orc.render_bwd(g, cam, dL.reshape(40, 48, 3))
+    check_grads(res["grads"], gr, 40, exempt_gaussians(g, cam, ref))
+
+
+def test_gradients_match_central_differences(gsp_lib):
+    g, cam, tgt = _grad_scene()
+    res = gpu_render(gsp_lib, g, [cam], targets=[tgt])
+    ref = orc.render(g, cam)
+    # pixels where C is within 1e-5 of the target take their L1 sign differently
+    near = np.abs(ref["rgb"] - tgt / 255.0).min(axis=2) < 1e-5
+    assert near.sum() == 0
+    items = [(i, n, c) for i in range(40) for n, k in zip(GROUPS, (3, 3, 4, 1, 48)) for c in range(k)]
+    fd1, fd2 = orc.fd_grad(g, cam, tgt, items)
+    kink = np.abs(fd1 - fd2) > 0.1 * np.maximum(np.abs(fd1), 1e-12)
+    an = np.array([res["grads"][n][i].ravel()[c] if res["grads"][n].ndim > 1 else res["grads"][n][i]
+                   for (i, n, c) in items])
+    skip = exempt_gaussians(g, cam, ref)
+    for name in GROUPS:
+        sel = np.array([it[1] == name and it[0] not in skip for it in items]) & ~kink
+        rms = np.sqrt(np.mean(fd1[sel] ** 2))
+        rel = np.abs(an[sel] - fd1[sel]) / np.maximum(np.abs(fd1[sel]), 1e-3 * rms)
+        assert rel.max() <= 1e-3, (name, rel.max())
+
+
+def test_l1_sign_map_equals_explicit_upstream_gradient(gsp_lib):
+    g, cam, tgt = _grad_scene()
+    a = gpu_render(gsp_lib, g, [cam], targets=[tgt])
+    diff = a["rgb"].astype(np.float64) - (tgt.reshape(-1, 3) / 255.0)
+    dL = np.sign(diff) / diff.size
+    assert (np.abs(diff) < 1e-6).sum() == 0
+    b = gpu_render(gsp_lib, g, [cam], dL=dL)
+    for name in GROUPS:
+        np.testing.assert_allclose(a["grads"][name], b["grads"][name], rtol=1e-5, atol=1e-12)
+
+
+def test_score_in_backward_equals_score_in_forward(gsp_lib):
+    g = synth.gaussians(2000, 0, seed=1)
+    cam = synth.camera_front(128, 128)
+    tgt = synth.image(128, 128, 2000)
+    e = oe.edge_map(tgt)["E"]
+    a = gpu_render(gsp_lib, g, [cam], targets=[tgt], edges=[e], score_in="fwd")
+    b = gpu_render(gsp_lib, g, [cam], targets=[tgt], edges=[e], score_in="bwd")
+    check_scores(b["score"], a["score"].astype(np.float64))
+
+
+def test_capacity_rows_beyond_count_are_ignored(gsp_lib):
+    g = synth.gaussians(300, 1, seed=4)
+    cam = synth.camera_front(64, 48)
+    a = gpu_render(gsp_lib, g, [cam], edges=[np.ones((48, 64))])
+    b = gpu_render(gsp_lib, g, [cam], edges=[np.ones((48, 64))], capacity=1000)
+    assert np.array_equal(a["rgb"], b["rgb"])
+    np.testing.assert_allclose(a["score"], b["score"][:300], rtol=1e-5, atol=1e-7)
+    assert np.all(b["score"][300:] == 0)
