@@ -234,10 +234,10 @@ static void project_one(int64_t i, const double *means, const double *log_scales
     }
     rec[P_RADIUS] = radius;
     if (radius >= 0) {
-        rec[P_TX0] = floor((rec[P_MX] - radius - 0.5) / ORC_TILE) - 1;
-        rec[P_TY0] = floor((rec[P_MY] - radius - 0.5) / ORC_TILE) - 1;
-        rec[P_TX1] = floor((rec[P_MX] + radius - 0.5) / ORC_TILE) + 1;
-        rec[P_TY1] = floor((rec[P_MY] + radius - 0.5) / ORC_TILE) + 1;
+        rec[P_TX0] = floor((rec[P_MX] - radius - 0.5) / ORC_TILE);
+        rec[P_TY0] = floor((rec[P_MY] - radius - 0.5) / ORC_TILE);
+        rec[P_TX1] = floor((rec[P_MX] + radius - 0.5) / ORC_TILE);
+        rec[P_TY1] = floor((rec[P_MY] + radius - 0.5) / ORC_TILE);
     }
 }
 
@@ -284,17 +284,24 @@ static int64_t sorted_order(int64_t n, const double *proj, int64_t *order)
  * tile, each list in compositing order. */
 typedef struct { int tx, ty; int64_t *start; int64_t *ids; } otiles;
 
-static void build_tiles(int64_t m, const int64_t *order, const double *proj, int width, int height, otiles *tl)
+static void build_tiles(int64_t m, const int64_t *order, const double *proj, int width, int height,
+                        const int *pix_region, otiles *tl)
 {
     int tx = (width + ORC_TILE - 1) / ORC_TILE, ty = (height + ORC_TILE - 1) / ORC_TILE;
     int64_t nt = (int64_t)tx * ty;
+    /* only the tiles that hold pixels of the region get lists */
+    int rx0 = 0, ry0 = 0, rx1 = tx - 1, ry1 = ty - 1;
+    if (pix_region) {
+        rx0 = pix_region[0] / ORC_TILE; ry0 = pix_region[1] / ORC_TILE;
+        rx1 = (pix_region[2] - 1) / ORC_TILE; ry1 = (pix_region[3] - 1) / ORC_TILE;
+    }
     int64_t *cnt = calloc(nt + 1, sizeof(int64_t));
     for (int pass = 0; pass < 2; pass++) {
         for (int64_t j = 0; j < m; j++) {
             const double *r = proj + order[j] * ORC_PROJ_STRIDE;
             if (r[P_RADIUS] < 0) continue;
-            int x0 = (int)fmax(r[P_TX0], 0), y0 = (int)fmax(r[P_TY0], 0);
-            int x1 = (int)fmin(r[P_TX1], tx - 1), y1 = (int)fmin(r[P_TY1], ty - 1);
+            int x0 = (int)fmax(r[P_TX0], rx0), y0 = (int)fmax(r[P_TY0], ry0);
+            int x1 = (int)fmin(r[P_TX1], rx1), y1 = (int)fmin(r[P_TY1], ry1);
             for (int yy = y0; yy <= y1; yy++)
                 for (int xx = x0; xx <= x1; xx++) {
                     int64_t t = (int64_t)yy * tx + xx;
@@ -361,7 +368,8 @@ int orc_render(int64_t n, const double *proj, int width, int height, const doubl
     int64_t *order = malloc(sizeof(int64_t) * (n > 0 ? n : 1));
     int64_t m = sorted_order(n, proj, order);
     otiles tl = {0};
-    if (!brute) build_tiles(m, order, proj, width, height, &tl);
+    int reg[4] = {x0, y0, x1, y1};
+    if (!brute) build_tiles(m, order, proj, width, height, reg, &tl);
     ocontrib *cb = malloc(sizeof(ocontrib) * (m > 0 ? m : 1));
     for (int y = y0; y < y1; y++)
         for (int x = x0; x < x1; x++) {
@@ -411,7 +419,7 @@ int orc_render_bwd(int64_t n, const double *means, const double *log_scales, con
     int64_t *order = malloc(sizeof(int64_t) * (n > 0 ? n : 1));
     int64_t m = sorted_order(n, proj, order);
     otiles tl = {0};
-    build_tiles(m, order, proj, width, height, &tl);
+    build_tiles(m, order, proj, width, height, NULL, &tl);
     ocontrib *cb = malloc(sizeof(ocontrib) * (m > 0 ? m : 1));
 
     for (int y = 0; y < height; y++)

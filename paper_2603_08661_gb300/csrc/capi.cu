@@ -20,18 +20,30 @@ struct StageTimer {
 };
 static StageTimer g_timer;
 
+// Inside stream capture the events must become event-record nodes of the
+// graph (external records), so that each replay records them.
+static void record(cudaEvent_t e, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
+}
+
 void stage_begin(const char *stage, cudaStream_t s)
 {
     if (!g_timer.name[0] || strcmp(g_timer.name, stage) != 0) return;
     if (2 * (g_timer.used + 1) > int(g_timer.ev.size())) return;
-    cudaEventRecord(g_timer.ev[2 * g_timer.used], s);
+    record(g_timer.ev[2 * g_timer.used], s);
     g_timer.open = true;
 }
 
 void stage_end(const char *stage, cudaStream_t s)
 {
     if (!g_timer.open || strcmp(g_timer.name, stage) != 0) return;
-    cudaEventRecord(g_timer.ev[2 * g_timer.used + 1], s);
+    record(g_timer.ev[2 * g_timer.used + 1], s);
     g_timer.used++;
     g_timer.open = false;
 }

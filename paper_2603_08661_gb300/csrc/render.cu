@@ -28,9 +28,6 @@
 namespace gsp {
 namespace {
 
-constexpr int kSortThreads = 256, kSortItems = 8, kSortTile = kSortThreads * kSortItems;
-constexpr int kChunk = 2048;  // depth-ordered Gaussians per binning block
-constexpr int kBinSmemBudget = 200 * 1024;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
@@ -63,22 +60,23 @@ struct Params {
 };
 
 struct State {
-    float4 *xyo;   // [V][cap] (mean x, mean y, opacity, depth key)
-    float4 *con;   // [V][cap] (conic A, B, C, 0)
+    float4 *xyo;   // [V][cap] (mean x, mean y, opacity, depth)
+    float4 *con;   // [V][cap] (-A/2, -B, -C/2, 0) of the conic Q = [[A, B], [B, C]]
     float4 *col;   // [V][cap] (r, g, b, clamp bits)
     uint2 *rect;   // [V][cap] (tx0 | ty0 << 16, tx1 | ty1 << 16); empty if tx1 < tx0
-    uint32_t *key, *key_alt;  // [V][cap]
-    int32_t *val, *val_alt;   // [V][cap]
+    uint32_t *key, *key_alt;  // depth keys [V][cap], sort scratch [cap]
+    int32_t *val, *val_alt;   // depth-ordered ids [V][cap], sort scratch [cap]
     unsigned *sort_hist;      // [256][nb_max]
     unsigned *sort_tot;       // [256]
-    int32_t *chunk_cnt;       // [C][total_tiles] (per view: [C][T_v] at tile_base * C)
+    int32_t *chunk_cnt;       // [total_tiles][nchunk_max] chunk totals, then exclusive offsets
+    unsigned char *bin_wcnt;  // per (view, chunk): [kBinWarps][T_v] per-warp tile counts
     long long *tile_start;    // [total_tiles + 1]
+    int32_t *ids;             // [pair_cap] Gaussian ids, tile-major, depth order inside a tile
     long long *pair_count;    // [1]
-    int32_t *ids;             // [pair_capacity]
     float4 *g2d;              // [V][cap][3]
     double *loss_acc;         // [1]
     int32_t *overflow;        // [1]
-    int nb_max;               // sort blocks for cap
+    int nb_max;               // depth-sort blocks for cap
     int nchunk_max;
     long long pair_cap;
 };
@@ -270,8 +268,10 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Vi
                 }
                 col[ch] = acc;
             }
+            // conic pre-scaled so that power = -1/2 d^T Q d = A' dx^2 + C' dy^2 + B' dx dy
+            // (A' = -A/2, B' = -B, C' = -C/2: exact scalings)
             st.xyo[o] = make_float4(mx, my, opac, P.tz);
-            st.con[o] = make_float4(P.c * id, -P.b * id, P.a * id, 0.f);
+            st.con[o] = make_float4(-0.5f * (P.c * id), P.b * id, -0.5f * (P.a * id), 0.f);
             st.col[o] = make_float4(col[0], col[1], col[2], __uint_as_float(clampbits));
         }
         st.rect[o] = rect;
@@ -280,40 +280,72 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Vi
 }
 
 // ------------------------------------------------------------ radix sort
+//
+// One stable LSD pass over (key, value) pairs, on digits of up to 8 bits.
+// Block tile: 8 warps x 512 elements, each warp owning a contiguous slice.
+//   rs_hist     per-block digit counts (warp-aggregated shared atomics)
+//   rs_scan     per digit, exclusive scan of the block counts
+//   rs_scatter  all loads issued up front; warp-private ranking (match +
+//               shared per-warp counters, no block barrier per item); the
+//               block is staged in shared memory in digit order and written
+//               out so that consecutive threads write one digit's run.
+// The element count is read on the device (a 32-bit or a 64-bit counter).
 
-__global__ void __launch_bounds__(kSortThreads) sort_count(const uint32_t *keys, const int32_t *count, int shift,
-                                                           unsigned *hist, int nb_max)
+constexpr int kRsThreads = 256, kRsWarps = kRsThreads / 32, kRsItems = 16;
+constexpr int kRsWarpTile = 32 * kRsItems, kRsTile = kRsThreads * kRsItems;
+
+struct SortCount {
+    const int32_t *n32;
+    const long long *n64;
+    const int32_t *skip;  // non-zero: nothing to do (pair overflow)
+    __device__ long long get() const { return n64 ? *n64 : (long long)*n32; }
+    __device__ bool skipped() const { return skip && *skip; }
+};
+
+template <typename K>
+__global__ void __launch_bounds__(kRsThreads) rs_hist(const K *keys, SortCount cnt, int shift, int bits,
+                                                      unsigned *bhist, int nb_max)
 {
     __shared__ unsigned h[256];
-    const int n = *count;
-    const int nb = (n + kSortTile - 1) / kSortTile;
-    if (int(blockIdx.x) >= nb) return;
+    if (cnt.skipped()) return;
+    const long long n = cnt.get();
+    const long long b0 = (long long)blockIdx.x * kRsTile;
+    if (b0 >= n) return;
+    const unsigned mask = (1u << bits) - 1u;
     h[threadIdx.x] = 0;
     __syncthreads();
-    const long long base = (long long)blockIdx.x * kSortTile;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long wb = b0 + (long long)wid * kRsWarpTile;
+    unsigned d[kRsItems];
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        long long e = base + j * kSortThreads + threadIdx.x;
-        if (e < n) atomicAdd(&h[(keys[e] >> shift) & 255u], 1u);
+    for (int j = 0; j < kRsItems; ++j) {
+        const long long e = wb + j * 32 + lane;
+        d[j] = e < n ? ((unsigned(keys[e]) >> shift) & mask) : 256u;
+    }
+#pragma unroll
+    for (int j = 0; j < kRsItems; ++j) {
+        const unsigned peers = __match_any_sync(0xffffffffu, d[j]);
+        if (d[j] < 256u && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[d[j]], __popc(peers));
     }
     __syncthreads();
-    hist[(size_t)threadIdx.x * nb_max + blockIdx.x] = h[threadIdx.x];
+    if (threadIdx.x <= mask) bhist[(size_t)threadIdx.x * nb_max + blockIdx.x] = h[threadIdx.x];
 }
 
-// One block per digit: exclusive scan of that digit's counts over blocks.
-__global__ void __launch_bounds__(256) sort_scan(unsigned *hist, int nb_max, const int32_t *count, unsigned *tot)
+// One block per digit: exclusive scan of that digit's block counts.
+__global__ void __launch_bounds__(256) rs_scan(unsigned *bhist, int nb_max, SortCount cnt, unsigned *dtot)
 {
     __shared__ unsigned wsum[8];
     __shared__ unsigned carry;
-    const int n = *count;
-    const int nb = (n + kSortTile - 1) / kSortTile;
-    unsigned *row = hist + (size_t)blockIdx.x * nb_max;
+    if (cnt.skipped()) return;
+    const long long n = cnt.get();
+    const int nb = int((n + kRsTile - 1) / kRsTile);
+    unsigned *row = bhist + (size_t)blockIdx.x * nb_max;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int b0 = 0; b0 < nb; b0 += 256) {
-        int b = b0 + threadIdx.x;
-        unsigned x = b < nb ? row[b] : 0u;
+        const int b = b0 + threadIdx.x;
+        const unsigned x = b < nb ? row[b] : 0u;
         unsigned inc = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -332,24 +364,66 @@ __global__ void __launch_bounds__(256) sort_scan(unsigned *hist, int nb_max, con
         if (threadIdx.x == 0) carry += all;
         __syncthreads();
     }
-    if (threadIdx.x == 0) tot[blockIdx.x] = carry;
+    if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
 }
 
-__global__ void __launch_bounds__(kSortThreads) sort_scatter(const uint32_t *kin, const int32_t *vin, uint32_t *kout,
-                                                             int32_t *vout, const int32_t *count, int shift,
-                                                             const unsigned *hist, int nb_max, const unsigned *tot)
+template <typename K>
+__global__ void __launch_bounds__(kRsThreads) rs_scatter(const K *kin, const int32_t *vin, K *kout, int32_t *vout,
+                                                         SortCount cnt, int shift, int bits, const unsigned *bhist,
+                                                         int nb_max, const unsigned *dtot)
 {
-    __shared__ unsigned base_d[256];
-    __shared__ unsigned run[256];
-    __shared__ unsigned wcnt[kSortThreads / 32][256];
-    __shared__ unsigned wsum[8];
-    const int n = *count;
-    const int nb = (n + kSortTile - 1) / kSortTile;
-    if (int(blockIdx.x) >= nb) return;
+    __shared__ unsigned gbase[256], lstart[256];
+    __shared__ unsigned wh[kRsWarps][256];
+    __shared__ unsigned wsum[kRsWarps];
+    __shared__ K sk[kRsTile];
+    __shared__ int32_t sv[kRsTile];
+    if (cnt.skipped()) return;
+    const long long n = cnt.get();
+    const long long b0 = (long long)blockIdx.x * kRsTile;
+    if (b0 >= n) return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    {   // digit base = exclusive scan of totals + this block's offset
-        unsigned x = tot[tid];
-        unsigned inc = x;
+    const unsigned mask = (1u << bits) - 1u;
+    const int nd = 1 << bits;
+    const long long wb = b0 + (long long)wid * kRsWarpTile;
+
+    K key[kRsItems];
+    int32_t val[kRsItems];
+    unsigned dig[kRsItems], rank[kRsItems];
+#pragma unroll
+    for (int j = 0; j < kRsItems; ++j) {
+        const long long e = wb + j * 32 + lane;
+        const bool ok = e < n;
+        key[j] = ok ? kin[e] : K(0);
+        val[j] = ok ? vin[e] : 0;
+        dig[j] = ok ? ((unsigned(key[j]) >> shift) & mask) : 256u;
+    }
+    for (int k = lane; k < 256; k += 32) wh[wid][k] = 0;
+    __syncwarp();
+    // warp-private stable ranks, items in (j, lane) order
+#pragma unroll
+    for (int j = 0; j < kRsItems; ++j) {
+        const unsigned d = dig[j];
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        unsigned before = 0;
+        if (lane == leader && d < 256u) {
+            before = wh[wid][d];
+            wh[wid][d] = before + __popc(peers);
+        }
+        before = __shfl_sync(0xffffffffu, before, leader);
+        rank[j] = before + __popc(peers & ((1u << lane) - 1u));
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: offsets of the warps, block total; global base of the digit
+    unsigned tot = 0;
+    for (int w = 0; w < kRsWarps; ++w) {
+        const unsigned c = wh[w][tid];
+        wh[w][tid] = tot;
+        tot += c;
+    }
+    {
+        unsigned inc = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
@@ -357,115 +431,165 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter(const uint32_t *kin
         }
         if (lane == 31) wsum[wid] = inc;
         __syncthreads();
-        unsigned wb = 0;
-        for (int w = 0; w < wid; ++w) wb += wsum[w];
-        base_d[tid] = wb + inc - x + hist[(size_t)tid * nb_max + blockIdx.x];
-        run[tid] = 0;
+        unsigned base = 0;
+        for (int w = 0; w < wid; ++w) base += wsum[w];
+        lstart[tid] = base + inc - tot;
+        // digit base over all blocks: exclusive scan of the digit totals
+        const unsigned x = tid < nd ? dtot[tid] : 0u;
+        inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        __syncthreads();
+        if (lane == 31) wsum[wid] = inc;
+        __syncthreads();
+        base = 0;
+        for (int w = 0; w < wid; ++w) base += wsum[w];
+        gbase[tid] = base + inc - x + (tid < nd ? bhist[(size_t)tid * nb_max + blockIdx.x] : 0u);
     }
-    const long long base = (long long)blockIdx.x * kSortTile;
-    for (int j = 0; j < kSortItems; ++j) {
-        for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][tid] = 0;
-        __syncthreads();
-        long long e = base + j * kSortThreads + tid;
-        bool valid = e < n;
-        uint32_t k = valid ? kin[e] : 0u;
-        int32_t val = valid ? vin[e] : 0;
-        unsigned d = valid ? ((k >> shift) & 255u) : 256u;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        unsigned lrank = __popc(peers & ((1u << lane) - 1u));
-        if (valid && lrank == 0) wcnt[wid][d] = __popc(peers);
-        __syncthreads();
-        {   // per digit: prefix over warps, carried across items
-            unsigned r = run[tid];
-            for (int w = 0; w < kSortThreads / 32; ++w) {
-                unsigned c = wcnt[w][tid];
-                wcnt[w][tid] = r;
-                r += c;
-            }
-            run[tid] = r;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kRsItems; ++j) {
+        if (dig[j] < 256u) {
+            const unsigned p = lstart[dig[j]] + wh[wid][dig[j]] + rank[j];
+            sk[p] = key[j];
+            sv[p] = val[j];
         }
-        __syncthreads();
-        if (valid) {
-            unsigned pos = base_d[d] + wcnt[wid][d] + lrank;
-            kout[pos] = k;
-            vout[pos] = val;
-        }
-        __syncthreads();
+    }
+    __syncthreads();
+    const int cnt_blk = int(min((long long)kRsTile, n - b0));
+    for (int i = tid; i < cnt_blk; i += kRsThreads) {
+        const K k = sk[i];
+        const unsigned d = (unsigned(k) >> shift) & mask;
+        const long long pos = (long long)gbase[d] + (i - lstart[d]);
+        kout[pos] = k;
+        vout[pos] = sv[i];
     }
 }
 
 // ---------------------------------------------------------------- binning
+//
+// Stable count-and-scatter of the depth-ordered Gaussians into per-tile
+// lists (a transposition of the Gaussian x tile incidence, no sort over the
+// pairs).  The depth order of each view is cut into chunks of 1024 ranks, one
+// block per chunk, 128 ranks per warp.  A warp visits its Gaussians in rank
+// order, lanes spread over each one's tile rectangle, and keeps per-tile
+// counters in shared memory, so ranks stay in depth order inside every tile.
+//   bin_count    per chunk: per-warp tile counts (bytes, shared memory),
+//                written out, and the chunk's tile totals (tile-major)
+//   bin_scan     one warp per tile: exclusive scan over the chunks
+//   bin_starts   one block: exclusive scan over the tiles (int64 starts),
+//                capacity check
+//   bin_scatter  per chunk: warp cursors = tile start + chunk offset + the
+//                counts of the earlier warps; the walk writes each id to its
+//                slot.
+
+constexpr int kBinChunk = 1024, kBinWarps = 8, kBinThreads = kBinWarps * 32;
+constexpr int kBinPerWarp = kBinChunk / kBinWarps;  // 128 ranks: per-warp counts fit a byte
 
 __device__ __forceinline__ void rect_unpack(uint2 r, int &tx0, int &ty0, int &tx1, int &ty1)
 {
     tx0 = int(r.x & 0xffffu); ty0 = int(r.x >> 16); tx1 = int(r.y & 0xffffu); ty1 = int(r.y >> 16);
 }
 
-// Per-warp tile counts of one chunk of depth-ordered Gaussians.
-__device__ void chunk_warp_counts(const ViewP &V, const uint2 *rect, const int32_t *sorted, int n, int chunk,
-                                  int nwarps, int T, int *cnt /* [nwarps][T] */)
+// Visit the tiles of ranks [r0, r0 + 32) of one view that lie in tile rows
+// [ty_lo, ty_hi], in rank order: the 32
+// rectangles are fetched in one parallel load, then the warp takes one
+// Gaussian at a time with its lanes over that rectangle's (distinct) tiles.
+// fn(tile, id) is called per lane and item; consecutive Gaussians are
+// separated by __syncwarp, so per-tile updates happen in rank order.
+template <class Fn>
+__device__ __forceinline__ void walk_tiles(int tiles_x, const uint2 *rect, const int32_t *sorted, int n, int r0,
+                                           int ty_lo, int ty_hi, Fn fn)
 {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < nwarps * T; t += blockDim.x) cnt[t] = 0;
-    __syncthreads();
-    const int per = kChunk / nwarps;
-    const int b0 = chunk * kChunk + wid * per;
-    int *mine = cnt + wid * T;
-    for (int p = b0; p < b0 + per && p < n; ++p) {
-        int g = sorted[p];
+    const int lane = threadIdx.x & 31;
+    const int r = r0 + lane;
+    int g = -1;
+    uint2 rc = make_uint2(1u, 0u);
+    if (r < n) {
+        g = sorted[r];
+        rc = rect[g];
+    }
+    for (int j = 0; j < 32; ++j) {
+        const unsigned rx = __shfl_sync(0xffffffffu, rc.x, j), ry = __shfl_sync(0xffffffffu, rc.y, j);
+        const int gj = __shfl_sync(0xffffffffu, g, j);
         int tx0, ty0, tx1, ty1;
-        rect_unpack(rect[g], tx0, ty0, tx1, ty1);
-        if (tx1 < tx0) continue;
-        int wr = tx1 - tx0 + 1, area = wr * (ty1 - ty0 + 1);
+        rect_unpack(make_uint2(rx, ry), tx0, ty0, tx1, ty1);
+        ty0 = max(ty0, ty_lo);
+        ty1 = min(ty1, ty_hi);
+        if (tx1 < tx0 || ty1 < ty0) continue;
+        const int wr = tx1 - tx0 + 1, area = wr * (ty1 - ty0 + 1);
+        // exact for wr < 500: the fractional part of (c + 0.5) / wr stays >= 0.5 / wr from 0 and 1
+        const float inv = 1.0f / float(wr);
         for (int c = lane; c < area; c += 32) {
-            int yy = c / wr;
-            mine[(ty0 + yy) * V.tiles_x + tx0 + (c - yy * wr)]++;
+            const int yy = int((float(c) + 0.5f) * inv);
+            fn((ty0 + yy) * tiles_x + tx0 + (c - yy * wr), gj);
         }
         __syncwarp();
     }
-    __syncthreads();
 }
 
-__global__ void bin_count(const __grid_constant__ Views vs, int v, State st, const int32_t *count, int nwarps)
+__global__ void __launch_bounds__(kBinThreads) bin_count(const __grid_constant__ Views vs, int v, State st,
+                                                         long long cap, const int32_t *count)
 {
-    extern __shared__ int bsm[];
+    extern __shared__ unsigned char bsm[];  // [kBinWarps][T] byte counts
     const ViewP &V = vs.v[v];
     const int n = *count;
     const int T = V.tiles_x * V.tiles_y;
     const int chunk = blockIdx.x;
-    if (chunk * kChunk >= n) return;
-    chunk_warp_counts(V, st.rect, st.val, n, chunk, nwarps, T, bsm);
-    int32_t *dst = st.chunk_cnt + (size_t)V.tile_base * st.nchunk_max + (size_t)chunk * T;
-    for (int t = threadIdx.x; t < T; t += blockDim.x) {
-        int sum = 0;
-        for (int w = 0; w < nwarps; ++w) sum += bsm[w * T + t];
-        dst[t] = sum;
+    if (chunk * kBinChunk >= n) return;
+    const int wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kBinWarps * T; i += kBinThreads) bsm[i] = 0;
+    __syncthreads();
+    unsigned char *mine = bsm + wid * T;
+    const uint2 *rect = st.rect + (size_t)v * cap;
+    const int32_t *sorted = st.val + (size_t)v * cap;
+    const int base = chunk * kBinChunk + wid * kBinPerWarp;
+    for (int r0 = base; r0 < base + kBinPerWarp && r0 < n; r0 += 32) {
+        walk_tiles(V.tiles_x, rect, sorted, n, r0, 0, V.tiles_y - 1, [&](int tile, int) { mine[tile] += 1; });
+    }
+    __syncthreads();
+    // per-warp counts (coalesced) and the chunk's tile totals (tile-major)
+    unsigned char *wout = st.bin_wcnt + ((size_t)V.tile_base * st.nchunk_max + (size_t)chunk * T) * kBinWarps;
+    for (int i = threadIdx.x; i < kBinWarps * T; i += kBinThreads) wout[i] = bsm[i];
+    int32_t *cc = st.chunk_cnt + (size_t)V.tile_base * st.nchunk_max;
+    for (int t = threadIdx.x; t < T; t += kBinThreads) {
+        int s = 0;
+#pragma unroll
+        for (int w = 0; w < kBinWarps; ++w) s += bsm[w * T + t];
+        cc[(size_t)t * st.nchunk_max + chunk] = s;
     }
 }
 
-// One thread per global tile: exclusive scan over chunks (in place), totals out.
-__global__ void bin_scan_chunks(const __grid_constant__ Views vs, State st, const int32_t *count)
+// One warp per global tile: exclusive scan over the chunks of its view, in place.
+__global__ void __launch_bounds__(256) bin_scan(const __grid_constant__ Views vs, State st, const int32_t *count)
 {
-    int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gt = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (gt >= vs.total_tiles) return;
     const int n = *count;
-    const int nc = (n + kChunk - 1) / kChunk;
-    int v = find_view(vs, gt);
-    const ViewP &V = vs.v[v];
-    const int T = V.tiles_x * V.tiles_y;
-    int t = gt - V.tile_base;
-    int32_t *col = st.chunk_cnt + (size_t)V.tile_base * st.nchunk_max + t;
-    long long run = 0;
-    for (int c = 0; c < nc; ++c) {
-        int x = col[(size_t)c * T];
-        col[(size_t)c * T] = int(run);
-        run += x;
+    const int nc = (n + kBinChunk - 1) / kBinChunk;
+    int32_t *col = st.chunk_cnt + (size_t)gt * st.nchunk_max;
+    long long carry = 0;
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+        const int c = c0 + lane;
+        const int x = c < nc ? col[c] : 0;
+        int inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (c < nc) col[c] = int(carry) + inc - x;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
     }
-    st.tile_start[gt + 1] = run;  // totals; turned into starts by bin_scan_tiles
+    if (lane == 0) st.tile_start[gt + 1] = carry;  // totals; bin_starts turns them into starts
 }
 
-// Single block: exclusive scan of the tile totals into tile starts; capacity check.
-__global__ void __launch_bounds__(1024) bin_scan_tiles(int total_tiles, State st, int32_t *status)
+// One block: exclusive scan of the tile totals into starts; capacity check.
+__global__ void __launch_bounds__(1024) bin_starts(int total_tiles, State st, int32_t *status)
 {
     __shared__ long long wsum[32];
     __shared__ long long carry;
@@ -473,12 +597,12 @@ __global__ void __launch_bounds__(1024) bin_scan_tiles(int total_tiles, State st
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int b0 = 0; b0 < total_tiles; b0 += 1024) {
-        int t = b0 + threadIdx.x;
-        long long x = t < total_tiles ? st.tile_start[t + 1] : 0;
+        const int t = b0 + threadIdx.x;
+        const long long x = t < total_tiles ? st.tile_start[t + 1] : 0;
         long long inc = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            const long long y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
         if (lane == 31) wsum[wid] = inc;
@@ -488,7 +612,7 @@ __global__ void __launch_bounds__(1024) bin_scan_tiles(int total_tiles, State st
             if (w < wid) wb += wsum[w];
             all += wsum[w];
         }
-        long long c0 = carry;
+        const long long c0 = carry;
         __syncthreads();
         if (t < total_tiles) st.tile_start[t] = c0 + wb + inc - x;
         if (threadIdx.x == 0) carry = c0 + all;
@@ -497,51 +621,50 @@ __global__ void __launch_bounds__(1024) bin_scan_tiles(int total_tiles, State st
     if (threadIdx.x == 0) {
         st.tile_start[total_tiles] = carry;
         *st.pair_count = carry;
-        int over = carry > st.pair_cap;
+        const int over = carry > st.pair_cap;
         *st.overflow = over;
         if (over) set_status(status, GSP_ERR_CAPACITY);
     }
 }
 
-__global__ void bin_scatter(const __grid_constant__ Views vs, int v, State st, const int32_t *count, int nwarps)
+__global__ void __launch_bounds__(kBinThreads) bin_scatter(const __grid_constant__ Views vs, int v, State st,
+                                                           long long cap, const int32_t *count, int ty_lo,
+                                                           int ty_hi)
 {
-    extern __shared__ int bsm[];
+    extern __shared__ unsigned char bsm_raw[];
     if (*st.overflow) return;
     const ViewP &V = vs.v[v];
     const int n = *count;
     const int T = V.tiles_x * V.tiles_y;
     const int chunk = blockIdx.x;
-    if (chunk * kChunk >= n) return;
-    chunk_warp_counts(V, st.rect, st.val, n, chunk, nwarps, T, bsm);
-    // per-warp write cursors, relative to the view's first pair
+    if (chunk * kBinChunk >= n) return;
+    int *base = reinterpret_cast<int *>(bsm_raw);                          // [T]
+    unsigned short *cur = reinterpret_cast<unsigned short *>(base + T);   // [kBinWarps][T]
     const long long view_base = st.tile_start[V.tile_base];
-    const int32_t *coff = st.chunk_cnt + (size_t)V.tile_base * st.nchunk_max + (size_t)chunk * T;
-    for (int t = threadIdx.x; t < T; t += blockDim.x) {
-        int r = int(st.tile_start[V.tile_base + t] - view_base) + coff[t];
-        for (int w = 0; w < nwarps; ++w) {
-            int c = bsm[w * T + t];
-            bsm[w * T + t] = r;
-            r += c;
+    const unsigned char *wc = st.bin_wcnt + ((size_t)V.tile_base * st.nchunk_max + (size_t)chunk * T) * kBinWarps;
+    const int32_t *cc = st.chunk_cnt + (size_t)V.tile_base * st.nchunk_max;
+    for (int t = threadIdx.x; t < T; t += kBinThreads) {
+        base[t] = int(st.tile_start[V.tile_base + t] - view_base) + cc[(size_t)t * st.nchunk_max + chunk];
+        unsigned run = 0;
+#pragma unroll
+        for (int w = 0; w < kBinWarps; ++w) {
+            cur[w * T + t] = (unsigned short)run;
+            run += wc[w * T + t];
         }
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int per = kChunk / nwarps;
-    const int b0 = chunk * kChunk + wid * per;
-    int *mine = bsm + wid * T;
+    const int wid = threadIdx.x >> 5;
+    unsigned short *mine = cur + wid * T;
+    const uint2 *rect = st.rect + (size_t)v * cap;
+    const int32_t *sorted = st.val + (size_t)v * cap;
     int32_t *out = st.ids + view_base;
-    for (int p = b0; p < b0 + per && p < n; ++p) {
-        int g = st.val[p];
-        int tx0, ty0, tx1, ty1;
-        rect_unpack(st.rect[g], tx0, ty0, tx1, ty1);
-        if (tx1 < tx0) continue;
-        int wr = tx1 - tx0 + 1, area = wr * (ty1 - ty0 + 1);
-        for (int c = lane; c < area; c += 32) {
-            int yy = c / wr;
-            int t = (ty0 + yy) * V.tiles_x + tx0 + (c - yy * wr);
-            out[mine[t]++] = g;
-        }
-        __syncwarp();
+    const int b0 = chunk * kBinChunk + wid * kBinPerWarp;
+    for (int r0 = b0; r0 < b0 + kBinPerWarp && r0 < n; r0 += 32) {
+        walk_tiles(V.tiles_x, rect, sorted, n, r0, ty_lo, ty_hi, [&](int tile, int gid) {
+            const unsigned short k = mine[tile];
+            mine[tile] = (unsigned short)(k + 1);
+            out[base[tile] + k] = gid;
+        });
     }
 }
 
@@ -549,22 +672,24 @@ __global__ void bin_scatter(const __grid_constant__ Views vs, int v, State st, c
 
 struct Alpha {
     float G, raw, alpha, dx, dy;
+    bool pass;
 };
 
 // Identical in the forward and the backward kernel (explicitly rounded ops),
-// so both take the same 1/255 decision.
+// so both take the same 1/255 decision.  The exponential is evaluated for every
+// lane (a branch around it costs more than the MUFU op it saves).
 __device__ __forceinline__ Alpha eval_alpha(float4 xyo, float4 con, float px, float py)
 {
     Alpha r;
     r.dx = __fsub_rn(px, xyo.x);
     r.dy = __fsub_rn(py, xyo.y);
-    float t1 = __fmul_rn(con.x, __fmul_rn(r.dx, r.dx));
-    float t2 = __fmul_rn(con.z, __fmul_rn(r.dy, r.dy));
-    float t3 = __fmul_rn(con.y, __fmul_rn(r.dx, r.dy));
-    float power = __fmaf_rn(-0.5f, __fadd_rn(t1, t2), -t3);
+    const float power =
+        __fmaf_rn(con.x, __fmul_rn(r.dx, r.dx), __fmaf_rn(con.z, __fmul_rn(r.dy, r.dy),
+                                                          __fmul_rn(con.y, __fmul_rn(r.dx, r.dy))));
     r.G = __expf(power);
     r.raw = __fmul_rn(xyo.z, r.G);
     r.alpha = fminf(kAlphaMax, r.raw);
+    r.pass = r.alpha >= kAlphaMin;
     return r;
 }
 
@@ -621,7 +746,7 @@ __global__ void __launch_bounds__(kTilePix) composite_fwd(const __grid_constant_
             float w = 0.f;
             if (!done) {
                 Alpha a = eval_alpha(s_xyo[j], s_con[j], px, py);
-                if (a.alpha >= kAlphaMin) {
+                if (a.pass) {
                     float Tn = __fmul_rn(T, __fsub_rn(1.f, a.alpha));
                     if (Tn < kTMin) {
                         done = true;
@@ -770,7 +895,7 @@ __global__ void __launch_bounds__(kTilePix) composite_bwd(const __grid_constant_
             bool active = false;
             if (pos < last) {
                 Alpha a = eval_alpha(s_xyo[j], s_con[j], px, py);
-                if (a.alpha >= kAlphaMin) {
+                if (a.pass) {
                     active = true;
                     const float4 c = s_col[j];
                     const float one_m = __fsub_rn(1.f, a.alpha);
@@ -784,11 +909,12 @@ __global__ void __launch_bounds__(kTilePix) composite_bwd(const __grid_constant_
                     acc1 = acc1 * one_m + c.y * a.alpha;
                     acc2 = acc2 * one_m + c.z * a.alpha;
                     if (a.raw < kAlphaMax) {
-                        const float4 q = s_con[j];
+                        const float4 q = s_con[j];  // (-A/2, -B, -C/2)
                         const float dpow = dalpha * s_xyo[j].z * a.G;
                         val[5] = dalpha * a.G;
-                        val[0] = dpow * (q.x * a.dx + q.y * a.dy);
-                        val[1] = dpow * (q.y * a.dx + q.z * a.dy);
+                        // d power / d mean = (A dx + B dy, B dx + C dy)
+                        val[0] = dpow * (-2.f * q.x * a.dx - q.y * a.dy);
+                        val[1] = dpow * (-q.y * a.dx - 2.f * q.z * a.dy);
                         val[2] = -0.5f * dpow * a.dx * a.dx;
                         val[3] = -dpow * a.dx * a.dy;
                         val[4] = -0.5f * dpow * a.dy * a.dy;
@@ -996,14 +1122,15 @@ Layout render_layout(void *ws, long long cap, int nv, int total_tiles, long long
     s.key_alt = c.take<uint32_t>((size_t)cap);
     s.val = c.take<int32_t>(vc);
     s.val_alt = c.take<int32_t>((size_t)cap);
-    s.nb_max = int(div_up(cap, kSortTile));
+    s.nb_max = int(div_up(cap, kRsTile));
     s.sort_hist = c.take<unsigned>((size_t)256 * s.nb_max);
     s.sort_tot = c.take<unsigned>(256);
-    s.nchunk_max = int(div_up(cap, kChunk));
-    s.chunk_cnt = c.take<int32_t>((size_t)s.nchunk_max * total_tiles);
+    s.nchunk_max = int(div_up(cap, kBinChunk));
+    s.chunk_cnt = c.take<int32_t>((size_t)total_tiles * s.nchunk_max);
+    s.bin_wcnt = c.take<unsigned char>((size_t)total_tiles * s.nchunk_max * kBinWarps);
     s.tile_start = c.take<long long>((size_t)total_tiles + 1);
-    s.pair_count = c.take<long long>(1);
     s.ids = c.take<int32_t>((size_t)pair_cap);
+    s.pair_count = c.take<long long>(1);
     s.g2d = c.take<float4>(vc * 3);
     s.loss_acc = c.take<double>(1);
     s.overflow = c.take<int32_t>(1);
@@ -1073,13 +1200,6 @@ Params make_params(const gsp_gaussians *g)
     return p;
 }
 
-int bin_warps(int T)
-{
-    int nw = 4;
-    while (nw > 1 && size_t(nw) * T * sizeof(int) > size_t(kBinSmemBudget)) nw >>= 1;
-    return nw;
-}
-
 }  // namespace
 }  // namespace gsp
 
@@ -1120,8 +1240,8 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     if (score && !edge) return GSP_ERR_INVALID_ARG;
     if (loss_out && !targets) return GSP_ERR_INVALID_ARG;
     for (int v = 0; v < nv; ++v) {
-        int T = vs.v[v].tiles_x * vs.v[v].tiles_y;
-        if (size_t(T) * sizeof(int) > size_t(kBinSmemBudget)) return GSP_ERR_UNSUPPORTED;
+        const size_t T = size_t(vs.v[v].tiles_x) * vs.v[v].tiles_y;
+        if (T * (sizeof(int) + kBinWarps * sizeof(unsigned short)) > 200 * 1024) return GSP_ERR_UNSUPPORTED;
     }
     const long long cap = g->capacity;
     Layout L = render_layout(nullptr, cap, nv, vs.total_tiles, opts->pair_capacity);
@@ -1142,11 +1262,12 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     for (int v = 0; v < nv; ++v) {
         uint32_t *k0 = S.key + (size_t)v * cap, *k1 = S.key_alt;
         int32_t *v0 = S.val + (size_t)v * cap, *v1 = S.val_alt;
+        const SortCount sc{g->count, nullptr, nullptr};
         for (int pass = 0; pass < 4; ++pass) {
-            sort_count<<<S.nb_max, kSortThreads, 0, s>>>(k0, g->count, 8 * pass, S.sort_hist, S.nb_max);
-            sort_scan<<<256, 256, 0, s>>>(S.sort_hist, S.nb_max, g->count, S.sort_tot);
-            sort_scatter<<<S.nb_max, kSortThreads, 0, s>>>(k0, v0, k1, v1, g->count, 8 * pass, S.sort_hist,
-                                                           S.nb_max, S.sort_tot);
+            rs_hist<uint32_t><<<S.nb_max, kRsThreads, 0, s>>>(k0, sc, 8 * pass, 8, S.sort_hist, S.nb_max);
+            rs_scan<<<256, 256, 0, s>>>(S.sort_hist, S.nb_max, sc, S.sort_tot);
+            rs_scatter<uint32_t><<<S.nb_max, kRsThreads, 0, s>>>(k0, v0, k1, v1, sc, 8 * pass, 8, S.sort_hist,
+                                                                 S.nb_max, S.sort_tot);
             uint32_t *tk = k0; k0 = k1; k1 = tk;
             int32_t *tv = v0; v0 = v1; v1 = tv;
         }
@@ -1154,29 +1275,20 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     stage_end("depth_sort", s);
     GSP_LAUNCH_CHECK();
     stage_begin("bin", s);
-    // binning: per-chunk tile counts (per view), scans, stable scatter
+    // binning: per-chunk tile counts, scans, stable scatter (per view for the chunk kernels)
     for (int v = 0; v < nv; ++v) {
         const int T = vs.v[v].tiles_x * vs.v[v].tiles_y;
-        const int nw = bin_warps(T);
-        const size_t smem = size_t(nw) * T * sizeof(int);
+        const size_t smem = size_t(kBinWarps) * T;
         GSP_CUDA_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        State Sv = S;
-        Sv.rect = S.rect + (size_t)v * cap;
-        Sv.val = S.val + (size_t)v * cap;
-        bin_count<<<S.nchunk_max, nw * 32, smem, s>>>(vs, v, Sv, g->count, nw);
+        bin_count<<<S.nchunk_max, kBinThreads, smem, s>>>(vs, v, S, cap, g->count);
     }
-    GSP_LAUNCH_CHECK();
-    bin_scan_chunks<<<div_up(vs.total_tiles, 128), 128, 0, s>>>(vs, S, g->count);
-    bin_scan_tiles<<<1, 1024, 0, s>>>(vs.total_tiles, S, dev_status);
+    bin_scan<<<div_up((long long)vs.total_tiles * 32, 256), 256, 0, s>>>(vs, S, g->count);
+    bin_starts<<<1, 1024, 0, s>>>(vs.total_tiles, S, dev_status);
     for (int v = 0; v < nv; ++v) {
         const int T = vs.v[v].tiles_x * vs.v[v].tiles_y;
-        const int nw = bin_warps(T);
-        const size_t smem = size_t(nw) * T * sizeof(int);
+        const size_t smem = size_t(T) * (sizeof(int) + kBinWarps * sizeof(unsigned short));
         GSP_CUDA_TRY(cudaFuncSetAttribute(bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        State Sv = S;
-        Sv.rect = S.rect + (size_t)v * cap;
-        Sv.val = S.val + (size_t)v * cap;
-        bin_scatter<<<S.nchunk_max, nw * 32, smem, s>>>(vs, v, Sv, g->count, nw);
+        bin_scatter<<<S.nchunk_max, kBinThreads, smem, s>>>(vs, v, S, cap, g->count, 0, vs.v[v].tiles_y - 1);
     }
     stage_end("bin", s);
     GSP_LAUNCH_CHECK();
