@@ -244,6 +244,32 @@ gsp_status gsp_topk_mask(const float *scores, const int32_t *count, int64_t capa
                          size_t workspace_bytes, int32_t *dev_status, gsp_stream_t stream);
 
 /*
+ * Allocation-free variant of gsp_topk_mask (the paper has no counterpart).
+ *
+ * For callers that cannot allocate device memory when they call: code being
+ * captured into a CUDA graph (cudaMalloc is not allowed during capture),
+ * real-time loops that forbid allocation after start-up, and hosts whose
+ * device memory belongs to another allocator.  Same arguments and result as
+ * gsp_topk_mask, but no workspace: the scratch (about 73 KB) is a static
+ * device array inside the library that every GPU which loads the library
+ * holds until the process exits.  The caller still passes scores, count,
+ * mask_out and selected_out.
+ * - capacity must be <= GSP_TOPK_STATIC_MAX_CAPACITY, else GSP_ERR_INVALID_ARG
+ *   is returned and nothing is enqueued.
+ * - The first call on a device looks up the array's device address on that
+ *   device (cudaGetSymbolAddress); make that first call before any stream
+ *   capture.
+ * - All calls share the one array and the kernels re-initialise what must
+ *   start at zero; calls that overlap on the GPU (other streams, other host
+ *   threads) race on it and must be serialised by the caller.
+ * - No device memory is allocated or freed by this call.
+ */
+#define GSP_TOPK_STATIC_MAX_CAPACITY (1 << 24)
+gsp_status gsp_topk_mask_static(const float *scores, const int32_t *count, int64_t capacity, int64_t k,
+                                uint8_t *mask_out, int32_t *selected_out, int32_t *dev_status,
+                                gsp_stream_t stream);
+
+/*
  * Long-Axis-Split in place (Alg. 1, with Alg. 2's column read of R).
  *
  * mask       device uint8 [capacity]: split Gaussian i < N iff mask[i] != 0; or NULL,

@@ -17,6 +17,7 @@ GSP_OK, GSP_ERR_INVALID_ARG, GSP_ERR_CUDA, GSP_ERR_CAPACITY, GSP_ERR_TIMEOUT, GS
 GSP_MAX_VIEWS = 64
 GSP_TILE = 16
 GSP_EDGE_FUSED, GSP_EDGE_PLAIN = 0, 1
+GSP_TOPK_STATIC_MAX_CAPACITY = 1 << 24
 
 
 class ImageDesc(ctypes.Structure):
@@ -71,6 +72,7 @@ SIGNATURES = {
     "gsp_las_workspace_size": (c_sz, [c_i64]),
     "gsp_topk_mask": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
     "gsp_las_split": (c_i32, [P(Gaussians), c_vp, c_vp, c_i64, P(LasParams), c_vp, c_sz, c_vp, c_vp]),
+    "gsp_topk_mask_static": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),
 }
 
 _lib = None

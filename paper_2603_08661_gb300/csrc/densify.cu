@@ -429,3 +429,66 @@ extern "C" gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask,
     GSP_LAUNCH_CHECK();
     return GSP_OK;
 }
+
+// ------------------------------------------------- allocation-free top-k
+//
+// Some callers cannot allocate device memory at the time they call us: code
+// that is being captured into a CUDA graph (cudaMalloc is not allowed during
+// capture), real-time loops that forbid allocation after start-up, and hosts
+// whose device memory belongs to another allocator.  gsp_topk_mask_static
+// serves them with the same selection as gsp_topk_mask, its scratch held in
+// this file-scope device array instead of a caller workspace.  Every GPU that
+// loads the library keeps the array until the process exits.
+
+namespace gsp {
+namespace {
+
+constexpr long long kStaticTopkMaxCap = GSP_TOPK_STATIC_MAX_CAPACITY;
+constexpr size_t kStaticTopkBytes =
+    256 + 256 + kSelBins * sizeof(unsigned) + 256 +
+    sizeof(unsigned) * size_t((kStaticTopkMaxCap + kBlockItems - 1) / kBlockItems + 1) + 256;
+
+static __device__ __align__(256) unsigned char g_topk_scratch[kStaticTopkBytes];
+
+constexpr int kMaxDevices = 64;
+static void *g_topk_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once
+// per device; the host-side symbol is only a stand-in for it).
+gsp_status static_topk_scratch(void **out)
+{
+    int dev = 0;
+    GSP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return GSP_ERR_UNSUPPORTED;
+    if (!g_topk_scratch_ptr[dev]) {
+        void *p = nullptr;
+        GSP_CUDA_TRY(cudaGetSymbolAddress(&p, g_topk_scratch));
+        g_topk_scratch_ptr[dev] = p;
+    }
+    *out = g_topk_scratch_ptr[dev];
+    return GSP_OK;
+}
+
+}  // namespace
+}  // namespace gsp
+
+extern "C" gsp_status gsp_topk_mask_static(const float *scores, const int32_t *count, int64_t capacity, int64_t k,
+                                           uint8_t *mask_out, int32_t *selected_out, int32_t *dev_status,
+                                           gsp_stream_t stream)
+{
+    if (!scores || !count || !mask_out || !dev_status || capacity < 1) return GSP_ERR_INVALID_ARG;
+    if (capacity > kStaticTopkMaxCap) return GSP_ERR_INVALID_ARG;
+    void *scratch = nullptr;
+    gsp_status st = static_topk_scratch(&scratch);
+    if (st != GSP_OK) return st;
+    // same carving as a workspace, without the mask (the caller's output)
+    Carver c(scratch);
+    DensifyLayout L{};
+    L.sel = c.take<SelState>(1);
+    L.hist = c.take<unsigned>(kSelBins);
+    L.sums = c.take<unsigned>(div_up(capacity, kBlockItems) + 1);
+    L.mask = nullptr;
+    if (c.size() > kStaticTopkBytes) return GSP_ERR_UNSUPPORTED;
+    return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L,
+                        reinterpret_cast<cudaStream_t>(stream));
+}
