@@ -69,39 +69,42 @@ __global__ void sel_hist(const float *scores, const SelState *s, int shift, int 
         if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
-// Pick the digit holding the remaining-th largest key (one block).
+// Pick the digit holding the remaining-th largest key (one block): thread t
+// owns bins [nb - (t+1) per, nb - t per) counted from the top; a block scan
+// of the segment sums finds the segment, its owner walks its bins.
 __global__ void __launch_bounds__(kThreads) sel_pick(SelState *s, int shift, int bits, unsigned *hist)
 {
-    __shared__ unsigned seg_s[kThreads];
+    __shared__ unsigned wsum[kThreads / 32];
     __shared__ int s_bin;
     __shared__ unsigned s_above;
     const int nb = 1 << bits;
     const int per = nb / kThreads;
     const unsigned rem = s->remaining;
-    // segments are taken from the top: thread t owns bins [nb - (t+1) per, nb - t per)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned seg = 0;
     for (int k = 0; k < per; ++k) seg += hist[nb - 1 - (threadIdx.x * per + k)];
-    seg_s[threadIdx.x] = seg;
+    unsigned inc = seg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    if (threadIdx.x == 0) s_bin = -1;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        s_bin = -1;
-        if (rem > 0) {
-            unsigned acc = 0;
-            for (int t = 0; t < kThreads && s_bin < 0; ++t) {
-                if (acc + seg_s[t] >= rem) {
-                    for (int k = 0; k < per; ++k) {
-                        int b = nb - 1 - (t * per + k);
-                        if (acc + hist[b] >= rem) {
-                            s_bin = b;
-                            s_above = acc;
-                            break;
-                        }
-                        acc += hist[b];
-                    }
-                } else {
-                    acc += seg_s[t];
-                }
+    unsigned base = 0;
+    for (int w = 0; w < wid; ++w) base += wsum[w];
+    const unsigned before = base + inc - seg;  // keys in higher segments
+    if (rem > 0 && before < rem && rem <= before + seg) {
+        unsigned acc = before;
+        for (int k = 0; k < per; ++k) {
+            const int b = nb - 1 - (threadIdx.x * per + k);
+            if (acc + hist[b] >= rem) {
+                s_bin = b;
+                s_above = acc;
+                break;
             }
+            acc += hist[b];
         }
     }
     __syncthreads();
@@ -226,6 +229,7 @@ struct LasArgs {
     float k_off, log_long, log_other, beta;
     const uint8_t *mask;
     const unsigned *rank_off;  // block offsets; [nblocks] = total selected
+    int32_t *src;              // [cap]: parent of appended child slot n + r
     int32_t *status;
 };
 
@@ -284,11 +288,28 @@ __global__ void __launch_bounds__(kThreads) las_kernel(LasArgs a)
         for (int k = 0; k < 3; ++k) a.log_scales[3 * dst + k] = nls[k];
         for (int k = 0; k < 4; ++k) a.quats[4 * dst + k] = q[k];
         a.opac[dst] = nop;
-        for (int k = 0; k < 3 * a.K; ++k) a.sh[(size_t)dst * 3 * a.K + k] = a.sh[(size_t)i * 3 * a.K + k];
+        a.src[dst - n] = int32_t(i);
         // child 0 (in place)
         a.means[3 * i] = m0 + dx; a.means[3 * i + 1] = m1 + dy; a.means[3 * i + 2] = m2 + dz;
         for (int k = 0; k < 3; ++k) a.log_scales[3 * i + k] = nls[k];
         a.opac[i] = nop;
+    }
+}
+
+// SH rows of the appended children, copied with consecutive threads on
+// consecutive floats of a row.
+__global__ void __launch_bounds__(256) las_copy_sh(LasArgs a)
+{
+    const long long n = *a.count;
+    const int nb = int((n + kBlockItems - 1) / kBlockItems);
+    const long long total = n > 0 ? a.rank_off[nb] : 0;
+    if (n + total > a.cap) return;
+    const int row = 3 * a.K;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total * row;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long c = e / row;
+        const int k = int(e - c * row);
+        a.sh[(size_t)(n + c) * row + k] = a.sh[(size_t)a.src[c] * row + k];
     }
 }
 
@@ -309,6 +330,7 @@ struct DensifyLayout {
     unsigned *hist;
     unsigned *sums;
     uint8_t *mask;
+    int32_t *src;
     size_t bytes;
 };
 
@@ -320,6 +342,7 @@ DensifyLayout densify_layout(void *ws, long long cap)
     L.hist = c.take<unsigned>(kSelBins);
     L.sums = c.take<unsigned>(div_up(cap, kBlockItems) + 1);
     L.mask = c.take<uint8_t>((size_t)cap);
+    L.src = c.take<int32_t>((size_t)cap);
     L.bytes = c.size();
     return L;
 }
@@ -421,11 +444,13 @@ extern "C" gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask,
     a.beta = p->beta;
     a.mask = mask;
     a.rank_off = L.sums;
+    a.src = L.src;
     a.status = dev_status;
     las_kernel<<<nblk, kThreads, 0, s>>>(a);
+    las_copy_sh<<<4 * num_sms(), 256, 0, s>>>(a);
     las_commit<<<1, 1, 0, s>>>(g->count, cap, L.sums, dev_status);
     stage_end("las", s);
-    note_launches(4);
+    note_launches(5);
     GSP_LAUNCH_CHECK();
     return GSP_OK;
 }

@@ -32,6 +32,10 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 constexpr float kNear = 0.2f;
+constexpr int kRowCap = 16;  // tile rows per Gaussian with an exact column interval
+// pixels per compositing thread (a vertical run): measured best at 1 for the
+// forward and 2 for the adjoint (fewer warp reductions per pixel)
+constexpr int kFwdPixPerThread = 1, kBwdPixPerThread = 2;
 
 struct ViewP {
     float vm[12];
@@ -64,18 +68,23 @@ struct State {
     float4 *con;   // [V][cap] (-A/2, -B, -C/2, 0) of the conic Q = [[A, B], [B, C]]
     float4 *col;   // [V][cap] (r, g, b, clamp bits)
     uint2 *rect;   // [V][cap] (tx0 | ty0 << 16, tx1 | ty1 << 16); empty if tx1 < tx0
+    uchar2 *rowint;  // [V][cap][kRowCap] per tile row of the rectangle: columns (lo, hi) - tx0 the
+                     // 1/255 ellipse reaches (lo > hi: none); rows past kRowCap are not culled
     uint32_t *key, *key_alt;  // depth keys [V][cap], sort scratch [cap]
     int32_t *val, *val_alt;   // depth-ordered ids [V][cap], sort scratch [cap]
     unsigned *sort_hist;      // [256][nb_max]
     unsigned *sort_tot;       // [256]
-    int32_t *chunk_cnt;       // [total_tiles][nchunk_max] chunk totals, then exclusive offsets
+    int32_t *chunk_pos;       // [total_tiles][nchunk_max] segment counts, then positions in the tile list
+    uint32_t *seg_start;      // [total_tiles][nchunk_max] in-region offsets, then absolute starts in ids
     unsigned char *bin_wcnt;  // per (view, chunk): [kBinWarps][T_v] per-warp tile counts
-    long long *tile_start;    // [total_tiles + 1]
-    int32_t *ids;             // [pair_cap] Gaussian ids, tile-major, depth order inside a tile
+    long long *chunk_tot;     // [V][nchunk_max] pairs per chunk, then region starts
+    int32_t *tile_len;        // [total_tiles] list length of each tile
+    int32_t *ids;             // [pair_cap] Gaussian ids: chunk regions, tile-major inside a region
     long long *pair_count;    // [1]
     float4 *g2d;              // [V][cap][3]
     double *loss_acc;         // [1]
     int32_t *overflow;        // [1]
+    const int32_t *n_dev;     // the caller's device count of live Gaussians
     int nb_max;               // depth-sort blocks for cap
     int nchunk_max;
     long long pair_cap;
@@ -208,6 +217,25 @@ __device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + expf(-
 
 // --------------------------------------------------------------- projection
 
+// The SH coefficients of one Gaussian (3K floats) into registers; 16-byte
+// loads when the row length allows (K = 4, 16).
+template <int K>
+__device__ __forceinline__ void load_sh(const float *row, float *out)
+{
+    if constexpr ((3 * K) % 4 == 0) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+        for (int q = 0; q < 3 * K / 4; ++q) {
+            const float4 v = r4[q];
+            out[4 * q] = v.x; out[4 * q + 1] = v.y; out[4 * q + 2] = v.z; out[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 3 * K; ++q) out[q] = row[q];
+    }
+}
+
+template <int K>
 __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Views vs, Params p, State st)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -225,7 +253,8 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Vi
     float ls[3] = {p.log_scales[3 * i], p.log_scales[3 * i + 1], p.log_scales[3 * i + 2]};
     float q4[4] = {p.quats[4 * i], p.quats[4 * i + 1], p.quats[4 * i + 2], p.quats[4 * i + 3]};
     float opac = sigmoidf_(p.opac[i]);
-    const float *shp = p.sh + (size_t)i * p.K * 3;
+    float shv[3 * K];
+    load_sh<K>(p.sh + (size_t)i * K * 3, shv);
     for (int v = 0; v < vs.n; ++v) {
         const ViewP &V = vs.v[v];
         const long long o = v * cap + i;
@@ -248,6 +277,34 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Vi
             int ty1 = min(int(floorf((my + ey - 0.5f) / kTile)), V.tiles_y - 1);
             if (tx0 <= tx1 && ty0 <= ty1) {
                 rect = make_uint2(unsigned(tx0) | (unsigned(ty0) << 16), unsigned(tx1) | (unsigned(ty1) << 16));
+                // exact column interval of the ellipse d^T Sigma2^-1 d <= lim over the strip of
+                // pixel-centre rows of each tile row: at height dy the ellipse spans
+                // x = (b/c) dy +- sqrt((lim - dy^2/c)(a - b^2/c)); the upper bound is concave in
+                // dy and peaks at the rightmost point dy = b sqrt(lim/a), the lower one mirrors it
+                const float la = fmaxf(lim, 0.f);
+                const float ymax = sqrtf(la * P.c);
+                const float dyr = P.b * sqrtf(la / P.a);
+                const float schur = fmaxf(P.a - P.b * P.b / P.c, 0.f);
+                uchar2 *ri = st.rowint + o * kRowCap;
+                const int nrows = min(ty1 - ty0 + 1, kRowCap);  // the walk reads only these rows
+                for (int yy = 0; yy < nrows; ++yy) {
+                    const int ty = ty0 + yy;
+                    uchar2 iv = make_uchar2(255, 0);
+                    {
+                        const float lo = fmaxf(float(ty * kTile) + 0.5f - my, -ymax);
+                        const float hi = fminf(float(ty * kTile + kTile - 1) + 0.5f - my, ymax);
+                        if (lo <= hi) {
+                            const float d1 = fminf(fmaxf(dyr, lo), hi), d2 = fminf(fmaxf(-dyr, lo), hi);
+                            const float xr = P.b / P.c * d1 + sqrtf(fmaxf(la - d1 * d1 / P.c, 0.f) * schur);
+                            const float xl = P.b / P.c * d2 - sqrtf(fmaxf(la - d2 * d2 / P.c, 0.f) * schur);
+                            const float m = 0.01f + 1e-4f * (fabsf(xl) + fabsf(xr));
+                            const int c0 = max(int(floorf((mx + xl - m - 0.5f) / kTile)), tx0);
+                            const int c1 = min(int(floorf((mx + xr + m - 0.5f) / kTile)), tx1);
+                            if (c0 <= c1) iv = make_uchar2((unsigned char)(c0 - tx0), (unsigned char)(c1 - tx0));
+                        }
+                    }
+                    ri[yy] = iv;
+                }
             } else {
                 ok = false;
             }
@@ -255,13 +312,14 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Vi
             float dx = mu[0] - V.ccx, dy = mu[1] - V.ccy, dz = mu[2] - V.ccz;
             float rn = __frsqrt_rn(dx * dx + dy * dy + dz * dz);
             float Y[16];
-            sh_eval(dx * rn, dy * rn, dz * rn, p.K, Y);
+            sh_eval(dx * rn, dy * rn, dz * rn, K, Y);
             float col[3];
             unsigned clampbits = 0;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 float acc = 0.5f;
-                for (int k = 0; k < p.K; ++k) acc += shp[3 * k + ch] * Y[k];
+#pragma unroll
+                for (int k = 0; k < K; ++k) acc += shv[3 * k + ch] * Y[k];
                 if (acc < 0.f) {
                     clampbits |= 1u << ch;
                     acc = 0.f;
@@ -291,7 +349,7 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Vi
 //               out so that consecutive threads write one digit's run.
 // The element count is read on the device (a 32-bit or a 64-bit counter).
 
-constexpr int kRsThreads = 256, kRsWarps = kRsThreads / 32, kRsItems = 16;
+constexpr int kRsThreads = 256, kRsWarps = kRsThreads / 32, kRsItems = 8;
 constexpr int kRsWarpTile = 32 * kRsItems, kRsTile = kRsThreads * kRsItems;
 
 struct SortCount {
@@ -477,14 +535,22 @@ __global__ void __launch_bounds__(kRsThreads) rs_scatter(const K *kin, const int
 // block per chunk, 128 ranks per warp.  A warp visits its Gaussians in rank
 // order, lanes spread over each one's tile rectangle, and keeps per-tile
 // counters in shared memory, so ranks stay in depth order inside every tile.
-//   bin_count    per chunk: per-warp tile counts (bytes, shared memory),
-//                written out, and the chunk's tile totals (tile-major)
-//   bin_scan     one warp per tile: exclusive scan over the chunks
-//   bin_starts   one block: exclusive scan over the tiles (int64 starts),
-//                capacity check
-//   bin_scatter  per chunk: warp cursors = tile start + chunk offset + the
-//                counts of the earlier warps; the walk writes each id to its
-//                slot.
+//
+// Each chunk writes its pairs into a region of its own, tile-major inside the
+// region: the 32-byte sectors of a region are filled by one block during its
+// lifetime, so L2 writes them back complete (a layout with every tile's list
+// contiguous makes adjacent chunks share sectors and forces read-modify-write
+// in DRAM).  A tile's list is the chain of its segments over the chunks, in
+// chunk order; segment c of tile t starts at seg_start[t][c] and at position
+// chunk_pos[t][c] of the tile's list.
+//   bin_count    per chunk: per-warp tile counts (bytes, shared memory) written
+//                out; per-tile chunk counts and their in-region offsets
+//   bin_regions  one block: exclusive scan of the chunk totals into region
+//                starts; pair total and capacity check
+//   bin_scan     one warp per tile: segment positions in the tile's list,
+//                absolute segment starts, list length
+//   bin_scatter  per chunk: warp cursors = segment start + the counts of the
+//                earlier warps; the walk writes each id to its slot
 
 constexpr int kBinChunk = 1024, kBinWarps = 8, kBinThreads = kBinWarps * 32;
 constexpr int kBinPerWarp = kBinChunk / kBinWarps;  // 128 ranks: per-warp counts fit a byte
@@ -494,15 +560,16 @@ __device__ __forceinline__ void rect_unpack(uint2 r, int &tx0, int &ty0, int &tx
     tx0 = int(r.x & 0xffffu); ty0 = int(r.x >> 16); tx1 = int(r.y & 0xffffu); ty1 = int(r.y >> 16);
 }
 
-// Visit the tiles of ranks [r0, r0 + 32) of one view that lie in tile rows
-// [ty_lo, ty_hi], in rank order: the 32
+// Visit the tiles of ranks [r0, r0 + 32) of one view in rank order: the 32
 // rectangles are fetched in one parallel load, then the warp takes one
-// Gaussian at a time with its lanes over that rectangle's (distinct) tiles.
-// fn(tile, id) is called per lane and item; consecutive Gaussians are
-// separated by __syncwarp, so per-tile updates happen in rank order.
+// Gaussian at a time with its lanes over that rectangle's (distinct) tiles,
+// keeping the tiles inside the row's column interval (the tiles the 1/255
+// ellipse reaches).  fn(tile, id) is called per lane and kept item;
+// consecutive Gaussians are separated by __syncwarp, so per-tile updates
+// happen in rank order.
 template <class Fn>
-__device__ __forceinline__ void walk_tiles(int tiles_x, const uint2 *rect, const int32_t *sorted, int n, int r0,
-                                           int ty_lo, int ty_hi, Fn fn)
+__device__ __forceinline__ void walk_tiles(int tiles_x, const uint2 *rect, const uchar2 *rowint,
+                                           const int32_t *sorted, int n, int r0, Fn fn)
 {
     const int lane = threadIdx.x & 31;
     const int r = r0 + lane;
@@ -514,18 +581,23 @@ __device__ __forceinline__ void walk_tiles(int tiles_x, const uint2 *rect, const
     }
     for (int j = 0; j < 32; ++j) {
         const unsigned rx = __shfl_sync(0xffffffffu, rc.x, j), ry = __shfl_sync(0xffffffffu, rc.y, j);
-        const int gj = __shfl_sync(0xffffffffu, g, j);
         int tx0, ty0, tx1, ty1;
         rect_unpack(make_uint2(rx, ry), tx0, ty0, tx1, ty1);
-        ty0 = max(ty0, ty_lo);
-        ty1 = min(ty1, ty_hi);
-        if (tx1 < tx0 || ty1 < ty0) continue;
+        if (tx1 < tx0) continue;
+        const int gj = __shfl_sync(0xffffffffu, g, j);
+        const uchar2 *ri = rowint + (size_t)gj * kRowCap;
         const int wr = tx1 - tx0 + 1, area = wr * (ty1 - ty0 + 1);
         // exact for wr < 500: the fractional part of (c + 0.5) / wr stays >= 0.5 / wr from 0 and 1
         const float inv = 1.0f / float(wr);
         for (int c = lane; c < area; c += 32) {
             const int yy = int((float(c) + 0.5f) * inv);
-            fn((ty0 + yy) * tiles_x + tx0 + (c - yy * wr), gj);
+            const int xx = c - yy * wr;
+            bool keep = true;
+            if (yy < kRowCap) {
+                const uchar2 iv = ri[yy];
+                keep = xx >= int(iv.x) && xx <= int(iv.y);
+            }
+            if (keep) fn((ty0 + yy) * tiles_x + tx0 + xx, gj);
         }
         __syncwarp();
     }
@@ -535,70 +607,69 @@ __global__ void __launch_bounds__(kBinThreads) bin_count(const __grid_constant__
                                                          long long cap, const int32_t *count)
 {
     extern __shared__ unsigned char bsm[];  // [kBinWarps][T] byte counts
+    __shared__ unsigned wsum[kBinWarps];
     const ViewP &V = vs.v[v];
     const int n = *count;
     const int T = V.tiles_x * V.tiles_y;
     const int chunk = blockIdx.x;
     if (chunk * kBinChunk >= n) return;
-    const int wid = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kBinWarps * T; i += kBinThreads) bsm[i] = 0;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < kBinWarps * T; i += kBinThreads) bsm[i] = 0;
     __syncthreads();
     unsigned char *mine = bsm + wid * T;
     const uint2 *rect = st.rect + (size_t)v * cap;
     const int32_t *sorted = st.val + (size_t)v * cap;
     const int base = chunk * kBinChunk + wid * kBinPerWarp;
-    for (int r0 = base; r0 < base + kBinPerWarp && r0 < n; r0 += 32) {
-        walk_tiles(V.tiles_x, rect, sorted, n, r0, 0, V.tiles_y - 1, [&](int tile, int) { mine[tile] += 1; });
-    }
+    for (int r0 = base; r0 < base + kBinPerWarp && r0 < n; r0 += 32)
+        walk_tiles(V.tiles_x, rect, st.rowint + (size_t)v * cap * kRowCap, sorted, n, r0,
+                   [&](int tile, int) { mine[tile] += 1; });
     __syncthreads();
-    // per-warp counts (coalesced) and the chunk's tile totals (tile-major)
     unsigned char *wout = st.bin_wcnt + ((size_t)V.tile_base * st.nchunk_max + (size_t)chunk * T) * kBinWarps;
-    for (int i = threadIdx.x; i < kBinWarps * T; i += kBinThreads) wout[i] = bsm[i];
-    int32_t *cc = st.chunk_cnt + (size_t)V.tile_base * st.nchunk_max;
-    for (int t = threadIdx.x; t < T; t += kBinThreads) {
-        int s = 0;
+    for (int i = tid; i < kBinWarps * T; i += kBinThreads) wout[i] = bsm[i];
+    // per-tile chunk counts and their exclusive offsets inside the chunk's region
+    const int per = (T + kBinThreads - 1) / kBinThreads;
+    const int t0 = tid * per;
+    unsigned mysum = 0;
+    for (int t = t0; t < min(t0 + per, T); ++t)
+        for (int w = 0; w < kBinWarps; ++w) mysum += bsm[w * T + t];
+    unsigned inc = mysum;
 #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    unsigned run = inc - mysum, all = 0;
+    for (int w = 0; w < kBinWarps; ++w) {
+        if (w < wid) run += wsum[w];
+        all += wsum[w];
+    }
+    const size_t row0 = (size_t)V.tile_base * st.nchunk_max + chunk;
+    for (int t = t0; t < min(t0 + per, T); ++t) {
+        unsigned s = 0;
         for (int w = 0; w < kBinWarps; ++w) s += bsm[w * T + t];
-        cc[(size_t)t * st.nchunk_max + chunk] = s;
+        st.chunk_pos[row0 + (size_t)t * st.nchunk_max] = int32_t(s);
+        st.seg_start[row0 + (size_t)t * st.nchunk_max] = run;
+        run += s;
     }
+    if (tid == 0) st.chunk_tot[(size_t)v * st.nchunk_max + chunk] = all;
 }
 
-// One warp per global tile: exclusive scan over the chunks of its view, in place.
-__global__ void __launch_bounds__(256) bin_scan(const __grid_constant__ Views vs, State st, const int32_t *count)
-{
-    const int gt = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gt >= vs.total_tiles) return;
-    const int n = *count;
-    const int nc = (n + kBinChunk - 1) / kBinChunk;
-    int32_t *col = st.chunk_cnt + (size_t)gt * st.nchunk_max;
-    long long carry = 0;
-    for (int c0 = 0; c0 < nc; c0 += 32) {
-        const int c = c0 + lane;
-        const int x = c < nc ? col[c] : 0;
-        int inc = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (c < nc) col[c] = int(carry) + inc - x;
-        carry += __shfl_sync(0xffffffffu, inc, 31);
-    }
-    if (lane == 0) st.tile_start[gt + 1] = carry;  // totals; bin_starts turns them into starts
-}
-
-// One block: exclusive scan of the tile totals into starts; capacity check.
-__global__ void __launch_bounds__(1024) bin_starts(int total_tiles, State st, int32_t *status)
+// One block: exclusive scan of the chunk totals (all views, chunk-major per
+// view) into region starts; the grand total is the pair count.
+__global__ void __launch_bounds__(1024) bin_regions(int nv, State st, const int32_t *count, int32_t *status)
 {
     __shared__ long long wsum[32];
     __shared__ long long carry;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nc = (*count + kBinChunk - 1) / kBinChunk;
+    const int total = nv * st.nchunk_max;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int b0 = 0; b0 < total_tiles; b0 += 1024) {
-        const int t = b0 + threadIdx.x;
-        const long long x = t < total_tiles ? st.tile_start[t + 1] : 0;
+    for (int b0 = 0; b0 < total; b0 += 1024) {
+        const int i = b0 + threadIdx.x;
+        const long long x = (i < total && (i % st.nchunk_max) < nc) ? st.chunk_tot[i] : 0;
         long long inc = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -614,12 +685,11 @@ __global__ void __launch_bounds__(1024) bin_starts(int total_tiles, State st, in
         }
         const long long c0 = carry;
         __syncthreads();
-        if (t < total_tiles) st.tile_start[t] = c0 + wb + inc - x;
+        if (i < total) st.chunk_tot[i] = c0 + wb + inc - x;
         if (threadIdx.x == 0) carry = c0 + all;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        st.tile_start[total_tiles] = carry;
         *st.pair_count = carry;
         const int over = carry > st.pair_cap;
         *st.overflow = over;
@@ -627,9 +697,39 @@ __global__ void __launch_bounds__(1024) bin_starts(int total_tiles, State st, in
     }
 }
 
+// One warp per global tile: positions of its segments in the tile's list,
+// absolute segment starts, list length.
+__global__ void __launch_bounds__(256) bin_scan(const __grid_constant__ Views vs, State st, const int32_t *count)
+{
+    const int gt = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gt >= vs.total_tiles) return;
+    const int v = find_view(vs, gt);
+    const int nc = (*count + kBinChunk - 1) / kBinChunk;
+    int32_t *pos = st.chunk_pos + (size_t)gt * st.nchunk_max;
+    uint32_t *seg = st.seg_start + (size_t)gt * st.nchunk_max;
+    const long long *region = st.chunk_tot + (size_t)v * st.nchunk_max;
+    int carry = 0;
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+        const int c = c0 + lane;
+        const int x = c < nc ? pos[c] : 0;
+        int inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (c < nc) {
+            pos[c] = carry + inc - x;
+            seg[c] = uint32_t(region[c] + seg[c]);
+        }
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) st.tile_len[gt] = carry;
+}
+
 __global__ void __launch_bounds__(kBinThreads) bin_scatter(const __grid_constant__ Views vs, int v, State st,
-                                                           long long cap, const int32_t *count, int ty_lo,
-                                                           int ty_hi)
+                                                           long long cap, const int32_t *count)
 {
     extern __shared__ unsigned char bsm_raw[];
     if (*st.overflow) return;
@@ -638,13 +738,12 @@ __global__ void __launch_bounds__(kBinThreads) bin_scatter(const __grid_constant
     const int T = V.tiles_x * V.tiles_y;
     const int chunk = blockIdx.x;
     if (chunk * kBinChunk >= n) return;
-    int *base = reinterpret_cast<int *>(bsm_raw);                          // [T]
+    uint32_t *base = reinterpret_cast<uint32_t *>(bsm_raw);                // [T]
     unsigned short *cur = reinterpret_cast<unsigned short *>(base + T);   // [kBinWarps][T]
-    const long long view_base = st.tile_start[V.tile_base];
     const unsigned char *wc = st.bin_wcnt + ((size_t)V.tile_base * st.nchunk_max + (size_t)chunk * T) * kBinWarps;
-    const int32_t *cc = st.chunk_cnt + (size_t)V.tile_base * st.nchunk_max;
+    const uint32_t *seg = st.seg_start + (size_t)V.tile_base * st.nchunk_max + chunk;
     for (int t = threadIdx.x; t < T; t += kBinThreads) {
-        base[t] = int(st.tile_start[V.tile_base + t] - view_base) + cc[(size_t)t * st.nchunk_max + chunk];
+        base[t] = seg[(size_t)t * st.nchunk_max];
         unsigned run = 0;
 #pragma unroll
         for (int w = 0; w < kBinWarps; ++w) {
@@ -657,15 +756,29 @@ __global__ void __launch_bounds__(kBinThreads) bin_scatter(const __grid_constant
     unsigned short *mine = cur + wid * T;
     const uint2 *rect = st.rect + (size_t)v * cap;
     const int32_t *sorted = st.val + (size_t)v * cap;
-    int32_t *out = st.ids + view_base;
     const int b0 = chunk * kBinChunk + wid * kBinPerWarp;
     for (int r0 = b0; r0 < b0 + kBinPerWarp && r0 < n; r0 += 32) {
-        walk_tiles(V.tiles_x, rect, sorted, n, r0, ty_lo, ty_hi, [&](int tile, int gid) {
+        walk_tiles(V.tiles_x, rect, st.rowint + (size_t)v * cap * kRowCap, sorted, n, r0,
+                   [&](int tile, int gid) {
             const unsigned short k = mine[tile];
             mine[tile] = (unsigned short)(k + 1);
-            out[base[tile] + k] = gid;
+            st.ids[(size_t)base[tile] + k] = gid;
         });
     }
+}
+
+// Gaussian id at position p of tile gt's list: the segment is found by a
+// binary search over the tile's segment positions (nc chunks).
+__device__ __forceinline__ int list_id(const State &st, int gt, int nc, int p)
+{
+    const int32_t *pos = st.chunk_pos + (size_t)gt * st.nchunk_max;
+    int lo = 0, hi = nc;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pos + mid) <= p) lo = mid;
+        else hi = mid;
+    }
+    return st.ids[(size_t)__ldg(st.seg_start + (size_t)gt * st.nchunk_max + lo) + (p - __ldg(pos + lo))];
 }
 
 // ------------------------------------------------------------- compositing
@@ -698,19 +811,21 @@ __device__ __forceinline__ float target_value(const ViewP &V, int x, int y, int 
     return __fdiv_rn(float(V.tgt[(long long)y * V.tgt_pitch + 3 * x + ch]), 255.f);
 }
 
-struct FwdOut {
-    float *rgb, *T, *score, *edge;
-    int32_t *last;
-};
+// Forward compositing: one block per 16x16 tile, each thread a vertical run
+// of PPT pixels.  The tile's list is staged through shared memory in batches
+// of kBatch Gaussians; the block leaves when every pixel has stopped.
+constexpr int kBatch = 256;
 
-__global__ void __launch_bounds__(kTilePix) composite_fwd(const __grid_constant__ Views vs, State st, long long cap,
-                                                          const float *edge, float *rgb_out, float *T_out,
-                                                          int32_t *last_out, float *score)
+template <int PPT>
+__global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_constant__ Views vs, State st,
+                                                                long long cap, const float *edge, float *rgb_out,
+                                                                float *T_out, int32_t *last_out, float *score)
 {
-    __shared__ float4 s_xyo[kTilePix], s_con[kTilePix], s_col[kTilePix];
-    __shared__ int32_t s_id[kTilePix];
-    __shared__ float s_score[kTilePix];
-    __shared__ float s_red[kTilePix / 32];
+    constexpr int NT = kTilePix / PPT;
+    __shared__ float4 s_xyo[kBatch], s_con[kBatch], s_col[kBatch];
+    __shared__ int32_t s_id[kBatch];
+    __shared__ float s_score[kBatch];
+    __shared__ float s_red[NT / 32];
     if (*st.overflow) return;
     const int gt = blockIdx.x;
     const int v = find_view(vs, gt);
@@ -718,81 +833,100 @@ __global__ void __launch_bounds__(kTilePix) composite_fwd(const __grid_constant_
     const int lt = gt - V.tile_base;
     const int tyy = lt / V.tiles_x, txx = lt - tyy * V.tiles_x;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int x = txx * kTile + (tid & (kTile - 1)), y = tyy * kTile + tid / kTile;
-    const bool inside = x < V.w && y < V.h;
-    const float px = x + 0.5f, py = y + 0.5f;
-    const long long pid = V.pix_off + (long long)y * V.w + x;
-    const float E = (edge && inside) ? edge[pid] : 0.f;
-    const long long start = st.tile_start[gt], end = st.tile_start[gt + 1];
+    const int x = txx * kTile + (tid & (kTile - 1));
+    const int y0 = tyy * kTile + (tid / kTile) * PPT;
+    const float px = x + 0.5f;
+    const int len = st.tile_len[gt];
+    const int nc = (*st.n_dev + kBinChunk - 1) / kBinChunk;
     const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
 
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int last = 0;
-    bool done = !inside;
-    for (long long b = start; b < end; b += kTilePix) {
-        if (__syncthreads_count(done) == kTilePix) break;
-        long long k = b + tid;
-        if (k < end) {
-            int id = st.ids[k];
-            s_id[tid] = id;
-            s_xyo[tid] = xyo[id];
-            s_con[tid] = con[id];
-            s_col[tid] = col[id];
-        }
-        if (score) s_score[tid] = 0.f;
-        __syncthreads();
-        const int cnt = int(min((long long)kTilePix, end - b));
-        for (int j = 0; j < cnt; ++j) {
-            float w = 0.f;
-            if (!done) {
-                Alpha a = eval_alpha(s_xyo[j], s_con[j], px, py);
-                if (a.pass) {
-                    float Tn = __fmul_rn(T, __fsub_rn(1.f, a.alpha));
-                    if (Tn < kTMin) {
-                        done = true;
-                    } else {
-                        w = __fmul_rn(a.alpha, T);
-                        float4 c = s_col[j];
-                        C0 = __fmaf_rn(c.x, w, C0);
-                        C1 = __fmaf_rn(c.y, w, C1);
-                        C2 = __fmaf_rn(c.z, w, C2);
-                        T = Tn;
-                        last = int(b - start) + j + 1;
-                    }
-                }
-            }
-            if (score) {
-                float sv = w * E;
-                if (__any_sync(0xffffffffu, sv != 0.f)) {
+    float T[PPT], C0[PPT], C1[PPT], C2[PPT], E[PPT];
+    int last[PPT];
+    bool done[PPT];
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-                    if (lane == 0) atomicAdd(&s_score[j], sv);
+    for (int m = 0; m < PPT; ++m) {
+        const int y = y0 + m;
+        const bool inside = x < V.w && y < V.h;
+        T[m] = 1.f; C0[m] = C1[m] = C2[m] = 0.f; last[m] = 0;
+        done[m] = !inside;
+        E[m] = (edge && inside) ? edge[V.pix_off + (long long)y * V.w + x] : 0.f;
+    }
+    for (int b = 0; b < len; b += kBatch) {
+        bool all = true;
+#pragma unroll
+        for (int m = 0; m < PPT; ++m) all = all && done[m];
+        if (__syncthreads_count(all) == NT) break;
+        for (int q = tid; q < kBatch; q += NT) {
+            const int k = b + q;
+            if (k < len) {
+                const int id = list_id(st, gt, nc, k);
+                s_id[q] = id;
+                s_xyo[q] = xyo[id];
+                s_con[q] = con[id];
+                s_col[q] = col[id];
+            }
+            if (score) s_score[q] = 0.f;
+        }
+        __syncthreads();
+        const int cnt = min(kBatch, len - b);
+        for (int j = 0; j < cnt; ++j) {
+            const float4 gx = s_xyo[j], gc = s_con[j];
+            float sv = 0.f;
+#pragma unroll
+            for (int m = 0; m < PPT; ++m) {
+                if (done[m]) continue;
+                const Alpha a = eval_alpha(gx, gc, px, y0 + m + 0.5f);
+                if (!a.pass) continue;
+                const float Tn = __fmul_rn(T[m], __fsub_rn(1.f, a.alpha));
+                if (Tn < kTMin) {
+                    done[m] = true;
+                    continue;
                 }
+                const float w = __fmul_rn(a.alpha, T[m]);
+                const float4 c = s_col[j];
+                C0[m] = __fmaf_rn(c.x, w, C0[m]);
+                C1[m] = __fmaf_rn(c.y, w, C1[m]);
+                C2[m] = __fmaf_rn(c.z, w, C2[m]);
+                T[m] = Tn;
+                last[m] = b + j + 1;
+                sv = __fmaf_rn(w, E[m], sv);
+            }
+            if (score && __any_sync(0xffffffffu, sv != 0.f)) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+                if (lane == 0) atomicAdd(&s_score[j], sv);
             }
         }
         __syncthreads();
-        if (score && tid < cnt && s_score[tid] != 0.f) atomicAdd(&score[s_id[tid]], s_score[tid]);
+        if (score)
+            for (int q = tid; q < cnt; q += NT)
+                if (s_score[q] != 0.f) atomicAdd(&score[s_id[q]], s_score[q]);
     }
-    if (inside) {
-        rgb_out[3 * pid + 0] = C0;
-        rgb_out[3 * pid + 1] = C1;
-        rgb_out[3 * pid + 2] = C2;
-        T_out[pid] = T;
-        last_out[pid] = last;
+    float l = 0.f;
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+        const int y = y0 + m;
+        if (x < V.w && y < V.h) {
+            const long long pid = V.pix_off + (long long)y * V.w + x;
+            rgb_out[3 * pid + 0] = C0[m];
+            rgb_out[3 * pid + 1] = C1[m];
+            rgb_out[3 * pid + 2] = C2[m];
+            T_out[pid] = T[m];
+            last_out[pid] = last[m];
+            if (V.tgt)
+                l += fabsf(C0[m] - target_value(V, x, y, 0)) + fabsf(C1[m] - target_value(V, x, y, 1)) +
+                     fabsf(C2[m] - target_value(V, x, y, 2));
+        }
     }
     if (V.tgt) {
-        float l = 0.f;
-        if (inside)
-            l = fabsf(C0 - target_value(V, x, y, 0)) + fabsf(C1 - target_value(V, x, y, 1)) +
-                fabsf(C2 - target_value(V, x, y, 2));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
         if (lane == 0) s_red[wid] = l;
         __syncthreads();
         if (tid == 0) {
-            double s = 0.0;
-            for (int w = 0; w < kTilePix / 32; ++w) s += s_red[w];
-            atomicAdd(st.loss_acc, s);
+            double sum = 0.0;
+            for (int w = 0; w < NT / 32; ++w) sum += s_red[w];
+            atomicAdd(st.loss_acc, sum);
         }
     }
 }
@@ -803,34 +937,77 @@ __global__ void loss_finalise(State st, long long total_pix, float *loss_out)
     *loss_out = float(*st.loss_acc / (3.0 * double(total_pix)));
 }
 
-// Sum of 16 per-lane values over the warp: lane L ends up holding the total of
-// value (L >> 1).  16 shuffles instead of 16 x 5.
-__device__ __forceinline__ float warp_transpose_reduce16(float v[16])
+// Sum of 10 per-lane values over the warp in 12 shuffles (instead of 10 x 5):
+// at each butterfly level a lane keeps part of its values and sends the
+// rest.  Returns the total this lane owns; *idx is its value index, or -1 on
+// the lanes that hold a duplicate.  Owners: lanes {0, 2, 4, 8, 12} + 16 h hold
+// values {0, 1, 2, 3, 4} + 5 h.
+__device__ __forceinline__ float warp_transpose_reduce10(float v[10], int *idx)
 {
     const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    // level 16: keep 5
 #pragma unroll
-    for (int half = 8, mask = 16; half >= 1; half >>= 1, mask >>= 1) {
-        const bool upper = lane & mask;
-#pragma unroll
-        for (int k = 0; k < half; ++k) {
-            float send = upper ? v[k] : v[k + half];
-            float keep = upper ? v[k + half] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
-        }
+    for (int k = 0; k < 5; ++k) {
+        const float send = b4 ? v[k] : v[k + 5];
+        const float keep = b4 ? v[k + 5] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    // level 8: b3 = 0 keeps 3 (0, 1, 2), b3 = 1 keeps 2 (3, 4)
+    float r0 = __shfl_xor_sync(0xffffffffu, b3 ? v[0] : v[3], 8);
+    float r1 = __shfl_xor_sync(0xffffffffu, b3 ? v[1] : v[4], 8);
+    float r2 = __shfl_xor_sync(0xffffffffu, b3 ? v[2] : 0.f, 8);
+    float a0, a1, a2;
+    if (!b3) {
+        a0 = v[0] + r0; a1 = v[1] + r1; a2 = v[2] + r2;
+    } else {
+        a0 = v[3] + r0; a1 = v[4] + r1; a2 = 0.f;
+    }
+    // level 4: (b3 = 0) b2 = 0 keeps 2 (a0, a1), b2 = 1 keeps a2; (b3 = 1) each keeps one
+    float s0 = !b3 ? (b2 ? a0 : a2) : (b2 ? a0 : a1);
+    float s1 = (!b3 && b2) ? a1 : 0.f;
+    s0 = __shfl_xor_sync(0xffffffffu, s0, 4);
+    s1 = __shfl_xor_sync(0xffffffffu, s1, 4);
+    float c0, c1;
+    if (!b3) {
+        if (!b2) { c0 = a0 + s0; c1 = a1 + s1; } else { c0 = a2 + s0; c1 = 0.f; }
+    } else {
+        c0 = (b2 ? a1 : a0) + s0;
+        c1 = 0.f;
+    }
+    // level 2: lanes with two values split them, the others add
+    const bool two = !b3 && !b2;
+    float t0 = __shfl_xor_sync(0xffffffffu, two ? (b1 ? c0 : c1) : c0, 2);
+    float d = (two && b1) ? c1 + t0 : c0 + t0;
+    // level 1
+    d += __shfl_xor_sync(0xffffffffu, d, 1);
+    const int base = b4 ? 5 : 0;
+    int k = -1;
+    if ((lane & 1) == 0) {
+        if (two) k = base + (b1 ? 1 : 0);
+        else if (!b1) k = base + (!b3 ? 2 : (b2 ? 4 : 3));
+    }
+    *idx = k;
+    return d;
 }
 
 constexpr int kG2 = 10;  // mean x, mean y, conic A, B, C, opacity, r, g, b, score
 
-__global__ void __launch_bounds__(kTilePix) composite_bwd(const __grid_constant__ Views vs, State st, long long cap,
-                                                          const float *dL_drgb, const float *rgb, const float *T_fin,
-                                                          const int32_t *last_idx, const float *edge, float *score,
-                                                          float inv_norm)
+// Adjoint of the compositing, replayed back to front from T_final and the
+// last position, each thread a vertical run of PPT pixels.  For each
+// Gaussian the thread sums its pixels' contributions, the warp reduces them
+// (transpose reduction), warps meet in shared accumulators, and one global
+// atomic per (Gaussian, tile, value) leaves the block.
+template <int PPT>
+__global__ void __launch_bounds__(kTilePix / PPT) composite_bwd(const __grid_constant__ Views vs, State st,
+                                                                long long cap, const float *dL_drgb, const float *rgb,
+                                                                const float *T_fin, const int32_t *last_idx,
+                                                                const float *edge, float *score, float inv_norm)
 {
-    __shared__ float4 s_xyo[kTilePix], s_con[kTilePix], s_col[kTilePix];
-    __shared__ int32_t s_id[kTilePix];
-    __shared__ float s_acc[kTilePix][kG2];
+    constexpr int NT = kTilePix / PPT;
+    __shared__ float4 s_xyo[kBatch], s_con[kBatch], s_col[kBatch];
+    __shared__ int32_t s_id[kBatch];
+    __shared__ float s_acc[kBatch][kG2];
     __shared__ int s_maxlast;
     if (*st.overflow) return;
     const int gt = blockIdx.x;
@@ -838,104 +1015,113 @@ __global__ void __launch_bounds__(kTilePix) composite_bwd(const __grid_constant_
     const ViewP &V = vs.v[v];
     const int lt = gt - V.tile_base;
     const int tyy = lt / V.tiles_x, txx = lt - tyy * V.tiles_x;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int x = txx * kTile + (tid & (kTile - 1)), y = tyy * kTile + tid / kTile;
-    const bool inside = x < V.w && y < V.h;
-    const float px = x + 0.5f, py = y + 0.5f;
-    const long long pid = V.pix_off + (long long)y * V.w + x;
-    const long long start = st.tile_start[gt];
-    const int list_len = int(st.tile_start[gt + 1] - start);
+    const int tid = threadIdx.x;
+    const int x = txx * kTile + (tid & (kTile - 1));
+    const int y0 = tyy * kTile + (tid / kTile) * PPT;
+    const float px = x + 0.5f;
+    const int list_len = st.tile_len[gt];
+    const int nc = (*st.n_dev + kBinChunk - 1) / kBinChunk;
     const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
     float4 *g2d = st.g2d + (size_t)v * cap * 3;
+    const bool want_score = score && edge;
 
-    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, E = 0.f;
-    int last = 0;
-    if (inside) {
-        T = T_fin[pid];
-        last = min(max(last_idx[pid], 0), list_len);
-        E = edge ? edge[pid] : 0.f;
-        if (dL_drgb) {
-            g0 = dL_drgb[3 * pid];
-            g1 = dL_drgb[3 * pid + 1];
-            g2 = dL_drgb[3 * pid + 2];
-        } else {
-            float d0 = rgb[3 * pid] - target_value(V, x, y, 0);
-            float d1 = rgb[3 * pid + 1] - target_value(V, x, y, 1);
-            float d2 = rgb[3 * pid + 2] - target_value(V, x, y, 2);
-            g0 = ((d0 > 0.f) - (d0 < 0.f)) * inv_norm;
-            g1 = ((d1 > 0.f) - (d1 < 0.f)) * inv_norm;
-            g2 = ((d2 > 0.f) - (d2 < 0.f)) * inv_norm;
+    float T[PPT], g0[PPT], g1[PPT], g2[PPT], E[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
+    int last[PPT];
+    int mylast = 0;
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+        const int y = y0 + m;
+        T[m] = 1.f; g0[m] = g1[m] = g2[m] = 0.f; E[m] = 0.f; last[m] = 0;
+        acc0[m] = acc1[m] = acc2[m] = 0.f;
+        if (x < V.w && y < V.h) {
+            const long long pid = V.pix_off + (long long)y * V.w + x;
+            T[m] = T_fin[pid];
+            last[m] = min(max(last_idx[pid], 0), list_len);
+            E[m] = edge ? edge[pid] : 0.f;
+            if (dL_drgb) {
+                g0[m] = dL_drgb[3 * pid];
+                g1[m] = dL_drgb[3 * pid + 1];
+                g2[m] = dL_drgb[3 * pid + 2];
+            } else {
+                const float d0 = rgb[3 * pid] - target_value(V, x, y, 0);
+                const float d1 = rgb[3 * pid + 1] - target_value(V, x, y, 1);
+                const float d2 = rgb[3 * pid + 2] - target_value(V, x, y, 2);
+                g0[m] = ((d0 > 0.f) - (d0 < 0.f)) * inv_norm;
+                g1[m] = ((d1 > 0.f) - (d1 < 0.f)) * inv_norm;
+                g2[m] = ((d2 > 0.f) - (d2 < 0.f)) * inv_norm;
+            }
+            mylast = max(mylast, last[m]);
         }
     }
-    const bool want_score = score && edge;
     if (tid == 0) s_maxlast = 0;
-    for (int k = tid; k < kTilePix * kG2; k += kTilePix) (&s_acc[0][0])[k] = 0.f;
+    for (int k = tid; k < kBatch * kG2; k += NT) (&s_acc[0][0])[k] = 0.f;
     __syncthreads();
-    atomicMax(&s_maxlast, last);
+    atomicMax(&s_maxlast, mylast);
     __syncthreads();
     const int maxlast = s_maxlast;
-    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;  // colour behind, normalised
 
-    for (int hi = maxlast; hi > 0; hi -= kTilePix) {
-        const int lo = max(hi - kTilePix, 0);
+    for (int hi = maxlast; hi > 0; hi -= kBatch) {
+        const int lo = max(hi - kBatch, 0);
         const int cnt = hi - lo;
-        if (tid < cnt) {
-            int id = st.ids[start + lo + tid];
-            s_id[tid] = id;
-            s_xyo[tid] = xyo[id];
-            s_con[tid] = con[id];
-            s_col[tid] = col[id];
+        for (int q = tid; q < cnt; q += NT) {
+            const int id = list_id(st, gt, nc, lo + q);
+            s_id[q] = id;
+            s_xyo[q] = xyo[id];
+            s_con[q] = con[id];
+            s_col[q] = col[id];
         }
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
             const int pos = lo + j;
-            float val[16];
+            const float4 gx = s_xyo[j], gc = s_con[j];
+            float val[kG2];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) val[k] = 0.f;
+            for (int k = 0; k < kG2; ++k) val[k] = 0.f;
             bool active = false;
-            if (pos < last) {
-                Alpha a = eval_alpha(s_xyo[j], s_con[j], px, py);
-                if (a.pass) {
-                    active = true;
-                    const float4 c = s_col[j];
-                    const float one_m = __fsub_rn(1.f, a.alpha);
-                    T = __fdiv_rn(T, one_m);
-                    const float w = a.alpha * T;
-                    val[6] = w * g0;
-                    val[7] = w * g1;
-                    val[8] = w * g2;
-                    const float dalpha = T * (g0 * (c.x - acc0) + g1 * (c.y - acc1) + g2 * (c.z - acc2));
-                    acc0 = acc0 * one_m + c.x * a.alpha;
-                    acc1 = acc1 * one_m + c.y * a.alpha;
-                    acc2 = acc2 * one_m + c.z * a.alpha;
-                    if (a.raw < kAlphaMax) {
-                        const float4 q = s_con[j];  // (-A/2, -B, -C/2)
-                        const float dpow = dalpha * s_xyo[j].z * a.G;
-                        val[5] = dalpha * a.G;
-                        // d power / d mean = (A dx + B dy, B dx + C dy)
-                        val[0] = dpow * (-2.f * q.x * a.dx - q.y * a.dy);
-                        val[1] = dpow * (-q.y * a.dx - 2.f * q.z * a.dy);
-                        val[2] = -0.5f * dpow * a.dx * a.dx;
-                        val[3] = -dpow * a.dx * a.dy;
-                        val[4] = -0.5f * dpow * a.dy * a.dy;
-                    }
-                    if (want_score) val[9] = w * E;
+#pragma unroll
+            for (int m = 0; m < PPT; ++m) {
+                if (pos >= last[m]) continue;
+                const Alpha a = eval_alpha(gx, gc, px, y0 + m + 0.5f);
+                if (!a.pass) continue;
+                active = true;
+                const float4 c = s_col[j];
+                const float one_m = __fsub_rn(1.f, a.alpha);
+                T[m] = __fdiv_rn(T[m], one_m);
+                const float w = a.alpha * T[m];
+                val[6] += w * g0[m];
+                val[7] += w * g1[m];
+                val[8] += w * g2[m];
+                const float dalpha =
+                    T[m] * (g0[m] * (c.x - acc0[m]) + g1[m] * (c.y - acc1[m]) + g2[m] * (c.z - acc2[m]));
+                acc0[m] = acc0[m] * one_m + c.x * a.alpha;
+                acc1[m] = acc1[m] * one_m + c.y * a.alpha;
+                acc2[m] = acc2[m] * one_m + c.z * a.alpha;
+                if (a.raw < kAlphaMax) {
+                    // gc = (-A/2, -B, -C/2); d power / d mean = (A dx + B dy, B dx + C dy)
+                    const float dpow = dalpha * gx.z * a.G;
+                    val[5] += dalpha * a.G;
+                    val[0] += dpow * (-2.f * gc.x * a.dx - gc.y * a.dy);
+                    val[1] += dpow * (-gc.y * a.dx - 2.f * gc.z * a.dy);
+                    val[2] += -0.5f * dpow * a.dx * a.dx;
+                    val[3] += -dpow * a.dx * a.dy;
+                    val[4] += -0.5f * dpow * a.dy * a.dy;
                 }
+                if (want_score) val[9] += w * E[m];
             }
             if (__any_sync(0xffffffffu, active)) {
-                float r = warp_transpose_reduce16(val);
-                if ((lane & 1) == 0 && (lane >> 1) < kG2 && r != 0.f) atomicAdd(&s_acc[j][lane >> 1], r);
+                int k;
+                const float r = warp_transpose_reduce10(val, &k);
+                if (k >= 0 && r != 0.f) atomicAdd(&s_acc[j][k], r);
             }
         }
         __syncthreads();
-        if (tid < cnt) {
-            float *a = s_acc[tid];
-            const long long o = (long long)s_id[tid] * 3;
-            float *gp = reinterpret_cast<float *>(g2d + o);
+        for (int q = tid; q < cnt; q += NT) {
+            float *a = s_acc[q];
+            float *gp = reinterpret_cast<float *>(g2d + (long long)s_id[q] * 3);
 #pragma unroll
             for (int k = 0; k < 9; ++k)
                 if (a[k] != 0.f) atomicAdd(gp + k, a[k]);
-            if (want_score && a[9] != 0.f) atomicAdd(&score[s_id[tid]], a[9]);
+            if (want_score && a[9] != 0.f) atomicAdd(&score[s_id[q]], a[9]);
 #pragma unroll
             for (int k = 0; k < kG2; ++k) a[k] = 0.f;
         }
@@ -945,6 +1131,7 @@ __global__ void __launch_bounds__(kTilePix) composite_bwd(const __grid_constant_
 
 // Chain the screen-space gradients to the parameters, one thread per Gaussian,
 // summing over views.
+template <int K>
 __global__ void __launch_bounds__(128) project_bwd(const __grid_constant__ Views vs, Params p, State st,
                                                   float *gm, float *gls, float *gq, float *go, float *gsh,
                                                   int accumulate)
@@ -953,16 +1140,16 @@ __global__ void __launch_bounds__(128) project_bwd(const __grid_constant__ Views
     if (i >= *p.count) return;
     if (*st.overflow) return;
     const long long cap = p.cap;
-    const int K = p.K;
     float mu[3] = {p.means[3 * i], p.means[3 * i + 1], p.means[3 * i + 2]};
     float ls[3] = {p.log_scales[3 * i], p.log_scales[3 * i + 1], p.log_scales[3 * i + 2]};
     float q4[4] = {p.quats[4 * i], p.quats[4 * i + 1], p.quats[4 * i + 2], p.quats[4 * i + 3]};
     const float opac = sigmoidf_(p.opac[i]);
-    const float *shp = p.sh + (size_t)i * K * 3;
+    float shv[3 * K];
+    load_sh<K>(p.sh + (size_t)i * K * 3, shv);
     float G_mu[3] = {0.f, 0.f, 0.f}, G_ls[3] = {0.f, 0.f, 0.f}, G_q[4] = {0.f, 0.f, 0.f, 0.f}, G_o = 0.f;
-    float G_sh[48];
+    float G_sh[3 * K];
 #pragma unroll
-    for (int k = 0; k < 48; ++k) G_sh[k] = 0.f;
+    for (int k = 0; k < 3 * K; ++k) G_sh[k] = 0.f;
     const float qn2 = q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3];
     const float qinv = __frsqrt_rn(qn2);
     const float qh[4] = {q4[0] * qinv, q4[1] * qinv, q4[2] * qinv, q4[3] * qinv};
@@ -1074,11 +1261,11 @@ __global__ void __launch_bounds__(128) project_bwd(const __grid_constant__ Views
         for (int k = 0; k < 16; ++k) wsh[k] = 0.f;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            if (clampbits & (1u << ch)) continue;
-            const float g = gcol[ch];
+            const float g = (clampbits & (1u << ch)) ? 0.f : gcol[ch];
+#pragma unroll
             for (int k = 0; k < K; ++k) {
                 G_sh[3 * k + ch] += g * Y[k];
-                wsh[k] += g * shp[3 * k + ch];
+                wsh[k] += g * shv[3 * k + ch];
             }
         }
         float gu[3];
@@ -1088,16 +1275,26 @@ __global__ void __launch_bounds__(128) project_bwd(const __grid_constant__ Views
         G_mu[1] += (gu[1] - uy * ud) * rn;
         G_mu[2] += (gu[2] - uz * ud) * rn;
     }
+    float *gshr = gsh + (size_t)i * 3 * K;
     if (accumulate) {
         for (int j = 0; j < 3; ++j) gm[3 * i + j] += G_mu[j], gls[3 * i + j] += G_ls[j];
         for (int j = 0; j < 4; ++j) gq[4 * i + j] += G_q[j];
         go[i] += G_o;
-        for (int k = 0; k < 3 * K; ++k) gsh[(size_t)i * 3 * K + k] += G_sh[k];
+#pragma unroll
+        for (int k = 0; k < 3 * K; ++k) gshr[k] += G_sh[k];
     } else {
         for (int j = 0; j < 3; ++j) gm[3 * i + j] = G_mu[j], gls[3 * i + j] = G_ls[j];
         for (int j = 0; j < 4; ++j) gq[4 * i + j] = G_q[j];
         go[i] = G_o;
-        for (int k = 0; k < 3 * K; ++k) gsh[(size_t)i * 3 * K + k] = G_sh[k];
+        if constexpr ((3 * K) % 4 == 0) {
+            float4 *o4 = reinterpret_cast<float4 *>(gshr);
+#pragma unroll
+            for (int q = 0; q < 3 * K / 4; ++q)
+                o4[q] = make_float4(G_sh[4 * q], G_sh[4 * q + 1], G_sh[4 * q + 2], G_sh[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3 * K; ++k) gshr[k] = G_sh[k];
+        }
     }
 }
 
@@ -1118,6 +1315,7 @@ Layout render_layout(void *ws, long long cap, int nv, int total_tiles, long long
     s.con = c.take<float4>(vc);
     s.col = c.take<float4>(vc);
     s.rect = c.take<uint2>(vc);
+    s.rowint = c.take<uchar2>(vc * kRowCap);
     s.key = c.take<uint32_t>(vc);
     s.key_alt = c.take<uint32_t>((size_t)cap);
     s.val = c.take<int32_t>(vc);
@@ -1126,9 +1324,11 @@ Layout render_layout(void *ws, long long cap, int nv, int total_tiles, long long
     s.sort_hist = c.take<unsigned>((size_t)256 * s.nb_max);
     s.sort_tot = c.take<unsigned>(256);
     s.nchunk_max = int(div_up(cap, kBinChunk));
-    s.chunk_cnt = c.take<int32_t>((size_t)total_tiles * s.nchunk_max);
+    s.chunk_pos = c.take<int32_t>((size_t)total_tiles * s.nchunk_max);
+    s.seg_start = c.take<uint32_t>((size_t)total_tiles * s.nchunk_max);
     s.bin_wcnt = c.take<unsigned char>((size_t)total_tiles * s.nchunk_max * kBinWarps);
-    s.tile_start = c.take<long long>((size_t)total_tiles + 1);
+    s.chunk_tot = c.take<long long>((size_t)nv * s.nchunk_max);
+    s.tile_len = c.take<int32_t>((size_t)total_tiles);
     s.ids = c.take<int32_t>((size_t)pair_cap);
     s.pair_count = c.take<long long>(1);
     s.g2d = c.take<float4>(vc * 3);
@@ -1239,9 +1439,10 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
         return GSP_ERR_INVALID_ARG;
     if (score && !edge) return GSP_ERR_INVALID_ARG;
     if (loss_out && !targets) return GSP_ERR_INVALID_ARG;
+    if (opts->pair_capacity > 0xffffffffLL) return GSP_ERR_UNSUPPORTED;  // 32-bit segment starts
     for (int v = 0; v < nv; ++v) {
         const size_t T = size_t(vs.v[v].tiles_x) * vs.v[v].tiles_y;
-        if (T * (sizeof(int) + kBinWarps * sizeof(unsigned short)) > 200 * 1024) return GSP_ERR_UNSUPPORTED;
+        if (T * (sizeof(uint32_t) + kBinWarps * sizeof(unsigned short)) > 200 * 1024) return GSP_ERR_UNSUPPORTED;
     }
     const long long cap = g->capacity;
     Layout L = render_layout(nullptr, cap, nv, vs.total_tiles, opts->pair_capacity);
@@ -1249,12 +1450,18 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     if (st != GSP_OK) return st;
     L = render_layout(ws, cap, nv, vs.total_tiles, opts->pair_capacity);
     State S = L.st;
+    S.n_dev = g->count;
     Params P = make_params(g);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
     GSP_CUDA_TRY(cudaMemsetAsync(S.loss_acc, 0, sizeof(double), s));
     stage_begin("project", s);
-    project_kernel<<<div_up(cap, 256), 256, 0, s>>>(vs, P, S);
+    switch (P.K) {
+    case 1: project_kernel<1><<<div_up(cap, 256), 256, 0, s>>>(vs, P, S); break;
+    case 4: project_kernel<4><<<div_up(cap, 256), 256, 0, s>>>(vs, P, S); break;
+    case 9: project_kernel<9><<<div_up(cap, 256), 256, 0, s>>>(vs, P, S); break;
+    default: project_kernel<16><<<div_up(cap, 256), 256, 0, s>>>(vs, P, S); break;
+    }
     stage_end("project", s);
     GSP_LAUNCH_CHECK();
     stage_begin("depth_sort", s);
@@ -1282,18 +1489,19 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
         GSP_CUDA_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         bin_count<<<S.nchunk_max, kBinThreads, smem, s>>>(vs, v, S, cap, g->count);
     }
+    bin_regions<<<1, 1024, 0, s>>>(nv, S, g->count, dev_status);
     bin_scan<<<div_up((long long)vs.total_tiles * 32, 256), 256, 0, s>>>(vs, S, g->count);
-    bin_starts<<<1, 1024, 0, s>>>(vs.total_tiles, S, dev_status);
     for (int v = 0; v < nv; ++v) {
         const int T = vs.v[v].tiles_x * vs.v[v].tiles_y;
-        const size_t smem = size_t(T) * (sizeof(int) + kBinWarps * sizeof(unsigned short));
+        const size_t smem = size_t(T) * (sizeof(uint32_t) + kBinWarps * sizeof(unsigned short));
         GSP_CUDA_TRY(cudaFuncSetAttribute(bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        bin_scatter<<<S.nchunk_max, kBinThreads, smem, s>>>(vs, v, S, cap, g->count, 0, vs.v[v].tiles_y - 1);
+        bin_scatter<<<S.nchunk_max, kBinThreads, smem, s>>>(vs, v, S, cap, g->count);
     }
     stage_end("bin", s);
     GSP_LAUNCH_CHECK();
     stage_begin("composite_fwd", s);
-    composite_fwd<<<vs.total_tiles, kTilePix, 0, s>>>(vs, S, cap, edge, rgb_out, T_final, last_idx, score);
+    composite_fwd<kFwdPixPerThread><<<vs.total_tiles, kTilePix / kFwdPixPerThread, 0, s>>>(
+        vs, S, cap, edge, rgb_out, T_final, last_idx, score);
     stage_end("composite_fwd", s);
     GSP_LAUNCH_CHECK();
     note_launches(2 + 12 * nv + 2 * nv + 2 + 1);
@@ -1329,17 +1537,26 @@ extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *c
     if (st != GSP_OK) return st;
     L = render_layout(ws, cap, nv, vs.total_tiles, opts->pair_capacity);
     State S = L.st;
+    S.n_dev = g->count;
     Params P = make_params(g);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const float inv_norm = float(1.0 / (3.0 * double(vs.total_pix)));
     stage_begin("composite_bwd", s);
-    composite_bwd<<<vs.total_tiles, kTilePix, 0, s>>>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score,
-                                                      inv_norm);
+    composite_bwd<kBwdPixPerThread><<<vs.total_tiles, kTilePix / kBwdPixPerThread, 0, s>>>(
+        vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm);
     stage_end("composite_bwd", s);
     GSP_LAUNCH_CHECK();
     stage_begin("project_bwd", s);
-    project_bwd<<<div_up(cap, 128), 128, 0, s>>>(vs, P, S, grad_means, grad_log_scales, grad_quats,
-                                                 grad_opacity_logits, grad_sh, accumulate);
+#define GSP_PBWD(KK)                                                                                   \
+    project_bwd<KK><<<div_up(cap, 128), 128, 0, s>>>(vs, P, S, grad_means, grad_log_scales, grad_quats, \
+                                                     grad_opacity_logits, grad_sh, accumulate)
+    switch (P.K) {
+    case 1: GSP_PBWD(1); break;
+    case 4: GSP_PBWD(4); break;
+    case 9: GSP_PBWD(9); break;
+    default: GSP_PBWD(16); break;
+    }
+#undef GSP_PBWD
     stage_end("project_bwd", s);
     note_launches(2);
     GSP_LAUNCH_CHECK();
