@@ -359,14 +359,72 @@ static int composite_pixel(const int64_t *cand, int64_t nc, const double *proj, 
     return n;
 }
 
+/* The valid Gaussians in compositing order (returns their number). */
+int64_t orc_order(int64_t n, const double *proj, int64_t *order) { return sorted_order(n, proj, order); }
+
+/* Mark (mark[id] = 1) the Gaussians whose result at one of the npx listed
+ * pixels (xy = x0, y0, x1, y1, ...) moves when one gate decision at that pixel
+ * goes the other way: every Gaussian composited there, every candidate whose
+ * alpha lies within `window` relative of 1/255 (or whose unclamped alpha lies
+ * that close to the 0.99 clamp), the one at which compositing stops and the
+ * next candidate past it that passes the alpha gate.  order holds
+ * the m valid Gaussians in compositing order; candidates are the tile-list
+ * members of the pixel's tile, as in orc_render.  Used to exempt Gaussians
+ * from parity checks next to gates decided in different precisions. */
+int orc_gate_affected(int64_t m, const int64_t *order, const double *proj, int64_t npx, const int32_t *xy,
+                      double window, uint8_t *mark)
+{
+    /* tile rectangles in compositing order, contiguous */
+    int32_t *rect = malloc(sizeof(int32_t) * 4 * (size_t)(m > 0 ? m : 1));
+    for (int64_t j = 0; j < m; j++) {
+        const double *r = proj + order[j] * ORC_PROJ_STRIDE;
+        int32_t *q = rect + 4 * j;
+        if (r[P_RADIUS] < 0) { q[0] = 1; q[2] = 0; q[1] = 1; q[3] = 0; continue; }
+        q[0] = (int32_t)r[P_TX0]; q[1] = (int32_t)r[P_TY0]; q[2] = (int32_t)r[P_TX1]; q[3] = (int32_t)r[P_TY1];
+    }
+    for (int64_t p = 0; p < npx; p++) {
+        int x = xy[2 * p], y = xy[2 * p + 1];
+        int tx = x / ORC_TILE, ty = y / ORC_TILE;
+        double px = x + 0.5, py = y + 0.5, T = 1.0;
+        int stopped = 0;
+        for (int64_t j = 0; j < m; j++) {
+            const int32_t *q = rect + 4 * j;
+            if (tx < q[0] || tx > q[2] || ty < q[1] || ty > q[3]) continue;
+            const double *r = proj + order[j] * ORC_PROJ_STRIDE;
+            double dx = px - r[P_MX], dy = py - r[P_MY];
+            double power = -0.5 * (r[P_CON_A] * dx * dx + 2.0 * r[P_CON_B] * dx * dy + r[P_CON_C] * dy * dy);
+            double raw = r[P_OPAC] * exp(power);
+            double alpha = raw < 0.99 ? raw : 0.99;
+            if (rel_gap(alpha, 1.0 / 255.0) < window) mark[order[j]] = 1;
+            if (alpha < 1.0 / 255.0) continue;
+            /* the alpha clamp at 0.99 switches the geometry gradient on and off */
+            if (rel_gap(raw, 0.99) < window) mark[order[j]] = 1;
+            mark[order[j]] = 1;
+            if (stopped) break;
+            double Tn = T * (1.0 - alpha);
+            if (Tn < 1e-4) stopped = 1;
+            T = Tn;
+        }
+    }
+    free(rect);
+    return 0;
+}
+
 /* Render the pixel region [x0,x1) x [y0,y1).  brute = 1 composites every
  * valid Gaussian at every pixel (no tiles, no footprint test). */
 int orc_render(int64_t n, const double *proj, int width, int height, const double *edge, int brute,
                int x0, int y0, int x1, int y1, double *rgb, double *T_out, int32_t *ncontrib,
-               int64_t *last_id, double *score, double *gate_gap)
+               int64_t *last_id, double *score, double *gate_gap, const int64_t *given_order, int64_t given_m)
 {
+    /* given_order (nullable): the valid Gaussians already in compositing order */
     int64_t *order = malloc(sizeof(int64_t) * (n > 0 ? n : 1));
-    int64_t m = sorted_order(n, proj, order);
+    int64_t m;
+    if (given_order) {
+        m = given_m;
+        memcpy(order, given_order, sizeof(int64_t) * (size_t)m);
+    } else {
+        m = sorted_order(n, proj, order);
+    }
     otiles tl = {0};
     int reg[4] = {x0, y0, x1, y1};
     if (!brute) build_tiles(m, order, proj, width, height, reg, &tl);
@@ -411,19 +469,22 @@ int orc_render_bwd(int64_t n, const double *means, const double *log_scales, con
                    const double *opac_logits, const double *sh, int sh_degree, const float *viewmat,
                    const double *intr, int width, int height, const double *proj, const double *dLdC,
                    double *g_means, double *g_log_scales, double *g_quats, double *g_opac, double *g_sh,
-                   double *g2d_out)
+                   double *g2d_out, const int *region)
 {
+    /* region (nullable): only pixels of [x0,x1) x [y0,y1) carry dL/dC (the others are taken as 0) */
+    int rx0 = 0, ry0 = 0, rx1 = width, ry1 = height;
+    if (region) { rx0 = region[0]; ry0 = region[1]; rx1 = region[2]; ry1 = region[3]; }
     int K = (sh_degree + 1) * (sh_degree + 1);
     (void)opac_logits; /* sigmoid(o) is read from the projected record */
     double *g2d = calloc((size_t)(n > 0 ? n : 1) * 9, sizeof(double));
     int64_t *order = malloc(sizeof(int64_t) * (n > 0 ? n : 1));
     int64_t m = sorted_order(n, proj, order);
     otiles tl = {0};
-    build_tiles(m, order, proj, width, height, NULL, &tl);
+    build_tiles(m, order, proj, width, height, region, &tl);
     ocontrib *cb = malloc(sizeof(ocontrib) * (m > 0 ? m : 1));
 
-    for (int y = 0; y < height; y++)
-        for (int x = 0; x < width; x++) {
+    for (int y = ry0; y < ry1; y++)
+        for (int x = rx0; x < rx1; x++) {
             int64_t t = (int64_t)(y / ORC_TILE) * tl.tx + x / ORC_TILE;
             double T;
             int nk = composite_pixel(tl.ids + tl.start[t], tl.start[t + 1] - tl.start[t], proj, x + 0.5,

@@ -32,9 +32,13 @@ def lib():
         i64, ci = ctypes.c_int64, ctypes.c_int
         _lib.orc_project.argtypes = [i64, _dp, _dp, _dp, _dp, _dp, ci, _fp, _dp, ci, ci, _dp]
         _lib.orc_render.argtypes = [i64, _dp, ci, ci, _dp, ci, ci, ci, ci, ci, _dp, _dp, _i32p,
-                                    _i64p, _dp, _dp]
+                                    _i64p, _dp, _dp, _i64p, i64]
+        _lib.orc_order.argtypes = [i64, _dp, _i64p]
+        _lib.orc_order.restype = i64
+        _lib.orc_gate_affected.argtypes = [i64, _i64p, _dp, i64, _i32p, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_uint8)]
         _lib.orc_render_bwd.argtypes = [i64, _dp, _dp, _dp, _dp, _dp, ci, _fp, _dp, ci, ci, _dp,
-                                        _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+                                        _dp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_int)]
         _lib.orc_sh_basis.argtypes = [i64, _dp, _dp]
         _lib.orc_quat_to_rot.argtypes = [i64, _dp, _dp]
     return _lib
@@ -80,8 +84,31 @@ def project(g: dict, cam: dict) -> np.ndarray:
     return out
 
 
-def render(g: dict, cam: dict, edge=None, brute: bool = False, region=None, proj=None) -> dict:
-    """Composite the view (or the pixel region (x0, y0, x1, y1) of it)."""
+def order(proj: np.ndarray) -> np.ndarray:
+    """The valid Gaussians in compositing order (ascending depth key, then index)."""
+    out = np.zeros(proj.shape[0], dtype=np.int64)
+    m = lib().orc_order(proj.shape[0], _p(np.ascontiguousarray(proj)), _p(out, _i64p))
+    return out[:m]
+
+
+def gate_affected(proj: np.ndarray, mask: np.ndarray, window: float, order_=None) -> np.ndarray:
+    """Boolean array over the Gaussians: True where the result at a pixel of
+    mask (H x W) moves when a gate decision at that pixel flips (see
+    orc_gate_affected)."""
+    o = order(proj) if order_ is None else np.ascontiguousarray(order_, dtype=np.int64)
+    ys, xs = np.nonzero(mask)
+    xy = np.ascontiguousarray(np.stack([xs, ys], axis=1), dtype=np.int32)
+    mark = np.zeros(proj.shape[0], dtype=np.uint8)
+    lib().orc_gate_affected(o.shape[0], _p(o, _i64p), _p(np.ascontiguousarray(proj)), xy.shape[0],
+                            _p(xy, _i32p), float(window), _p(mark, ctypes.POINTER(ctypes.c_uint8)))
+    return mark.astype(bool)
+
+
+def render(g: dict, cam: dict, edge=None, brute: bool = False, region=None, proj=None, order=None) -> dict:
+    """Composite the view (or the pixel region (x0, y0, x1, y1) of it).
+
+    order (optional): the compositing order of the valid Gaussians of proj
+    (as returned by order()), to skip the sort."""
     proj = project(g, cam) if proj is None else proj
     w, h = int(cam["width"]), int(cam["height"])
     n = proj.shape[0]
@@ -93,14 +120,18 @@ def render(g: dict, cam: dict, edge=None, brute: bool = False, region=None, proj
     gap = np.full((h, w), np.inf)
     score = np.zeros(n)
     e = None if edge is None else np.ascontiguousarray(edge, dtype=np.float64)
+    o = None if order is None else np.ascontiguousarray(order, dtype=np.int64)
     lib().orc_render(n, _p(np.ascontiguousarray(proj)), w, h, _p(e), int(brute), x0, y0, x1, y1,
-                     _p(rgb), _p(T), _p(nc, _i32p), _p(last, _i64p), _p(score), _p(gap))
+                     _p(rgb), _p(T), _p(nc, _i32p), _p(last, _i64p), _p(score), _p(gap),
+                     _p(o, _i64p), 0 if o is None else o.shape[0])
     return {"rgb": rgb, "T": T, "ncontrib": nc, "last_id": last, "score": score,
             "gate_gap": gap, "proj": proj}
 
 
-def render_bwd(g: dict, cam: dict, dLdC: np.ndarray, proj=None) -> dict:
-    """Analytic adjoint: parameter gradients of sum(dLdC * C)."""
+def render_bwd(g: dict, cam: dict, dLdC: np.ndarray, proj=None, region=None) -> dict:
+    """Analytic adjoint: parameter gradients of sum(dLdC * C).
+
+    region (x0, y0, x1, y1), optional: dLdC is taken as zero outside it."""
     m, s, q, o, sh = _params64(g)
     vm, intr, w, h = _cam(cam)
     proj = project(g, cam) if proj is None else proj
@@ -112,7 +143,8 @@ def render_bwd(g: dict, cam: dict, dLdC: np.ndarray, proj=None) -> dict:
     lib().orc_render_bwd(n, _p(m), _p(s), _p(q), _p(o), _p(sh), int(g["sh_degree"]), _p(vm, _fp),
                          _p(intr), w, h, _p(np.ascontiguousarray(proj)), _p(d), _p(out["means"]),
                          _p(out["log_scales"]), _p(out["quats"]), _p(out["opacity_logits"]),
-                         _p(out["sh"]), _p(out["g2d"]))
+                         _p(out["sh"]), _p(out["g2d"]),
+                         None if region is None else (ctypes.c_int * 4)(*[int(r) for r in region]))
     return out
 
 
@@ -139,18 +171,37 @@ def _union(a, b):
     return (min(a[0], b[0]), min(a[1], b[1]), max(a[2], b[2]), max(a[3], b[3]))
 
 
+def _reorder(order_all: np.ndarray, keys: np.ndarray, i: int, new_key: float, valid: bool):
+    """Compositing order with Gaussian i moved to its new depth key (or removed)."""
+    o = order_all[order_all != i]
+    if not valid:
+        return o
+    k = np.float32(new_key)
+    ko = keys[o]
+    # first position whose (key, index) is greater than (k, i)
+    pos = np.searchsorted(ko, k, side="left")
+    while pos < o.shape[0] and ko[pos] == k and o[pos] < i:
+        pos += 1
+    return np.insert(o, pos, i)
+
+
 def fd_grad(g: dict, cam: dict, target_u8: np.ndarray, items, rel_h: float = 1e-5, proj=None):
     """Central finite differences of the L1 loss for (index, name, component) items.
 
     The loss change caused by one Gaussian is confined to its footprint, so
     only the pixels of the union of the footprints at theta, theta +- h are
-    re-composited.  Returns (fd(h), fd(h/2)) arrays; entries where the two
-    disagree sit on a kink (L1 sign flip, alpha clamp or gate, depth swap).
+    re-composited, with the compositing order of the other Gaussians kept, and
+    the loss difference is summed per pixel (unchanged pixels cancel exactly).
+    Returns (fd(h), fd(h/2)) arrays; entries where the two disagree sit on a
+    kink (L1 sign flip, alpha clamp or gate, depth swap).
     """
     w, h = int(cam["width"]), int(cam["height"])
     base = {k: (np.array(v, dtype=np.float64, copy=True) if isinstance(v, np.ndarray) else v)
             for k, v in g.items()}
-    proj = project(base, cam) if proj is None else proj
+    # a private copy whose row i is swapped in place for each perturbed record
+    proj = project(base, cam) if proj is None else np.array(proj, copy=True)
+    order_all = order(proj)
+    keys = proj[:, P_ZKEY].astype(np.float32)
     t = target_u8.astype(np.float64) / 255.0
     npix3 = w * h * 3
     res = []
@@ -172,12 +223,18 @@ def fd_grad(g: dict, cam: dict, target_u8: np.ndarray, items, rel_h: float = 1e-
                 vals.append(0.0)
                 continue
             losses = []
+            saved, saved_key = proj[i].copy(), keys[i]
+            x0, y0, x1, y1 = region
             for rec in recs:
-                pj = proj.copy()
-                pj[i] = rec
-                out = render(base, cam, region=region, proj=pj)
-                x0, y0, x1, y1 = region
-                losses.append(np.abs(out["rgb"][y0:y1, x0:x1] - t[y0:y1, x0:x1]).sum())
-            vals.append((losses[0] - losses[1]) / (2.0 * hh) / npix3)
+                proj[i] = rec
+                keys[i] = np.float32(rec[P_ZKEY])
+                o = _reorder(order_all, keys, i, rec[P_ZKEY], rec[P_VALID] != 0)
+                out = render(base, cam, region=region, proj=proj, order=o)
+                losses.append(out["rgb"][y0:y1, x0:x1])
+            proj[i], keys[i] = saved, saved_key
+            # difference per pixel first: pixels the step leaves alone give exact zeros
+            tt = t[y0:y1, x0:x1]
+            dl = (np.abs(losses[0] - tt) - np.abs(losses[1] - tt)).sum()
+            vals.append(dl / (2.0 * hh) / npix3)
         res.append(np.array(vals))
     return res[0], res[1]

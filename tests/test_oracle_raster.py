@@ -213,3 +213,79 @@ def test_l1_loss_sign_of_zero_is_zero():
     loss, d = orc.l1_loss(rgb, tgt)
     assert abs(loss - 1.0 / 3.0) < 1e-15
     np.testing.assert_array_equal(d, [[[0.0, 1.0 / 3.0, 0.0]]])
+
+
+def _stack_scene(n=6):
+    logit = math.log(0.95 / 0.05)
+    return {"means": np.array([[0.0, 0.0, 0.1 * i] for i in range(n)], np.float32),
+            "log_scales": np.full((n, 3), math.log(2.0), np.float32),
+            "quats": np.array([[1.0, 0, 0, 0]] * n, np.float32),
+            "opacity_logits": np.full(n, logit, np.float32),
+            "sh": np.zeros((n, 1, 3), np.float32), "sh_degree": 0}
+
+
+def test_gate_affected_marks_contributors_stop_candidate_and_next():
+    # three composited, the fourth stops compositing, the fifth is the next
+    # candidate past the stop, the sixth is never reached
+    g, cam = _stack_scene(), synth.camera_front(16, 16)
+    proj = orc.project(g, cam)
+    mask = np.zeros((16, 16), bool)
+    mask[8, 8] = True
+    assert orc.render(g, cam)["ncontrib"][8, 8] == 3
+    np.testing.assert_array_equal(orc.gate_affected(proj, mask, 0.0), [1, 1, 1, 1, 1, 0])
+    assert not orc.gate_affected(proj, np.zeros((16, 16), bool), 0.0).any()
+
+
+def test_gate_affected_with_wide_window_marks_every_tile_candidate():
+    g = synth.gaussians(300, 0, seed=9)
+    g["opacity_logits"][:] = -3.0  # faint: compositing never stops at the pixel
+    cam = synth.camera_front(64, 48)
+    proj = orc.project(g, cam)
+    mask = np.zeros((48, 64), bool)
+    mask[20, 37] = True  # tile (2, 1)
+    assert orc.render(g, cam)["T"][20, 37] > 1e-2
+    ok = (proj[:, orc.P_VALID] > 0) & (proj[:, orc.P_RADIUS] >= 0)
+    member = ok & (proj[:, orc.P_TX0] <= 2) & (proj[:, orc.P_TX1] >= 2) & (proj[:, orc.P_TY0] <= 1) & \
+        (proj[:, orc.P_TY1] >= 1)
+    assert member.sum() > 10
+    np.testing.assert_array_equal(orc.gate_affected(proj, mask, 2.0), member)  # relative gaps are <= 1
+
+
+def test_order_is_depth_key_then_index():
+    g = synth.gaussians(500, 0, seed=4)
+    g["means"][::7, 2] = g["means"][0, 2]  # equal depth keys, broken by index
+    cam = synth.camera_front(64, 64)
+    proj = orc.project(g, cam)
+    valid = np.nonzero(proj[:, orc.P_VALID] > 0)[0]
+    keys = proj[valid, orc.P_ZKEY].astype(np.float32)
+    expect = valid[np.lexsort((valid, keys))]
+    np.testing.assert_array_equal(orc.order(proj), expect)
+    a = orc.render(g, cam, proj=proj)
+    b = orc.render(g, cam, proj=proj, order=expect)
+    for key in ("rgb", "T", "ncontrib", "last_id"):
+        np.testing.assert_array_equal(a[key], b[key])
+
+
+def test_reorder_equals_sorting_with_the_new_key():
+    rng = np.random.default_rng(3)
+    keys = rng.integers(0, 20, 200).astype(np.float32)
+    base = np.lexsort((np.arange(200), keys))
+    for i in rng.choice(200, 20, replace=False):
+        k2 = keys.copy()
+        k2[i] = np.float32(rng.integers(0, 20))
+        expect = np.lexsort((np.arange(200), k2))
+        np.testing.assert_array_equal(orc._reorder(base, k2, int(i), float(k2[i]), True), expect)
+        np.testing.assert_array_equal(orc._reorder(base, k2, int(i), 0.0, False), expect[expect != i])
+
+
+def test_region_adjoint_equals_masked_upstream_gradient():
+    g, cam, _ = _fd_scene()
+    rng = np.random.default_rng(2)
+    d = rng.normal(size=(40, 48, 3))
+    box = (11, 7, 30, 25)
+    m = np.zeros_like(d)
+    m[box[1]:box[3], box[0]:box[2]] = d[box[1]:box[3], box[0]:box[2]]
+    a = orc.render_bwd(g, cam, d, region=box)
+    b = orc.render_bwd(g, cam, m)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        np.testing.assert_allclose(a[k], b[k], rtol=1e-12, atol=1e-300)
