@@ -2,8 +2,9 @@
 
 Tolerances (stated with the workload): NMS masks bit-exact except at pixels
 whose compared magnitudes or direction-bin boundary differ by < 1e-6
-relative (oracle.edge.nms_exempt); E within 1e-5 relative where both keep;
-medians within 1e-5 relative.
+relative (oracle.edge.nms_exempt); medians within 1e-5 relative of the
+oracle's lower median over the same kept set (exempt pixels may change the
+set, and with it the median's rank); E within 1e-5 relative where both keep.
 """
 import numpy as np
 import pytest
@@ -39,13 +40,25 @@ def _compare(img, e_gpu, m_gpu, med_gpu, taps=None):
     assert bad.sum() == 0, f"{bad.sum()} non-exempt NMS differences"
     both = keep & ref["keep"]
     assert np.all(e_gpu[~keep] == 0.0)
-    if both.any():
-        rel = np.abs(e_gpu[both] - ref["E"][both]) / ref["E"][both]
-        assert rel.max() <= 1e-5, rel.max()
-    if ref["median"] > 0:
-        assert abs(med_gpu - ref["median"]) <= 1e-5 * ref["median"]
+    # The median is taken over the kept set (Sec. 2.1, closing paragraph), and
+    # exempt near-ties may change that set; so the GPU median is compared with
+    # the oracle's lower median over the GPU's kept set, and the oracle's own
+    # median must lie within as many ranks as there are differing pixels.
+    n_diff = int((keep != ref["keep"]).sum())
+    med_same = oe.lower_median(ref["M"][keep])
+    if med_same > 0:
+        assert abs(med_gpu - med_same) <= 1e-5 * med_same, (med_gpu, med_same, n_diff)
     else:
         assert med_gpu == 0.0
+    if ref["median"] > 0:
+        srt = np.sort(ref["M"][ref["keep"]])
+        r = (srt.size - 1) // 2
+        lo, hi = srt[max(r - n_diff, 0)], srt[min(r + n_diff, srt.size - 1)]
+        assert lo * (1 - 1e-6) <= med_gpu <= hi * (1 + 1e-6), (med_gpu, lo, hi, n_diff)
+    if both.any() and med_same > 0:
+        e_ref = ref["M"][both] / med_same
+        rel = np.abs(e_gpu[both] - e_ref) / e_ref
+        assert rel.max() <= 1e-5, (rel.max(), n_diff)
     return ex.sum()
 
 
