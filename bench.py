@@ -131,25 +131,37 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# algorithmic bytes per launch of each stage for this workload
-def algorithmic_bytes(stage, n, k_sh, npix, pairs, contrib_pairs):
+# Algorithmic work per launch of each stage (the minimum the stage must move or
+# compute for this workload): ("hbm", bytes) or ("alu", FP32 flops).
+#   compositing: every pixel tests the list entries before its last contributor
+#   (14 flops: offset, quadratic form, exponential, opacity, clamp, gate); each
+#   composited pair then costs 12 flops forward (transmittance, colour, score)
+#   and 52 flops in the adjoint (transmittance replay, colour, opacity, mean
+#   and conic gradients, score)
+FLOPS_EVAL, FLOPS_FWD_CONTRIB, FLOPS_BWD_CONTRIB = 14, 12, 52
+FP32_LANES_PER_SM = 128
+
+
+def stage_work(stage, n, k_sh, npix, pairs, evals, contrib):
     param_b = 4 * (3 + 3 + 4 + 1 + 3 * k_sh)
     rec_b = 48 + 4 + 8  # projected record + depth key + tile rectangle
-    if stage == "project":
-        return n * (param_b + rec_b)
-    if stage == "project_bwd":
-        return n * (param_b + 36 + param_b)
-    if stage == "depth_sort":
-        return n * 4 * (4 + 4) * 2
-    if stage == "bin":
-        return n * 8 * 2 + pairs * 4
-    if stage == "composite_fwd":
-        return npix * (4 + 3 + 12 + 4 + 4) + contrib_pairs * (4 + 52)
-    if stage == "composite_bwd":
-        return npix * (4 + 4 + 12 + 3 + 4) + contrib_pairs * (4 + 52 + 40)
-    if stage == "edge_fused":
-        return npix * (3 + 4)
-    return None
+    table = {
+        "edge_fused": ("hbm", npix * (3 + 4)),
+        "project": ("hbm", n * (param_b + rec_b)),
+        "depth_sort": ("hbm", n * 4 * (4 + 4) * 2),
+        "bin": ("hbm", n * (4 + 8) * 2 + pairs * 4),
+        "composite_fwd": ("alu", FLOPS_EVAL * evals + FLOPS_FWD_CONTRIB * contrib),
+        "composite_bwd": ("alu", FLOPS_EVAL * evals + FLOPS_BWD_CONTRIB * contrib),
+        "project_bwd": ("hbm", n * (param_b + 36 + param_b)),
+        "topk": ("hbm", n * 4 * 3),
+        "las": ("hbm", int(SPLIT_FRACTION * n) * 2 * param_b + n),
+    }
+    return table.get(stage)
+
+
+def alu_peak_tflops(n_sm, sm_max_mhz):
+    """FP32 peak from unit counts and clock: SMs x 128 lanes x 2 flops (FMA) x clock."""
+    return n_sm * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
 
 
 STAGES = ["edge_fused", "project", "depth_sort", "bin", "composite_fwd", "composite_bwd", "project_bwd",
@@ -245,8 +257,11 @@ def run_gsp(args, rank, world):
         scores[0].zero_()
     gsp.StageTimer.disarm()
     torch.cuda.synchronize()
-    dominant = max((s for s in breakdown if algorithmic_bytes(s, n, k_sh, npix, 1, 1) is not None),
-                   key=lambda s: breakdown[s])
+    dominant = max(breakdown, key=lambda s: breakdown[s])
+    # data-dependent work counts of the workload (the scene is identical every step)
+    stats = rends[0].stats().cpu()
+    contrib = int(stats[1])
+    evals = int(fwd_bufs["last"].to(torch.int64).sum().item())
 
     # capture one graph per copy; the dominant stage is bracketed by library events
     use_graph = not args.no_graph
@@ -355,14 +370,27 @@ def run_gsp(args, rank, world):
                "note": "parameters and target image copied from pinned host memory, loss and count read back"}
 
     hbm, peak_kind = peaks()
-    algo = algorithmic_bytes(dominant, n, k_sh, npix, pairs, pairs)
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clk.max_mhz or 2070
+    alu_peak = alu_peak_tflops(props.multi_processor_count, sm_max)
     dom_avg_ms = dom_ms / max(dom_cnt, 1)
-    achieved = algo / (dom_avg_ms * 1e-3) / 1e9 if algo and dom_avg_ms > 0 else None
-    roof = {"kernel": dominant, "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
-            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
-            "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-            else "fallback 6.8 TB/s", "avg_launch_ms": round(dom_avg_ms, 5), "launches": dom_cnt,
-            "algorithmic_bytes_per_launch": algo}
+
+    def roofline(stage, ms):
+        bound, amount = stage_work(stage, n, k_sh, npix, pairs, evals, contrib)
+        if bound == "hbm":
+            ach = amount / (ms * 1e-3) / 1e9
+            return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(ach / hbm, 4), "algorithmic_per_launch": amount}
+        ach = amount / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 1), "unit": "TFLOP/s",
+                "frac": round(ach / alu_peak, 4), "algorithmic_per_launch": amount}
+
+    roof = roofline(dominant, dom_avg_ms)
+    roof.update({"kernel": dominant, "traffic": None, "avg_launch_ms": round(dom_avg_ms, 5), "launches": dom_cnt,
+                 "peak_source": (f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if roof["bound"] == "hbm" else
+                                 f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                 f"{sm_max} MHz")})
+    stages_roof = {st: dict(roofline(st, ms), ms=round(ms, 4)) for st, ms in breakdown.items()}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -379,7 +407,8 @@ def run_gsp(args, rank, world):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clk.summary(), "plain": plain,
-        "stages_ms": {k: round(v, 4) for k, v in breakdown.items()},
+        "stages": stages_roof,
+        "work_counts": {"pairs": pairs, "evaluations": evals, "composited": contrib},
     }
     return line
 

@@ -191,8 +191,10 @@ gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *cams, int32_
                           const gsp_render_opts *opts, void *workspace, size_t workspace_bytes,
                           int32_t *dev_status, gsp_stream_t stream);
 
-/* Number of tile-Gaussian pairs the last gsp_render_fwd on this workspace produced
- * (device int64 inside the workspace; valid after that call completes). */
+/* Statistics of the last gsp_render_fwd on this workspace (device int64[2] inside
+ * the workspace; valid after that call completes; no counterpart in the paper):
+ * [0] tile-Gaussian pairs (exact, also when they exceeded pair_capacity),
+ * [1] composited (pixel, Gaussian) pairs, i.e. the terms of the sums for C. */
 const int64_t *gsp_render_pair_count_ptr(const void *workspace, int64_t capacity,
                                          int32_t sh_degree, const gsp_camera *cams,
                                          int32_t num_views, const gsp_render_opts *opts);

@@ -192,11 +192,15 @@ class Renderer:
             self.ws = _workspace(self.ws_bytes, device)
         self.device = device
 
-    def pair_count(self) -> torch.Tensor:
+    def stats(self) -> torch.Tensor:
+        """Device int64[2] of the last forward: tile-Gaussian pairs, composited pairs."""
         p = lib().gsp_render_pair_count_ptr(_ptr(self.ws), self.gs.capacity, self.gs.sh_degree, self.cams,
                                             self.nv, ctypes.byref(self.opts))
         off = int(p) - self.ws.data_ptr()
-        return self.ws[off:off + 8].view(torch.int64)
+        return self.ws[off:off + 16].view(torch.int64)
+
+    def pair_count(self) -> torch.Tensor:
+        return self.stats()[0:1]
 
     def _targets(self, targets):
         if targets is None:

@@ -23,6 +23,8 @@
 // over the block (warp transpose-reduction, shared-memory accumulation, one
 // global atomic per Gaussian, tile and value) and then chains them to the
 // parameters, one thread per Gaussian over all views.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gsp {
@@ -44,6 +46,8 @@ struct ViewP {
     int w, h;
     int tiles_x, tiles_y;
     int tile_base;        // first global tile of the view
+    int sx, sy;           // supertiles per row / column
+    int super_base;       // first global supertile of the view
     long long pix_off;    // first pixel of the view
     const uint8_t *tgt;   // target image (or null)
     long long tgt_pitch;
@@ -53,6 +57,8 @@ struct Views {
     ViewP v[GSP_MAX_VIEWS];
     int n;
     int total_tiles;
+    int total_super;
+    int smax;             // largest supertile count of a view
     long long total_pix;
 };
 
@@ -74,19 +80,27 @@ struct State {
     int32_t *val, *val_alt;   // depth-ordered ids [V][cap], sort scratch [cap]
     unsigned *sort_hist;      // [256][nb_max]
     unsigned *sort_tot;       // [256]
-    int32_t *chunk_pos;       // [total_tiles][nchunk_max] segment counts, then positions in the tile list
-    uint32_t *seg_start;      // [total_tiles][nchunk_max] in-region offsets, then absolute starts in ids
-    unsigned char *bin_wcnt;  // per (view, chunk): [kBinWarps][T_v] per-warp tile counts
-    long long *chunk_tot;     // [V][nchunk_max] pairs per chunk, then region starts
-    int32_t *tile_len;        // [total_tiles] list length of each tile
-    int32_t *ids;             // [pair_cap] Gaussian ids: chunk regions, tile-major inside a region
-    long long *pair_count;    // [1]
+    unsigned *count1;         // [total_super][nch1_max] level-1 chunk counts, then offsets
+    unsigned *len1;           // [total_super] supertile list lengths
+    unsigned *list1_start;    // [total_super] supertile list starts in id1
+    unsigned *chunk2_base;    // [total_super + 1] first level-2 chunk of each supertile
+    int32_t *id1;             // [pair_cap] supertile lists of Gaussian ids
+    unsigned long long *mask1;  // [pair_cap] tile mask of each supertile entry
+    unsigned *count2;         // [chunk2_cap][64] level-2 chunk counts, then offsets
+    unsigned *tile_len;       // [total_tiles] list length of each tile
+    unsigned *tile_start;     // [total_tiles] first position of each tile's list in ids
+    int32_t *ids;             // [pair_cap] Gaussian ids, tile lists one after another
+    int32_t *order_fwd;       // [total_tiles] tiles by descending list length
+    int32_t *order_bwd;       // [total_tiles] tiles by descending last contributor
+    unsigned *tile_work;      // [total_tiles] largest last-contributor position of each tile
+    long long *contrib;       // [1] composited (pixel, Gaussian) pairs of the forward pass
+    long long *pairs_total;   // [1] tile-Gaussian pairs (exact, also when over capacity)
     float4 *g2d;              // [V][cap][3]
     double *loss_acc;         // [1]
     int32_t *overflow;        // [1]
     const int32_t *n_dev;     // the caller's device count of live Gaussians
     int nb_max;               // depth-sort blocks for cap
-    int nchunk_max;
+    int nch1_max;             // level-1 chunks for cap
     long long pair_cap;
 };
 
@@ -235,12 +249,13 @@ __device__ __forceinline__ void load_sh(const float *row, float *out)
     }
 }
 
+// Projects Gaussian i < capacity into every view; returns its tile-Gaussian pairs.
 template <int K>
-__global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Views vs, Params p, State st)
+__device__ __forceinline__ unsigned long long project_one(const Views &vs, const Params &p, const State &st,
+                                                          long long i)
 {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= p.cap) return;
     const int n = *p.count;
+    unsigned long long pairs = 0;
     const long long cap = p.cap;
     for (int v = 0; v < vs.n; ++v) {
         st.val[v * cap + i] = int32_t(i);
@@ -248,7 +263,7 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Vi
         st.g2d[(v * cap + i) * 3 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         st.g2d[(v * cap + i) * 3 + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (i >= n) return;
+    if (i >= n) return 0;
     float mu[3] = {p.means[3 * i], p.means[3 * i + 1], p.means[3 * i + 2]};
     float ls[3] = {p.log_scales[3 * i], p.log_scales[3 * i + 1], p.log_scales[3 * i + 2]};
     float q4[4] = {p.quats[4 * i], p.quats[4 * i + 1], p.quats[4 * i + 2], p.quats[4 * i + 3]};
@@ -286,8 +301,16 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Vi
                 const float dyr = P.b * sqrtf(la / P.a);
                 const float schur = fmaxf(P.a - P.b * P.b / P.c, 0.f);
                 uchar2 *ri = st.rowint + o * kRowCap;
-                const int nrows = min(ty1 - ty0 + 1, kRowCap);  // the walk reads only these rows
-                for (int yy = 0; yy < nrows; ++yy) {
+                const int nrows = min(ty1 - ty0 + 1, kRowCap);  // binning reads only these rows
+                const int wr = tx1 - tx0 + 1;
+                // rows past kRowCap, and every row of a rectangle wider than 255 tiles
+                // (marked (0, 255)), keep the whole rectangle width
+                pairs += (unsigned long long)(ty1 - ty0 + 1 - nrows) * wr;
+                for (int yy = 0; yy < nrows && wr > 255; ++yy) {
+                    ri[yy] = make_uchar2(0, 255);
+                    pairs += wr;
+                }
+                for (int yy = 0; yy < nrows && wr <= 255; ++yy) {
                     const int ty = ty0 + yy;
                     uchar2 iv = make_uchar2(255, 0);
                     {
@@ -300,7 +323,10 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Vi
                             const float m = 0.01f + 1e-4f * (fabsf(xl) + fabsf(xr));
                             const int c0 = max(int(floorf((mx + xl - m - 0.5f) / kTile)), tx0);
                             const int c1 = min(int(floorf((mx + xr + m - 0.5f) / kTile)), tx1);
-                            if (c0 <= c1) iv = make_uchar2((unsigned char)(c0 - tx0), (unsigned char)(c1 - tx0));
+                            if (c0 <= c1) {
+                                iv = make_uchar2((unsigned char)(c0 - tx0), (unsigned char)(c1 - tx0));
+                                pairs += c1 - c0 + 1;
+                            }
                         }
                     }
                     ri[yy] = iv;
@@ -328,13 +354,26 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Vi
             }
             // conic pre-scaled so that power = -1/2 d^T Q d = A' dx^2 + C' dy^2 + B' dx dy
             // (A' = -A/2, B' = -B, C' = -C/2: exact scalings)
-            st.xyo[o] = make_float4(mx, my, opac, P.tz);
-            st.con[o] = make_float4(-0.5f * (P.c * id), P.b * id, -0.5f * (P.a * id), 0.f);
+            // .w slots: half-extents of the footprint's bounding box (compositing culls
+            // whole warps with them)
+            st.xyo[o] = make_float4(mx, my, opac, ex);
+            st.con[o] = make_float4(-0.5f * (P.c * id), P.b * id, -0.5f * (P.a * id), ey);
             st.col[o] = make_float4(col[0], col[1], col[2], __uint_as_float(clampbits));
         }
         st.rect[o] = rect;
         st.key[o] = ok ? __float_as_uint(P.tz) : 0xffffffffu;
     }
+    return pairs;
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Views vs, Params p, State st)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    unsigned long long pairs = i < p.cap ? project_one<K>(vs, p, st, i) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(reinterpret_cast<unsigned long long *>(st.pairs_total), pairs);
 }
 
 // ------------------------------------------------------------ radix sort
@@ -529,256 +568,530 @@ __global__ void __launch_bounds__(kRsThreads) rs_scatter(const K *kin, const int
 
 // ---------------------------------------------------------------- binning
 //
-// Stable count-and-scatter of the depth-ordered Gaussians into per-tile
-// lists (a transposition of the Gaussian x tile incidence, no sort over the
-// pairs).  The depth order of each view is cut into chunks of 1024 ranks, one
-// block per chunk, 128 ranks per warp.  A warp visits its Gaussians in rank
-// order, lanes spread over each one's tile rectangle, and keeps per-tile
-// counters in shared memory, so ranks stay in depth order inside every tile.
-//
-// Each chunk writes its pairs into a region of its own, tile-major inside the
-// region: the 32-byte sectors of a region are filled by one block during its
-// lifetime, so L2 writes them back complete (a layout with every tile's list
-// contiguous makes adjacent chunks share sectors and forces read-modify-write
-// in DRAM).  A tile's list is the chain of its segments over the chunks, in
-// chunk order; segment c of tile t starts at seg_start[t][c] and at position
-// chunk_pos[t][c] of the tile's list.
-//   bin_count    per chunk: per-warp tile counts (bytes, shared memory) written
-//                out; per-tile chunk counts and their in-region offsets
-//   bin_regions  one block: exclusive scan of the chunk totals into region
-//                starts; pair total and capacity check
-//   bin_scan     one warp per tile: segment positions in the tile's list,
-//                absolute segment starts, list length
-//   bin_scatter  per chunk: warp cursors = segment start + the counts of the
-//                earlier warps; the walk writes each id to its slot
+// Stable two-level counting sort of the depth-ordered Gaussians into per-tile
+// lists (no sort over the pairs).  Tiles are grouped into 8x8 supertiles.
+//   level 1  the depth order of each view is partitioned, stably, into one
+//            list per supertile the Gaussian's tile rectangle touches
+//   level 2  each supertile list is partitioned, stably, into its 64 tile
+//            lists, which come out contiguous (tile-major) in `ids`
+// Work is cut into warp chunks of 256 ranks (level 1) or 256 entries of one
+// supertile list (level 2).  Each level counts per (chunk, bin), scans the
+// counts per bin over the chunks, and scatters with the chunk's cursors:
+//   l1_count    per chunk: supertile counts (shared-memory atomics, order-free)
+//   l1_scan     one block per supertile: chunk offsets inside its list
+//   bin_tops    one block: list starts, level-2 chunk bases, capacity check
+//   l1_scatter  per chunk: warp-ordered scatter of the ids (a min-reduction
+//               walks the supertiles of the warp's 32 Gaussians in ascending
+//               order; lanes sharing a supertile write in lane = rank order)
+//   l2_count    per chunk: the 64-bit tile mask of each entry (rows of the
+//               rectangle inside the supertile, culled by the exact column
+//               intervals), stored; per-tile counts from warp ballots
+//   l2_scan     one block per supertile: chunk offsets per tile, list lengths
+//   tile_scan   one block: list starts of all tiles
+//   l2_scatter  per chunk: for each tile and round, a ballot gives every lane
+//               its slot; each store writes a contiguous run of the list
 
-constexpr int kBinChunk = 1024, kBinWarps = 8, kBinThreads = kBinWarps * 32;
-constexpr int kBinPerWarp = kBinChunk / kBinWarps;  // 128 ranks: per-warp counts fit a byte
+constexpr int kSuper = 8;                 // supertile edge, in tiles
+constexpr int kBinRanks = 256;            // ranks (level 1) or entries (level 2) per warp chunk
+constexpr int kBinRounds = kBinRanks / 32;
+constexpr int kBinWarps = 4, kBinThreads = kBinWarps * 32;
+constexpr int kMaxSuper = 2048;           // supertiles per view (shared-memory tables)
 
 __device__ __forceinline__ void rect_unpack(uint2 r, int &tx0, int &ty0, int &tx1, int &ty1)
 {
     tx0 = int(r.x & 0xffffu); ty0 = int(r.x >> 16); tx1 = int(r.y & 0xffffu); ty1 = int(r.y >> 16);
 }
 
-// Visit the tiles of ranks [r0, r0 + 32) of one view in rank order: the 32
-// rectangles are fetched in one parallel load, then the warp takes one
-// Gaussian at a time with its lanes over that rectangle's (distinct) tiles,
-// keeping the tiles inside the row's column interval (the tiles the 1/255
-// ellipse reaches).  fn(tile, id) is called per lane and kept item;
-// consecutive Gaussians are separated by __syncwarp, so per-tile updates
-// happen in rank order.
-template <class Fn>
-__device__ __forceinline__ void walk_tiles(int tiles_x, const uint2 *rect, const uchar2 *rowint,
-                                           const int32_t *sorted, int n, int r0, Fn fn)
+__device__ __forceinline__ int find_view_super(const Views &vs, int gs)
 {
-    const int lane = threadIdx.x & 31;
-    const int r = r0 + lane;
-    int g = -1;
-    uint2 rc = make_uint2(1u, 0u);
-    if (r < n) {
-        g = sorted[r];
-        rc = rect[g];
+    int v = 0;
+    while (v + 1 < vs.n && vs.v[v + 1].super_base <= gs) ++v;
+    return v;
+}
+
+// Columns [lo, hi] of tile row ty0 + yy that the 1/255 ellipse reaches (lo > hi: none).
+__device__ __forceinline__ void row_interval(const uchar2 *ri, int yy, int tx0, int tx1, int &lo, int &hi)
+{
+    lo = tx0;
+    hi = tx1;
+    if (yy < kRowCap) {
+        const uchar2 iv = ri[yy];
+        lo = tx0 + int(iv.x);
+        hi = iv.y == 255 ? tx1 : tx0 + int(iv.y);
     }
-    for (int j = 0; j < 32; ++j) {
-        const unsigned rx = __shfl_sync(0xffffffffu, rc.x, j), ry = __shfl_sync(0xffffffffu, rc.y, j);
-        int tx0, ty0, tx1, ty1;
-        rect_unpack(make_uint2(rx, ry), tx0, ty0, tx1, ty1);
-        if (tx1 < tx0) continue;
-        const int gj = __shfl_sync(0xffffffffu, g, j);
-        const uchar2 *ri = rowint + (size_t)gj * kRowCap;
-        const int wr = tx1 - tx0 + 1, area = wr * (ty1 - ty0 + 1);
-        // exact for wr < 500: the fractional part of (c + 0.5) / wr stays >= 0.5 / wr from 0 and 1
-        const float inv = 1.0f / float(wr);
-        for (int c = lane; c < area; c += 32) {
-            const int yy = int((float(c) + 0.5f) * inv);
-            const int xx = c - yy * wr;
-            bool keep = true;
-            if (yy < kRowCap) {
-                const uchar2 iv = ri[yy];
-                keep = xx >= int(iv.x) && xx <= int(iv.y);
-            }
-            if (keep) fn((ty0 + yy) * tiles_x + tx0 + xx, gj);
+}
+
+// Tiles of supertile (sx, sy) the ellipse reaches: bit (ty - 8 sy) * 8 + (tx - 8 sx).
+__device__ __forceinline__ unsigned long long entry_mask(uint2 rc, const uchar2 *ri, int sx, int sy)
+{
+    int tx0, ty0, tx1, ty1;
+    rect_unpack(rc, tx0, ty0, tx1, ty1);
+    const int bx = sx * kSuper, by = sy * kSuper;
+    unsigned long long m = 0;
+#pragma unroll
+    for (int r = 0; r < kSuper; ++r) {
+        const int ty = by + r;
+        if (ty < ty0 || ty > ty1) continue;
+        int lo, hi;
+        row_interval(ri, ty - ty0, tx0, tx1, lo, hi);
+        lo = max(lo, bx);
+        hi = min(hi, bx + kSuper - 1);
+        if (lo <= hi)
+            m |= (unsigned long long)((0xffu >> (kSuper - 1 - (hi - lo))) << (lo - bx)) << (r * kSuper);
+    }
+    return m;
+}
+
+// Level-1 chunk `task` (over all views): its view, first rank and rank count.
+struct L1Task {
+    int v, chunk, r0, cnt;
+};
+
+__device__ __forceinline__ L1Task l1_task(int task, int n)
+{
+    const int nch = (n + kBinRanks - 1) / kBinRanks;
+    L1Task t;
+    t.v = task / nch;
+    t.chunk = task - t.v * nch;
+    t.r0 = t.chunk * kBinRanks;
+    t.cnt = min(kBinRanks, n - t.r0);
+    return t;
+}
+
+__global__ void __launch_bounds__(kBinThreads) l1_count(const __grid_constant__ Views vs, State st, long long cap)
+{
+    extern __shared__ unsigned l1_tab[];  // [kBinWarps][smax]
+    if (*st.overflow) return;
+    const int n = *st.n_dev;
+    const int nch = (n + kBinRanks - 1) / kBinRanks;
+    const int ntask = nch * vs.n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned *tab = l1_tab + wid * vs.smax;
+    for (int s = lane; s < vs.smax; s += 32) tab[s] = 0;
+    __syncwarp();
+    for (int task = blockIdx.x * kBinWarps + wid; task < ntask; task += gridDim.x * kBinWarps) {
+        const L1Task t = l1_task(task, n);
+        const ViewP &V = vs.v[t.v];
+        const int32_t *sorted = st.val + (size_t)t.v * cap;
+        const uint2 *rect = st.rect + (size_t)t.v * cap;
+        for (int k = 0; k < kBinRounds; ++k) {
+            const int r = 32 * k + lane;
+            if (r >= t.cnt) break;
+            const uint2 rc = rect[sorted[t.r0 + r]];
+            int tx0, ty0, tx1, ty1;
+            rect_unpack(rc, tx0, ty0, tx1, ty1);
+            if (tx1 < tx0) continue;
+            for (int sy = ty0 / kSuper; sy <= ty1 / kSuper; ++sy)
+                for (int sx = tx0 / kSuper; sx <= tx1 / kSuper; ++sx) atomicAdd(&tab[sy * V.sx + sx], 1u);
+        }
+        __syncwarp();
+        const int S = V.sx * V.sy;
+        for (int s = lane; s < S; s += 32) {
+            st.count1[(size_t)(V.super_base + s) * st.nch1_max + t.chunk] = tab[s];
+            tab[s] = 0;
         }
         __syncwarp();
     }
 }
 
-__global__ void __launch_bounds__(kBinThreads) bin_count(const __grid_constant__ Views vs, int v, State st,
-                                                         long long cap, const int32_t *count)
+// Block-wide exclusive scan of one value per thread (256 threads); returns the
+// exclusive prefix and stores the total in *total.
+__device__ __forceinline__ unsigned long long block_excl_scan256(unsigned long long x, unsigned long long *wsum,
+                                                                 unsigned long long *total)
 {
-    extern __shared__ unsigned char bsm[];  // [kBinWarps][T] byte counts
-    __shared__ unsigned wsum[kBinWarps];
-    const ViewP &V = vs.v[v];
-    const int n = *count;
-    const int T = V.tiles_x * V.tiles_y;
-    const int chunk = blockIdx.x;
-    if (chunk * kBinChunk >= n) return;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int i = tid; i < kBinWarps * T; i += kBinThreads) bsm[i] = 0;
-    __syncthreads();
-    unsigned char *mine = bsm + wid * T;
-    const uint2 *rect = st.rect + (size_t)v * cap;
-    const int32_t *sorted = st.val + (size_t)v * cap;
-    const int base = chunk * kBinChunk + wid * kBinPerWarp;
-    for (int r0 = base; r0 < base + kBinPerWarp && r0 < n; r0 += 32)
-        walk_tiles(V.tiles_x, rect, st.rowint + (size_t)v * cap * kRowCap, sorted, n, r0,
-                   [&](int tile, int) { mine[tile] += 1; });
-    __syncthreads();
-    unsigned char *wout = st.bin_wcnt + ((size_t)V.tile_base * st.nchunk_max + (size_t)chunk * T) * kBinWarps;
-    for (int i = tid; i < kBinWarps * T; i += kBinThreads) wout[i] = bsm[i];
-    // per-tile chunk counts and their exclusive offsets inside the chunk's region
-    const int per = (T + kBinThreads - 1) / kBinThreads;
-    const int t0 = tid * per;
-    unsigned mysum = 0;
-    for (int t = t0; t < min(t0 + per, T); ++t)
-        for (int w = 0; w < kBinWarps; ++w) mysum += bsm[w * T + t];
-    unsigned inc = mysum;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long inc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += y;
     }
     if (lane == 31) wsum[wid] = inc;
     __syncthreads();
-    unsigned run = inc - mysum, all = 0;
-    for (int w = 0; w < kBinWarps; ++w) {
-        if (w < wid) run += wsum[w];
+    unsigned long long base = 0, all = 0;
+    for (int w = 0; w < 8; ++w) {
+        if (w < wid) base += wsum[w];
         all += wsum[w];
     }
-    const size_t row0 = (size_t)V.tile_base * st.nchunk_max + chunk;
-    for (int t = t0; t < min(t0 + per, T); ++t) {
-        unsigned s = 0;
-        for (int w = 0; w < kBinWarps; ++w) s += bsm[w * T + t];
-        st.chunk_pos[row0 + (size_t)t * st.nchunk_max] = int32_t(s);
-        st.seg_start[row0 + (size_t)t * st.nchunk_max] = run;
-        run += s;
-    }
-    if (tid == 0) st.chunk_tot[(size_t)v * st.nchunk_max + chunk] = all;
+    *total = all;
+    __syncthreads();
+    return base + inc - x;
 }
 
-// One block: exclusive scan of the chunk totals (all views, chunk-major per
-// view) into region starts; the grand total is the pair count.
-__global__ void __launch_bounds__(1024) bin_regions(int nv, State st, const int32_t *count, int32_t *status)
+// One block per supertile (all views): offsets of the chunks inside its list.
+__global__ void __launch_bounds__(256) l1_scan(const __grid_constant__ Views vs, State st)
 {
-    __shared__ long long wsum[32];
-    __shared__ long long carry;
+    __shared__ unsigned long long wsum[8];
+    if (*st.overflow) return;
+    const int gs = blockIdx.x;
+    const int n = *st.n_dev;
+    const int nch = (n + kBinRanks - 1) / kBinRanks;
+    unsigned *row = st.count1 + (size_t)gs * st.nch1_max;
+    const int q = (nch + 255) / 256;
+    const int c0 = threadIdx.x * q, c1 = min(c0 + q, nch);
+    unsigned long long sum = 0;
+    for (int c = c0; c < c1; ++c) sum += row[c];
+    unsigned long long total;
+    unsigned long long run = block_excl_scan256(sum, wsum, &total);
+    for (int c = c0; c < c1; ++c) {
+        const unsigned x = row[c];
+        row[c] = unsigned(run);
+        run += x;
+    }
+    if (threadIdx.x == 0) st.len1[gs] = unsigned(total);
+}
+
+// One block: starts of the supertile lists, level-2 chunk bases, capacity check.
+__global__ void __launch_bounds__(1024) bin_tops(int total_super, State st, int32_t *status)
+{
+    __shared__ unsigned long long wsum[2][32];
+    __shared__ unsigned long long carry[2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nc = (*count + kBinChunk - 1) / kBinChunk;
-    const int total = nv * st.nchunk_max;
-    if (threadIdx.x == 0) carry = 0;
+    if (threadIdx.x == 0) carry[0] = carry[1] = 0;
     __syncthreads();
-    for (int b0 = 0; b0 < total; b0 += 1024) {
-        const int i = b0 + threadIdx.x;
-        const long long x = (i < total && (i % st.nchunk_max) < nc) ? st.chunk_tot[i] : 0;
-        long long inc = x;
+    const bool over0 = *st.overflow;
+    for (int b0 = 0; b0 < total_super; b0 += 1024) {
+        const int gs = b0 + threadIdx.x;
+        const unsigned long long len = (!over0 && gs < total_super) ? st.len1[gs] : 0;
+        const unsigned long long nc = (len + kBinRanks - 1) / kBinRanks;
+        unsigned long long a = len, b = nc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            const unsigned long long ya = __shfl_up_sync(0xffffffffu, a, o);
+            const unsigned long long yb = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) { a += ya; b += yb; }
+        }
+        if (lane == 31) { wsum[0][wid] = a; wsum[1][wid] = b; }
+        __syncthreads();
+        unsigned long long ba = 0, bb = 0, ta = 0, tb = 0;
+        for (int w = 0; w < 32; ++w) {
+            if (w < wid) { ba += wsum[0][w]; bb += wsum[1][w]; }
+            ta += wsum[0][w];
+            tb += wsum[1][w];
+        }
+        const unsigned long long ca = carry[0], cb = carry[1];
+        __syncthreads();
+        if (gs < total_super) {
+            st.list1_start[gs] = unsigned(ca + ba + a - len);
+            st.chunk2_base[gs] = unsigned(cb + bb + b - nc);
+        }
+        if (threadIdx.x == 0) { carry[0] = ca + ta; carry[1] = cb + tb; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        st.chunk2_base[total_super] = over0 ? 0u : unsigned(carry[1]);
+        const int over = over0 || *st.pairs_total > st.pair_cap || (long long)carry[0] > st.pair_cap;
+        *st.overflow = over;
+        if (over) {
+            st.chunk2_base[total_super] = 0;
+            set_status(status, GSP_ERR_CAPACITY);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBinThreads) l1_scatter(const __grid_constant__ Views vs, State st, long long cap)
+{
+    extern __shared__ unsigned l1_cur[];  // [kBinWarps][smax]
+    if (*st.overflow) return;
+    const int n = *st.n_dev;
+    const int nch = (n + kBinRanks - 1) / kBinRanks;
+    const int ntask = nch * vs.n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned *cur = l1_cur + wid * vs.smax;
+    for (int task = blockIdx.x * kBinWarps + wid; task < ntask; task += gridDim.x * kBinWarps) {
+        const L1Task t = l1_task(task, n);
+        const ViewP &V = vs.v[t.v];
+        const int S = V.sx * V.sy;
+        for (int s = lane; s < S; s += 32)
+            cur[s] = st.list1_start[V.super_base + s] +
+                     st.count1[(size_t)(V.super_base + s) * st.nch1_max + t.chunk];
+        __syncwarp();
+        const int32_t *sorted = st.val + (size_t)t.v * cap;
+        const uint2 *rect = st.rect + (size_t)t.v * cap;
+        for (int k = 0; k < kBinRounds; ++k) {
+            if (32 * k >= t.cnt) break;
+            const int r = 32 * k + lane;
+            int g = -1;
+            int sx0 = 0, sx1 = -1, sy1 = -1, csx = 0, csy = 0;
+            bool live = false;
+            if (r < t.cnt) {
+                g = sorted[t.r0 + r];
+                int tx0, ty0, tx1, ty1;
+                rect_unpack(rect[g], tx0, ty0, tx1, ty1);
+                if (tx1 >= tx0) {
+                    sx0 = tx0 / kSuper; sx1 = tx1 / kSuper; sy1 = ty1 / kSuper;
+                    csx = sx0; csy = ty0 / kSuper;
+                    live = true;
+                }
+            }
+            // supertiles of the round in ascending order; every lane's current
+            // cell is its smallest unwritten one, so the minimum is shared by all
+            // lanes whose rectangle contains it
+            for (;;) {
+                const unsigned key = live ? unsigned(csy * V.sx + csx) : 0xffffffffu;
+                const unsigned smin = __reduce_min_sync(0xffffffffu, key);
+                if (smin == 0xffffffffu) break;
+                const bool mine = key == smin;
+                const unsigned bal = __ballot_sync(0xffffffffu, mine);
+                unsigned base = 0;
+                if (lane == 0) {
+                    base = cur[smin];
+                    cur[smin] = base + __popc(bal);
+                }
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (mine) {
+                    st.id1[base + __popc(bal & lt)] = g;
+                    if (++csx > sx1) {
+                        csx = sx0;
+                        if (++csy > sy1) live = false;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Level-2 chunk c: its supertile (largest gs with chunk2_base[gs] <= c).
+__device__ __forceinline__ int l2_super(const State &st, int total_super, unsigned c)
+{
+    int lo = 0, hi = total_super;  // chunk2_base[lo] <= c < chunk2_base[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (st.chunk2_base[mid] <= c) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kBinThreads) l2_count(const __grid_constant__ Views vs, State st, long long cap)
+{
+    if (*st.overflow) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned nchunk = st.chunk2_base[vs.total_super];
+    for (unsigned c = blockIdx.x * kBinWarps + wid; c < nchunk; c += gridDim.x * kBinWarps) {
+        const int gs = l2_super(st, vs.total_super, c);
+        const int v = find_view_super(vs, gs);
+        const ViewP &V = vs.v[v];
+        const int s = gs - V.super_base;
+        const int sy = s / V.sx, sx = s - sy * V.sx;
+        const unsigned e0 = st.list1_start[gs] + (c - st.chunk2_base[gs]) * kBinRanks;
+        const unsigned e1 = st.list1_start[gs] + st.len1[gs];
+        const uint2 *rect = st.rect + (size_t)v * cap;
+        const uchar2 *rowint = st.rowint + (size_t)v * cap * kRowCap;
+        unsigned long long m[kBinRounds];
+#pragma unroll
+        for (int k = 0; k < kBinRounds; ++k) {
+            const unsigned e = e0 + 32 * k + lane;
+            m[k] = 0;
+            if (e < e1) {
+                const int g = st.id1[e];
+                m[k] = entry_mask(rect[g], rowint + (size_t)g * kRowCap, sx, sy);
+                st.mask1[e] = m[k];
+            }
+        }
+        // per-lane counts of each tile over the lane's 8 entries, bit-sliced: four
+        // 64-bit planes hold a 4-bit counter per tile (carry-save additions)
+        unsigned long long p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+#pragma unroll
+        for (int k = 0; k < kBinRounds; ++k) {
+            const unsigned long long c0 = p0 & m[k];
+            p0 ^= m[k];
+            const unsigned long long c1 = p1 & c0;
+            p1 ^= c0;
+            const unsigned long long c2 = p2 & c1;
+            p2 ^= c1;
+            p3 |= c2;
+        }
+        unsigned mc0 = 0, mc1 = 0;
+#pragma unroll
+        for (int b = 0; b < 64; ++b) {
+            const unsigned cnt_lane = unsigned((p0 >> b) & 1ull) | (unsigned((p1 >> b) & 1ull) << 1) |
+                                      (unsigned((p2 >> b) & 1ull) << 2) | (unsigned((p3 >> b) & 1ull) << 3);
+            const unsigned cnt = __reduce_add_sync(0xffffffffu, cnt_lane);
+            if (lane == (b & 31)) {
+                if (b < 32) mc0 = cnt;
+                else mc1 = cnt;
+            }
+        }
+        st.count2[(size_t)c * 64 + lane] = mc0;
+        st.count2[(size_t)c * 64 + 32 + lane] = mc1;
+    }
+}
+
+// Global tile of bit b of supertile (sx, sy) of view V, or -1 outside the view.
+__device__ __forceinline__ int super_tile(const ViewP &V, int sx, int sy, int b)
+{
+    const int tx = sx * kSuper + (b & (kSuper - 1)), ty = sy * kSuper + b / kSuper;
+    return (tx < V.tiles_x && ty < V.tiles_y) ? V.tile_base + ty * V.tiles_x + tx : -1;
+}
+
+// One block per supertile: offsets of its chunks inside each tile's list, and
+// the tiles' list lengths.  Thread (group, b): tile b over a quarter of the chunks.
+__global__ void __launch_bounds__(256) l2_scan(const __grid_constant__ Views vs, State st)
+{
+    __shared__ unsigned part[4][64];
+    const int gs = blockIdx.x;
+    const int v = find_view_super(vs, gs);
+    const ViewP &V = vs.v[v];
+    const int s = gs - V.super_base;
+    const int sy = s / V.sx, sx = s - sy * V.sx;
+    const int b = threadIdx.x & 63, grp = threadIdx.x >> 6;
+    const bool over = *st.overflow;
+    const unsigned cb0 = over ? 0u : st.chunk2_base[gs], cb1 = over ? 0u : st.chunk2_base[gs + 1];
+    const unsigned nch = cb1 - cb0, q = (nch + 3) / 4;
+    const unsigned c0 = cb0 + grp * q, c1 = min(c0 + q, cb1);
+    unsigned sum = 0;
+    for (unsigned c = c0; c < c1; ++c) sum += st.count2[(size_t)c * 64 + b];
+    part[grp][b] = sum;
+    __syncthreads();
+    unsigned run = 0;
+    for (int g2 = 0; g2 < grp; ++g2) run += part[g2][b];
+    for (unsigned c = c0; c < c1; ++c) {
+        const unsigned x = st.count2[(size_t)c * 64 + b];
+        st.count2[(size_t)c * 64 + b] = run;
+        run += x;
+    }
+    if (grp == 3) {
+        const int gt = super_tile(V, sx, sy, b);
+        if (gt >= 0) st.tile_len[gt] = run;
+    }
+}
+
+// 8-bit logarithmic bucket of a work estimate: 3 bits of mantissa under the
+// position of the leading one.
+__device__ __forceinline__ unsigned work_bucket(unsigned v)
+{
+    if (v == 0) return 0;
+    const int l = 31 - __clz(v);
+    const unsigned f = l >= 3 ? (v >> (l - 3)) & 7u : (v << (3 - l)) & 7u;
+    return unsigned(l) * 8u + f;
+}
+
+// One block of 1024 threads: tiles in descending order of work (counting sort
+// on work_bucket), so that the longest tiles are dispatched first and the
+// launch does not end on a tail of heavy tiles.
+__device__ void order_tiles_desc(const unsigned *work, int total_tiles, int32_t *order)
+{
+    __shared__ unsigned hist[256];
+    __shared__ unsigned wsum[8];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid < 256) hist[tid] = 0;
+    __syncthreads();
+    for (int t = tid; t < total_tiles; t += blockDim.x) atomicAdd(&hist[255u - work_bucket(work[t])], 1u);
+    __syncthreads();
+    unsigned x = 0, inc = 0;
+    if (tid < 256) {
+        x = hist[tid];
+        inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[wid] = inc;
+    }
+    __syncthreads();
+    if (tid < 256) {
+        unsigned base = 0;
+        for (int w = 0; w < wid; ++w) base += wsum[w];
+        hist[tid] = base + inc - x;
+    }
+    __syncthreads();
+    for (int t = tid; t < total_tiles; t += blockDim.x) order[atomicAdd(&hist[255u - work_bucket(work[t])], 1u)] = t;
+}
+
+// One block: exclusive scan of the tile list lengths into list starts; the
+// total is checked against the pair capacity once more before any id is written.
+__global__ void __launch_bounds__(1024) tile_scan(int total_tiles, State st, int32_t *status)
+{
+    __shared__ unsigned long long wsum[32];
+    __shared__ unsigned long long carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < total_tiles; b0 += 1024) {
+        const int i = b0 + threadIdx.x;
+        const unsigned long long x = i < total_tiles ? st.tile_len[i] : 0;
+        unsigned long long inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
         if (lane == 31) wsum[wid] = inc;
         __syncthreads();
-        long long wb = 0, all = 0;
+        unsigned long long wb = 0, all = 0;
         for (int w = 0; w < 32; ++w) {
             if (w < wid) wb += wsum[w];
             all += wsum[w];
         }
-        const long long c0 = carry;
+        const unsigned long long c0 = carry;
         __syncthreads();
-        if (i < total) st.chunk_tot[i] = c0 + wb + inc - x;
+        if (i < total_tiles) st.tile_start[i] = unsigned(c0 + wb + inc - x);
         if (threadIdx.x == 0) carry = c0 + all;
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        *st.pair_count = carry;
-        const int over = carry > st.pair_cap;
-        *st.overflow = over;
-        if (over) set_status(status, GSP_ERR_CAPACITY);
+    if (threadIdx.x == 0 && (long long)carry > st.pair_cap) {
+        *st.overflow = 1;
+        set_status(status, GSP_ERR_CAPACITY);
     }
+    order_tiles_desc(st.tile_len, total_tiles, st.order_fwd);
 }
 
-// One warp per global tile: positions of its segments in the tile's list,
-// absolute segment starts, list length.
-__global__ void __launch_bounds__(256) bin_scan(const __grid_constant__ Views vs, State st, const int32_t *count)
+// One block: the adjoint's tile order, by the forward's last-contributor positions.
+__global__ void __launch_bounds__(1024) tile_order_bwd(int total_tiles, State st)
 {
-    const int gt = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gt >= vs.total_tiles) return;
-    const int v = find_view(vs, gt);
-    const int nc = (*count + kBinChunk - 1) / kBinChunk;
-    int32_t *pos = st.chunk_pos + (size_t)gt * st.nchunk_max;
-    uint32_t *seg = st.seg_start + (size_t)gt * st.nchunk_max;
-    const long long *region = st.chunk_tot + (size_t)v * st.nchunk_max;
-    int carry = 0;
-    for (int c0 = 0; c0 < nc; c0 += 32) {
-        const int c = c0 + lane;
-        const int x = c < nc ? pos[c] : 0;
-        int inc = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (c < nc) {
-            pos[c] = carry + inc - x;
-            seg[c] = uint32_t(region[c] + seg[c]);
-        }
-        carry += __shfl_sync(0xffffffffu, inc, 31);
-    }
-    if (lane == 0) st.tile_len[gt] = carry;
+    order_tiles_desc(st.tile_work, total_tiles, st.order_bwd);
 }
 
-__global__ void __launch_bounds__(kBinThreads) bin_scatter(const __grid_constant__ Views vs, int v, State st,
-                                                           long long cap, const int32_t *count)
+__global__ void __launch_bounds__(kBinThreads) l2_scatter(const __grid_constant__ Views vs, State st)
 {
-    extern __shared__ unsigned char bsm_raw[];
     if (*st.overflow) return;
-    const ViewP &V = vs.v[v];
-    const int n = *count;
-    const int T = V.tiles_x * V.tiles_y;
-    const int chunk = blockIdx.x;
-    if (chunk * kBinChunk >= n) return;
-    uint32_t *base = reinterpret_cast<uint32_t *>(bsm_raw);                // [T]
-    unsigned short *cur = reinterpret_cast<unsigned short *>(base + T);   // [kBinWarps][T]
-    const unsigned char *wc = st.bin_wcnt + ((size_t)V.tile_base * st.nchunk_max + (size_t)chunk * T) * kBinWarps;
-    const uint32_t *seg = st.seg_start + (size_t)V.tile_base * st.nchunk_max + chunk;
-    for (int t = threadIdx.x; t < T; t += kBinThreads) {
-        base[t] = seg[(size_t)t * st.nchunk_max];
-        unsigned run = 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned nchunk = st.chunk2_base[vs.total_super];
+    for (unsigned c = blockIdx.x * kBinWarps + wid; c < nchunk; c += gridDim.x * kBinWarps) {
+        const int gs = l2_super(st, vs.total_super, c);
+        const int v = find_view_super(vs, gs);
+        const ViewP &V = vs.v[v];
+        const int s = gs - V.super_base;
+        const int sy = s / V.sx, sx = s - sy * V.sx;
+        const unsigned e0 = st.list1_start[gs] + (c - st.chunk2_base[gs]) * kBinRanks;
+        const unsigned e1 = st.list1_start[gs] + st.len1[gs];
+        int g[kBinRounds];
+        unsigned long long m[kBinRounds];
+        unsigned long long any = 0;
 #pragma unroll
-        for (int w = 0; w < kBinWarps; ++w) {
-            cur[w * T + t] = (unsigned short)run;
-            run += wc[w * T + t];
+        for (int k = 0; k < kBinRounds; ++k) {
+            const unsigned e = e0 + 32 * k + lane;
+            g[k] = 0;
+            m[k] = 0;
+            if (e < e1) {
+                g[k] = st.id1[e];
+                m[k] = st.mask1[e];
+            }
+            any |= m[k];
+        }
+        const unsigned any_lo = __reduce_or_sync(0xffffffffu, unsigned(any));
+        const unsigned any_hi = __reduce_or_sync(0xffffffffu, unsigned(any >> 32));
+        const int gt0 = super_tile(V, sx, sy, lane), gt1 = super_tile(V, sx, sy, lane + 32);
+        const unsigned cur0 = gt0 >= 0 ? st.tile_start[gt0] + st.count2[(size_t)c * 64 + lane] : 0u;
+        const unsigned cur1 = gt1 >= 0 ? st.tile_start[gt1] + st.count2[(size_t)c * 64 + 32 + lane] : 0u;
+#pragma unroll
+        for (int b = 0; b < 64; ++b) {
+            if (!(((b < 32 ? any_lo : any_hi) >> (b & 31)) & 1u)) continue;
+            unsigned base = __shfl_sync(0xffffffffu, b < 32 ? cur0 : cur1, b & 31);
+#pragma unroll
+            for (int k = 0; k < kBinRounds; ++k) {
+                const bool bit = (m[k] >> b) & 1ull;
+                const unsigned bal = __ballot_sync(0xffffffffu, bit);
+                if (bit) st.ids[base + __popc(bal & lt)] = g[k];
+                base += __popc(bal);
+            }
         }
     }
-    __syncthreads();
-    const int wid = threadIdx.x >> 5;
-    unsigned short *mine = cur + wid * T;
-    const uint2 *rect = st.rect + (size_t)v * cap;
-    const int32_t *sorted = st.val + (size_t)v * cap;
-    const int b0 = chunk * kBinChunk + wid * kBinPerWarp;
-    for (int r0 = b0; r0 < b0 + kBinPerWarp && r0 < n; r0 += 32) {
-        walk_tiles(V.tiles_x, rect, st.rowint + (size_t)v * cap * kRowCap, sorted, n, r0,
-                   [&](int tile, int gid) {
-            const unsigned short k = mine[tile];
-            mine[tile] = (unsigned short)(k + 1);
-            st.ids[(size_t)base[tile] + k] = gid;
-        });
-    }
-}
-
-// Gaussian id at position p of tile gt's list: the segment is found by a
-// binary search over the tile's segment positions (nc chunks).
-__device__ __forceinline__ int list_id(const State &st, int gt, int nc, int p)
-{
-    const int32_t *pos = st.chunk_pos + (size_t)gt * st.nchunk_max;
-    int lo = 0, hi = nc;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(pos + mid) <= p) lo = mid;
-        else hi = mid;
-    }
-    return st.ids[(size_t)__ldg(st.seg_start + (size_t)gt * st.nchunk_max + lo) + (p - __ldg(pos + lo))];
 }
 
 // ------------------------------------------------------------- compositing
@@ -826,8 +1139,10 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
     __shared__ int32_t s_id[kBatch];
     __shared__ float s_score[kBatch];
     __shared__ float s_red[NT / 32];
+    __shared__ unsigned s_maxlast;
+    __shared__ unsigned long long s_contrib;
     if (*st.overflow) return;
-    const int gt = blockIdx.x;
+    const int gt = st.order_fwd[blockIdx.x];
     const int v = find_view(vs, gt);
     const ViewP &V = vs.v[v];
     const int lt = gt - V.tile_base;
@@ -836,9 +1151,19 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
     const int x = txx * kTile + (tid & (kTile - 1));
     const int y0 = tyy * kTile + (tid / kTile) * PPT;
     const float px = x + 0.5f;
-    const int len = st.tile_len[gt];
-    const int nc = (*st.n_dev + kBinChunk - 1) / kBinChunk;
+    const int len = int(st.tile_len[gt]);
+    const int32_t *list = st.ids + st.tile_start[gt];
     const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
+    // the warp's pixel centres: 16 columns x 2 PPT rows, centre (wcx, wcy)
+    const float wcx = txx * kTile + 0.5f * kTile;
+    const float wcy = tyy * kTile + (32 * wid / kTile) * PPT + PPT;
+    const float whw = 0.5f * kTile - 0.5f, whh = PPT - 0.5f;
+    if (tid == 0) {
+        s_maxlast = 0;
+        s_contrib = 0;
+    }
+    __syncthreads();
+    unsigned ncontrib = 0;
 
     float T[PPT], C0[PPT], C1[PPT], C2[PPT], E[PPT];
     int last[PPT];
@@ -859,7 +1184,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
         for (int q = tid; q < kBatch; q += NT) {
             const int k = b + q;
             if (k < len) {
-                const int id = list_id(st, gt, nc, k);
+                const int id = list[k];
                 s_id[q] = id;
                 s_xyo[q] = xyo[id];
                 s_con[q] = con[id];
@@ -871,6 +1196,8 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
         const int cnt = min(kBatch, len - b);
         for (int j = 0; j < cnt; ++j) {
             const float4 gx = s_xyo[j], gc = s_con[j];
+            // the footprint's bounding box misses every pixel of the warp (warp-uniform)
+            if (fabsf(gx.x - wcx) > gx.w + whw || fabsf(gx.y - wcy) > gc.w + whh) continue;
             float sv = 0.f;
 #pragma unroll
             for (int m = 0; m < PPT; ++m) {
@@ -882,6 +1209,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
                     done[m] = true;
                     continue;
                 }
+                ++ncontrib;
                 const float w = __fmul_rn(a.alpha, T[m]);
                 const float4 c = s_col[j];
                 C0[m] = __fmaf_rn(c.x, w, C0[m]);
@@ -901,6 +1229,24 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
         if (score)
             for (int q = tid; q < cnt; q += NT)
                 if (s_score[q] != 0.f) atomicAdd(&score[s_id[q]], s_score[q]);
+    }
+    {
+        // per-tile statistics: largest last position (orders the adjoint's tiles)
+        // and the number of composited pairs
+        unsigned ml = 0;
+#pragma unroll
+        for (int m = 0; m < PPT; ++m) ml = max(ml, unsigned(last[m]));
+        ml = __reduce_max_sync(0xffffffffu, ml);
+        const unsigned nc = __reduce_add_sync(0xffffffffu, ncontrib);
+        if (lane == 0) {
+            atomicMax(&s_maxlast, ml);
+            atomicAdd(&s_contrib, (unsigned long long)nc);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            st.tile_work[gt] = s_maxlast;
+            atomicAdd(reinterpret_cast<unsigned long long *>(st.contrib), s_contrib);
+        }
     }
     float l = 0.f;
 #pragma unroll
@@ -999,7 +1345,7 @@ constexpr int kG2 = 10;  // mean x, mean y, conic A, B, C, opacity, r, g, b, sco
 // (transpose reduction), warps meet in shared accumulators, and one global
 // atomic per (Gaussian, tile, value) leaves the block.
 template <int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT) composite_bwd(const __grid_constant__ Views vs, State st,
+__global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) composite_bwd(const __grid_constant__ Views vs, State st,
                                                                 long long cap, const float *dL_drgb, const float *rgb,
                                                                 const float *T_fin, const int32_t *last_idx,
                                                                 const float *edge, float *score, float inv_norm)
@@ -1010,7 +1356,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_bwd(const __grid_con
     __shared__ float s_acc[kBatch][kG2];
     __shared__ int s_maxlast;
     if (*st.overflow) return;
-    const int gt = blockIdx.x;
+    const int gt = st.order_bwd[blockIdx.x];
     const int v = find_view(vs, gt);
     const ViewP &V = vs.v[v];
     const int lt = gt - V.tile_base;
@@ -1019,11 +1365,16 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_bwd(const __grid_con
     const int x = txx * kTile + (tid & (kTile - 1));
     const int y0 = tyy * kTile + (tid / kTile) * PPT;
     const float px = x + 0.5f;
-    const int list_len = st.tile_len[gt];
-    const int nc = (*st.n_dev + kBinChunk - 1) / kBinChunk;
+    const int list_len = int(st.tile_len[gt]);
+    const int32_t *list = st.ids + st.tile_start[gt];
     const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
     float4 *g2d = st.g2d + (size_t)v * cap * 3;
     const bool want_score = score && edge;
+    const int wid = tid >> 5;
+    // the warp's pixel centres: 16 columns x 2 PPT rows, centre (wcx, wcy)
+    const float wcx = txx * kTile + 0.5f * kTile;
+    const float wcy = tyy * kTile + (32 * wid / kTile) * PPT + PPT;
+    const float whw = 0.5f * kTile - 0.5f, whh = PPT - 0.5f;
 
     float T[PPT], g0[PPT], g1[PPT], g2[PPT], E[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
     int last[PPT];
@@ -1059,21 +1410,24 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_bwd(const __grid_con
     atomicMax(&s_maxlast, mylast);
     __syncthreads();
     const int maxlast = s_maxlast;
+    const int wlast = int(__reduce_max_sync(0xffffffffu, unsigned(mylast)));  // the warp's last position
 
     for (int hi = maxlast; hi > 0; hi -= kBatch) {
         const int lo = max(hi - kBatch, 0);
         const int cnt = hi - lo;
         for (int q = tid; q < cnt; q += NT) {
-            const int id = list_id(st, gt, nc, lo + q);
+            const int id = list[lo + q];
             s_id[q] = id;
             s_xyo[q] = xyo[id];
             s_con[q] = con[id];
             s_col[q] = col[id];
         }
         __syncthreads();
-        for (int j = cnt - 1; j >= 0; --j) {
+        for (int j = min(cnt, wlast - lo) - 1; j >= 0; --j) {
             const int pos = lo + j;
             const float4 gx = s_xyo[j], gc = s_con[j];
+            // the footprint's bounding box misses every pixel of the warp (warp-uniform)
+            if (fabsf(gx.x - wcx) > gx.w + whw || fabsf(gx.y - wcy) > gc.w + whh) continue;
             float val[kG2];
 #pragma unroll
             for (int k = 0; k < kG2; ++k) val[k] = 0.f;
@@ -1086,7 +1440,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_bwd(const __grid_con
                 active = true;
                 const float4 c = s_col[j];
                 const float one_m = __fsub_rn(1.f, a.alpha);
-                T[m] = __fdiv_rn(T[m], one_m);
+                T[m] = __fdividef(T[m], one_m);
                 const float w = a.alpha * T[m];
                 val[6] += w * g0[m];
                 val[7] += w * g1[m];
@@ -1300,17 +1654,20 @@ __global__ void __launch_bounds__(128) project_bwd(const __grid_constant__ Views
 
 // ------------------------------------------------------------------- host
 
+constexpr int kCounters = 4;
+
 struct Layout {
     State st;
     size_t bytes;
 };
 
-Layout render_layout(void *ws, long long cap, int nv, int total_tiles, long long pair_cap)
+Layout render_layout(void *ws, long long cap, const Views &vs, long long pair_cap)
 {
     Carver c(ws);
     Layout L{};
     State &s = L.st;
-    const size_t vc = (size_t)nv * cap;
+    const size_t vc = (size_t)vs.n * cap;
+    const size_t total_tiles = (size_t)vs.total_tiles, total_super = (size_t)vs.total_super;
     s.xyo = c.take<float4>(vc);
     s.con = c.take<float4>(vc);
     s.col = c.take<float4>(vc);
@@ -1323,17 +1680,29 @@ Layout render_layout(void *ws, long long cap, int nv, int total_tiles, long long
     s.nb_max = int(div_up(cap, kRsTile));
     s.sort_hist = c.take<unsigned>((size_t)256 * s.nb_max);
     s.sort_tot = c.take<unsigned>(256);
-    s.nchunk_max = int(div_up(cap, kBinChunk));
-    s.chunk_pos = c.take<int32_t>((size_t)total_tiles * s.nchunk_max);
-    s.seg_start = c.take<uint32_t>((size_t)total_tiles * s.nchunk_max);
-    s.bin_wcnt = c.take<unsigned char>((size_t)total_tiles * s.nchunk_max * kBinWarps);
-    s.chunk_tot = c.take<long long>((size_t)nv * s.nchunk_max);
-    s.tile_len = c.take<int32_t>((size_t)total_tiles);
+    s.nch1_max = int(div_up(cap, kBinRanks));
+    s.count1 = c.take<unsigned>(total_super * s.nch1_max);
+    s.len1 = c.take<unsigned>(total_super);
+    s.list1_start = c.take<unsigned>(total_super);
+    s.chunk2_base = c.take<unsigned>(total_super + 1);
+    s.id1 = c.take<int32_t>((size_t)pair_cap);
+    s.mask1 = c.take<unsigned long long>((size_t)pair_cap);
+    // level-2 chunks: at most one partial chunk per supertile beyond pair_cap / 256 full ones
+    s.count2 = c.take<unsigned>(((size_t)pair_cap / kBinRanks + total_super + 1) * 64);
+    s.tile_len = c.take<unsigned>(total_tiles);
+    s.tile_start = c.take<unsigned>(total_tiles);
     s.ids = c.take<int32_t>((size_t)pair_cap);
-    s.pair_count = c.take<long long>(1);
+    s.order_fwd = c.take<int32_t>(total_tiles);
+    s.order_bwd = c.take<int32_t>(total_tiles);
+    s.tile_work = c.take<unsigned>(total_tiles);
     s.g2d = c.take<float4>(vc * 3);
-    s.loss_acc = c.take<double>(1);
-    s.overflow = c.take<int32_t>(1);
+    // counters cleared by one memset per forward pass: pair total, composited
+    // pairs, loss sum, overflow flag
+    long long *ctr = c.take<long long>(kCounters);
+    s.pairs_total = ctr;
+    s.contrib = ctr + 1;
+    s.loss_acc = reinterpret_cast<double *>(ctr + 2);
+    s.overflow = reinterpret_cast<int32_t *>(ctr + 3);
     s.pair_cap = pair_cap;
     L.bytes = c.size();
     return L;
@@ -1343,7 +1712,7 @@ gsp_status build_views(const gsp_camera *cams, int nv, const gsp_image_desc *tar
 {
     if (!cams || nv < 1) return GSP_ERR_INVALID_ARG;
     if (nv > GSP_MAX_VIEWS) return GSP_ERR_UNSUPPORTED;
-    int tiles = 0;
+    int tiles = 0, supers = 0, smax = 0;
     long long pix = 0;
     for (int v = 0; v < nv; ++v) {
         const gsp_camera &c = cams[v];
@@ -1362,6 +1731,12 @@ gsp_status build_views(const gsp_camera *cams, int nv, const gsp_image_desc *tar
         V.tiles_x = int(div_up(c.width, kTile));
         V.tiles_y = int(div_up(c.height, kTile));
         if (V.tiles_x > 65535 || V.tiles_y > 65535) return GSP_ERR_UNSUPPORTED;
+        V.sx = int(div_up(V.tiles_x, kSuper));
+        V.sy = int(div_up(V.tiles_y, kSuper));
+        if ((long long)V.sx * V.sy > kMaxSuper) return GSP_ERR_UNSUPPORTED;
+        V.super_base = supers;
+        supers += V.sx * V.sy;
+        smax = max(smax, V.sx * V.sy);
         V.tile_base = tiles;
         V.pix_off = c.pixel_offset;
         tiles += V.tiles_x * V.tiles_y;
@@ -1378,6 +1753,8 @@ gsp_status build_views(const gsp_camera *cams, int nv, const gsp_image_desc *tar
     }
     vs.n = nv;
     vs.total_tiles = tiles;
+    vs.total_super = supers;
+    vs.smax = smax;
     vs.total_pix = pix;
     return GSP_OK;
 }
@@ -1412,7 +1789,7 @@ extern "C" size_t gsp_render_workspace_size(int64_t capacity, int32_t sh_degree,
     if (build_views(cams, nv, nullptr, vs) != GSP_OK || !opts || opts->pair_capacity < 1 || capacity < 1 ||
         sh_degree < 0 || sh_degree > 3)
         return 0;
-    return render_layout(nullptr, capacity, nv, vs.total_tiles, opts->pair_capacity).bytes;
+    return render_layout(nullptr, capacity, vs, opts->pair_capacity).bytes;
 }
 
 extern "C" const int64_t *gsp_render_pair_count_ptr(const void *ws, int64_t capacity, int32_t sh_degree,
@@ -1422,7 +1799,7 @@ extern "C" const int64_t *gsp_render_pair_count_ptr(const void *ws, int64_t capa
     (void)sh_degree;
     if (!ws || build_views(cams, nv, nullptr, vs) != GSP_OK || !opts) return nullptr;
     return reinterpret_cast<const int64_t *>(
-        render_layout(const_cast<void *>(ws), capacity, nv, vs.total_tiles, opts->pair_capacity).st.pair_count);
+        render_layout(const_cast<void *>(ws), capacity, vs, opts->pair_capacity).st.pairs_total);
 }
 
 extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *cams, int32_t nv,
@@ -1439,22 +1816,18 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
         return GSP_ERR_INVALID_ARG;
     if (score && !edge) return GSP_ERR_INVALID_ARG;
     if (loss_out && !targets) return GSP_ERR_INVALID_ARG;
-    if (opts->pair_capacity > 0xffffffffLL) return GSP_ERR_UNSUPPORTED;  // 32-bit segment starts
-    for (int v = 0; v < nv; ++v) {
-        const size_t T = size_t(vs.v[v].tiles_x) * vs.v[v].tiles_y;
-        if (T * (sizeof(uint32_t) + kBinWarps * sizeof(unsigned short)) > 200 * 1024) return GSP_ERR_UNSUPPORTED;
-    }
+    if (opts->pair_capacity > 0xffffffffLL) return GSP_ERR_UNSUPPORTED;  // 32-bit list positions
     const long long cap = g->capacity;
-    Layout L = render_layout(nullptr, cap, nv, vs.total_tiles, opts->pair_capacity);
+    Layout L = render_layout(nullptr, cap, vs, opts->pair_capacity);
     st = check_workspace(ws, ws_bytes, L.bytes);
     if (st != GSP_OK) return st;
-    L = render_layout(ws, cap, nv, vs.total_tiles, opts->pair_capacity);
+    L = render_layout(ws, cap, vs, opts->pair_capacity);
     State S = L.st;
     S.n_dev = g->count;
     Params P = make_params(g);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
-    GSP_CUDA_TRY(cudaMemsetAsync(S.loss_acc, 0, sizeof(double), s));
+    GSP_CUDA_TRY(cudaMemsetAsync(S.pairs_total, 0, kCounters * sizeof(long long), s));
     stage_begin("project", s);
     switch (P.K) {
     case 1: project_kernel<1><<<div_up(cap, 256), 256, 0, s>>>(vs, P, S); break;
@@ -1482,20 +1855,19 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     stage_end("depth_sort", s);
     GSP_LAUNCH_CHECK();
     stage_begin("bin", s);
-    // binning: per-chunk tile counts, scans, stable scatter (per view for the chunk kernels)
-    for (int v = 0; v < nv; ++v) {
-        const int T = vs.v[v].tiles_x * vs.v[v].tiles_y;
-        const size_t smem = size_t(kBinWarps) * T;
-        GSP_CUDA_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        bin_count<<<S.nchunk_max, kBinThreads, smem, s>>>(vs, v, S, cap, g->count);
-    }
-    bin_regions<<<1, 1024, 0, s>>>(nv, S, g->count, dev_status);
-    bin_scan<<<div_up((long long)vs.total_tiles * 32, 256), 256, 0, s>>>(vs, S, g->count);
-    for (int v = 0; v < nv; ++v) {
-        const int T = vs.v[v].tiles_x * vs.v[v].tiles_y;
-        const size_t smem = size_t(T) * (sizeof(uint32_t) + kBinWarps * sizeof(unsigned short));
-        GSP_CUDA_TRY(cudaFuncSetAttribute(bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        bin_scatter<<<S.nchunk_max, kBinThreads, smem, s>>>(vs, v, S, cap, g->count);
+    {
+        const int nsm = num_sms();
+        const size_t smem = size_t(kBinWarps) * vs.smax * sizeof(unsigned);
+        const unsigned l1_blocks = unsigned(std::min<long long>(
+            std::max<long long>(div_up((long long)nv * S.nch1_max, kBinWarps), 1), 16LL * nsm));
+        l1_count<<<l1_blocks, kBinThreads, smem, s>>>(vs, S, cap);
+        l1_scan<<<vs.total_super, 256, 0, s>>>(vs, S);
+        bin_tops<<<1, 1024, 0, s>>>(vs.total_super, S, dev_status);
+        l1_scatter<<<l1_blocks, kBinThreads, smem, s>>>(vs, S, cap);
+        l2_count<<<16 * nsm, kBinThreads, 0, s>>>(vs, S, cap);
+        l2_scan<<<vs.total_super, 256, 0, s>>>(vs, S);
+        tile_scan<<<1, 1024, 0, s>>>(vs.total_tiles, S, dev_status);
+        l2_scatter<<<16 * nsm, kBinThreads, 0, s>>>(vs, S);
     }
     stage_end("bin", s);
     GSP_LAUNCH_CHECK();
@@ -1504,7 +1876,7 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
         vs, S, cap, edge, rgb_out, T_final, last_idx, score);
     stage_end("composite_fwd", s);
     GSP_LAUNCH_CHECK();
-    note_launches(2 + 12 * nv + 2 * nv + 2 + 1);
+    note_launches(2 + 12 * nv + 8 + 1);
     if (loss_out) {
         loss_finalise<<<1, 1, 0, s>>>(S, vs.total_pix, loss_out);
         note_launches(1);
@@ -1532,16 +1904,17 @@ extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *c
     if (!dL_drgb && (!targets || !rgb)) return GSP_ERR_INVALID_ARG;
     if (score && !edge) return GSP_ERR_INVALID_ARG;
     const long long cap = g->capacity;
-    Layout L = render_layout(nullptr, cap, nv, vs.total_tiles, opts->pair_capacity);
+    Layout L = render_layout(nullptr, cap, vs, opts->pair_capacity);
     st = check_workspace(ws, ws_bytes, L.bytes);
     if (st != GSP_OK) return st;
-    L = render_layout(ws, cap, nv, vs.total_tiles, opts->pair_capacity);
+    L = render_layout(ws, cap, vs, opts->pair_capacity);
     State S = L.st;
     S.n_dev = g->count;
     Params P = make_params(g);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const float inv_norm = float(1.0 / (3.0 * double(vs.total_pix)));
     stage_begin("composite_bwd", s);
+    tile_order_bwd<<<1, 1024, 0, s>>>(vs.total_tiles, S);
     composite_bwd<kBwdPixPerThread><<<vs.total_tiles, kTilePix / kBwdPixPerThread, 0, s>>>(
         vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm);
     stage_end("composite_bwd", s);
@@ -1558,7 +1931,7 @@ extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *c
     }
 #undef GSP_PBWD
     stage_end("project_bwd", s);
-    note_launches(2);
+    note_launches(3);
     GSP_LAUNCH_CHECK();
     return GSP_OK;
 }

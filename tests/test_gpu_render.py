@@ -46,6 +46,7 @@ def gpu_render(gsp, g, cams, targets=None, edges=None, dL=None, pair_capacity=1 
     torch.cuda.synchronize()
     res = {"status": int(out["status"].item()), "rgb": out["rgb"].cpu().numpy(), "T": out["T"].cpu().numpy(),
            "last": out["last"].cpu().numpy(), "pairs": int(r.pair_count().item()),
+           "contrib": int(r.stats()[1].item()),
            "score": score.cpu().numpy() if score is not None else None,
            "loss": float(out["loss"].item()) if out["loss"] is not None else None}
     if grads is not None:
@@ -118,6 +119,9 @@ def test_tiny_config_matches_oracle(gsp_lib):
     assert res["status"] == 0
     ref = orc.render(g, cam, edge=e)
     check_image(res, [ref], [cam])
+    # composited (pixel, Gaussian) pairs: exact outside gate-exempt pixels
+    ex = ref["gate_gap"] < GATE_REL
+    assert abs(res["contrib"] - int(ref["ncontrib"].sum())) <= int(ref["ncontrib"][ex].sum()) + int(ex.sum())
     check_scores(res["score"], ref["score"], exempt_gaussians(g, cam, ref))
     loss_ref, _ = orc.l1_loss(ref["rgb"], tgt)
     assert abs(res["loss"] - loss_ref) <= 1e-5 * loss_ref
@@ -135,6 +139,8 @@ def test_tiny_scenes_against_brute_force(gsp_lib, seed):
     res = gpu_render(gsp_lib, g, [cam], edges=[e])
     ref = orc.render(g, cam, edge=e, brute=True)
     check_image(res, [ref], [cam])
+    ex = ref["gate_gap"] < GATE_REL
+    assert abs(res["contrib"] - int(ref["ncontrib"].sum())) <= int(ref["ncontrib"][ex].sum()) + int(ex.sum())
     check_scores(res["score"], ref["score"], exempt_gaussians(g, cam, ref))
 
 
