@@ -185,13 +185,17 @@ def _reorder(order_all: np.ndarray, keys: np.ndarray, i: int, new_key: float, va
     return np.insert(o, pos, i)
 
 
-def fd_grad(g: dict, cam: dict, target_u8: np.ndarray, items, rel_h: float = 1e-5, proj=None):
+def fd_grad(g: dict, cam: dict, target_u8: np.ndarray, items, rel_h: float = 1e-5, proj=None,
+            loss_mask=None):
     """Central finite differences of the L1 loss for (index, name, component) items.
 
     The loss change caused by one Gaussian is confined to its footprint, so
     only the pixels of the union of the footprints at theta, theta +- h are
     re-composited, with the compositing order of the other Gaussians kept, and
     the loss difference is summed per pixel (unchanged pixels cancel exactly).
+    loss_mask (H x W bool, optional) restricts the loss sum to those pixels
+    (same normalisation 1 / (3 H W)); only the footprint pixels inside the
+    mask's bounding box are then re-composited.
     Returns (fd(h), fd(h/2)) arrays; entries where the two disagree sit on a
     kink (L1 sign flip, alpha clamp or gate, depth swap).
     """
@@ -204,6 +208,10 @@ def fd_grad(g: dict, cam: dict, target_u8: np.ndarray, items, rel_h: float = 1e-
     keys = proj[:, P_ZKEY].astype(np.float32)
     t = target_u8.astype(np.float64) / 255.0
     npix3 = w * h * 3
+    box = None
+    if loss_mask is not None:
+        ys, xs = np.nonzero(loss_mask)
+        box = (int(xs.min()), int(ys.min()), int(xs.max()) + 1, int(ys.max()) + 1) if ys.size else (0, 0, 0, 0)
     res = []
     for step_scale in (1.0, 0.5):
         vals = []
@@ -219,6 +227,9 @@ def fd_grad(g: dict, cam: dict, target_u8: np.ndarray, items, rel_h: float = 1e-
                 recs.append(project(one, cam)[0])
             region = _union(_union(_footprint(proj[i], w, h), _footprint(recs[0], w, h)),
                             _footprint(recs[1], w, h))
+            if region is not None and box is not None:
+                region = (max(region[0], box[0]), max(region[1], box[1]), min(region[2], box[2]),
+                          min(region[3], box[3]))
             if region is None or region[0] >= region[2] or region[1] >= region[3]:
                 vals.append(0.0)
                 continue
@@ -234,7 +245,10 @@ def fd_grad(g: dict, cam: dict, target_u8: np.ndarray, items, rel_h: float = 1e-
             proj[i], keys[i] = saved, saved_key
             # difference per pixel first: pixels the step leaves alone give exact zeros
             tt = t[y0:y1, x0:x1]
-            dl = (np.abs(losses[0] - tt) - np.abs(losses[1] - tt)).sum()
+            dpix = np.abs(losses[0] - tt) - np.abs(losses[1] - tt)
+            if loss_mask is not None:
+                dpix = dpix * loss_mask[y0:y1, x0:x1, None]
+            dl = dpix.sum()
             vals.append(dl / (2.0 * hh) / npix3)
         res.append(np.array(vals))
     return res[0], res[1]

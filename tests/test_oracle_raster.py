@@ -207,6 +207,32 @@ def test_adjoint_matches_central_differences():
         assert err[sel & ~kink].max() < 1e-4, name
 
 
+def test_masked_loss_differences_match_masked_adjoint():
+    """fd_grad with a loss mask differentiates the L1 loss summed over the mask
+    only: it must equal the adjoint of dL/dC zeroed outside the mask, and a
+    full mask must give exactly the unmasked differences."""
+    g, cam, tgt = _fd_scene()
+    out = orc.render(g, cam)
+    _, dldc = orc.l1_loss(out["rgb"], tgt)
+    mask = np.zeros((40, 48), bool)
+    mask[9:27, 13:37] = True
+    gr = orc.render_bwd(g, cam, dldc * mask[:, :, None])
+    items = [(i, name, c) for i in range(0, 40, 3) for name, c in
+             (("means", 0), ("means", 2), ("log_scales", 1), ("quats", 0), ("opacity_logits", 0), ("sh", 0),
+              ("sh", 47))]
+    fd1, fd2 = orc.fd_grad(g, cam, tgt, items, loss_mask=mask)
+    an = np.array([gr[n][i].ravel()[c] if gr[n].ndim > 1 else gr[n][i] for (i, n, c) in items])
+    kink = np.abs(fd1 - fd2) > 0.1 * np.maximum(np.abs(fd1), 1e-12)
+    assert kink.sum() <= 2
+    rms = np.sqrt(np.mean(an ** 2))
+    assert rms > 0 and np.count_nonzero(an) > len(items) // 2
+    err = np.abs(an - fd1) / np.maximum(np.abs(fd1), 1e-3 * rms)
+    assert err[~kink].max() < 1e-4
+    full = orc.fd_grad(g, cam, tgt, items[:6], loss_mask=np.ones((40, 48), bool))
+    plain = orc.fd_grad(g, cam, tgt, items[:6])
+    np.testing.assert_array_equal(full[0], plain[0])
+
+
 def test_l1_loss_sign_of_zero_is_zero():
     rgb = np.array([[[0.0, 1.0, 128 / 255.0]]])
     tgt = np.array([[[0, 0, 128]]], dtype=np.uint8)
