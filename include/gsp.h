@@ -161,8 +161,19 @@ typedef struct gsp_camera {
 } gsp_camera;
 
 typedef struct gsp_render_opts {
-    int64_t pair_capacity; /* maximum tile-Gaussian pairs summed over views (>= 1) */
+    int64_t pair_capacity; /* maximum tile-Gaussian pairs summed over views (>= 1, < 2^32); the
+                              supertile entries of the binning (one per Gaussian, view and 8x8-tile
+                              block its tile rectangle touches) share the same bound */
+    int32_t fwd_variant;   /* forward compositing variant, 0 .. GSP_FWD_VARIANTS - 1 (0: default) */
+    int32_t bwd_variant;   /* adjoint compositing variant, 0 .. GSP_BWD_VARIANTS - 1 (0: default) */
 } gsp_render_opts;
+
+/* Compositing variants (pixels per thread, Gaussians staged per shared-memory batch).
+ * The results do not depend on the variant, only the speed does; an autotuner picks
+ * one per workload.  Forward: (1, 256), (2, 256), (1, 128), (2, 128).
+ * Adjoint: (2, 256), (1, 256), (4, 256), (2, 128). */
+#define GSP_FWD_VARIANTS 4
+#define GSP_BWD_VARIANTS 4
 
 /* Workspace bytes for a fwd/bwd pair over these cameras (host array). */
 size_t gsp_render_workspace_size(int64_t capacity, int32_t sh_degree, const gsp_camera *cams,
@@ -209,7 +220,9 @@ const int64_t *gsp_render_pair_count_ptr(const void *workspace, int64_t capacity
  *            them, accumulate == 0 overwrites rows [0, N)
  * score      device float [capacity] += edge score, or NULL (needs edge != NULL);
  *            lets a caller fuse the score into the backward pass instead of the forward
- * workspace  the workspace of the matching gsp_render_fwd (same sizes)
+ * workspace  the workspace of the matching gsp_render_fwd (same sizes); the adjoint may be
+ *            called any number of times after one forward pass (each call starts its
+ *            screen-space sums from zero)
  */
 gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *cams, int32_t num_views,
                           const gsp_image_desc *targets, const float *dL_drgb, const float *rgb,

@@ -18,6 +18,7 @@ GSP_MAX_VIEWS = 64
 GSP_TILE = 16
 GSP_EDGE_FUSED, GSP_EDGE_PLAIN = 0, 1
 GSP_TOPK_STATIC_MAX_CAPACITY = 1 << 24
+GSP_FWD_VARIANTS, GSP_BWD_VARIANTS = 4, 4
 
 
 class ImageDesc(ctypes.Structure):
@@ -41,7 +42,7 @@ class Camera(ctypes.Structure):
 
 
 class RenderOpts(ctypes.Structure):
-    _fields_ = [("pair_capacity", c_i64)]
+    _fields_ = [("pair_capacity", c_i64), ("fwd_variant", c_i32), ("bwd_variant", c_i32)]
 
 
 class LasParams(ctypes.Structure):

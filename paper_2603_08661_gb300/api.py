@@ -170,7 +170,7 @@ class Renderer:
     """Workspace and camera set of one gsp_render_fwd / gsp_render_bwd pairing."""
 
     def __init__(self, gs: GaussianSet, cams: list, pair_capacity: int, device="cuda",
-                 workspace: torch.Tensor | None = None):
+                 workspace: torch.Tensor | None = None, variants: tuple[int, int] = (0, 0)):
         self.gs = gs
         self.nv = len(cams)
         self.cams = (L.Camera * self.nv)()
@@ -181,7 +181,7 @@ class Renderer:
             self.offsets.append(off)
             off += int(c["width"]) * int(c["height"])
         self.total_pix = off
-        self.opts = L.RenderOpts(int(pair_capacity))
+        self.opts = L.RenderOpts(int(pair_capacity), int(variants[0]), int(variants[1]))
         self.ws_bytes = lib().gsp_render_workspace_size(gs.capacity, gs.sh_degree, self.cams, self.nv,
                                                         ctypes.byref(self.opts))
         if self.ws_bytes == 0:
@@ -191,6 +191,14 @@ class Renderer:
         else:
             self.ws = _workspace(self.ws_bytes, device)
         self.device = device
+
+    @property
+    def variants(self) -> tuple[int, int]:
+        return int(self.opts.fwd_variant), int(self.opts.bwd_variant)
+
+    @variants.setter
+    def variants(self, v: tuple[int, int]):
+        self.opts.fwd_variant, self.opts.bwd_variant = int(v[0]), int(v[1])
 
     def stats(self) -> torch.Tensor:
         """Device int64[2] of the last forward: tile-Gaussian pairs, composited pairs."""

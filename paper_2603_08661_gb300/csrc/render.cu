@@ -35,9 +35,6 @@ constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 constexpr float kNear = 0.2f;
 constexpr int kRowCap = 16;  // tile rows per Gaussian with an exact column interval
-// pixels per compositing thread (a vertical run): measured best at 1 for the
-// forward and 2 for the adjoint (fewer warp reductions per pixel)
-constexpr int kFwdPixPerThread = 1, kBwdPixPerThread = 2;
 
 struct ViewP {
     float vm[12];
@@ -76,10 +73,10 @@ struct State {
     uint2 *rect;   // [V][cap] (tx0 | ty0 << 16, tx1 | ty1 << 16); empty if tx1 < tx0
     uchar2 *rowint;  // [V][cap][kRowCap] per tile row of the rectangle: columns (lo, hi) - tx0 the
                      // 1/255 ellipse reaches (lo > hi: none); rows past kRowCap are not culled
-    uint32_t *key, *key_alt;  // depth keys [V][cap], sort scratch [cap]
-    int32_t *val, *val_alt;   // depth-ordered ids [V][cap], sort scratch [cap]
-    unsigned *sort_hist;      // [256][nb_max]
-    unsigned *sort_tot;       // [256]
+    uint32_t *key, *key_alt;  // depth keys [V][cap], sort scratch [V][cap]
+    int32_t *val, *val_alt;   // depth-ordered ids [V][cap], sort scratch [V][cap]
+    unsigned *sort_hist;      // [V][256][nb_max]
+    unsigned *sort_tot;       // [V][256]
     unsigned *count1;         // [total_super][nch1_max] level-1 chunk counts, then offsets
     unsigned *len1;           // [total_super] supertile list lengths
     unsigned *list1_start;    // [total_super] supertile list starts in id1
@@ -259,9 +256,6 @@ __device__ __forceinline__ unsigned long long project_one(const Views &vs, const
     const long long cap = p.cap;
     for (int v = 0; v < vs.n; ++v) {
         st.val[v * cap + i] = int32_t(i);
-        st.g2d[(v * cap + i) * 3 + 0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        st.g2d[(v * cap + i) * 3 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        st.g2d[(v * cap + i) * 3 + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (i >= n) return 0;
     float mu[3] = {p.means[3 * i], p.means[3 * i + 1], p.means[3 * i + 2]};
@@ -401,9 +395,12 @@ struct SortCount {
 
 template <typename K>
 __global__ void __launch_bounds__(kRsThreads) rs_hist(const K *keys, SortCount cnt, int shift, int bits,
-                                                      unsigned *bhist, int nb_max)
+                                                      unsigned *bhist, int nb_max, long long seg)
 {
     __shared__ unsigned h[256];
+    // blockIdx.y: the segment (view); its keys start at y * seg, its counts at y * 256 * nb_max
+    keys += (size_t)blockIdx.y * seg;
+    bhist += (size_t)blockIdx.y * 256 * nb_max;
     if (cnt.skipped()) return;
     const long long n = cnt.get();
     const long long b0 = (long long)blockIdx.x * kRsTile;
@@ -431,6 +428,8 @@ __global__ void __launch_bounds__(kRsThreads) rs_hist(const K *keys, SortCount c
 // One block per digit: exclusive scan of that digit's block counts.
 __global__ void __launch_bounds__(256) rs_scan(unsigned *bhist, int nb_max, SortCount cnt, unsigned *dtot)
 {
+    bhist += (size_t)blockIdx.y * 256 * nb_max;
+    dtot += (size_t)blockIdx.y * 256;
     __shared__ unsigned wsum[8];
     __shared__ unsigned carry;
     if (cnt.skipped()) return;
@@ -467,8 +466,14 @@ __global__ void __launch_bounds__(256) rs_scan(unsigned *bhist, int nb_max, Sort
 template <typename K>
 __global__ void __launch_bounds__(kRsThreads) rs_scatter(const K *kin, const int32_t *vin, K *kout, int32_t *vout,
                                                          SortCount cnt, int shift, int bits, const unsigned *bhist,
-                                                         int nb_max, const unsigned *dtot)
+                                                         int nb_max, const unsigned *dtot, long long seg)
 {
+    kin += (size_t)blockIdx.y * seg;
+    vin += (size_t)blockIdx.y * seg;
+    kout += (size_t)blockIdx.y * seg;
+    vout += (size_t)blockIdx.y * seg;
+    bhist += (size_t)blockIdx.y * 256 * nb_max;
+    dtot += (size_t)blockIdx.y * 256;
     __shared__ unsigned gbase[256], lstart[256];
     __shared__ unsigned wh[kRsWarps][256];
     __shared__ unsigned wsum[kRsWarps];
@@ -1126,18 +1131,17 @@ __device__ __forceinline__ float target_value(const ViewP &V, int x, int y, int 
 
 // Forward compositing: one block per 16x16 tile, each thread a vertical run
 // of PPT pixels.  The tile's list is staged through shared memory in batches
-// of kBatch Gaussians; the block leaves when every pixel has stopped.
-constexpr int kBatch = 256;
+// of BATCH Gaussians; the block leaves when every pixel has stopped.
 
-template <int PPT>
+template <int PPT, int BATCH>
 __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_constant__ Views vs, State st,
                                                                 long long cap, const float *edge, float *rgb_out,
                                                                 float *T_out, int32_t *last_out, float *score)
 {
     constexpr int NT = kTilePix / PPT;
-    __shared__ float4 s_xyo[kBatch], s_con[kBatch], s_col[kBatch];
-    __shared__ int32_t s_id[kBatch];
-    __shared__ float s_score[kBatch];
+    __shared__ float4 s_xyo[BATCH], s_con[BATCH], s_col[BATCH];
+    __shared__ int32_t s_id[BATCH];
+    __shared__ float s_score[BATCH];
     __shared__ float s_red[NT / 32];
     __shared__ unsigned s_maxlast;
     __shared__ unsigned long long s_contrib;
@@ -1176,12 +1180,12 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
         done[m] = !inside;
         E[m] = (edge && inside) ? edge[V.pix_off + (long long)y * V.w + x] : 0.f;
     }
-    for (int b = 0; b < len; b += kBatch) {
+    for (int b = 0; b < len; b += BATCH) {
         bool all = true;
 #pragma unroll
         for (int m = 0; m < PPT; ++m) all = all && done[m];
         if (__syncthreads_count(all) == NT) break;
-        for (int q = tid; q < kBatch; q += NT) {
+        for (int q = tid; q < BATCH; q += NT) {
             const int k = b + q;
             if (k < len) {
                 const int id = list[k];
@@ -1193,7 +1197,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
             if (score) s_score[q] = 0.f;
         }
         __syncthreads();
-        const int cnt = min(kBatch, len - b);
+        const int cnt = min(BATCH, len - b);
         for (int j = 0; j < cnt; ++j) {
             const float4 gx = s_xyo[j], gc = s_con[j];
             // the footprint's bounding box misses every pixel of the warp (warp-uniform)
@@ -1344,16 +1348,16 @@ constexpr int kG2 = 10;  // mean x, mean y, conic A, B, C, opacity, r, g, b, sco
 // Gaussian the thread sums its pixels' contributions, the warp reduces them
 // (transpose reduction), warps meet in shared accumulators, and one global
 // atomic per (Gaussian, tile, value) leaves the block.
-template <int PPT>
+template <int PPT, int BATCH>
 __global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) composite_bwd(const __grid_constant__ Views vs, State st,
                                                                 long long cap, const float *dL_drgb, const float *rgb,
                                                                 const float *T_fin, const int32_t *last_idx,
                                                                 const float *edge, float *score, float inv_norm)
 {
     constexpr int NT = kTilePix / PPT;
-    __shared__ float4 s_xyo[kBatch], s_con[kBatch], s_col[kBatch];
-    __shared__ int32_t s_id[kBatch];
-    __shared__ float s_acc[kBatch][kG2];
+    __shared__ float4 s_xyo[BATCH], s_con[BATCH], s_col[BATCH];
+    __shared__ int32_t s_id[BATCH];
+    __shared__ float s_acc[BATCH][kG2];
     __shared__ int s_maxlast;
     if (*st.overflow) return;
     const int gt = st.order_bwd[blockIdx.x];
@@ -1405,15 +1409,15 @@ __global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) c
         }
     }
     if (tid == 0) s_maxlast = 0;
-    for (int k = tid; k < kBatch * kG2; k += NT) (&s_acc[0][0])[k] = 0.f;
+    for (int k = tid; k < BATCH * kG2; k += NT) (&s_acc[0][0])[k] = 0.f;
     __syncthreads();
     atomicMax(&s_maxlast, mylast);
     __syncthreads();
     const int maxlast = s_maxlast;
     const int wlast = int(__reduce_max_sync(0xffffffffu, unsigned(mylast)));  // the warp's last position
 
-    for (int hi = maxlast; hi > 0; hi -= kBatch) {
-        const int lo = max(hi - kBatch, 0);
+    for (int hi = maxlast; hi > 0; hi -= BATCH) {
+        const int lo = max(hi - BATCH, 0);
         const int cnt = hi - lo;
         for (int q = tid; q < cnt; q += NT) {
             const int id = list[lo + q];
@@ -1440,7 +1444,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) c
                 active = true;
                 const float4 c = s_col[j];
                 const float one_m = __fsub_rn(1.f, a.alpha);
-                T[m] = __fdividef(T[m], one_m);
+                T[m] = __fdiv_rn(T[m], one_m);
                 const float w = a.alpha * T[m];
                 val[6] += w * g0[m];
                 val[7] += w * g1[m];
@@ -1652,6 +1656,31 @@ __global__ void __launch_bounds__(128) project_bwd(const __grid_constant__ Views
     }
 }
 
+// Compositing variants (pixels per thread, batch depth); index 0 is the default.
+// gsp_render_opts selects one per pass; the autotuner times them on the workload.
+struct Variant {
+    int ppt, batch;
+};
+constexpr Variant kFwdVariants[] = {{1, 256}, {2, 256}, {1, 128}, {2, 128}};
+constexpr Variant kBwdVariants[] = {{2, 256}, {1, 256}, {4, 256}, {2, 128}};
+constexpr int kNumFwdVariants = sizeof(kFwdVariants) / sizeof(Variant);
+constexpr int kNumBwdVariants = sizeof(kBwdVariants) / sizeof(Variant);
+
+template <int PPT, int BATCH>
+void launch_fwd(const Views &vs, const State &S, long long cap, const float *edge, float *rgb, float *T, int32_t *last,
+                float *score, cudaStream_t s)
+{
+    composite_fwd<PPT, BATCH><<<vs.total_tiles, kTilePix / PPT, 0, s>>>(vs, S, cap, edge, rgb, T, last, score);
+}
+
+template <int PPT, int BATCH>
+void launch_bwd(const Views &vs, const State &S, long long cap, const float *dL, const float *rgb, const float *T,
+                const int32_t *last, const float *edge, float *score, float inv_norm, cudaStream_t s)
+{
+    composite_bwd<PPT, BATCH><<<vs.total_tiles, kTilePix / PPT, 0, s>>>(vs, S, cap, dL, rgb, T, last, edge, score,
+                                                                       inv_norm);
+}
+
 // ------------------------------------------------------------------- host
 
 constexpr int kCounters = 4;
@@ -1674,12 +1703,12 @@ Layout render_layout(void *ws, long long cap, const Views &vs, long long pair_ca
     s.rect = c.take<uint2>(vc);
     s.rowint = c.take<uchar2>(vc * kRowCap);
     s.key = c.take<uint32_t>(vc);
-    s.key_alt = c.take<uint32_t>((size_t)cap);
+    s.key_alt = c.take<uint32_t>(vc);
     s.val = c.take<int32_t>(vc);
-    s.val_alt = c.take<int32_t>((size_t)cap);
+    s.val_alt = c.take<int32_t>(vc);
     s.nb_max = int(div_up(cap, kRsTile));
-    s.sort_hist = c.take<unsigned>((size_t)256 * s.nb_max);
-    s.sort_tot = c.take<unsigned>(256);
+    s.sort_hist = c.take<unsigned>((size_t)vs.n * 256 * s.nb_max);
+    s.sort_tot = c.take<unsigned>((size_t)vs.n * 256);
     s.nch1_max = int(div_up(cap, kBinRanks));
     s.count1 = c.take<unsigned>(total_super * s.nch1_max);
     s.len1 = c.take<unsigned>(total_super);
@@ -1817,6 +1846,9 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     if (score && !edge) return GSP_ERR_INVALID_ARG;
     if (loss_out && !targets) return GSP_ERR_INVALID_ARG;
     if (opts->pair_capacity > 0xffffffffLL) return GSP_ERR_UNSUPPORTED;  // 32-bit list positions
+    if (opts->fwd_variant < 0 || opts->fwd_variant >= kNumFwdVariants || opts->bwd_variant < 0 ||
+        opts->bwd_variant >= kNumBwdVariants)
+        return GSP_ERR_INVALID_ARG;
     const long long cap = g->capacity;
     Layout L = render_layout(nullptr, cap, vs, opts->pair_capacity);
     st = check_workspace(ws, ws_bytes, L.bytes);
@@ -1838,16 +1870,18 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     stage_end("project", s);
     GSP_LAUNCH_CHECK();
     stage_begin("depth_sort", s);
-    // depth sort, per view (4 passes of 8 bits; an even count leaves the result in key/val)
-    for (int v = 0; v < nv; ++v) {
-        uint32_t *k0 = S.key + (size_t)v * cap, *k1 = S.key_alt;
-        int32_t *v0 = S.val + (size_t)v * cap, *v1 = S.val_alt;
+    // depth sort of every view at once (blockIdx.y = view): 4 stable passes of 8 bits;
+    // an even count leaves the result in key/val
+    {
+        uint32_t *k0 = S.key, *k1 = S.key_alt;
+        int32_t *v0 = S.val, *v1 = S.val_alt;
         const SortCount sc{g->count, nullptr, nullptr};
+        const dim3 gb(S.nb_max, nv), gs(256, nv);
         for (int pass = 0; pass < 4; ++pass) {
-            rs_hist<uint32_t><<<S.nb_max, kRsThreads, 0, s>>>(k0, sc, 8 * pass, 8, S.sort_hist, S.nb_max);
-            rs_scan<<<256, 256, 0, s>>>(S.sort_hist, S.nb_max, sc, S.sort_tot);
-            rs_scatter<uint32_t><<<S.nb_max, kRsThreads, 0, s>>>(k0, v0, k1, v1, sc, 8 * pass, 8, S.sort_hist,
-                                                                 S.nb_max, S.sort_tot);
+            rs_hist<uint32_t><<<gb, kRsThreads, 0, s>>>(k0, sc, 8 * pass, 8, S.sort_hist, S.nb_max, cap);
+            rs_scan<<<gs, 256, 0, s>>>(S.sort_hist, S.nb_max, sc, S.sort_tot);
+            rs_scatter<uint32_t><<<gb, kRsThreads, 0, s>>>(k0, v0, k1, v1, sc, 8 * pass, 8, S.sort_hist, S.nb_max,
+                                                           S.sort_tot, cap);
             uint32_t *tk = k0; k0 = k1; k1 = tk;
             int32_t *tv = v0; v0 = v1; v1 = tv;
         }
@@ -1872,11 +1906,15 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     stage_end("bin", s);
     GSP_LAUNCH_CHECK();
     stage_begin("composite_fwd", s);
-    composite_fwd<kFwdPixPerThread><<<vs.total_tiles, kTilePix / kFwdPixPerThread, 0, s>>>(
-        vs, S, cap, edge, rgb_out, T_final, last_idx, score);
+    switch (opts->fwd_variant) {
+    case 1: launch_fwd<kFwdVariants[1].ppt, kFwdVariants[1].batch>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
+    case 2: launch_fwd<kFwdVariants[2].ppt, kFwdVariants[2].batch>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
+    case 3: launch_fwd<kFwdVariants[3].ppt, kFwdVariants[3].batch>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
+    default: launch_fwd<kFwdVariants[0].ppt, kFwdVariants[0].batch>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
+    }
     stage_end("composite_fwd", s);
     GSP_LAUNCH_CHECK();
-    note_launches(2 + 12 * nv + 8 + 1);
+    note_launches(2 + 12 + 8 + 1);
     if (loss_out) {
         loss_finalise<<<1, 1, 0, s>>>(S, vs.total_pix, loss_out);
         note_launches(1);
@@ -1902,6 +1940,7 @@ extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *c
         !grad_opacity_logits || !grad_sh)
         return GSP_ERR_INVALID_ARG;
     if (!dL_drgb && (!targets || !rgb)) return GSP_ERR_INVALID_ARG;
+    if (opts->bwd_variant < 0 || opts->bwd_variant >= kNumBwdVariants) return GSP_ERR_INVALID_ARG;
     if (score && !edge) return GSP_ERR_INVALID_ARG;
     const long long cap = g->capacity;
     Layout L = render_layout(nullptr, cap, vs, opts->pair_capacity);
@@ -1914,9 +1953,15 @@ extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *c
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const float inv_norm = float(1.0 / (3.0 * double(vs.total_pix)));
     stage_begin("composite_bwd", s);
+    // the screen-space gradients accumulate from zero in every adjoint call
+    GSP_CUDA_TRY(cudaMemsetAsync(S.g2d, 0, sizeof(float4) * 3 * (size_t)nv * cap, s));
     tile_order_bwd<<<1, 1024, 0, s>>>(vs.total_tiles, S);
-    composite_bwd<kBwdPixPerThread><<<vs.total_tiles, kTilePix / kBwdPixPerThread, 0, s>>>(
-        vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm);
+    switch (opts->bwd_variant) {
+    case 1: launch_bwd<kBwdVariants[1].ppt, kBwdVariants[1].batch>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
+    case 2: launch_bwd<kBwdVariants[2].ppt, kBwdVariants[2].batch>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
+    case 3: launch_bwd<kBwdVariants[3].ppt, kBwdVariants[3].batch>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
+    default: launch_bwd<kBwdVariants[0].ppt, kBwdVariants[0].batch>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
+    }
     stage_end("composite_bwd", s);
     GSP_LAUNCH_CHECK();
     stage_begin("project_bwd", s);
@@ -1931,7 +1976,7 @@ extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *c
     }
 #undef GSP_PBWD
     stage_end("project_bwd", s);
-    note_launches(3);
+    note_launches(4);
     GSP_LAUNCH_CHECK();
     return GSP_OK;
 }

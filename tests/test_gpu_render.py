@@ -3,7 +3,8 @@
 Tolerances: rendered RGB and T_final within 1e-4 absolute; per-Gaussian edge
 scores within 1e-4 relative; gradients within 1e-4 relative of the oracle's
 analytic adjoint (floor 1e-2 x the RMS of the parameter group: FP32 sums over
-thousands of pixel contributions carry ~1e-6 x RMS of rounding) and 1e-3
+thousands of pixel contributions carry ~1e-6 x RMS of rounding; means,
+log-scales and quaternions compared per Gaussian as vectors, conftest.grad_rel) and 1e-3
 relative of its central finite differences (floor 1e-3 x RMS).  Pixels whose oracle
 evaluation passes a gate (alpha = 1/255, T (1 - alpha) = 1e-4) within
 GATE_REL relative are exempt and counted; so are the Gaussians composited
@@ -15,6 +16,7 @@ import numpy as np
 import pytest
 
 import synth
+from conftest import grad_rel
 from oracle import edge as oe
 from oracle import raster as orc
 
@@ -106,8 +108,8 @@ def check_grads(gr_gpu, gr_ref, n, skip=(), tol=1e-4, floor=1e-2):
         rms = np.sqrt(np.mean(b[keep] ** 2)) if keep.any() else 0.0
         if rms == 0:
             continue
-        rel = np.abs(a - b) / np.maximum(np.abs(b), floor * rms)
-        assert rel[keep].max() <= tol, (name, rel[keep].max())
+        rel = grad_rel(name, a[keep], b[keep], floor * rms)
+        assert rel.max() <= tol, (name, rel.max())
 
 
 def test_tiny_config_matches_oracle(gsp_lib):
@@ -237,8 +239,10 @@ def test_l1_sign_map_equals_explicit_upstream_gradient(gsp_lib):
     # exact ties (empty pixels against black) have sign 0 on both paths
     assert ((np.abs(diff) < 1e-6) & (diff != 0)).sum() == 0
     b = gpu_render(gsp_lib, g, [cam], dL=dL)
+    # the two runs sum the same FP32 terms in unspecified (atomic) order
     for name in GROUPS:
-        np.testing.assert_allclose(a["grads"][name], b["grads"][name], rtol=1e-5, atol=1e-12)
+        scale = np.sqrt(np.mean(a["grads"][name] ** 2))
+        np.testing.assert_allclose(a["grads"][name], b["grads"][name], rtol=1e-5, atol=1e-6 * scale)
 
 
 def test_score_in_backward_equals_score_in_forward(gsp_lib):
