@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--gaussians", type=int, default=N_GAUSS)
+    ap.add_argument("--no-extra", action="store_true", help="skip the multi-view and densification-loop legs")
     return ap.parse_args()
 
 
@@ -413,6 +414,151 @@ def run_gsp(args, rank, world):
     return line
 
 
+# ------------------------------------------------- extra workloads (same run)
+
+def _probe_pairs(gsp, gs, cams):
+    """Tile-Gaussian pairs of the scene (a small probe: the count is exact even
+    beyond the probe's capacity)."""
+    import torch
+    probe = gsp.Renderer(gs, cams, pair_capacity=1 << 20)
+    probe.forward()
+    torch.cuda.synchronize()
+    pairs = int(probe.pair_count().item())
+    del probe
+    torch.cuda.empty_cache()
+    return pairs
+
+
+def _event_ms(fn, reps):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_multiview(steps=5, warmup=3):
+    """3M SH-3 Gaussians, 8 ring views of uneven resolution: forward + L1 +
+    adjoint with the edge score, all views in one call per pass, captured as a
+    CUDA graph with autotuned compositing variants, against the plain path
+    (one call per view and pass, default variants, no graph)."""
+    import torch
+
+    import paper_2603_08661_gb300 as gsp
+    import synth
+    n, nv = 3_000_000, 8
+    g = synth.gaussians(n, 3, seed=1)
+    cams = [synth.camera_ring(k, nv) for k in range(nv)]
+    gs = gsp.GaussianSet.from_arrays(g, capacity=n)
+    del g
+    targets = [gsp.pitched_image(torch.from_numpy(synth.image(c["height"], c["width"], 2000 + k)).cuda(), 16)
+               for k, c in enumerate(cams)]
+    E, _, _, st = gsp.edge_map(targets)
+    pairs = _probe_pairs(gsp, gs, cams)
+    r = gsp.Renderer(gs, cams, pair_capacity=int(pairs * 1.02) + 4096)
+    variants = gsp.autotune.tune(r, targets=targets)
+    score = torch.zeros(n, device="cuda")
+    grads = {k: torch.zeros_like(getattr(gs, k)) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    npix = r.total_pix
+    bufs = {"rgb": torch.empty((npix, 3), device="cuda"), "T": torch.empty(npix, device="cuda"),
+            "last": torch.empty(npix, dtype=torch.int32, device="cuda"), "loss": torch.empty(1, device="cuda")}
+    status = gsp.new_status()
+
+    def it():
+        out = r.forward(targets=targets, status=status, out=bufs)
+        r.backward(out, targets=targets, edge=E, score=score, grads=grads, status=status)
+
+    it()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            it()
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(warmup):
+        graph.replay()
+    ms_graph = _event_ms(graph.replay, steps)
+    torch.cuda.synchronize()
+    gsp.raise_on_device_status(status, "multiview")
+    # plain path: one single-view call per view and pass, default variants, eager
+    del r
+    torch.cuda.empty_cache()
+    per_view = []
+    big = 0
+    for k, c in enumerate(cams):
+        pv = _probe_pairs(gsp, gs, [c])
+        big = max(big, pv)
+    ws = None
+    for k, c in enumerate(cams):
+        rv = gsp.Renderer(gs, [c], pair_capacity=int(big * 1.02) + 4096, workspace=ws)
+        ws = rv.ws
+        per_view.append(rv)
+    offs = [0]
+    for c in cams:
+        offs.append(offs[-1] + c["width"] * c["height"])
+    Ev = [E[offs[k]:offs[k + 1]] for k in range(nv)]
+
+    def it_plain():
+        for k, rv in enumerate(per_view):
+            out = rv.forward(targets=[targets[k]], status=status)
+            rv.backward(out, targets=[targets[k]], edge=Ev[k], score=score, grads=grads, status=status,
+                        accumulate=k > 0)
+
+    for _ in range(warmup):
+        it_plain()
+    ms_plain = _event_ms(it_plain, steps)
+    torch.cuda.synchronize()
+    gsp.raise_on_device_status(status, "multiview plain")
+    return {"workload": "3M Gaussians SH3, 8 ring views 640x480..1920x1080 (8.76 Mpix): fwd + L1 + bwd + edge score",
+            "pairs": pairs, "variants": list(variants), "ms_per_iter_batched_graph": round(ms_graph, 3),
+            "ms_per_iter_plain_per_view": round(ms_plain, 3), "mpix_per_s_batched": round(npix / ms_graph / 1e3, 1),
+            "steps": steps}
+
+
+def run_densify_loop(iterations=200, warmup=3):
+    """500K -> 1M Gaussians (SH degree 0, as the tiny configuration) on 4 ring
+    views of 1237x822: 200 graph-replayed iterations of fwd + L1 + bwd with the
+    edge score + SGD (lr 1e-3), a top-k (50K) + LAS event every 20."""
+    import torch
+
+    import paper_2603_08661_gb300 as gsp
+    import synth
+    n0, cap, nv = 500_000, 1_000_000, 4
+    g = synth.gaussians(n0, 0, seed=1)
+    cams = [synth.camera_ring(k, nv, resolutions=[(WIDTH, HEIGHT)]) for k in range(nv)]
+    gs = gsp.GaussianSet.from_arrays(g, capacity=cap)
+    targets = [gsp.pitched_image(torch.from_numpy(synth.image(HEIGHT, WIDTH, 2000 + k)).cuda(), 16)
+               for k in range(nv)]
+    pairs0 = _probe_pairs(gsp, gs, cams)
+    loop = gsp.DensifyLoop(gs, cams, targets, lr=1e-3, every=20, k_event=50_000,
+                           pair_capacity=int(pairs0 * 2.5) + 4096)
+    saved = {k: getattr(gs, k).clone() for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "count")}
+    loop.capture()
+    loop.run(warmup)
+    torch.cuda.synchronize()
+    for k, v in saved.items():
+        getattr(gs, k).copy_(v)
+    loop.score.zero_()
+    loop.iteration_count = 0
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    loop.run(iterations)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    gsp.raise_on_device_status(loop.status, "densify loop")
+    return {"workload": "500K -> 1M Gaussians SH0, 4 ring views 1237x822, 200 iterations, top-k 50K + LAS every 20",
+            "iterations": iterations, "total_ms": round(ms, 2), "ms_per_iter": round(ms / iterations, 4),
+            "final_gaussians": int(gs.count.item()), "pairs_at_start": pairs0,
+            "loss_last": round(float(loop.loss().item()), 6)}
+
+
 # --------------------------------------------------------------- oracle
 
 def cpu_baseline(g, cam, tgt_np, budget_s=20.0, region=None):
@@ -524,6 +670,12 @@ def main():
         line = run_reference(args, rank, world)
     else:
         line = run_gsp(args, rank, world)
+        if world == 1 and not args.no_extra:
+            import torch
+            torch.cuda.empty_cache()
+            line["multiview"] = run_multiview()
+            torch.cuda.empty_cache()
+            line["densify_loop"] = run_densify_loop()
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:

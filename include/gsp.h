@@ -62,7 +62,7 @@ int32_t gsp_version(void);
  * once, at capture).
  * gsp_stage_timer_arm: from now on, every occurrence of the named stage
  * ("edge_fused", "edge_plain", "project", "depth_sort", "bin", "composite_fwd",
- * "composite_bwd", "project_bwd", "topk", "las"; NULL disarms) is bracketed by
+ * "composite_bwd", "project_bwd", "topk", "las", "sgd"; NULL disarms) is bracketed by
  * a pair of CUDA events recorded on the caller's stream, up to max_records
  * occurrences; re-arming discards earlier records.
  * gsp_stage_timer_read: waits for the recorded events and returns the summed
@@ -301,6 +301,21 @@ gsp_status gsp_topk_mask_static(const float *scores, const int32_t *count, int64
 gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask, const float *scores,
                          int64_t k, const gsp_las_params *p, void *workspace,
                          size_t workspace_bytes, int32_t *dev_status, gsp_stream_t stream);
+
+/* ======================================================================
+ * Optimiser step of the densification loop (the paper does not state its
+ * optimiser; the workloads use plain SGD).
+ * ==================================================================== */
+
+/*
+ * theta <- theta - lr * grad on rows [0, N) (device count) of every parameter
+ * group, computed as one FMA per element (fma(-lr, grad, theta)); rows >= N
+ * are not touched.  grad_* are device buffers shaped like the parameters.
+ * One launch, asynchronous on the caller's stream.
+ */
+gsp_status gsp_sgd_step(const gsp_gaussians *g, float *grad_means, float *grad_log_scales,
+                        float *grad_quats, float *grad_opacity_logits, float *grad_sh, float lr,
+                        gsp_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -8,6 +8,7 @@ The compute lives in libgsp.so (C ABI, include/gsp.h), built for sm_103a by
 * topk_mask, las_split - Sec. 2.2 selection and Long-Axis-Split (Alg. 1-2)
 * GaussianRenderL1    - torch.autograd.Function over the forward / adjoint
 * autotune.tune       - picks the fastest compositing variants for a workload
+* DensifyLoop         - device-resident loop: fwd/L1/bwd+score/SGD, top-k + LAS events
 
 Importing fails loudly when libgsp.so is missing; there is no CPU fallback.
 """
@@ -20,3 +21,4 @@ from .api import (LAS_CONFIG, LAS_PAPER, GaussianSet, Renderer, StageTimer, came
                   raise_on_device_status, topk_mask)
 from .autograd import GaussianRenderL1  # noqa: E402,F401
 from . import autotune  # noqa: E402,F401
+from .loop import DensifyLoop  # noqa: E402,F401

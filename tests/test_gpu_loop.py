@@ -1,0 +1,116 @@
+"""The device-resident densification loop, scaled down: 4 views, 4,000 -> 6,000
+Gaussians in 4 events of 500 every 5 iterations, SGD with lr 1e-3.
+
+* The first iteration's gradients (L1 loss over all pixels of the 4 views)
+  match the oracle's analytic adjoint (sums over views: 1e-4 for all but
+  max(2, 0.1 %) of the Gaussians, 1e-3 for all), and the SGD step is one FMA
+  per element.
+* A densification event equals the oracle's top-k on the accumulated scores
+  (exact) and its Long-Axis-Split of the pre-event state (1e-6).
+* The CUDA-graph driver and the autograd driver agree on an iteration, and
+  the graph driver reaches the budget with the count on the device.
+"""
+import numpy as np
+import pytest
+
+import synth
+from conftest import assert_grads_close
+from oracle import densify as od
+from oracle import raster as orc
+
+pytestmark = pytest.mark.gpu
+
+N0, CAP, K_EVENT, EVERY, LR = 4000, 6000, 500, 5, 1e-3
+W, H, V = 96, 64, 4
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def _make(gsp):
+    import torch
+    g = synth.gaussians(N0, 3, seed=11)
+    g["log_scales"] = (g["log_scales"] + 0.8).astype(np.float32)
+    cams = [synth.camera_ring(k, V, resolutions=[(W, H)]) for k in range(V)]
+    tg = [synth.image(H, W, 2000 + k) for k in range(V)]
+    gs = gsp.GaussianSet.from_arrays(g, capacity=CAP)
+    loop = gsp.DensifyLoop(gs, cams, [torch.from_numpy(t).cuda() for t in tg], lr=LR, every=EVERY,
+                           k_event=K_EVENT, pair_capacity=1 << 22)
+    return g, cams, tg, gs, loop
+
+
+def _host(gs, n):
+    return {k: getattr(gs, k)[:n].cpu().numpy().astype(np.float64) for k in GROUPS}
+
+
+def test_first_iteration_gradients_and_sgd_step(gsp_lib):
+    import torch
+    g, cams, tg, gs, loop = _make(gsp_lib)
+    p0 = {k: getattr(gs, k)[:N0].cpu().numpy() for k in GROUPS}
+    loop.iteration()
+    torch.cuda.synchronize()
+    assert int(loop.status.item()) == 0
+    p1 = {k: getattr(gs, k)[:N0].cpu().numpy() for k in GROUPS}
+    gg = {k: loop.grads[k][:N0].cpu().numpy() for k in GROUPS}
+    # SGD: one FMA per element, fma(-lr, grad, theta) rounded once to FP32
+    for k in GROUPS:
+        ref = (p0[k].astype(np.float64) + np.float64(np.float32(-LR)) * gg[k].astype(np.float64)).astype(np.float32)
+        ulp = np.spacing(np.abs(ref))
+        assert np.all(np.abs(p1[k].astype(np.float64) - ref) <= ulp)
+    # gradients of the L1 loss (mean over all pixels of all views) against the oracle
+    total = V * W * H
+    ref_g = {k: 0.0 for k in GROUPS}
+    for cam, t in zip(cams, tg):
+        out = orc.render(g, cam)
+        diff = out["rgb"] - t / 255.0
+        assert ((np.abs(diff) < 1e-5) & (diff != 0)).sum() == 0  # no L1 sign is a near-tie
+        gr = orc.render_bwd(g, cam, np.sign(diff) / (3.0 * total))
+        for k in GROUPS:
+            ref_g[k] = ref_g[k] + gr[k].reshape(N0, -1)
+    for k in GROUPS:
+        a = gg[k].reshape(N0, -1).astype(np.float64)
+        b = ref_g[k]
+        rms = np.sqrt(np.mean(b ** 2))
+        assert_grads_close(k, a, b, 1e-2 * rms)
+
+
+def test_event_matches_oracle_topk_and_split(gsp_lib):
+    import torch
+    g, cams, tg, gs, loop = _make(gsp_lib)
+    for _ in range(EVERY):
+        loop.iteration()
+    torch.cuda.synchronize()
+    before = _host(gs, N0)
+    before["sh_degree"] = 3
+    scores = loop.score[:N0].cpu().numpy()
+    loop.event()
+    torch.cuda.synchronize()
+    assert int(loop.status.item()) == 0 and int(gs.count.item()) == N0 + K_EVENT
+    mask = loop.mask[:N0].cpu().numpy().astype(bool)
+    assert np.array_equal(mask, od.topk_mask(scores.astype(np.float64), K_EVENT))
+    p32 = {k: float(np.float32(v)) for k, v in od.CONFIG_PRESET.items()}
+    ref = od.las_split(before, mask, **p32)
+    for k in GROUPS:
+        got = getattr(gs, k)[:N0 + K_EVENT].cpu().numpy().astype(np.float64).reshape(N0 + K_EVENT, -1)
+        want = ref[k].reshape(N0 + K_EVENT, -1)
+        assert (np.abs(got - want) / np.maximum(1.0, np.abs(want))).max() <= 1e-6, k
+    assert float(loop.score.abs().max().item()) == 0.0
+
+
+def test_graph_driver_reaches_budget_and_agrees_with_autograd(gsp_lib):
+    import torch
+    _, _, _, gs_a, loop_a = _make(gsp_lib)
+    _, _, _, gs_b, loop_b = _make(gsp_lib)
+    la = loop_a.step_autograd()
+    loop_b.run(1)
+    torch.cuda.synchronize()
+    assert abs(float(la.item()) - float(loop_b.loss().item())) <= 1e-6 * float(la.item())
+    for k in GROUPS:
+        torch.testing.assert_close(getattr(gs_a, k), getattr(gs_b, k), rtol=1e-6, atol=1e-9)
+    losses = [float(loop_b.loss().item())]
+    for _ in range(4 * EVERY - 1):
+        loop_b.run(1)
+        losses.append(float(loop_b.loss().item()))
+    torch.cuda.synchronize()
+    assert int(loop_b.status.item()) == 0
+    assert int(gs_b.count.item()) == N0 + 4 * K_EVENT == CAP
+    assert np.all(np.isfinite(losses))
+    assert all(torch.isfinite(getattr(gs_b, k)).all() for k in GROUPS)
