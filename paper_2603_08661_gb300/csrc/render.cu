@@ -35,6 +35,7 @@ constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 constexpr float kNear = 0.2f;
 constexpr int kRowCap = 16;  // tile rows per Gaussian with an exact column interval
+constexpr int kProjBwdThreads = 128;
 
 struct ViewP {
     float vm[12];
@@ -230,6 +231,45 @@ __device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + expf(-
 
 // The SH coefficients of one Gaussian (3K floats) into registers; 16-byte
 // loads when the row length allows (K = 4, 16).
+// acc[ch] += sum_k row[3k + ch] * Y[k], the coefficients streamed from memory in
+// 16-byte loads (row-major [K][3]; terms added in ascending k per channel).
+template <int K>
+__device__ __forceinline__ void sh_weighted(const float *row, const float Y[16], float acc[3])
+{
+    if constexpr ((3 * K) % 4 == 0) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+        for (int q = 0; q < 3 * K / 4; ++q) {
+            const float4 v = __ldg(r4 + q);
+            const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[(4 * q + j) % 3] += e[j] * Y[(4 * q + j) / 3];
+        }
+    } else {
+#pragma unroll
+        for (int el = 0; el < 3 * K; ++el) acc[el % 3] += __ldg(row + el) * Y[el / 3];
+    }
+}
+
+// w[k] += sum_ch g[ch] * row[3k + ch] (ascending ch per k), streamed like sh_weighted.
+template <int K>
+__device__ __forceinline__ void sh_contract(const float *row, const float g[3], float w[16])
+{
+    if constexpr ((3 * K) % 4 == 0) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+        for (int q = 0; q < 3 * K / 4; ++q) {
+            const float4 v = __ldg(r4 + q);
+            const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w[(4 * q + j) / 3] += g[(4 * q + j) % 3] * e[j];
+        }
+    } else {
+#pragma unroll
+        for (int el = 0; el < 3 * K; ++el) w[el / 3] += g[el % 3] * __ldg(row + el);
+    }
+}
+
 template <int K>
 __device__ __forceinline__ void load_sh(const float *row, float *out)
 {
@@ -262,8 +302,7 @@ __device__ __forceinline__ unsigned long long project_one(const Views &vs, const
     float ls[3] = {p.log_scales[3 * i], p.log_scales[3 * i + 1], p.log_scales[3 * i + 2]};
     float q4[4] = {p.quats[4 * i], p.quats[4 * i + 1], p.quats[4 * i + 2], p.quats[4 * i + 3]};
     float opac = sigmoidf_(p.opac[i]);
-    float shv[3 * K];
-    load_sh<K>(p.sh + (size_t)i * K * 3, shv);
+    const float *shrow = p.sh + (size_t)i * K * 3;
     for (int v = 0; v < vs.n; ++v) {
         const ViewP &V = vs.v[v];
         const long long o = v * cap + i;
@@ -333,18 +372,15 @@ __device__ __forceinline__ unsigned long long project_one(const Views &vs, const
             float rn = __frsqrt_rn(dx * dx + dy * dy + dz * dz);
             float Y[16];
             sh_eval(dx * rn, dy * rn, dz * rn, K, Y);
-            float col[3];
+            float col[3] = {0.5f, 0.5f, 0.5f};
+            sh_weighted<K>(shrow, Y, col);
             unsigned clampbits = 0;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                float acc = 0.5f;
-#pragma unroll
-                for (int k = 0; k < K; ++k) acc += shv[3 * k + ch] * Y[k];
-                if (acc < 0.f) {
+                if (col[ch] < 0.f) {
                     clampbits |= 1u << ch;
-                    acc = 0.f;
+                    col[ch] = 0.f;
                 }
-                col[ch] = acc;
             }
             // conic pre-scaled so that power = -1/2 d^T Q d = A' dx^2 + C' dy^2 + B' dx dy
             // (A' = -A/2, B' = -B, C' = -C/2: exact scalings)
@@ -361,7 +397,7 @@ __device__ __forceinline__ unsigned long long project_one(const Views &vs, const
 }
 
 template <int K>
-__global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Views vs, Params p, State st)
+__global__ void __launch_bounds__(256, 4) project_kernel(const __grid_constant__ Views vs, Params p, State st)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     unsigned long long pairs = i < p.cap ? project_one<K>(vs, p, st, i) : 0ull;
@@ -1084,16 +1120,26 @@ __global__ void __launch_bounds__(kBinThreads) l2_scatter(const __grid_constant_
         const int gt0 = super_tile(V, sx, sy, lane), gt1 = super_tile(V, sx, sy, lane + 32);
         const unsigned cur0 = gt0 >= 0 ? st.tile_start[gt0] + st.count2[(size_t)c * 64 + lane] : 0u;
         const unsigned cur1 = gt1 >= 0 ? st.tile_start[gt1] + st.count2[(size_t)c * 64 + 32 + lane] : 0u;
+        // two halves of 32 tiles: the masks' 32-bit halves are shifted once per tile
+        // (a rolled loop: unrolling all 64 tiles overflows the instruction cache)
 #pragma unroll
-        for (int b = 0; b < 64; ++b) {
-            if (!(((b < 32 ? any_lo : any_hi) >> (b & 31)) & 1u)) continue;
-            unsigned base = __shfl_sync(0xffffffffu, b < 32 ? cur0 : cur1, b & 31);
+        for (int half = 0; half < 2; ++half) {
+            unsigned mh[kBinRounds];
 #pragma unroll
-            for (int k = 0; k < kBinRounds; ++k) {
-                const bool bit = (m[k] >> b) & 1ull;
-                const unsigned bal = __ballot_sync(0xffffffffu, bit);
-                if (bit) st.ids[base + __popc(bal & lt)] = g[k];
-                base += __popc(bal);
+            for (int k = 0; k < kBinRounds; ++k) mh[k] = half ? unsigned(m[k] >> 32) : unsigned(m[k]);
+            unsigned present = half ? any_hi : any_lo;
+            const unsigned cur = half ? cur1 : cur0;
+            while (present) {
+                const int b = __ffs(present) - 1;
+                present &= present - 1;
+                unsigned base = __shfl_sync(0xffffffffu, cur, b);
+#pragma unroll
+                for (int k = 0; k < kBinRounds; ++k) {
+                    const bool bit = (mh[k] >> b) & 1u;
+                    const unsigned bal = __ballot_sync(0xffffffffu, bit);
+                    if (bit) st.ids[base + __popc(bal & lt)] = g[k];
+                    base += __popc(bal);
+                }
             }
         }
     }
@@ -1489,8 +1535,10 @@ __global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) c
 
 // Chain the screen-space gradients to the parameters, one thread per Gaussian,
 // summing over views.
+// The SH gradients accumulate over the views in a per-thread row of shared
+// memory (3K + 1 floats: an odd stride keeps the rows on distinct banks).
 template <int K>
-__global__ void __launch_bounds__(128) project_bwd(const __grid_constant__ Views vs, Params p, State st,
+__global__ void __launch_bounds__(kProjBwdThreads) project_bwd(const __grid_constant__ Views vs, Params p, State st,
                                                   float *gm, float *gls, float *gq, float *go, float *gsh,
                                                   int accumulate)
 {
@@ -1502,10 +1550,10 @@ __global__ void __launch_bounds__(128) project_bwd(const __grid_constant__ Views
     float ls[3] = {p.log_scales[3 * i], p.log_scales[3 * i + 1], p.log_scales[3 * i + 2]};
     float q4[4] = {p.quats[4 * i], p.quats[4 * i + 1], p.quats[4 * i + 2], p.quats[4 * i + 3]};
     const float opac = sigmoidf_(p.opac[i]);
-    float shv[3 * K];
-    load_sh<K>(p.sh + (size_t)i * K * 3, shv);
+    const float *shrow = p.sh + (size_t)i * K * 3;
     float G_mu[3] = {0.f, 0.f, 0.f}, G_ls[3] = {0.f, 0.f, 0.f}, G_q[4] = {0.f, 0.f, 0.f, 0.f}, G_o = 0.f;
-    float G_sh[3 * K];
+    extern __shared__ float pb_smem[];
+    float *G_sh = pb_smem + threadIdx.x * (3 * K + 1);
 #pragma unroll
     for (int k = 0; k < 3 * K; ++k) G_sh[k] = 0.f;
     const float qn2 = q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3];
@@ -1617,15 +1665,13 @@ __global__ void __launch_bounds__(128) project_bwd(const __grid_constant__ Views
         float wsh[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) wsh[k] = 0.f;
+        const float gm3[3] = {(clampbits & 1u) ? 0.f : gcol[0], (clampbits & 2u) ? 0.f : gcol[1],
+                              (clampbits & 4u) ? 0.f : gcol[2]};
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            const float g = (clampbits & (1u << ch)) ? 0.f : gcol[ch];
+        for (int ch = 0; ch < 3; ++ch)
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                G_sh[3 * k + ch] += g * Y[k];
-                wsh[k] += g * shv[3 * k + ch];
-            }
-        }
+            for (int k = 0; k < K; ++k) G_sh[3 * k + ch] += gm3[ch] * Y[k];
+        sh_contract<K>(shrow, gm3, wsh);
         float gu[3];
         sh_grad_dot(ux, uy, uz, K, wsh, gu);
         const float ud = gu[0] * ux + gu[1] * uy + gu[2] * uz;
@@ -1965,9 +2011,11 @@ extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *c
     stage_end("composite_bwd", s);
     GSP_LAUNCH_CHECK();
     stage_begin("project_bwd", s);
-#define GSP_PBWD(KK)                                                                                   \
-    project_bwd<KK><<<div_up(cap, 128), 128, 0, s>>>(vs, P, S, grad_means, grad_log_scales, grad_quats, \
-                                                     grad_opacity_logits, grad_sh, accumulate)
+#define GSP_PBWD(KK)                                                                                           \
+    project_bwd<KK><<<div_up(cap, kProjBwdThreads), kProjBwdThreads,                                             \
+                      sizeof(float) * kProjBwdThreads * (3 * (KK) + 1), s>>>(vs, P, S, grad_means, grad_log_scales, \
+                                                                             grad_quats, grad_opacity_logits, grad_sh, \
+                                                                             accumulate)
     switch (P.K) {
     case 1: GSP_PBWD(1); break;
     case 4: GSP_PBWD(4); break;
