@@ -16,16 +16,23 @@
 // are gathered and resolved on bits [18:9] and [8:0].
 //
 // Fused mode runs every stage of every view in one cooperative launch:
-//   A  per 64x16 tile: stencil chain in shared memory, NMS, write M_thin to
-//      E_out, per-view histogram of bits [30:19]
+//   A  per 64x16 tile: the tile's RGB halo box is staged in shared memory by a
+//      2-D TMA copy (double-buffered: the next tile's copy overlaps this
+//      tile's work; views whose base or pitch is not 16-byte aligned are read
+//      directly), stencil chain in shared memory, NMS, write M_thin to E_out,
+//      per-view histogram of bits [30:19]
 //   -- grid barrier --
 //   B  each block finds its views' median bin and gathers its candidates
+//      (per tile in shared memory, one reservation per tile)
 //   -- grid barrier --
 //   C  block v resolves view v's median from its candidates
 //   -- grid barrier --
 //   D  each block divides its kept pixels by the median, in place
 // Plain mode launches one kernel per stage and per view, with every
 // intermediate in global memory (the unfused reference path).
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "common.cuh"
 
@@ -50,8 +57,16 @@ struct EdgeView {
     int tiles_x;
     int tile_base;
     int ntiles;
-    int pad;
+    int tma;  // 1: the view's halo tiles are staged by TMA (16-byte aligned base and pitch)
 };
+
+// TMA box of one tile's input: the RGB bytes of its halo (TW + 8 pixels plus
+// the alignment slack: the box starts 16 bytes before the tile's first pixel,
+// a 16-byte boundary since TW * 3 is a multiple of 16) x (TH + 8) rows.
+constexpr int kBoxW = 224, kBoxH = TH + 8;
+constexpr int kBoxLead = 16;  // bytes between the box start and pixel x0 - 0
+static_assert(3 * (TW + 4) + kBoxLead <= kBoxW && (3 * TW) % 16 == 0 && kBoxW % 16 == 0, "TMA box");
+static_assert(kBoxLead >= 3 * 4, "the box reaches the left halo");
 
 struct EdgeArgs {
     EdgeView v[GSP_MAX_VIEWS];
@@ -68,27 +83,52 @@ struct EdgeArgs {
     unsigned *bar;         // grid barrier state [2]
     int32_t *status;
     long long spin_limit;
+    CUtensorMap tmap[GSP_MAX_VIEWS];  // uint8 [h][3w] with row pitch, box kBoxW x kBoxH
 };
 
+// Stage buffers of one tile; a buffer is reused once its stage is consumed
+// (I -> Sx/Sy -> Hx/Hy -> M/Gx/Gy): I and Hx/Hy share one region, Sx/Sy and
+// M/Gx/Gy the other.
 struct TileSmem {
-    int I[IH][IW];
-    float Sx[SH][SW], Sy[SH][SW];
-    float Hx[HH][HW], Hy[HH][HW];
-    float M[MH][MW];
-    float Gx[TH][TW], Gy[TH][TW];
+    union {
+        int I[IH][IW];
+        struct {
+            float Hx[HH][HW], Hy[HH][HW];
+        };
+    };
+    union {
+        struct {
+            float Sx[SH][SW], Sy[SH][SW];
+        };
+        struct {
+            float M[MH][MW];
+            float Gx[TH][TW], Gy[TH][TW];
+        };
+    };
+};
+
+// Staged RGB boxes (two, for the next tile's copy to overlap this tile) and
+// their barriers.
+struct StageSmem {
+    alignas(128) uint8_t box[2][kBoxH][kBoxW];
+    unsigned long long bar[2];
 };
 
 __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
-// Stencil chain for one 64x16 output tile at (x0, y0) of view V.
+// Stencil chain for one 64x16 output tile at (x0, y0) of view V.  box: the
+// tile's staged RGB bytes (rows y0 - 4 .., bytes from 3 x0 - kBoxLead), or
+// null to read the image directly.  Clamp-to-edge indexes the box (or the
+// image) at clamped coordinates; the box holds every clamped pixel.
 __device__ void tile_stencil(const EdgeView &V, int x0, int y0, float w0, float w1, float w2,
-                             TileSmem &s)
+                             const uint8_t (*box)[kBoxW], TileSmem &s)
 {
     const int tid = threadIdx.x;
     for (int idx = tid; idx < IH * IW; idx += NT) {
         int r = idx / IW, c = idx - r * IW;
         int yy = clampi(y0 - 4 + r, 0, V.h - 1), xx = clampi(x0 - 4 + c, 0, V.w - 1);
-        const uint8_t *p = V.rgb + (long long)yy * V.pitch + 3 * xx;
+        const uint8_t *p = box ? &box[yy - (y0 - 4)][3 * (xx - x0) + kBoxLead]
+                               : V.rgb + (long long)yy * V.pitch + 3 * xx;
         s.I[r][c] = 299 * int(p[0]) + 587 * int(p[1]) + 114 * int(p[2]);
     }
     __syncthreads();
@@ -203,18 +243,6 @@ __device__ void block_find_bin(const unsigned *hist, int nbins, unsigned rank, i
     __syncthreads();
 }
 
-__device__ __forceinline__ void warp_append(float val, bool pred, unsigned *counter, float *dst)
-{
-    unsigned m = __ballot_sync(0xffffffffu, pred);
-    if (!m) return;
-    const int lane = threadIdx.x & 31;
-    int leader = __ffs(m) - 1;
-    unsigned base = 0;
-    if (lane == leader) base = atomicAdd(counter, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (pred) dst[base + __popc(m & ((1u << lane) - 1))] = val;
-}
-
 // Resolve the median of view v from its candidates (rank `rank` among them,
 // all sharing bin b1 of bits [30:19]); one block.  Returns the float bits.
 __device__ unsigned select_from_candidates(const float *cand, unsigned count, unsigned rank, int b1,
@@ -242,11 +270,46 @@ __device__ unsigned select_from_candidates(const float *cand, unsigned count, un
     return (unsigned(b1) << kShift1) | (unsigned(b2) << kShift2) | unsigned(b3);
 }
 
+// 2-D tiled TMA load of one box into shared memory, completed on bar.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tile_origin(const EdgeArgs &a, int t, int &v, int &x0, int &y0)
+{
+    v = find_view(a, t);
+    const EdgeView &V = a.v[v];
+    const int lt = t - V.tile_base;
+    const int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
+    x0 = tx * TW;
+    y0 = ty * TH;
+}
+
+// Thread 0: stage tile t's RGB box into buffer buf (views without TMA are read directly).
+__device__ __forceinline__ void issue_box(const EdgeArgs &a, StageSmem &stg, int t, int buf)
+{
+    int v, x0, y0;
+    tile_origin(a, t, v, x0, y0);
+    if (!a.v[v].tma) return;
+    // the previous reads of this buffer (generic proxy) precede the async copy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(&stg.bar[buf], unsigned(kBoxW * kBoxH));
+    tma_load_2d(&stg.box[buf][0][0], &a.tmap[v], 3 * x0 - kBoxLead, y0 - 4, &stg.bar[buf]);
+}
+
 __global__ void __launch_bounds__(NT) edge_fused_kernel(const __grid_constant__ EdgeArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileSmem &s = *reinterpret_cast<TileSmem *>(smem_raw);
-    unsigned *hist_s = reinterpret_cast<unsigned *>(smem_raw + sizeof(TileSmem));
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    // TMA destinations need 128-byte alignment: the launch adds 128 bytes of slack
+    unsigned char *smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+    StageSmem &stg = *reinterpret_cast<StageSmem *>(smem_raw);
+    TileSmem &s = *reinterpret_cast<TileSmem *>(smem_raw + sizeof(StageSmem));
+    unsigned *hist_s = reinterpret_cast<unsigned *>(smem_raw + sizeof(StageSmem) + sizeof(TileSmem));
     const int tid = threadIdx.x;
     const int G = gridDim.x;
     const int t_begin = int((long long)a.total_tiles * blockIdx.x / G);
@@ -254,9 +317,20 @@ __global__ void __launch_bounds__(NT) edge_fused_kernel(const __grid_constant__ 
     const float scale = 1.0f / 255000.0f;
 
     // ---- phase A: stencil, NMS, M_thin -> E, histogram of bits [30:19]
+    // The next tile's box is copied by TMA while this tile is computed.
+    if (tid == 0) {
+        mbar_init(&stg.bar[0], 1);
+        mbar_init(&stg.bar[1], 1);
+    }
+    __syncthreads();
+    if (tid == 0 && t_begin < t_end) issue_box(a, stg, t_begin, 0);
+    unsigned uses[2] = {0u, 0u};  // completed phases of each buffer's barrier (block-uniform)
     int cur_view = -1;
-    for (int t = t_begin; t < t_end; ++t) {
-        int v = find_view(a, t);
+    for (int t = t_begin, it = 0; t < t_end; ++t, ++it) {
+        const int buf = it & 1;
+        if (tid == 0 && t + 1 < t_end) issue_box(a, stg, t + 1, buf ^ 1);
+        int v, x0, y0;
+        tile_origin(a, t, v, x0, y0);
         const EdgeView &V = a.v[v];
         if (v != cur_view) {
             if (cur_view >= 0) {
@@ -268,10 +342,17 @@ __global__ void __launch_bounds__(NT) edge_fused_kernel(const __grid_constant__ 
             for (int i = tid; i < kBins1; i += NT) hist_s[i] = 0;
             cur_view = v;
         }
-        int lt = t - V.tile_base;
-        int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
-        int x0 = tx * TW, y0 = ty * TH;
-        tile_stencil(V, x0, y0, a.w0, a.w1, a.w2, s);
+        if (V.tma) {
+            const bool mine = mbar_wait(&stg.bar[buf], uses[buf] & 1u, a.spin_limit);
+            if (!__syncthreads_and(mine)) {
+                set_status(a.status, GSP_ERR_TIMEOUT);
+                // let the copies in flight land before the block leaves (bounded)
+                mbar_wait(&stg.bar[buf ^ 1], uses[buf ^ 1] & 1u, a.spin_limit);
+                return;
+            }
+            ++uses[buf];
+        }
+        tile_stencil(V, x0, y0, a.w0, a.w1, a.w2, V.tma ? stg.box[buf] : nullptr, s);
         for (int idx = tid; idx < TH * TW; idx += NT) {
             int r = idx / TW, c = idx - r * TW;
             int y = y0 + r, x = x0 + c;
@@ -292,7 +373,10 @@ __global__ void __launch_bounds__(NT) edge_fused_kernel(const __grid_constant__ 
     }
     if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
 
-    // ---- phase B: median bin per view, gather this block's candidates
+    // ---- phase B: median bin per view; this block's candidates, gathered per
+    // tile in shared memory and appended with one reservation per tile
+    float *cbuf = reinterpret_cast<float *>(&s.I[0][0]);  // TH * TW floats (the stencil buffers are free)
+    __shared__ unsigned s_base;
     for (int t = t_begin; t < t_end;) {
         int v = find_view(a, t);
         const EdgeView &V = a.v[v];
@@ -309,14 +393,31 @@ __global__ void __launch_bounds__(NT) edge_fused_kernel(const __grid_constant__ 
             for (int tt = t; tt < t_stop; ++tt) {
                 int lt = tt - V.tile_base;
                 int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
-                for (int idx = tid; idx < TH * TW; idx += NT) {
-                    int r = idx / TW, c = idx - r * TW;
-                    int y = ty * TH + r, x = tx * TW + c;
-                    bool in = y < V.h && x < V.w;
-                    float mt = in ? a.E[V.out_off + (long long)y * V.w + x] : 0.f;
-                    bool pick = mt > 0.f && int(__float_as_uint(mt) >> kShift1) == b1;
-                    warp_append(mt, pick, a.cand_count + v, a.cand + V.out_off);
+                constexpr int kPer = TH * TW / NT;
+                float val[kPer];
+                unsigned mine = 0;
+#pragma unroll
+                for (int k = 0; k < kPer; ++k) {
+                    const int idx = tid + k * NT;
+                    const int r = idx / TW, c = idx - r * TW;
+                    const int y = ty * TH + r, x = tx * TW + c;
+                    const bool in = y < V.h && x < V.w;
+                    const float mt = in ? a.E[V.out_off + (long long)y * V.w + x] : 0.f;
+                    const bool pick = mt > 0.f && int(__float_as_uint(mt) >> kShift1) == b1;
+                    val[k] = pick ? mt : -1.f;
+                    mine += pick;
                 }
+                unsigned off;
+                const unsigned total = block_exclusive_scan(mine, &off);
+                if (total == 0) continue;
+#pragma unroll
+                for (int k = 0; k < kPer; ++k)
+                    if (val[k] >= 0.f) cbuf[off++] = val[k];
+                if (tid == 0) s_base = atomicAdd(a.cand_count + v, total);
+                __syncthreads();
+                float *dst = a.cand + V.out_off + s_base;
+                for (unsigned i = tid; i < total; i += NT) dst[i] = cbuf[i];
+                __syncthreads();
             }
         }
         t = t_stop;
@@ -580,6 +681,43 @@ EdgeLayout edge_layout(void *ws, const gsp_image_desc *imgs, int nv, int mode)
     return L;
 }
 
+// cuTensorMapEncodeTiled from the driver (looked up once through the runtime;
+// null when the driver does not provide it: every view then reads directly).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor map of a view's RGB bytes: uint8 [h][3 w] with the caller's row pitch,
+// box kBoxW x kBoxH; out-of-range box parts read as zero (never used: the
+// stencil indexes clamped coordinates).  False when TMA cannot stage the view.
+bool encode_view_map(const gsp_image_desc &d, CUtensorMap *map)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    if ((reinterpret_cast<uintptr_t>(d.rgb) & 15) || (d.pitch_bytes & 15) || d.pitch_bytes >= (1LL << 40)) return false;
+    const cuuint64_t dims[2] = {cuuint64_t(3) * cuuint64_t(d.width), cuuint64_t(d.height)};
+    const cuuint64_t strides[1] = {cuuint64_t(d.pitch_bytes)};
+    const cuuint32_t box[2] = {kBoxW, kBoxH};
+    const cuuint32_t elem[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(d.rgb), dims, strides, box, elem,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 gsp_status validate_edge(const gsp_image_desc *imgs, int nv, const gsp_edge_opts *o)
 {
     if (!imgs || nv < 1) return GSP_ERR_INVALID_ARG;
@@ -653,6 +791,7 @@ extern "C" gsp_status gsp_edge_map(const gsp_image_desc *imgs, int32_t nv, float
         V.ntiles = V.tiles_x * int(div_up(V.h, TH));
         V.tile_base = tiles;
         tiles += V.ntiles;
+        V.tma = o.mode == GSP_EDGE_FUSED && encode_view_map(imgs[v], &a.tmap[v]) ? 1 : 0;
     }
     a.nviews = nv;
     a.total_tiles = tiles;
@@ -673,7 +812,7 @@ extern "C" gsp_status gsp_edge_map(const gsp_image_desc *imgs, int32_t nv, float
     GSP_CUDA_TRY(cudaMemsetAsync(L.hist1, 0, zero_bytes, s));
 
     if (o.mode == GSP_EDGE_FUSED) {
-        const size_t smem = sizeof(TileSmem) + kBins1 * sizeof(unsigned);
+        const size_t smem = 128 + sizeof(StageSmem) + sizeof(TileSmem) + kBins1 * sizeof(unsigned);
         static bool attr_set = false;
         if (!attr_set) {
             GSP_CUDA_TRY(cudaFuncSetAttribute(edge_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
