@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--gaussians", type=int, default=N_GAUSS)
-    ap.add_argument("--no-extra", action="store_true", help="skip the multi-view and densification-loop legs")
+    ap.add_argument("--no-extra", action="store_true", help="skip the edge, multi-view and densification-loop legs")
+    ap.add_argument("--legs", default="main,edge,multiview,loop",
+                    help="comma-separated subset of main, edge, multiview, loop (profiling runs)")
     return ap.parse_args()
 
 
@@ -215,6 +217,10 @@ def run_gsp(args, rank, world):
         r = gsp.Renderer(c, [cam], pair_cap, device=dev, workspace=ws_r)
         ws_r = r.ws
         rends.append(r)
+    # compositing variants chosen by the project's autotuner for this workload
+    variants = gsp.autotune.tune(rends[0], targets=[target])
+    for r in rends:
+        r.variants = variants
     E = torch.empty(npix, dtype=torch.float32, device=dev)
     ws_e = torch.empty(1 << 26, dtype=torch.uint8, device=dev)
     ws_las = torch.empty(gsp._lib.load().gsp_las_workspace_size(cap), dtype=torch.uint8, device=dev)
@@ -403,7 +409,7 @@ def run_gsp(args, rank, world):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded scenes shaped like the paper's Mip-NeRF360 views)",
         "config": {"workload": WORKLOAD, "gaussians": n, "sh_degree": SH_DEGREE, "view": f"{WIDTH}x{HEIGHT}",
-                   "split_k": k_split, "pairs": pairs, "graph": use_graph,
+                   "split_k": k_split, "pairs": pairs, "graph": use_graph, "variants": list(variants),
                    "l2": "inputs larger than L2: every step uses its own 236 MB parameter copy",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps),
@@ -707,15 +713,15 @@ def main():
             pass
         line = run_reference(args, rank, world)
     else:
-        line = run_gsp(args, rank, world)
+        legs = set(args.legs.split(","))
+        line = run_gsp(args, rank, world) if "main" in legs else {"metric": METRIC, "legs": sorted(legs)}
         if world == 1 and not args.no_extra:
             import torch
-            torch.cuda.empty_cache()
-            line["edge_batched"] = run_edge_batched()
-            torch.cuda.empty_cache()
-            line["multiview"] = run_multiview()
-            torch.cuda.empty_cache()
-            line["densify_loop"] = run_densify_loop()
+            for name, key, fn in (("edge", "edge_batched", run_edge_batched), ("multiview", "multiview", run_multiview),
+                                  ("loop", "densify_loop", run_densify_loop)):
+                if name in legs:
+                    torch.cuda.empty_cache()
+                    line[key] = fn()
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:

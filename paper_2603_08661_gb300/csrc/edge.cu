@@ -22,12 +22,16 @@
 //      directly), stencil chain in shared memory, NMS, write M_thin to E_out,
 //      per-view histogram of bits [30:19]
 //   -- grid barrier --
-//   B  each block finds its views' median bin and gathers its candidates
-//      (per tile in shared memory, one reservation per tile)
+//   B0 block v finds view v's median bin of bits [30:19]
 //   -- grid barrier --
-//   C  block v resolves view v's median from its candidates
+//   B  every block streams its slice of every view (8 loads in flight per
+//      thread), appends the values in the median bin to the view's candidate
+//      list (one reservation per block round) and counts them on bits [18:9]
 //   -- grid barrier --
-//   D  each block divides its kept pixels by the median, in place
+//   C  block v resolves view v's median: the bin of bits [18:9] from that
+//      count, bits [8:0] from one pass over the candidates in it
+//   -- grid barrier --
+//   D  every block divides its slice of every view by the median, in place
 // Plain mode launches one kernel per stage and per view, with every
 // intermediate in global memory (the unfused reference path).
 
@@ -41,7 +45,6 @@ namespace {
 
 constexpr int TW = 64, TH = 16, NT = 256;
 constexpr int IW = TW + 8, IH = TH + 8;  // integer luma with a 4-pixel halo
-constexpr int SW = TW + 6, SH = TH + 6;  // Sobel responses
 constexpr int HW = TW + 2, HH = TH + 6;  // after the horizontal blur
 constexpr int MW = TW + 2, MH = TH + 2;  // magnitude with a 1-pixel ring
 constexpr int kBins1 = 4096, kShift1 = 19;
@@ -77,6 +80,8 @@ struct EdgeArgs {
     uint8_t *mask;
     float *median_out;
     unsigned *hist1;       // [V][kBins1]
+    unsigned *hist2;       // [V][kBins2] bits [18:9] of the candidates
+    unsigned *sel;         // [V][4]: kept count, median bin of bits [30:19], count below that bin
     unsigned *cand_count;  // [V]
     float *cand;           // candidate values, laid out like E
     unsigned *med_bits;    // [V]
@@ -86,25 +91,18 @@ struct EdgeArgs {
     CUtensorMap tmap[GSP_MAX_VIEWS];  // uint8 [h][3w] with row pitch, box kBoxW x kBoxH
 };
 
-// Stage buffers of one tile; a buffer is reused once its stage is consumed
-// (I -> Sx/Sy -> Hx/Hy -> M/Gx/Gy): I and Hx/Hy share one region, Sx/Sy and
-// M/Gx/Gy the other.
+// Stage buffers of one tile.  Sobel and the horizontal blur run fused in
+// registers (no Sobel buffer); the integer luma I is dead once the blur rows
+// exist, so M / Gx / Gy reuse its storage.
 struct TileSmem {
     union {
-        int I[IH][IW];
-        struct {
-            float Hx[HH][HW], Hy[HH][HW];
-        };
-    };
-    union {
-        struct {
-            float Sx[SH][SW], Sy[SH][SW];
-        };
+        alignas(16) int I[IH][IW];
         struct {
             float M[MH][MW];
             float Gx[TH][TW], Gy[TH][TW];
         };
     };
+    float Hx[HH][HW], Hy[HH][HW];
 };
 
 // Staged RGB boxes (two, for the next tile's copy to overlap this tile) and
@@ -120,48 +118,100 @@ __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? l
 // tile's staged RGB bytes (rows y0 - 4 .., bytes from 3 x0 - kBoxLead), or
 // null to read the image directly.  Clamp-to-edge indexes the box (or the
 // image) at clamped coordinates; the box holds every clamped pixel.
+//   luma   I (exact integers), 4 pixels per thread from three 32-bit words of
+//          the box where no clamping is needed
+//   sobel + horizontal blur, fused: a thread takes a row run of 6 outputs,
+//          forms the 10 exact integer Sobel pairs it needs in registers and
+//          blurs them (taps paired, same operation order as a plain pass)
+//   vertical blur + magnitude: a thread takes a column run of 6 outputs
+constexpr int kSegH = 6;                 // row run of the fused Sobel + horizontal blur
+constexpr int kSegV = 6;                 // column run of the vertical blur
+static_assert(HW % kSegH == 0 && MH % kSegV == 0, "segment runs");
+static_assert((HW / kSegH) * HH <= NT && (MH / kSegV) * MW <= NT, "one run per thread");
+
 __device__ void tile_stencil(const EdgeView &V, int x0, int y0, float w0, float w1, float w2,
                              const uint8_t (*box)[kBoxW], TileSmem &s)
 {
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < IH * IW; idx += NT) {
-        int r = idx / IW, c = idx - r * IW;
-        int yy = clampi(y0 - 4 + r, 0, V.h - 1), xx = clampi(x0 - 4 + c, 0, V.w - 1);
-        const uint8_t *p = box ? &box[yy - (y0 - 4)][3 * (xx - x0) + kBoxLead]
-                               : V.rgb + (long long)yy * V.pitch + 3 * xx;
-        s.I[r][c] = 299 * int(p[0]) + 587 * int(p[1]) + 114 * int(p[2]);
+    const bool interior = box && x0 >= 4 && x0 + TW + 4 <= V.w && y0 >= 4 && y0 + TH + 4 <= V.h;
+    if (interior) {
+        // 4 pixels from 12 bytes at box byte 3 c + 4 (c a multiple of 4: word aligned)
+        for (int g = tid; g < IH * (IW / 4); g += NT) {
+            const int r = g / (IW / 4), c = 4 * (g - r * (IW / 4));
+            const unsigned *w = reinterpret_cast<const unsigned *>(&box[r][3 * c + kBoxLead - 12]);
+            const unsigned a0 = w[0], a1 = w[1], a2 = w[2];
+            const int b0 = a0 & 255, b1 = (a0 >> 8) & 255, b2 = (a0 >> 16) & 255, b3 = a0 >> 24;
+            const int b4 = a1 & 255, b5 = (a1 >> 8) & 255, b6 = (a1 >> 16) & 255, b7 = a1 >> 24;
+            const int b8 = a2 & 255, b9 = (a2 >> 8) & 255, b10 = (a2 >> 16) & 255, b11 = a2 >> 24;
+            *reinterpret_cast<int4 *>(&s.I[r][c]) =
+                make_int4(299 * b0 + 587 * b1 + 114 * b2, 299 * b3 + 587 * b4 + 114 * b5,
+                          299 * b6 + 587 * b7 + 114 * b8, 299 * b9 + 587 * b10 + 114 * b11);
+        }
+    } else {
+        for (int idx = tid; idx < IH * IW; idx += NT) {
+            int r = idx / IW, c = idx - r * IW;
+            int yy = clampi(y0 - 4 + r, 0, V.h - 1), xx = clampi(x0 - 4 + c, 0, V.w - 1);
+            const uint8_t *p = box ? &box[yy - (y0 - 4)][3 * (xx - x0) + kBoxLead]
+                                   : V.rgb + (long long)yy * V.pitch + 3 * xx;
+            s.I[r][c] = 299 * int(p[0]) + 587 * int(p[1]) + 114 * int(p[2]);
+        }
     }
     __syncthreads();
-    for (int idx = tid; idx < SH * SW; idx += NT) {
-        int r = idx / SW, c = idx - r * SW;
-        int sx = (s.I[r][c + 2] - s.I[r][c]) + 2 * (s.I[r + 1][c + 2] - s.I[r + 1][c]) +
-                 (s.I[r + 2][c + 2] - s.I[r + 2][c]);
-        int sy = (s.I[r + 2][c] - s.I[r][c]) + 2 * (s.I[r + 2][c + 1] - s.I[r][c + 1]) +
-                 (s.I[r + 2][c + 2] - s.I[r][c + 2]);
-        s.Sx[r][c] = float(sx);
-        s.Sy[r][c] = float(sy);
+    // Sobel (exact integers) + horizontal blur: outputs H[r][c0 .. c0 + 5] use
+    // Sobel columns c0 .. c0 + 9, which use I rows r .. r + 2, columns c0 .. c0 + 11
+    if (tid < (HW / kSegH) * HH) {
+        const int r = tid / (HW / kSegH), c0 = kSegH * (tid - r * (HW / kSegH));
+        int i0[kSegH + 6], i1[kSegH + 6], i2[kSegH + 6];
+#pragma unroll
+        for (int j = 0; j < kSegH + 6; j += 2) {
+            const int2 u0 = *reinterpret_cast<const int2 *>(&s.I[r][c0 + j]);
+            const int2 u1 = *reinterpret_cast<const int2 *>(&s.I[r + 1][c0 + j]);
+            const int2 u2 = *reinterpret_cast<const int2 *>(&s.I[r + 2][c0 + j]);
+            i0[j] = u0.x; i0[j + 1] = u0.y;
+            i1[j] = u1.x; i1[j + 1] = u1.y;
+            i2[j] = u2.x; i2[j + 1] = u2.y;
+        }
+        float fx[kSegH + 4], fy[kSegH + 4];
+#pragma unroll
+        for (int j = 0; j < kSegH + 4; ++j) {
+            const int sx = (i0[j + 2] - i0[j]) + 2 * (i1[j + 2] - i1[j]) + (i2[j + 2] - i2[j]);
+            const int sy = (i2[j] - i0[j]) + 2 * (i2[j + 1] - i0[j + 1]) + (i2[j + 2] - i0[j + 2]);
+            fx[j] = float(sx);
+            fy[j] = float(sy);
+        }
+#pragma unroll
+        for (int j = 0; j < kSegH; ++j) {
+            const float ax1 = fx[j + 1] + fx[j + 3], ax2 = fx[j] + fx[j + 4];
+            const float ay1 = fy[j + 1] + fy[j + 3], ay2 = fy[j] + fy[j + 4];
+            s.Hx[r][c0 + j] = __fmaf_rn(w2, ax2, __fmaf_rn(w1, ax1, __fmul_rn(w0, fx[j + 2])));
+            s.Hy[r][c0 + j] = __fmaf_rn(w2, ay2, __fmaf_rn(w1, ay1, __fmul_rn(w0, fy[j + 2])));
+        }
     }
     __syncthreads();
-    for (int idx = tid; idx < HH * HW; idx += NT) {
-        int r = idx / HW, c = idx - r * HW;
-        float ax1 = s.Sx[r][c + 1] + s.Sx[r][c + 3], ax2 = s.Sx[r][c] + s.Sx[r][c + 4];
-        float ay1 = s.Sy[r][c + 1] + s.Sy[r][c + 3], ay2 = s.Sy[r][c] + s.Sy[r][c + 4];
-        s.Hx[r][c] = __fmaf_rn(w2, ax2, __fmaf_rn(w1, ax1, __fmul_rn(w0, s.Sx[r][c + 2])));
-        s.Hy[r][c] = __fmaf_rn(w2, ay2, __fmaf_rn(w1, ay1, __fmul_rn(w0, s.Sy[r][c + 2])));
-    }
-    __syncthreads();
-    for (int idx = tid; idx < MH * MW; idx += NT) {
-        int r = idx / MW, c = idx - r * MW;
-        float bx1 = __fadd_rn(s.Hx[r + 1][c], s.Hx[r + 3][c]), bx2 = __fadd_rn(s.Hx[r][c], s.Hx[r + 4][c]);
-        float by1 = __fadd_rn(s.Hy[r + 1][c], s.Hy[r + 3][c]), by2 = __fadd_rn(s.Hy[r][c], s.Hy[r + 4][c]);
-        float gx = __fmaf_rn(w2, bx2, __fmaf_rn(w1, bx1, __fmul_rn(w0, s.Hx[r + 2][c])));
-        float gy = __fmaf_rn(w2, by2, __fmaf_rn(w1, by1, __fmul_rn(w0, s.Hy[r + 2][c])));
-        int yy = y0 - 1 + r, xx = x0 - 1 + c;
-        bool inside = yy >= 0 && yy < V.h && xx >= 0 && xx < V.w;
-        s.M[r][c] = inside ? __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(gy, gy))) : 0.0f;
-        if (r >= 1 && r <= TH && c >= 1 && c <= TW) {
-            s.Gx[r - 1][c - 1] = gx;
-            s.Gy[r - 1][c - 1] = gy;
+    // vertical blur + magnitude: outputs M[r0 .. r0 + 5][c] use H rows r0 .. r0 + 9
+    if (tid < (MH / kSegV) * MW) {
+        const int seg = tid / MW, c = tid - seg * MW, r0 = kSegV * seg;
+        float hx[kSegV + 4], hy[kSegV + 4];
+#pragma unroll
+        for (int j = 0; j < kSegV + 4; ++j) {
+            hx[j] = s.Hx[r0 + j][c];
+            hy[j] = s.Hy[r0 + j][c];
+        }
+        const int xx = x0 - 1 + c;
+#pragma unroll
+        for (int j = 0; j < kSegV; ++j) {
+            const int r = r0 + j;
+            const float bx1 = __fadd_rn(hx[j + 1], hx[j + 3]), bx2 = __fadd_rn(hx[j], hx[j + 4]);
+            const float by1 = __fadd_rn(hy[j + 1], hy[j + 3]), by2 = __fadd_rn(hy[j], hy[j + 4]);
+            const float gx = __fmaf_rn(w2, bx2, __fmaf_rn(w1, bx1, __fmul_rn(w0, hx[j + 2])));
+            const float gy = __fmaf_rn(w2, by2, __fmaf_rn(w1, by1, __fmul_rn(w0, hy[j + 2])));
+            const int yy = y0 - 1 + r;
+            const bool inside = yy >= 0 && yy < V.h && xx >= 0 && xx < V.w;
+            s.M[r][c] = inside ? __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(gy, gy))) : 0.0f;
+            if (r >= 1 && r <= TH && c >= 1 && c <= TW) {
+                s.Gx[r - 1][c - 1] = gx;
+                s.Gy[r - 1][c - 1] = gy;
+            }
         }
     }
     __syncthreads();
@@ -241,33 +291,6 @@ __device__ void block_find_bin(const unsigned *hist, int nbins, unsigned rank, i
     *bin_out = s_bin;
     *below_out = s_below;
     __syncthreads();
-}
-
-// Resolve the median of view v from its candidates (rank `rank` among them,
-// all sharing bin b1 of bits [30:19]); one block.  Returns the float bits.
-__device__ unsigned select_from_candidates(const float *cand, unsigned count, unsigned rank, int b1,
-                                           unsigned *hist_smem /* kBins2 */)
-{
-    for (int i = threadIdx.x; i < kBins2; i += NT) hist_smem[i] = 0;
-    __syncthreads();
-    for (unsigned i = threadIdx.x; i < count; i += NT)
-        atomicAdd(&hist_smem[(__float_as_uint(cand[i]) >> kShift2) & (kBins2 - 1)], 1u);
-    __syncthreads();
-    int b2;
-    unsigned below2;
-    block_find_bin(hist_smem, kBins2, rank, &b2, &below2);
-    rank -= below2;
-    for (int i = threadIdx.x; i < kBins3; i += NT) hist_smem[i] = 0;
-    __syncthreads();
-    for (unsigned i = threadIdx.x; i < count; i += NT) {
-        unsigned bits = __float_as_uint(cand[i]);
-        if (((bits >> kShift2) & (kBins2 - 1)) == unsigned(b2)) atomicAdd(&hist_smem[bits & (kBins3 - 1)], 1u);
-    }
-    __syncthreads();
-    int b3;
-    unsigned below3;
-    block_find_bin(hist_smem, kBins3, rank, &b3, &below3);
-    return (unsigned(b1) << kShift1) | (unsigned(b2) << kShift2) | unsigned(b3);
 }
 
 // 2-D tiled TMA load of one box into shared memory, completed on bar.
@@ -373,71 +396,98 @@ __global__ void __launch_bounds__(NT) edge_fused_kernel(const __grid_constant__ 
     }
     if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
 
-    // ---- phase B: median bin per view; this block's candidates, gathered per
-    // tile in shared memory and appended with one reservation per tile
-    float *cbuf = reinterpret_cast<float *>(&s.I[0][0]);  // TH * TW floats (the stencil buffers are free)
-    __shared__ unsigned s_base;
-    for (int t = t_begin; t < t_end;) {
-        int v = find_view(a, t);
-        const EdgeView &V = a.v[v];
-        int t_stop = min(t_end, V.tile_base + V.ntiles);
-        const unsigned *h = a.hist1 + (size_t)v * kBins1;
-        unsigned seg = 0;
-        for (int k = 0; k < kBins1 / NT; ++k) seg += h[tid * (kBins1 / NT) + k];
-        unsigned before;
-        unsigned n = block_exclusive_scan(seg, &before);
-        if (n > 0) {
-            int b1;
-            unsigned below;
-            block_find_bin(h, kBins1, (n - 1) / 2, &b1, &below);
-            for (int tt = t; tt < t_stop; ++tt) {
-                int lt = tt - V.tile_base;
-                int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
-                constexpr int kPer = TH * TW / NT;
-                float val[kPer];
-                unsigned mine = 0;
-#pragma unroll
-                for (int k = 0; k < kPer; ++k) {
-                    const int idx = tid + k * NT;
-                    const int r = idx / TW, c = idx - r * TW;
-                    const int y = ty * TH + r, x = tx * TW + c;
-                    const bool in = y < V.h && x < V.w;
-                    const float mt = in ? a.E[V.out_off + (long long)y * V.w + x] : 0.f;
-                    const bool pick = mt > 0.f && int(__float_as_uint(mt) >> kShift1) == b1;
-                    val[k] = pick ? mt : -1.f;
-                    mine += pick;
-                }
-                unsigned off;
-                const unsigned total = block_exclusive_scan(mine, &off);
-                if (total == 0) continue;
-#pragma unroll
-                for (int k = 0; k < kPer; ++k)
-                    if (val[k] >= 0.f) cbuf[off++] = val[k];
-                if (tid == 0) s_base = atomicAdd(a.cand_count + v, total);
-                __syncthreads();
-                float *dst = a.cand + V.out_off + s_base;
-                for (unsigned i = tid; i < total; i += NT) dst[i] = cbuf[i];
-                __syncthreads();
-            }
-        }
-        t = t_stop;
-    }
-    if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
-
-    // ---- phase C: exact median of each view from its candidates
+    // ---- phase B0: each view's median bin of bits [30:19] and kept count (block v)
     for (int v = blockIdx.x; v < a.nviews; v += G) {
         const unsigned *h = a.hist1 + (size_t)v * kBins1;
         unsigned seg = 0;
         for (int k = 0; k < kBins1 / NT; ++k) seg += h[tid * (kBins1 / NT) + k];
         unsigned before;
-        unsigned n = block_exclusive_scan(seg, &before);
+        const unsigned n = block_exclusive_scan(seg, &before);
+        int b1 = 0;
+        unsigned below = 0;
+        if (n > 0) block_find_bin(h, kBins1, (n - 1) / 2, &b1, &below);
+        if (tid == 0) {
+            a.sel[4 * v + 0] = n;
+            a.sel[4 * v + 1] = unsigned(b1);
+            a.sel[4 * v + 2] = below;
+        }
+        __syncthreads();
+    }
+    if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
+
+    // ---- phase B: stream every view's slice of M_thin (8 loads in flight per
+    // thread); the candidates (kept values in the median bin) are compacted per
+    // block round, appended with one reservation, and counted on bits [18:9]
+    float *cbuf = reinterpret_cast<float *>(&s);  // NT * kStream floats (the stencil buffers are free)
+    constexpr int kStream = 8;
+    static_assert(sizeof(TileSmem) >= NT * kStream * sizeof(float), "candidate buffer");
+    __shared__ unsigned s_base;
+    for (int v = 0; v < a.nviews; ++v) {
+        const unsigned n = a.sel[4 * v + 0];
+        if (n == 0) continue;
+        const unsigned b1 = a.sel[4 * v + 1];
+        const EdgeView &V = a.v[v];
+        const long long npx = (long long)V.w * V.h;
+        const long long lo = npx * blockIdx.x / G, hi = npx * (blockIdx.x + 1) / G;
+        const float *src = a.E + V.out_off;
+        unsigned *h2 = a.hist2 + (size_t)v * kBins2;
+        for (long long base = lo; base < hi; base += NT * kStream) {
+            float val[kStream];
+            unsigned mine = 0;
+#pragma unroll
+            for (int k = 0; k < kStream; ++k) {
+                const long long e = base + k * NT + tid;
+                val[k] = e < hi ? src[e] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < kStream; ++k) {
+                const bool pick = val[k] > 0.f && (__float_as_uint(val[k]) >> kShift1) == b1;
+                if (!pick) val[k] = -1.f;
+                mine += pick;
+            }
+            unsigned off;
+            const unsigned total = block_exclusive_scan(mine, &off);
+            if (total == 0) continue;
+#pragma unroll
+            for (int k = 0; k < kStream; ++k)
+                if (val[k] >= 0.f) {
+                    cbuf[off++] = val[k];
+                    atomicAdd(&h2[(__float_as_uint(val[k]) >> kShift2) & (kBins2 - 1)], 1u);
+                }
+            if (tid == 0) s_base = atomicAdd(a.cand_count + v, total);
+            __syncthreads();
+            float *dst = a.cand + V.out_off + s_base;
+            for (unsigned i = tid; i < total; i += NT) dst[i] = cbuf[i];
+            __syncthreads();
+        }
+    }
+    if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
+
+    // ---- phase C: exact median of each view (block v): the level-2 bin from
+    // the candidates' histogram, then bits [8:0] among the candidates in it
+    for (int v = blockIdx.x; v < a.nviews; v += G) {
+        const unsigned n = a.sel[4 * v + 0];
         unsigned bits = 0;
         if (n > 0) {
-            int b1;
-            unsigned below;
-            block_find_bin(h, kBins1, (n - 1) / 2, &b1, &below);
-            bits = select_from_candidates(a.cand + a.v[v].out_off, a.cand_count[v], (n - 1) / 2 - below,
-                                          b1, hist_s);
+            const unsigned b1 = a.sel[4 * v + 1];
+            unsigned rank = (n - 1) / 2 - a.sel[4 * v + 2];
+            int b2;
+            unsigned below2;
+            block_find_bin(a.hist2 + (size_t)v * kBins2, kBins2, rank, &b2, &below2);
+            rank -= below2;
+            for (int i = tid; i < kBins3; i += NT) hist_s[i] = 0;
+            __syncthreads();
+            const float *cand = a.cand + a.v[v].out_off;
+            const unsigned count = a.cand_count[v];
+            for (unsigned i = tid; i < count; i += NT) {
+                const unsigned cb = __float_as_uint(cand[i]);
+                if (((cb >> kShift2) & (kBins2 - 1)) == unsigned(b2)) atomicAdd(&hist_s[cb & (kBins3 - 1)], 1u);
+            }
+            __syncthreads();
+            int b3;
+            unsigned below3;
+            block_find_bin(hist_s, kBins3, rank, &b3, &below3);
+            bits = (b1 << kShift1) | (unsigned(b2) << kShift2) | unsigned(b3);
         }
         if (tid == 0) {
             a.med_bits[v] = bits;
@@ -447,21 +497,25 @@ __global__ void __launch_bounds__(NT) edge_fused_kernel(const __grid_constant__ 
     }
     if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
 
-    // ---- phase D: E = M_thin / median
-    for (int t = t_begin; t < t_end; ++t) {
-        int v = find_view(a, t);
-        const EdgeView &V = a.v[v];
-        float med = __uint_as_float(a.med_bits[v]);
+    // ---- phase D: E = M_thin / median, streaming every view's slice
+    for (int v = 0; v < a.nviews; ++v) {
+        const float med = __uint_as_float(a.med_bits[v]);
         if (!(med > 0.f)) continue;
-        int lt = t - V.tile_base;
-        int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
-        for (int idx = tid; idx < TH * TW; idx += NT) {
-            int r = idx / TW, c = idx - r * TW;
-            int y = ty * TH + r, x = tx * TW + c;
-            if (y < V.h && x < V.w) {
-                long long o = V.out_off + (long long)y * V.w + x;
-                float mt = a.E[o];
-                if (mt > 0.f) a.E[o] = __fdiv_rn(mt, med);
+        const EdgeView &V = a.v[v];
+        const long long npx = (long long)V.w * V.h;
+        const long long lo = npx * blockIdx.x / G, hi = npx * (blockIdx.x + 1) / G;
+        float *e = a.E + V.out_off;
+        for (long long base = lo; base < hi; base += NT * kStream) {
+            float val[kStream];
+#pragma unroll
+            for (int k = 0; k < kStream; ++k) {
+                const long long i = base + k * NT + tid;
+                val[k] = i < hi ? e[i] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < kStream; ++k) {
+                const long long i = base + k * NT + tid;
+                if (i < hi && val[k] > 0.f) e[i] = __fdiv_rn(val[k], med);
             }
         }
     }
@@ -636,7 +690,7 @@ void fill_taps(const gsp_edge_opts &o, float &w0, float &w1, float &w2)
 }
 
 struct EdgeLayout {
-    unsigned *hist1, *cand_count, *med_bits, *bar;
+    unsigned *hist1, *hist2, *sel, *cand_count, *med_bits, *bar;
     float *cand;
     PlainBufs plain;
     size_t bytes;
@@ -647,6 +701,8 @@ EdgeLayout edge_layout(void *ws, const gsp_image_desc *imgs, int nv, int mode)
     Carver c(ws);
     EdgeLayout L{};
     L.hist1 = c.take<unsigned>((size_t)nv * kBins1);
+    L.hist2 = c.take<unsigned>((size_t)nv * kBins2);
+    L.sel = c.take<unsigned>((size_t)nv * 4);
     L.cand_count = c.take<unsigned>(nv);
     L.med_bits = c.take<unsigned>(nv);
     L.bar = c.take<unsigned>(2);
@@ -800,6 +856,8 @@ extern "C" gsp_status gsp_edge_map(const gsp_image_desc *imgs, int32_t nv, float
     a.mask = nms_mask_out;
     a.median_out = median_out;
     a.hist1 = L.hist1;
+    a.hist2 = L.hist2;
+    a.sel = L.sel;
     a.cand_count = L.cand_count;
     a.cand = L.cand;
     a.med_bits = L.med_bits;
