@@ -168,12 +168,14 @@ typedef struct gsp_render_opts {
     int32_t bwd_variant;   /* adjoint compositing variant, 0 .. GSP_BWD_VARIANTS - 1 (0: default) */
 } gsp_render_opts;
 
-/* Compositing variants (pixels per thread, Gaussians staged per shared-memory batch).
+/* Compositing variants (pixels per thread, Gaussians staged per shared-memory batch,
+ * warp-level culling of staged Gaussians by footprint box: c = on, n = off).
  * The results do not depend on the variant, only the speed does; an autotuner picks
- * one per workload.  Forward: (1, 256), (2, 256), (1, 128), (2, 128).
- * Adjoint: (2, 256), (1, 256), (4, 256), (2, 128). */
-#define GSP_FWD_VARIANTS 4
-#define GSP_BWD_VARIANTS 4
+ * one per workload.  Forward: (1, 256, c), (2, 256, c), (1, 128, c), (2, 128, c),
+ * (1, 128, n), (2, 128, n).  Adjoint: (2, 256, c), (1, 256, c), (4, 256, c),
+ * (2, 128, c), (2, 128, n), (4, 128, c). */
+#define GSP_FWD_VARIANTS 6
+#define GSP_BWD_VARIANTS 6
 
 /* Workspace bytes for a fwd/bwd pair over these cameras (host array). */
 size_t gsp_render_workspace_size(int64_t capacity, int32_t sh_degree, const gsp_camera *cams,

@@ -18,7 +18,7 @@ GSP_MAX_VIEWS = 64
 GSP_TILE = 16
 GSP_EDGE_FUSED, GSP_EDGE_PLAIN = 0, 1
 GSP_TOPK_STATIC_MAX_CAPACITY = 1 << 24
-GSP_FWD_VARIANTS, GSP_BWD_VARIANTS = 4, 4
+GSP_FWD_VARIANTS, GSP_BWD_VARIANTS = 6, 6
 
 
 class ImageDesc(ctypes.Structure):

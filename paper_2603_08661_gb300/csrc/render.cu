@@ -1179,7 +1179,7 @@ __device__ __forceinline__ float target_value(const ViewP &V, int x, int y, int 
 // of PPT pixels.  The tile's list is staged through shared memory in batches
 // of BATCH Gaussians; the block leaves when every pixel has stopped.
 
-template <int PPT, int BATCH>
+template <int PPT, int BATCH, bool CULL>
 __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_constant__ Views vs, State st,
                                                                 long long cap, const float *edge, float *rgb_out,
                                                                 float *T_out, int32_t *last_out, float *score)
@@ -1247,7 +1247,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
         for (int j = 0; j < cnt; ++j) {
             const float4 gx = s_xyo[j], gc = s_con[j];
             // the footprint's bounding box misses every pixel of the warp (warp-uniform)
-            if (fabsf(gx.x - wcx) > gx.w + whw || fabsf(gx.y - wcy) > gc.w + whh) continue;
+            if (CULL && (fabsf(gx.x - wcx) > gx.w + whw || fabsf(gx.y - wcy) > gc.w + whh)) continue;
             float sv = 0.f;
 #pragma unroll
             for (int m = 0; m < PPT; ++m) {
@@ -1394,7 +1394,7 @@ constexpr int kG2 = 10;  // mean x, mean y, conic A, B, C, opacity, r, g, b, sco
 // Gaussian the thread sums its pixels' contributions, the warp reduces them
 // (transpose reduction), warps meet in shared accumulators, and one global
 // atomic per (Gaussian, tile, value) leaves the block.
-template <int PPT, int BATCH>
+template <int PPT, int BATCH, bool CULL>
 __global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) composite_bwd(const __grid_constant__ Views vs, State st,
                                                                 long long cap, const float *dL_drgb, const float *rgb,
                                                                 const float *T_fin, const int32_t *last_idx,
@@ -1477,7 +1477,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) c
             const int pos = lo + j;
             const float4 gx = s_xyo[j], gc = s_con[j];
             // the footprint's bounding box misses every pixel of the warp (warp-uniform)
-            if (fabsf(gx.x - wcx) > gx.w + whw || fabsf(gx.y - wcy) > gc.w + whh) continue;
+            if (CULL && (fabsf(gx.x - wcx) > gx.w + whw || fabsf(gx.y - wcy) > gc.w + whh)) continue;
             float val[kG2];
 #pragma unroll
             for (int k = 0; k < kG2; ++k) val[k] = 0.f;
@@ -1702,29 +1702,35 @@ __global__ void __launch_bounds__(kProjBwdThreads) project_bwd(const __grid_cons
     }
 }
 
-// Compositing variants (pixels per thread, batch depth); index 0 is the default.
+// Compositing variants (pixels per thread, batch depth, warp culling); index 0 is the default.
 // gsp_render_opts selects one per pass; the autotuner times them on the workload.
 struct Variant {
     int ppt, batch;
+    bool cull;  // warp-level footprint-box culling of staged Gaussians
 };
-constexpr Variant kFwdVariants[] = {{1, 256}, {2, 256}, {1, 128}, {2, 128}};
-constexpr Variant kBwdVariants[] = {{2, 256}, {1, 256}, {4, 256}, {2, 128}};
+constexpr Variant kFwdVariants[] = {{1, 256, true}, {2, 256, true}, {1, 128, true}, {2, 128, true},
+                                    {1, 128, false}, {2, 128, false}};
+constexpr Variant kBwdVariants[] = {{2, 256, true}, {1, 256, true}, {4, 256, true}, {2, 128, true},
+                                    {2, 128, false}, {4, 128, true}};
 constexpr int kNumFwdVariants = sizeof(kFwdVariants) / sizeof(Variant);
 constexpr int kNumBwdVariants = sizeof(kBwdVariants) / sizeof(Variant);
 
-template <int PPT, int BATCH>
+template <int V>
 void launch_fwd(const Views &vs, const State &S, long long cap, const float *edge, float *rgb, float *T, int32_t *last,
                 float *score, cudaStream_t s)
 {
-    composite_fwd<PPT, BATCH><<<vs.total_tiles, kTilePix / PPT, 0, s>>>(vs, S, cap, edge, rgb, T, last, score);
+    constexpr Variant var = kFwdVariants[V];
+    composite_fwd<var.ppt, var.batch, var.cull>
+        <<<vs.total_tiles, kTilePix / var.ppt, 0, s>>>(vs, S, cap, edge, rgb, T, last, score);
 }
 
-template <int PPT, int BATCH>
+template <int V>
 void launch_bwd(const Views &vs, const State &S, long long cap, const float *dL, const float *rgb, const float *T,
                 const int32_t *last, const float *edge, float *score, float inv_norm, cudaStream_t s)
 {
-    composite_bwd<PPT, BATCH><<<vs.total_tiles, kTilePix / PPT, 0, s>>>(vs, S, cap, dL, rgb, T, last, edge, score,
-                                                                       inv_norm);
+    constexpr Variant var = kBwdVariants[V];
+    composite_bwd<var.ppt, var.batch, var.cull>
+        <<<vs.total_tiles, kTilePix / var.ppt, 0, s>>>(vs, S, cap, dL, rgb, T, last, edge, score, inv_norm);
 }
 
 // ------------------------------------------------------------------- host
@@ -1953,10 +1959,12 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     GSP_LAUNCH_CHECK();
     stage_begin("composite_fwd", s);
     switch (opts->fwd_variant) {
-    case 1: launch_fwd<kFwdVariants[1].ppt, kFwdVariants[1].batch>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
-    case 2: launch_fwd<kFwdVariants[2].ppt, kFwdVariants[2].batch>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
-    case 3: launch_fwd<kFwdVariants[3].ppt, kFwdVariants[3].batch>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
-    default: launch_fwd<kFwdVariants[0].ppt, kFwdVariants[0].batch>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
+    case 1: launch_fwd<1>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
+    case 2: launch_fwd<2>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
+    case 3: launch_fwd<3>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
+    case 4: launch_fwd<4>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
+    case 5: launch_fwd<5>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
+    default: launch_fwd<0>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
     }
     stage_end("composite_fwd", s);
     GSP_LAUNCH_CHECK();
@@ -2003,10 +2011,12 @@ extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *c
     GSP_CUDA_TRY(cudaMemsetAsync(S.g2d, 0, sizeof(float4) * 3 * (size_t)nv * cap, s));
     tile_order_bwd<<<1, 1024, 0, s>>>(vs.total_tiles, S);
     switch (opts->bwd_variant) {
-    case 1: launch_bwd<kBwdVariants[1].ppt, kBwdVariants[1].batch>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
-    case 2: launch_bwd<kBwdVariants[2].ppt, kBwdVariants[2].batch>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
-    case 3: launch_bwd<kBwdVariants[3].ppt, kBwdVariants[3].batch>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
-    default: launch_bwd<kBwdVariants[0].ppt, kBwdVariants[0].batch>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
+    case 1: launch_bwd<1>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
+    case 2: launch_bwd<2>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
+    case 3: launch_bwd<3>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
+    case 4: launch_bwd<4>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
+    case 5: launch_bwd<5>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
+    default: launch_bwd<0>(vs, S, cap, dL_drgb, rgb, T_final, last_idx, edge, score, inv_norm, s); break;
     }
     stage_end("composite_bwd", s);
     GSP_LAUNCH_CHECK();
