@@ -1148,7 +1148,7 @@ __global__ void __launch_bounds__(kBinThreads) l2_scatter(const __grid_constant_
 // ------------------------------------------------------------- compositing
 
 struct Alpha {
-    float G, raw, alpha, dx, dy;
+    float G, raw, alpha, dx, dy, dxx, dyy, dxy;
     bool pass;
 };
 
@@ -1160,9 +1160,10 @@ __device__ __forceinline__ Alpha eval_alpha(float4 xyo, float4 con, float px, fl
     Alpha r;
     r.dx = __fsub_rn(px, xyo.x);
     r.dy = __fsub_rn(py, xyo.y);
-    const float power =
-        __fmaf_rn(con.x, __fmul_rn(r.dx, r.dx), __fmaf_rn(con.z, __fmul_rn(r.dy, r.dy),
-                                                          __fmul_rn(con.y, __fmul_rn(r.dx, r.dy))));
+    r.dxx = __fmul_rn(r.dx, r.dx);
+    r.dyy = __fmul_rn(r.dy, r.dy);
+    r.dxy = __fmul_rn(r.dx, r.dy);
+    const float power = __fmaf_rn(con.x, r.dxx, __fmaf_rn(con.z, r.dyy, __fmul_rn(con.y, r.dxy)));
     r.G = __expf(power);
     r.raw = __fmul_rn(xyo.z, r.G);
     r.alpha = fminf(kAlphaMax, r.raw);
@@ -1387,7 +1388,7 @@ __device__ __forceinline__ float warp_transpose_reduce10(float v[10], int *idx)
     return d;
 }
 
-constexpr int kG2 = 10;  // mean x, mean y, conic A, B, C, opacity, r, g, b, score
+constexpr int kG2 = 10;  // moments dx, dy, dx^2, dx dy, dy^2 (-> mean x, y, conic A, B, C), opacity, r, g, b, score
 
 // Adjoint of the compositing, replayed back to front from T_final and the
 // last position, each thread a vertical run of PPT pixels.  For each
@@ -1501,14 +1502,15 @@ __global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) c
                 acc1[m] = acc1[m] * one_m + c.y * a.alpha;
                 acc2[m] = acc2[m] * one_m + c.z * a.alpha;
                 if (a.raw < kAlphaMax) {
-                    // gc = (-A/2, -B, -C/2); d power / d mean = (A dx + B dy, B dx + C dy)
+                    // moments of dpow = dL/dpower: the mean and conic gradients are
+                    // linear in them, the conic is applied once per Gaussian
                     const float dpow = dalpha * gx.z * a.G;
                     val[5] += dalpha * a.G;
-                    val[0] += dpow * (-2.f * gc.x * a.dx - gc.y * a.dy);
-                    val[1] += dpow * (-gc.y * a.dx - 2.f * gc.z * a.dy);
-                    val[2] += -0.5f * dpow * a.dx * a.dx;
-                    val[3] += -dpow * a.dx * a.dy;
-                    val[4] += -0.5f * dpow * a.dy * a.dy;
+                    val[0] += dpow * a.dx;
+                    val[1] += dpow * a.dy;
+                    val[2] += dpow * a.dxx;
+                    val[3] += dpow * a.dxy;
+                    val[4] += dpow * a.dyy;
                 }
                 if (want_score) val[9] += w * E[m];
             }
@@ -1522,6 +1524,17 @@ __global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) c
         for (int q = tid; q < cnt; q += NT) {
             float *a = s_acc[q];
             float *gp = reinterpret_cast<float *>(g2d + (long long)s_id[q] * 3);
+            // power = A' dx^2 + B' dx dy + C' dy^2 with (A', B', C') = s_con and
+            // dx = px - mean x: d power / d mean = -(2 A' dx + B' dy, B' dx + 2 C' dy),
+            // d power / d(A', B', C') = (dx^2, dx dy, dy^2) (the conic's own gradient
+            // then follows from A' = -A/2, B' = -B, C' = -C/2)
+            const float4 cq = s_con[q];
+            const float m1 = a[0], m2 = a[1];
+            a[0] = -2.f * cq.x * m1 - cq.y * m2;
+            a[1] = -cq.y * m1 - 2.f * cq.z * m2;
+            a[2] = -0.5f * a[2];
+            a[3] = -a[3];
+            a[4] = -0.5f * a[4];
 #pragma unroll
             for (int k = 0; k < 9; ++k)
                 if (a[k] != 0.f) atomicAdd(gp + k, a[k]);
