@@ -1427,14 +1427,18 @@ __global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) c
     const float wcy = tyy * kTile + (32 * wid / kTile) * PPT + PPT;
     const float whw = 0.5f * kTile - 0.5f, whh = PPT - 0.5f;
 
-    float T[PPT], g0[PPT], g1[PPT], g2[PPT], E[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
+    // S = g . (colour composited behind the current position, normalised by the
+    // transmittance in front of it): dL/dalpha_i = T_i (g . c_i - S_i), and
+    // S_{i-1} = S_i (1 - alpha_i) + alpha_i (g . c_i) (a scalar per pixel in place
+    // of the three colour channels)
+    float T[PPT], g0[PPT], g1[PPT], g2[PPT], E[PPT], S[PPT];
     int last[PPT];
     int mylast = 0;
 #pragma unroll
     for (int m = 0; m < PPT; ++m) {
         const int y = y0 + m;
         T[m] = 1.f; g0[m] = g1[m] = g2[m] = 0.f; E[m] = 0.f; last[m] = 0;
-        acc0[m] = acc1[m] = acc2[m] = 0.f;
+        S[m] = 0.f;
         if (x < V.w && y < V.h) {
             const long long pid = V.pix_off + (long long)y * V.w + x;
             T[m] = T_fin[pid];
@@ -1491,16 +1495,16 @@ __global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) c
                 active = true;
                 const float4 c = s_col[j];
                 const float one_m = __fsub_rn(1.f, a.alpha);
-                T[m] = __fdiv_rn(T[m], one_m);
+                // 1 - alpha >= 0.01: the fast quotient (2 ulp) keeps the replayed
+                // transmittance within a few ulp per step of the forward's
+                T[m] = __fdividef(T[m], one_m);
                 const float w = a.alpha * T[m];
                 val[6] += w * g0[m];
                 val[7] += w * g1[m];
                 val[8] += w * g2[m];
-                const float dalpha =
-                    T[m] * (g0[m] * (c.x - acc0[m]) + g1[m] * (c.y - acc1[m]) + g2[m] * (c.z - acc2[m]));
-                acc0[m] = acc0[m] * one_m + c.x * a.alpha;
-                acc1[m] = acc1[m] * one_m + c.y * a.alpha;
-                acc2[m] = acc2[m] * one_m + c.z * a.alpha;
+                const float gc_dot = g0[m] * c.x + g1[m] * c.y + g2[m] * c.z;
+                const float dalpha = T[m] * (gc_dot - S[m]);
+                S[m] = S[m] * one_m + a.alpha * gc_dot;
                 if (a.raw < kAlphaMax) {
                     // moments of dpow = dL/dpower: the mean and conic gradients are
                     // linear in them, the conic is applied once per Gaussian
