@@ -33,6 +33,8 @@ namespace {
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
+constexpr float kLog2E = 1.4426950408889634f;  // log2(e): the stored conic gives power in base 2
+constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kNear = 0.2f;
 constexpr int kRowCap = 16;  // tile rows per Gaussian with an exact column interval
 constexpr int kProjBwdThreads = 128;
@@ -383,11 +385,13 @@ __device__ __forceinline__ unsigned long long project_one(const Views &vs, const
                 }
             }
             // conic pre-scaled so that power = -1/2 d^T Q d = A' dx^2 + C' dy^2 + B' dx dy
-            // (A' = -A/2, B' = -B, C' = -C/2: exact scalings)
+            // (A' = -A/2, B' = -B, C' = -C/2), stored times log2(e): compositing takes
+            // G = 2^(stored form) without a scaling per pixel
             // .w slots: half-extents of the footprint's bounding box (compositing culls
             // whole warps with them)
+            const float ci = kLog2E * id;
             st.xyo[o] = make_float4(mx, my, opac, ex);
-            st.con[o] = make_float4(-0.5f * (P.c * id), P.b * id, -0.5f * (P.a * id), ey);
+            st.con[o] = make_float4(-0.5f * (P.c * ci), P.b * ci, -0.5f * (P.a * ci), ey);
             st.col[o] = make_float4(col[0], col[1], col[2], __uint_as_float(clampbits));
         }
         st.rect[o] = rect;
@@ -1163,8 +1167,8 @@ __device__ __forceinline__ Alpha eval_alpha(float4 xyo, float4 con, float px, fl
     r.dxx = __fmul_rn(r.dx, r.dx);
     r.dyy = __fmul_rn(r.dy, r.dy);
     r.dxy = __fmul_rn(r.dx, r.dy);
-    const float power = __fmaf_rn(con.x, r.dxx, __fmaf_rn(con.z, r.dyy, __fmul_rn(con.y, r.dxy)));
-    r.G = __expf(power);
+    const float power2 = __fmaf_rn(con.x, r.dxx, __fmaf_rn(con.z, r.dyy, __fmul_rn(con.y, r.dxy)));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r.G) : "f"(power2));
     r.raw = __fmul_rn(xyo.z, r.G);
     r.alpha = fminf(kAlphaMax, r.raw);
     r.pass = r.alpha >= kAlphaMin;
@@ -1532,8 +1536,8 @@ __global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) c
             // dx = px - mean x: d power / d mean = -(2 A' dx + B' dy, B' dx + 2 C' dy),
             // d power / d(A', B', C') = (dx^2, dx dy, dy^2) (the conic's own gradient
             // then follows from A' = -A/2, B' = -B, C' = -C/2)
-            const float4 cq = s_con[q];
-            const float m1 = a[0], m2 = a[1];
+            const float4 cq = s_con[q];  // times log2(e)
+            const float m1 = kLn2 * a[0], m2 = kLn2 * a[1];
             a[0] = -2.f * cq.x * m1 - cq.y * m2;
             a[1] = -cq.y * m1 - 2.f * cq.z * m2;
             a[2] = -0.5f * a[2];
