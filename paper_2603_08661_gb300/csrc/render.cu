@@ -1151,6 +1151,26 @@ __global__ void __launch_bounds__(kBinThreads) l2_scatter(const __grid_constant_
 
 // ------------------------------------------------------------- compositing
 
+// Pixel layout of a compositing block (one 16x16 tile, kTilePix / PPT threads):
+// each warp covers an 8-column x 4 PPT-row block (lanes 8 wide, 4 tall, each a
+// vertical run of PPT pixels), the warps 2 across.  A compact warp footprint
+// keeps the warp's pixels close, so fewer Gaussians reach only some of them.
+template <int PPT>
+struct WarpBlock {
+    int x, y0;            // the thread's column and first row (image pixels)
+    float wcx, wcy;       // centre of the warp's pixel centres
+    static constexpr float whw = 3.5f, whh = 2.f * PPT - 0.5f;  // their half-extents
+    __device__ __forceinline__ WarpBlock(int txx, int tyy, int tid)
+    {
+        const int lane = tid & 31, wid = tid >> 5;
+        const int wx = wid & 1, wy = wid >> 1;
+        x = txx * kTile + wx * 8 + (lane & 7);
+        y0 = tyy * kTile + (wy * 4 + (lane >> 3)) * PPT;
+        wcx = txx * kTile + wx * 8 + 4.f;
+        wcy = tyy * kTile + wy * 4 * PPT + 2.f * PPT;
+    }
+};
+
 struct Alpha {
     float G, raw, alpha, dx, dy, dxx, dyy, dxy;
     bool pass;
@@ -1203,16 +1223,13 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
     const int lt = gt - V.tile_base;
     const int tyy = lt / V.tiles_x, txx = lt - tyy * V.tiles_x;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int x = txx * kTile + (tid & (kTile - 1));
-    const int y0 = tyy * kTile + (tid / kTile) * PPT;
+    const WarpBlock<PPT> wb(txx, tyy, tid);
+    const int x = wb.x, y0 = wb.y0;
+    const float wcx = wb.wcx, wcy = wb.wcy, whw = wb.whw, whh = wb.whh;
     const float px = x + 0.5f;
     const int len = int(st.tile_len[gt]);
     const int32_t *list = st.ids + st.tile_start[gt];
     const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
-    // the warp's pixel centres: 16 columns x 2 PPT rows, centre (wcx, wcy)
-    const float wcx = txx * kTile + 0.5f * kTile;
-    const float wcy = tyy * kTile + (32 * wid / kTile) * PPT + PPT;
-    const float whw = 0.5f * kTile - 0.5f, whh = PPT - 0.5f;
     if (tid == 0) {
         s_maxlast = 0;
         s_contrib = 0;
@@ -1417,19 +1434,15 @@ __global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) c
     const int lt = gt - V.tile_base;
     const int tyy = lt / V.tiles_x, txx = lt - tyy * V.tiles_x;
     const int tid = threadIdx.x;
-    const int x = txx * kTile + (tid & (kTile - 1));
-    const int y0 = tyy * kTile + (tid / kTile) * PPT;
+    const WarpBlock<PPT> wb(txx, tyy, tid);
+    const int x = wb.x, y0 = wb.y0;
     const float px = x + 0.5f;
     const int list_len = int(st.tile_len[gt]);
     const int32_t *list = st.ids + st.tile_start[gt];
     const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
     float4 *g2d = st.g2d + (size_t)v * cap * 3;
     const bool want_score = score && edge;
-    const int wid = tid >> 5;
-    // the warp's pixel centres: 16 columns x 2 PPT rows, centre (wcx, wcy)
-    const float wcx = txx * kTile + 0.5f * kTile;
-    const float wcy = tyy * kTile + (32 * wid / kTile) * PPT + PPT;
-    const float whw = 0.5f * kTile - 0.5f, whh = PPT - 0.5f;
+    const float wcx = wb.wcx, wcy = wb.wcy, whw = wb.whw, whh = wb.whh;
 
     // S = g . (colour composited behind the current position, normalised by the
     // transmittance in front of it): dL/dalpha_i = T_i (g . c_i - S_i), and
