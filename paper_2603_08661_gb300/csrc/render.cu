@@ -71,7 +71,7 @@ struct Params {
 
 struct State {
     float4 *xyo;   // [V][cap] (mean x, mean y, opacity, depth)
-    float4 *con;   // [V][cap] (-A/2, -B, -C/2, 0) of the conic Q = [[A, B], [B, C]]
+    float4 *con;   // [V][cap] log2(e) (-A/2, -B, -C/2) of the conic Q = [[A, B], [B, C]], bbox half-height
     float4 *col;   // [V][cap] (r, g, b, clamp bits)
     uint2 *rect;   // [V][cap] (tx0 | ty0 << 16, tx1 | ty1 << 16); empty if tx1 < tx0
     uchar2 *rowint;  // [V][cap][kRowCap] per tile row of the rectangle: columns (lo, hi) - tx0 the
