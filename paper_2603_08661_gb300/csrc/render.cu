@@ -630,11 +630,13 @@ __global__ void __launch_bounds__(kRsThreads) rs_scatter(const K *kin, const int
 //               order; lanes sharing a supertile write in lane = rank order)
 //   l2_count    per chunk: the 64-bit tile mask of each entry (rows of the
 //               rectangle inside the supertile, culled by the exact column
-//               intervals), stored; per-tile counts from warp ballots
+//               intervals), stored; per-tile counts from the transposed masks
 //   l2_scan     one block per supertile: chunk offsets per tile, list lengths
 //   tile_scan   one block: list starts of all tiles
-//   l2_scatter  per chunk: for each tile and round, a ballot gives every lane
-//               its slot; each store writes a contiguous run of the list
+//   l2_scatter  per chunk and half supertile: the transposed masks give lane L
+//               the entries of tile L in order; it writes their chunk indices
+//               to a shared staging run, and the warp copies each tile's run
+//               out with coalesced stores
 
 constexpr int kSuper = 8;                 // supertile edge, in tiles
 constexpr int kBinRanks = 256;            // ranks (level 1) or entries (level 2) per warp chunk
@@ -898,6 +900,26 @@ __global__ void __launch_bounds__(kBinThreads) l1_scatter(const __grid_constant_
     }
 }
 
+// 32 x 32 bit-matrix transpose across the warp: lane L returns the word whose
+// bit i is bit L of lane i's x.  Stage j exchanges, between lanes L and L ^ j,
+// the off-diagonal j x j blocks of every 2j x 2j block: a rotate by j (left in
+// the lower lane, right in the upper one) moves the partner's block into place
+// and a mask merge keeps the lane's own diagonal block.
+__device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane)
+{
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        const unsigned m = j == 16 ? 0x0000ffffu : j == 8 ? 0x00ff00ffu : j == 4 ? 0x0f0f0f0fu
+                           : j == 2 ? 0x33333333u : 0x55555555u;
+        const bool upper = lane & j;
+        const unsigned y = __shfl_xor_sync(0xffffffffu, x, j);
+        const unsigned t = __funnelshift_l(y, y, upper ? 32 - j : j);
+        const unsigned keep = upper ? ~m : m;
+        x = (x & keep) | (t & ~keep);
+    }
+    return x;
+}
+
 // Level-2 chunk c: its supertile (largest gs with chunk2_base[gs] <= c).
 __device__ __forceinline__ int l2_super(const State &st, int total_super, unsigned c)
 {
@@ -936,29 +958,13 @@ __global__ void __launch_bounds__(kBinThreads) l2_count(const __grid_constant__ 
                 st.mask1[e] = m[k];
             }
         }
-        // per-lane counts of each tile over the lane's 8 entries, bit-sliced: four
-        // 64-bit planes hold a 4-bit counter per tile (carry-save additions)
-        unsigned long long p0 = 0, p1 = 0, p2 = 0, p3 = 0;
-#pragma unroll
-        for (int k = 0; k < kBinRounds; ++k) {
-            const unsigned long long c0 = p0 & m[k];
-            p0 ^= m[k];
-            const unsigned long long c1 = p1 & c0;
-            p1 ^= c0;
-            const unsigned long long c2 = p2 & c1;
-            p2 ^= c1;
-            p3 |= c2;
-        }
+        // per-tile counts: after the transpose lane L holds, per round, the
+        // entries of tile L (low half) and of tile L + 32 (high half)
         unsigned mc0 = 0, mc1 = 0;
 #pragma unroll
-        for (int b = 0; b < 64; ++b) {
-            const unsigned cnt_lane = unsigned((p0 >> b) & 1ull) | (unsigned((p1 >> b) & 1ull) << 1) |
-                                      (unsigned((p2 >> b) & 1ull) << 2) | (unsigned((p3 >> b) & 1ull) << 3);
-            const unsigned cnt = __reduce_add_sync(0xffffffffu, cnt_lane);
-            if (lane == (b & 31)) {
-                if (b < 32) mc0 = cnt;
-                else mc1 = cnt;
-            }
+        for (int k = 0; k < kBinRounds; ++k) {
+            mc0 += __popc(warp_transpose32(unsigned(m[k]), lane));
+            mc1 += __popc(warp_transpose32(unsigned(m[k] >> 32), lane));
         }
         st.count2[(size_t)c * 64 + lane] = mc0;
         st.count2[(size_t)c * 64 + 32 + lane] = mc1;
@@ -1093,9 +1099,14 @@ __global__ void __launch_bounds__(1024) tile_order_bwd(int total_tiles, State st
 
 __global__ void __launch_bounds__(kBinThreads) l2_scatter(const __grid_constant__ Views vs, State st)
 {
+    // per warp: the chunk's ids, and the staged chunk indices of one half
+    // supertile (at most 256 entries x 32 tiles)
+    __shared__ int32_t s_g[kBinWarps][kBinRanks];
+    __shared__ uint8_t s_stage[kBinWarps][kBinRanks * 32];
     if (*st.overflow) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
+    int32_t *sg = s_g[wid];
+    uint8_t *stg = s_stage[wid];
     const unsigned nchunk = st.chunk2_base[vs.total_super];
     for (unsigned c = blockIdx.x * kBinWarps + wid; c < nchunk; c += gridDim.x * kBinWarps) {
         const int gs = l2_super(st, vs.total_super, c);
@@ -1105,46 +1116,61 @@ __global__ void __launch_bounds__(kBinThreads) l2_scatter(const __grid_constant_
         const int sy = s / V.sx, sx = s - sy * V.sx;
         const unsigned e0 = st.list1_start[gs] + (c - st.chunk2_base[gs]) * kBinRanks;
         const unsigned e1 = st.list1_start[gs] + st.len1[gs];
-        int g[kBinRounds];
         unsigned long long m[kBinRounds];
-        unsigned long long any = 0;
 #pragma unroll
         for (int k = 0; k < kBinRounds; ++k) {
             const unsigned e = e0 + 32 * k + lane;
-            g[k] = 0;
+            int g = 0;
             m[k] = 0;
             if (e < e1) {
-                g[k] = st.id1[e];
+                g = st.id1[e];
                 m[k] = st.mask1[e];
             }
-            any |= m[k];
+            sg[32 * k + lane] = g;
         }
-        const unsigned any_lo = __reduce_or_sync(0xffffffffu, unsigned(any));
-        const unsigned any_hi = __reduce_or_sync(0xffffffffu, unsigned(any >> 32));
         const int gt0 = super_tile(V, sx, sy, lane), gt1 = super_tile(V, sx, sy, lane + 32);
         const unsigned cur0 = gt0 >= 0 ? st.tile_start[gt0] + st.count2[(size_t)c * 64 + lane] : 0u;
         const unsigned cur1 = gt1 >= 0 ? st.tile_start[gt1] + st.count2[(size_t)c * 64 + 32 + lane] : 0u;
-        // two halves of 32 tiles: the masks' 32-bit halves are shifted once per tile
-        // (a rolled loop: unrolling all 64 tiles overflows the instruction cache)
-#pragma unroll
+        __syncwarp();
+#pragma unroll 1
         for (int half = 0; half < 2; ++half) {
-            unsigned mh[kBinRounds];
+            // lane L: the entries (32 k + i) of tile 32 half + L, in chunk order
+            unsigned w[kBinRounds];
+            unsigned cnt = 0;
 #pragma unroll
-            for (int k = 0; k < kBinRounds; ++k) mh[k] = half ? unsigned(m[k] >> 32) : unsigned(m[k]);
-            unsigned present = half ? any_hi : any_lo;
+            for (int k = 0; k < kBinRounds; ++k) {
+                w[k] = warp_transpose32(half ? unsigned(m[k] >> 32) : unsigned(m[k]), lane);
+                cnt += __popc(w[k]);
+            }
+            unsigned inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const unsigned off = inc - cnt;
+            unsigned p = off;
+#pragma unroll
+            for (int k = 0; k < kBinRounds; ++k) {
+                unsigned x = w[k];
+                while (x) {
+                    const int i = __ffs(x) - 1;
+                    x &= x - 1;
+                    stg[p++] = uint8_t(32 * k + i);
+                }
+            }
+            __syncwarp();
             const unsigned cur = half ? cur1 : cur0;
+            unsigned present = __ballot_sync(0xffffffffu, cnt != 0);
             while (present) {
                 const int b = __ffs(present) - 1;
                 present &= present - 1;
-                unsigned base = __shfl_sync(0xffffffffu, cur, b);
-#pragma unroll
-                for (int k = 0; k < kBinRounds; ++k) {
-                    const bool bit = (mh[k] >> b) & 1u;
-                    const unsigned bal = __ballot_sync(0xffffffffu, bit);
-                    if (bit) st.ids[base + __popc(bal & lt)] = g[k];
-                    base += __popc(bal);
-                }
+                const unsigned nb = __shfl_sync(0xffffffffu, cnt, b);
+                const unsigned ob = __shfl_sync(0xffffffffu, off, b);
+                const unsigned cb = __shfl_sync(0xffffffffu, cur, b);
+                for (unsigned i = lane; i < nb; i += 32) st.ids[cb + i] = sg[stg[ob + i]];
             }
+            __syncwarp();
         }
     }
 }
