@@ -633,10 +633,8 @@ __global__ void __launch_bounds__(kRsThreads) rs_scatter(const K *kin, const int
 //               intervals), stored; per-tile counts from the transposed masks
 //   l2_scan     one block per supertile: chunk offsets per tile, list lengths
 //   tile_scan   one block: list starts of all tiles
-//   l2_scatter  per chunk and half supertile: the transposed masks give lane L
-//               the entries of tile L in order; it writes their chunk indices
-//               to a shared staging run, and the warp copies each tile's run
-//               out with coalesced stores
+//   l2_scatter  per chunk: for each tile and round, a ballot gives every lane
+//               its slot; each store writes a contiguous run of the list
 
 constexpr int kSuper = 8;                 // supertile edge, in tiles
 constexpr int kBinRanks = 256;            // ranks (level 1) or entries (level 2) per warp chunk
@@ -1099,14 +1097,9 @@ __global__ void __launch_bounds__(1024) tile_order_bwd(int total_tiles, State st
 
 __global__ void __launch_bounds__(kBinThreads) l2_scatter(const __grid_constant__ Views vs, State st)
 {
-    // per warp: the chunk's ids, and the staged chunk indices of one half
-    // supertile (at most 256 entries x 32 tiles)
-    __shared__ int32_t s_g[kBinWarps][kBinRanks];
-    __shared__ uint8_t s_stage[kBinWarps][kBinRanks * 32];
     if (*st.overflow) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int32_t *sg = s_g[wid];
-    uint8_t *stg = s_stage[wid];
+    const unsigned lt = (1u << lane) - 1u;
     const unsigned nchunk = st.chunk2_base[vs.total_super];
     for (unsigned c = blockIdx.x * kBinWarps + wid; c < nchunk; c += gridDim.x * kBinWarps) {
         const int gs = l2_super(st, vs.total_super, c);
@@ -1116,61 +1109,46 @@ __global__ void __launch_bounds__(kBinThreads) l2_scatter(const __grid_constant_
         const int sy = s / V.sx, sx = s - sy * V.sx;
         const unsigned e0 = st.list1_start[gs] + (c - st.chunk2_base[gs]) * kBinRanks;
         const unsigned e1 = st.list1_start[gs] + st.len1[gs];
+        int g[kBinRounds];
         unsigned long long m[kBinRounds];
+        unsigned long long any = 0;
 #pragma unroll
         for (int k = 0; k < kBinRounds; ++k) {
             const unsigned e = e0 + 32 * k + lane;
-            int g = 0;
+            g[k] = 0;
             m[k] = 0;
             if (e < e1) {
-                g = st.id1[e];
+                g[k] = st.id1[e];
                 m[k] = st.mask1[e];
             }
-            sg[32 * k + lane] = g;
+            any |= m[k];
         }
+        const unsigned any_lo = __reduce_or_sync(0xffffffffu, unsigned(any));
+        const unsigned any_hi = __reduce_or_sync(0xffffffffu, unsigned(any >> 32));
         const int gt0 = super_tile(V, sx, sy, lane), gt1 = super_tile(V, sx, sy, lane + 32);
         const unsigned cur0 = gt0 >= 0 ? st.tile_start[gt0] + st.count2[(size_t)c * 64 + lane] : 0u;
         const unsigned cur1 = gt1 >= 0 ? st.tile_start[gt1] + st.count2[(size_t)c * 64 + 32 + lane] : 0u;
-        __syncwarp();
-#pragma unroll 1
+        // two halves of 32 tiles: the masks' 32-bit halves are shifted once per tile
+        // (a rolled loop: unrolling all 64 tiles overflows the instruction cache)
+#pragma unroll
         for (int half = 0; half < 2; ++half) {
-            // lane L: the entries (32 k + i) of tile 32 half + L, in chunk order
-            unsigned w[kBinRounds];
-            unsigned cnt = 0;
+            unsigned mh[kBinRounds];
 #pragma unroll
-            for (int k = 0; k < kBinRounds; ++k) {
-                w[k] = warp_transpose32(half ? unsigned(m[k] >> 32) : unsigned(m[k]), lane);
-                cnt += __popc(w[k]);
-            }
-            unsigned inc = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            const unsigned off = inc - cnt;
-            unsigned p = off;
-#pragma unroll
-            for (int k = 0; k < kBinRounds; ++k) {
-                unsigned x = w[k];
-                while (x) {
-                    const int i = __ffs(x) - 1;
-                    x &= x - 1;
-                    stg[p++] = uint8_t(32 * k + i);
-                }
-            }
-            __syncwarp();
+            for (int k = 0; k < kBinRounds; ++k) mh[k] = half ? unsigned(m[k] >> 32) : unsigned(m[k]);
+            unsigned present = half ? any_hi : any_lo;
             const unsigned cur = half ? cur1 : cur0;
-            unsigned present = __ballot_sync(0xffffffffu, cnt != 0);
             while (present) {
                 const int b = __ffs(present) - 1;
                 present &= present - 1;
-                const unsigned nb = __shfl_sync(0xffffffffu, cnt, b);
-                const unsigned ob = __shfl_sync(0xffffffffu, off, b);
-                const unsigned cb = __shfl_sync(0xffffffffu, cur, b);
-                for (unsigned i = lane; i < nb; i += 32) st.ids[cb + i] = sg[stg[ob + i]];
+                unsigned base = __shfl_sync(0xffffffffu, cur, b);
+#pragma unroll
+                for (int k = 0; k < kBinRounds; ++k) {
+                    const bool bit = (mh[k] >> b) & 1u;
+                    const unsigned bal = __ballot_sync(0xffffffffu, bit);
+                    if (bit) st.ids[base + __popc(bal & lt)] = g[k];
+                    base += __popc(bal);
+                }
             }
-            __syncwarp();
         }
     }
 }
