@@ -149,7 +149,7 @@ typedef struct gsp_gaussians {
     float *opacity_logits; /* device [capacity]   (storage space: logit of the opacity) */
     float *sh;             /* device [capacity][K][3], K = (sh_degree + 1)^2 */
     int32_t *count;        /* device int32: number N of live Gaussians (0 <= N <= capacity) */
-    int64_t capacity;      /* >= 1 */
+    int64_t capacity;      /* 1 <= capacity < 2^30 */
     int32_t sh_degree;     /* 0..3 */
 } gsp_gaussians;
 

@@ -78,8 +78,9 @@ struct State {
                      // 1/255 ellipse reaches (lo > hi: none); rows past kRowCap are not culled
     uint32_t *key, *key_alt;  // depth keys [V][cap], sort scratch [V][cap]
     int32_t *val, *val_alt;   // depth-ordered ids [V][cap], sort scratch [V][cap]
-    unsigned *sort_hist;      // [V][256][nb_max]
-    unsigned *sort_tot;       // [V][256]
+    unsigned *sort_state;     // [V][4][nb_max][256] look-back words of the depth sort
+    unsigned *sort_ghist;     // [V][4][256] digit counts of the four passes
+    unsigned *sort_ticket;    // [V][4] tile tickets of the four passes
     unsigned *count1;         // [total_super][nch1_max] level-1 chunk counts, then offsets
     unsigned *len1;           // [total_super] supertile list lengths
     unsigned *list1_start;    // [total_super] supertile list starts in id1
@@ -410,134 +411,118 @@ __global__ void __launch_bounds__(256, 4) project_kernel(const __grid_constant__
     if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(reinterpret_cast<unsigned long long *>(st.pairs_total), pairs);
 }
 
-// ------------------------------------------------------------ radix sort
-//
-// One stable LSD pass over (key, value) pairs, on digits of up to 8 bits.
-// Block tile: 8 warps x 512 elements, each warp owning a contiguous slice.
-//   rs_hist     per-block digit counts (warp-aggregated shared atomics)
-//   rs_scan     per digit, exclusive scan of the block counts
-//   rs_scatter  all loads issued up front; warp-private ranking (match +
-//               shared per-warp counters, no block barrier per item); the
-//               block is staged in shared memory in digit order and written
-//               out so that consecutive threads write one digit's run.
-// The element count is read on the device (a 32-bit or a 64-bit counter).
-
+// Depth-sort tiles: 8 warps x 256 keys, each warp owning a contiguous slice.
 constexpr int kRsThreads = 256, kRsWarps = kRsThreads / 32, kRsItems = 8;
 constexpr int kRsWarpTile = 32 * kRsItems, kRsTile = kRsThreads * kRsItems;
 
 struct SortCount {
-    const int32_t *n32;
-    const long long *n64;
-    const int32_t *skip;  // non-zero: nothing to do (pair overflow)
-    __device__ long long get() const { return n64 ? *n64 : (long long)*n32; }
-    __device__ bool skipped() const { return skip && *skip; }
+    const int32_t *n32;  // the element count, read on the device
+    __device__ long long get() const { return (long long)*n32; }
 };
 
-template <typename K>
-__global__ void __launch_bounds__(kRsThreads) rs_hist(const K *keys, SortCount cnt, int shift, int bits,
-                                                      unsigned *bhist, int nb_max, long long seg)
+// -------------------------------------------------------------- depth sort
+//
+// Stable LSD radix sort of the depth keys of every view (blockIdx.y = view),
+// four passes of 8 bits.  ds_count counts the digits of all four passes at once
+// (the counts do not depend on the order of the keys).  Each pass is then one
+// kernel: a block takes a ticket (tiles of kRsTile keys go in ticket order),
+// ranks its tile per digit (warp-private stable ranks), publishes its digit
+// counts, and walks back over the lower tickets for each digit's exclusive
+// prefix (decoupled look-back).  A block publishes its count before it starts
+// its own walk, and a lower ticket belongs to a block that is already running,
+// so every walk ends; each poll loop is bounded all the same, and on expiry the
+// pass records GSP_ERR_TIMEOUT and sets the overflow flag so that the later
+// stages skip their work.
+//
+// Look-back word of (view, pass, tile, digit): bit 31 = inclusive prefix,
+// bit 30 = the tile's own count, bits 0..29 the value (capacity < 2^30).
+
+constexpr unsigned kLbInc = 1u << 31, kLbAgg = 1u << 30, kLbVal = kLbAgg - 1u;
+constexpr long long kSortSpinLimit = 1ll << 22;
+
+__global__ void __launch_bounds__(kRsThreads) ds_count(const uint32_t *keys, SortCount cnt, unsigned *ghist,
+                                                       unsigned *state, int nb_max, long long seg)
 {
-    __shared__ unsigned h[256];
-    // blockIdx.y: the segment (view); its keys start at y * seg, its counts at y * 256 * nb_max
+    __shared__ unsigned h[4][256];
     keys += (size_t)blockIdx.y * seg;
-    bhist += (size_t)blockIdx.y * 256 * nb_max;
-    if (cnt.skipped()) return;
+    ghist += (size_t)blockIdx.y * 4 * 256;
+    state += (size_t)blockIdx.y * 4 * nb_max * 256;  // the first pass's words of this view
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int i = tid; i < 4 * 256; i += kRsThreads) (&h[0][0])[i] = 0;
+    for (long long i = (long long)blockIdx.x * kRsThreads + tid; i < (long long)nb_max * 256;
+         i += (long long)gridDim.x * kRsThreads)
+        state[i] = 0;
+    __syncthreads();
     const long long n = cnt.get();
-    const long long b0 = (long long)blockIdx.x * kRsTile;
-    if (b0 >= n) return;
-    const unsigned mask = (1u << bits) - 1u;
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const long long wb = b0 + (long long)wid * kRsWarpTile;
-    unsigned d[kRsItems];
+    const unsigned lt = (1u << lane) - 1u;
+    for (long long e0 = (long long)blockIdx.x * kRsThreads; e0 < n; e0 += (long long)gridDim.x * kRsThreads) {
+        const long long e = e0 + tid;
+        const bool ok = e < n;
+        const unsigned k = ok ? keys[e] : 0u;
+        // the two low digits are spread: plain shared atomics; the two high ones
+        // (exponent and leading mantissa bits of a float depth) take few values:
+        // one atomic per group of equal digits in the warp
+        if (ok) {
+            atomicAdd(&h[0][k & 255u], 1u);
+            atomicAdd(&h[1][(k >> 8) & 255u], 1u);
+        }
 #pragma unroll
-    for (int j = 0; j < kRsItems; ++j) {
-        const long long e = wb + j * 32 + lane;
-        d[j] = e < n ? ((unsigned(keys[e]) >> shift) & mask) : 256u;
-    }
-#pragma unroll
-    for (int j = 0; j < kRsItems; ++j) {
-        const unsigned peers = __match_any_sync(0xffffffffu, d[j]);
-        if (d[j] < 256u && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[d[j]], __popc(peers));
+        for (int d = 2; d < 4; ++d) {
+            const unsigned dig = ok ? (k >> (8 * d)) & 255u : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, dig);
+            if (ok && (peers & lt) == 0) atomicAdd(&h[d][dig], __popc(peers));
+        }
     }
     __syncthreads();
-    if (threadIdx.x <= mask) bhist[(size_t)threadIdx.x * nb_max + blockIdx.x] = h[threadIdx.x];
+    for (int i = tid; i < 4 * 256; i += kRsThreads) {
+        const unsigned c = (&h[0][0])[i];
+        if (c) atomicAdd(ghist + i, c);
+    }
 }
 
-// One block per digit: exclusive scan of that digit's block counts.
-__global__ void __launch_bounds__(256) rs_scan(unsigned *bhist, int nb_max, SortCount cnt, unsigned *dtot)
+__global__ void __launch_bounds__(kRsThreads) ds_pass(const uint32_t *kin, const int32_t *vin, uint32_t *kout,
+                                                      int32_t *vout, SortCount cnt, int pass, const unsigned *ghist,
+                                                      unsigned *state, unsigned *ticket, int nb_max, long long seg,
+                                                      int32_t *overflow, int32_t *status)
 {
-    bhist += (size_t)blockIdx.y * 256 * nb_max;
-    dtot += (size_t)blockIdx.y * 256;
-    __shared__ unsigned wsum[8];
-    __shared__ unsigned carry;
-    if (cnt.skipped()) return;
-    const long long n = cnt.get();
-    const int nb = int((n + kRsTile - 1) / kRsTile);
-    unsigned *row = bhist + (size_t)blockIdx.x * nb_max;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int b0 = 0; b0 < nb; b0 += 256) {
-        const int b = b0 + threadIdx.x;
-        const unsigned x = b < nb ? row[b] : 0u;
-        unsigned inc = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (lane == 31) wsum[wid] = inc;
-        __syncthreads();
-        unsigned wb = 0, all = 0;
-        for (int w = 0; w < 8; ++w) {
-            if (w < wid) wb += wsum[w];
-            all += wsum[w];
-        }
-        if (b < nb) row[b] = carry + wb + inc - x;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += all;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
-}
-
-template <typename K>
-__global__ void __launch_bounds__(kRsThreads) rs_scatter(const K *kin, const int32_t *vin, K *kout, int32_t *vout,
-                                                         SortCount cnt, int shift, int bits, const unsigned *bhist,
-                                                         int nb_max, const unsigned *dtot, long long seg)
-{
-    kin += (size_t)blockIdx.y * seg;
-    vin += (size_t)blockIdx.y * seg;
-    kout += (size_t)blockIdx.y * seg;
-    vout += (size_t)blockIdx.y * seg;
-    bhist += (size_t)blockIdx.y * 256 * nb_max;
-    dtot += (size_t)blockIdx.y * 256;
+    const int view = blockIdx.y;
+    kin += (size_t)view * seg;
+    vin += (size_t)view * seg;
+    kout += (size_t)view * seg;
+    vout += (size_t)view * seg;
+    ghist += ((size_t)view * 4 + pass) * 256;
+    unsigned *lb = state + ((size_t)view * 4 + pass) * nb_max * 256;
+    __shared__ unsigned s_ticket;
+    __shared__ int s_fail;
     __shared__ unsigned gbase[256], lstart[256];
     __shared__ unsigned wh[kRsWarps][256];
     __shared__ unsigned wsum[kRsWarps];
-    __shared__ K sk[kRsTile];
+    __shared__ uint32_t sk[kRsTile];
     __shared__ int32_t sv[kRsTile];
-    if (cnt.skipped()) return;
-    const long long n = cnt.get();
-    const long long b0 = (long long)blockIdx.x * kRsTile;
-    if (b0 >= n) return;
+    if (*(volatile int32_t *)overflow) return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const unsigned mask = (1u << bits) - 1u;
-    const int nd = 1 << bits;
+    if (tid == 0) {
+        s_ticket = atomicAdd(ticket + view * 4 + pass, 1u);
+        s_fail = 0;
+    }
+    __syncthreads();
+    const int t = int(s_ticket);
+    const long long n = cnt.get();
+    const long long b0 = (long long)t * kRsTile;
+    if (b0 >= n) return;
+    const int shift = 8 * pass;
     const long long wb = b0 + (long long)wid * kRsWarpTile;
 
-    K key[kRsItems];
+    uint32_t key[kRsItems];
     int32_t val[kRsItems];
     unsigned dig[kRsItems], rank[kRsItems];
 #pragma unroll
     for (int j = 0; j < kRsItems; ++j) {
         const long long e = wb + j * 32 + lane;
         const bool ok = e < n;
-        key[j] = ok ? kin[e] : K(0);
+        key[j] = ok ? kin[e] : 0u;
         val[j] = ok ? vin[e] : 0;
-        dig[j] = ok ? ((unsigned(key[j]) >> shift) & mask) : 256u;
+        dig[j] = ok ? ((key[j] >> shift) & 255u) : 256u;
     }
     for (int k = lane; k < 256; k += 32) wh[wid][k] = 0;
     __syncwarp();
@@ -557,18 +542,22 @@ __global__ void __launch_bounds__(kRsThreads) rs_scatter(const K *kin, const int
         __syncwarp();
     }
     __syncthreads();
-    // per digit: offsets of the warps, block total; global base of the digit
+    // digit tid: the warps' offsets and the tile's count, published at once
     unsigned tot = 0;
     for (int w = 0; w < kRsWarps; ++w) {
         const unsigned c = wh[w][tid];
         wh[w][tid] = tot;
         tot += c;
     }
+    volatile unsigned *vlb = lb;
+    vlb[(size_t)t * 256 + tid] = (t == 0 ? kLbInc : kLbAgg) | tot;
+    // tile-local digit starts; digit starts over the view
+    unsigned gstart;
     {
         unsigned inc = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+            const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
         if (lane == 31) wsum[wid] = inc;
@@ -576,12 +565,11 @@ __global__ void __launch_bounds__(kRsThreads) rs_scatter(const K *kin, const int
         unsigned base = 0;
         for (int w = 0; w < wid; ++w) base += wsum[w];
         lstart[tid] = base + inc - tot;
-        // digit base over all blocks: exclusive scan of the digit totals
-        const unsigned x = tid < nd ? dtot[tid] : 0u;
+        const unsigned x = ghist[tid];
         inc = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+            const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
         __syncthreads();
@@ -589,9 +577,35 @@ __global__ void __launch_bounds__(kRsThreads) rs_scatter(const K *kin, const int
         __syncthreads();
         base = 0;
         for (int w = 0; w < wid; ++w) base += wsum[w];
-        gbase[tid] = base + inc - x + (tid < nd ? bhist[(size_t)tid * nb_max + blockIdx.x] : 0u);
+        gstart = base + inc - x;
     }
+    // look-back: the keys with digit tid in the lower tiles
+    unsigned prefix = 0;
+    if (t > 0) {
+        int j = t - 1;
+        long long polls = 0;
+        for (;;) {
+            const unsigned w = vlb[(size_t)j * 256 + tid];
+            if (w & (kLbInc | kLbAgg)) {
+                prefix += w & kLbVal;
+                if ((w & kLbInc) || --j < 0) break;
+            } else if (++polls > kSortSpinLimit) {
+                s_fail = 1;
+                break;
+            }
+        }
+        vlb[(size_t)t * 256 + tid] = kLbInc | (prefix + tot);
+    }
+    if (pass < 3) lb[(size_t)nb_max * 256 + (size_t)t * 256 + tid] = 0;  // the next pass's word
+    gbase[tid] = gstart + prefix;
     __syncthreads();
+    if (s_fail) {
+        if (tid == 0) {
+            set_status(status, GSP_ERR_TIMEOUT);
+            atomicExch(overflow, 1);
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < kRsItems; ++j) {
         if (dig[j] < 256u) {
@@ -603,8 +617,8 @@ __global__ void __launch_bounds__(kRsThreads) rs_scatter(const K *kin, const int
     __syncthreads();
     const int cnt_blk = int(min((long long)kRsTile, n - b0));
     for (int i = tid; i < cnt_blk; i += kRsThreads) {
-        const K k = sk[i];
-        const unsigned d = (unsigned(k) >> shift) & mask;
+        const uint32_t k = sk[i];
+        const unsigned d = (k >> shift) & 255u;
         const long long pos = (long long)gbase[d] + (i - lstart[d]);
         kout[pos] = k;
         vout[pos] = sv[i];
@@ -1778,6 +1792,7 @@ constexpr int kCounters = 4;
 struct Layout {
     State st;
     size_t bytes;
+    size_t clear_bytes;  // bytes of the region cleared per forward pass, from st.pairs_total
 };
 
 Layout render_layout(void *ws, long long cap, const Views &vs, long long pair_cap)
@@ -1797,8 +1812,7 @@ Layout render_layout(void *ws, long long cap, const Views &vs, long long pair_ca
     s.val = c.take<int32_t>(vc);
     s.val_alt = c.take<int32_t>(vc);
     s.nb_max = int(div_up(cap, kRsTile));
-    s.sort_hist = c.take<unsigned>((size_t)vs.n * 256 * s.nb_max);
-    s.sort_tot = c.take<unsigned>((size_t)vs.n * 256);
+    s.sort_state = c.take<unsigned>((size_t)vs.n * 4 * s.nb_max * 256);
     s.nch1_max = int(div_up(cap, kBinRanks));
     s.count1 = c.take<unsigned>(total_super * s.nch1_max);
     s.len1 = c.take<unsigned>(total_super);
@@ -1815,13 +1829,18 @@ Layout render_layout(void *ws, long long cap, const Views &vs, long long pair_ca
     s.order_bwd = c.take<int32_t>(total_tiles);
     s.tile_work = c.take<unsigned>(total_tiles);
     s.g2d = c.take<float4>(vc * 3);
-    // counters cleared by one memset per forward pass: pair total, composited
-    // pairs, loss sum, overflow flag
+    // cleared by one memset per forward pass (from pairs_total to clear_end):
+    // pair total, composited pairs, loss sum, overflow flag; the depth sort's
+    // digit counts and tickets
+    const size_t clear0 = c.size();  // where the counters start
     long long *ctr = c.take<long long>(kCounters);
     s.pairs_total = ctr;
     s.contrib = ctr + 1;
     s.loss_acc = reinterpret_cast<double *>(ctr + 2);
     s.overflow = reinterpret_cast<int32_t *>(ctr + 3);
+    s.sort_ghist = c.take<unsigned>((size_t)vs.n * 4 * 256);
+    s.sort_ticket = c.take<unsigned>((size_t)vs.n * 4);
+    L.clear_bytes = c.size() - clear0;
     s.pair_cap = pair_cap;
     L.bytes = c.size();
     return L;
@@ -1882,7 +1901,7 @@ gsp_status validate_gauss(const gsp_gaussians *g)
 {
     if (!g || !g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh || !g->count)
         return GSP_ERR_INVALID_ARG;
-    if (g->capacity < 1 || g->capacity > (1LL << 30)) return GSP_ERR_INVALID_ARG;
+    if (g->capacity < 1 || g->capacity >= (1LL << 30)) return GSP_ERR_INVALID_ARG;
     if (g->sh_degree < 0 || g->sh_degree > 3) return GSP_ERR_INVALID_ARG;
     return GSP_OK;
 }
@@ -1949,7 +1968,7 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     Params P = make_params(g);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
-    GSP_CUDA_TRY(cudaMemsetAsync(S.pairs_total, 0, kCounters * sizeof(long long), s));
+    GSP_CUDA_TRY(cudaMemsetAsync(S.pairs_total, 0, L.clear_bytes, s));
     stage_begin("project", s);
     switch (P.K) {
     case 1: project_kernel<1><<<div_up(cap, 256), 256, 0, s>>>(vs, P, S); break;
@@ -1960,18 +1979,17 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     stage_end("project", s);
     GSP_LAUNCH_CHECK();
     stage_begin("depth_sort", s);
-    // depth sort of every view at once (blockIdx.y = view): 4 stable passes of 8 bits;
-    // an even count leaves the result in key/val
+    // depth sort of every view at once (blockIdx.y = view): the digit counts of
+    // all passes, then 4 stable one-kernel passes of 8 bits; an even count
+    // leaves the result in key/val
     {
         uint32_t *k0 = S.key, *k1 = S.key_alt;
         int32_t *v0 = S.val, *v1 = S.val_alt;
-        const SortCount sc{g->count, nullptr, nullptr};
-        const dim3 gb(S.nb_max, nv), gs(256, nv);
+        const SortCount sc{g->count};
+        ds_count<<<dim3(num_sms(), nv), kRsThreads, 0, s>>>(k0, sc, S.sort_ghist, S.sort_state, S.nb_max, cap);
         for (int pass = 0; pass < 4; ++pass) {
-            rs_hist<uint32_t><<<gb, kRsThreads, 0, s>>>(k0, sc, 8 * pass, 8, S.sort_hist, S.nb_max, cap);
-            rs_scan<<<gs, 256, 0, s>>>(S.sort_hist, S.nb_max, sc, S.sort_tot);
-            rs_scatter<uint32_t><<<gb, kRsThreads, 0, s>>>(k0, v0, k1, v1, sc, 8 * pass, 8, S.sort_hist, S.nb_max,
-                                                           S.sort_tot, cap);
+            ds_pass<<<dim3(S.nb_max, nv), kRsThreads, 0, s>>>(k0, v0, k1, v1, sc, pass, S.sort_ghist, S.sort_state,
+                                                              S.sort_ticket, S.nb_max, cap, S.overflow, dev_status);
             uint32_t *tk = k0; k0 = k1; k1 = tk;
             int32_t *tv = v0; v0 = v1; v1 = tv;
         }
@@ -2006,7 +2024,7 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     }
     stage_end("composite_fwd", s);
     GSP_LAUNCH_CHECK();
-    note_launches(2 + 12 + 8 + 1);
+    note_launches(2 + 5 + 8 + 1);
     if (loss_out) {
         loss_finalise<<<1, 1, 0, s>>>(S, vs.total_pix, loss_out);
         note_launches(1);
