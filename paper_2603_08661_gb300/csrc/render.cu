@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(kRsThreads) ds_pass(const uint32_t *kin, const
 //            list per supertile the Gaussian's tile rectangle touches
 //   level 2  each supertile list is partitioned, stably, into its 64 tile
 //            lists, which come out contiguous (tile-major) in `ids`
-// Work is cut into warp chunks of 256 ranks (level 1) or 256 entries of one
+// Work is cut into warp chunks of 128 ranks (level 1) or 256 entries of one
 // supertile list (level 2).  Each level counts per (chunk, bin), scans the
 // counts per bin over the chunks, and scatters with the chunk's cursors:
 //   l1_count    per chunk: supertile counts (shared-memory atomics, order-free)
@@ -651,7 +651,9 @@ __global__ void __launch_bounds__(kRsThreads) ds_pass(const uint32_t *kin, const
 //               its slot; each store writes a contiguous run of the list
 
 constexpr int kSuper = 8;                 // supertile edge, in tiles
-constexpr int kBinRanks = 256;            // ranks (level 1) or entries (level 2) per warp chunk
+constexpr int kL1Ranks = 128;             // ranks per level-1 warp chunk
+constexpr int kL1Rounds = kL1Ranks / 32;
+constexpr int kBinRanks = 256;            // supertile entries per level-2 warp chunk
 constexpr int kBinRounds = kBinRanks / 32;
 constexpr int kBinWarps = 4, kBinThreads = kBinWarps * 32;
 constexpr int kMaxSuper = 2048;           // supertiles per view (shared-memory tables)
@@ -708,12 +710,12 @@ struct L1Task {
 
 __device__ __forceinline__ L1Task l1_task(int task, int n)
 {
-    const int nch = (n + kBinRanks - 1) / kBinRanks;
+    const int nch = (n + kL1Ranks - 1) / kL1Ranks;
     L1Task t;
     t.v = task / nch;
     t.chunk = task - t.v * nch;
-    t.r0 = t.chunk * kBinRanks;
-    t.cnt = min(kBinRanks, n - t.r0);
+    t.r0 = t.chunk * kL1Ranks;
+    t.cnt = min(kL1Ranks, n - t.r0);
     return t;
 }
 
@@ -722,7 +724,7 @@ __global__ void __launch_bounds__(kBinThreads) l1_count(const __grid_constant__ 
     extern __shared__ unsigned l1_tab[];  // [kBinWarps][smax]
     if (*st.overflow) return;
     const int n = *st.n_dev;
-    const int nch = (n + kBinRanks - 1) / kBinRanks;
+    const int nch = (n + kL1Ranks - 1) / kL1Ranks;
     const int ntask = nch * vs.n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned *tab = l1_tab + wid * vs.smax;
@@ -733,7 +735,7 @@ __global__ void __launch_bounds__(kBinThreads) l1_count(const __grid_constant__ 
         const ViewP &V = vs.v[t.v];
         const int32_t *sorted = st.val + (size_t)t.v * cap;
         const uint2 *rect = st.rect + (size_t)t.v * cap;
-        for (int k = 0; k < kBinRounds; ++k) {
+        for (int k = 0; k < kL1Rounds; ++k) {
             const int r = 32 * k + lane;
             if (r >= t.cnt) break;
             const uint2 rc = rect[sorted[t.r0 + r]];
@@ -784,7 +786,7 @@ __global__ void __launch_bounds__(256) l1_scan(const __grid_constant__ Views vs,
     if (*st.overflow) return;
     const int gs = blockIdx.x;
     const int n = *st.n_dev;
-    const int nch = (n + kBinRanks - 1) / kBinRanks;
+    const int nch = (n + kL1Ranks - 1) / kL1Ranks;
     unsigned *row = st.count1 + (size_t)gs * st.nch1_max;
     const int q = (nch + 255) / 256;
     const int c0 = threadIdx.x * q, c1 = min(c0 + q, nch);
@@ -853,7 +855,7 @@ __global__ void __launch_bounds__(kBinThreads) l1_scatter(const __grid_constant_
     extern __shared__ unsigned l1_cur[];  // [kBinWarps][smax]
     if (*st.overflow) return;
     const int n = *st.n_dev;
-    const int nch = (n + kBinRanks - 1) / kBinRanks;
+    const int nch = (n + kL1Ranks - 1) / kL1Ranks;
     const int ntask = nch * vs.n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -868,7 +870,7 @@ __global__ void __launch_bounds__(kBinThreads) l1_scatter(const __grid_constant_
         __syncwarp();
         const int32_t *sorted = st.val + (size_t)t.v * cap;
         const uint2 *rect = st.rect + (size_t)t.v * cap;
-        for (int k = 0; k < kBinRounds; ++k) {
+        for (int k = 0; k < kL1Rounds; ++k) {
             if (32 * k >= t.cnt) break;
             const int r = 32 * k + lane;
             int g = -1;
@@ -1813,7 +1815,7 @@ Layout render_layout(void *ws, long long cap, const Views &vs, long long pair_ca
     s.val_alt = c.take<int32_t>(vc);
     s.nb_max = int(div_up(cap, kRsTile));
     s.sort_state = c.take<unsigned>((size_t)vs.n * 4 * s.nb_max * 256);
-    s.nch1_max = int(div_up(cap, kBinRanks));
+    s.nch1_max = int(div_up(cap, kL1Ranks));
     s.count1 = c.take<unsigned>(total_super * s.nch1_max);
     s.len1 = c.take<unsigned>(total_super);
     s.list1_start = c.take<unsigned>(total_super);
