@@ -296,8 +296,8 @@ __global__ void __launch_bounds__(kThreads) las_kernel(LasArgs a)
     }
 }
 
-// SH rows of the appended children, copied with consecutive threads on
-// consecutive floats of a row.
+// SH rows of the appended children: one warp per row, consecutive lanes on
+// consecutive floats (the parent index is read once per row).
 __global__ void __launch_bounds__(256) las_copy_sh(LasArgs a)
 {
     const long long n = *a.count;
@@ -305,11 +305,12 @@ __global__ void __launch_bounds__(256) las_copy_sh(LasArgs a)
     const long long total = n > 0 ? a.rank_off[nb] : 0;
     if (n + total > a.cap) return;
     const int row = 3 * a.K;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total * row;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long c = e / row;
-        const int k = int(e - c * row);
-        a.sh[(size_t)(n + c) * row + k] = a.sh[(size_t)a.src[c] * row + k];
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    for (long long c = blockIdx.x * (long long)(blockDim.x / 32) + (threadIdx.x >> 5); c < total; c += warps) {
+        const float *src = a.sh + (size_t)a.src[c] * row;
+        float *dst = a.sh + (size_t)(n + c) * row;
+        for (int k = lane; k < row; k += 32) dst[k] = src[k];
     }
 }
 

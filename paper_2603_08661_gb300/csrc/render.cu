@@ -67,6 +67,8 @@ struct Params {
     const int32_t *count;
     long long cap;
     int K;  // SH coefficients per channel
+    int32_t *status = nullptr;  // device status word (bounded waits report here)
+    bool sh_bulk = false;       // sh is 16-byte aligned: the projection streams it by bulk copies
 };
 
 struct State {
@@ -236,21 +238,22 @@ __device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + expf(-
 // loads when the row length allows (K = 4, 16).
 // acc[ch] += sum_k row[3k + ch] * Y[k], the coefficients streamed from memory in
 // 16-byte loads (row-major [K][3]; terms added in ascending k per channel).
-template <int K>
+// SMEM: the row is in shared memory (generic loads instead of read-only global ones).
+template <int K, bool SMEM = false>
 __device__ __forceinline__ void sh_weighted(const float *row, const float Y[16], float acc[3])
 {
     if constexpr ((3 * K) % 4 == 0) {
         const float4 *r4 = reinterpret_cast<const float4 *>(row);
 #pragma unroll
         for (int q = 0; q < 3 * K / 4; ++q) {
-            const float4 v = __ldg(r4 + q);
+            const float4 v = SMEM ? r4[q] : __ldg(r4 + q);
             const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[(4 * q + j) % 3] += e[j] * Y[(4 * q + j) / 3];
         }
     } else {
 #pragma unroll
-        for (int el = 0; el < 3 * K; ++el) acc[el % 3] += __ldg(row + el) * Y[el / 3];
+        for (int el = 0; el < 3 * K; ++el) acc[el % 3] += (SMEM ? row[el] : __ldg(row + el)) * Y[el / 3];
     }
 }
 
@@ -290,10 +293,14 @@ __device__ __forceinline__ void load_sh(const float *row, float *out)
 }
 
 // Projects Gaussian i < capacity into every view; returns its tile-Gaussian pairs.
+// sh_s: the Gaussian's SH row in shared memory, valid once the bulk copy on bar
+// has landed (nullptr: read it from global memory).
 template <int K>
 __device__ __forceinline__ unsigned long long project_one(const Views &vs, const Params &p, const State &st,
-                                                          long long i)
+                                                          long long i, const float *sh_s,
+                                                          unsigned long long *bar)
 {
+    bool sh_ready = false;
     const int n = *p.count;
     unsigned long long pairs = 0;
     const long long cap = p.cap;
@@ -376,7 +383,15 @@ __device__ __forceinline__ unsigned long long project_one(const Views &vs, const
             float Y[16];
             sh_eval(dx * rn, dy * rn, dz * rn, K, Y);
             float col[3] = {0.5f, 0.5f, 0.5f};
-            sh_weighted<K>(shrow, Y, col);
+            if (sh_s && !sh_ready) {
+                sh_ready = mbar_wait(bar, 0, kDefaultSpinLimit);
+                if (!sh_ready) {
+                    set_status(p.status, GSP_ERR_TIMEOUT);
+                    sh_s = nullptr;  // the global row is still there
+                }
+            }
+            if (sh_s) sh_weighted<K, true>(sh_s, Y, col);
+            else sh_weighted<K>(shrow, Y, col);
             unsigned clampbits = 0;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
@@ -401,14 +416,52 @@ __device__ __forceinline__ unsigned long long project_one(const Views &vs, const
     return pairs;
 }
 
+// Dynamic shared memory of the projection: an mbarrier, then the block's SH rows.
+constexpr int kProjThreads = 256;
+constexpr size_t proj_smem_bytes(int K) { return 128 + size_t(kProjThreads) * 12 * K; }
+
 template <int K>
-__global__ void __launch_bounds__(256, 4) project_kernel(const __grid_constant__ Views vs, Params p, State st)
+__global__ void __launch_bounds__(kProjThreads, 4) project_kernel(const __grid_constant__ Views vs, Params p,
+                                                                  State st)
 {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    unsigned long long pairs = i < p.cap ? project_one<K>(vs, p, st, i) : 0ull;
+    extern __shared__ __align__(128) unsigned char proj_smem[];
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(proj_smem);
+    float *s_sh = reinterpret_cast<float *>(proj_smem + 128);
+    // the block's SH rows are contiguous: one bulk copy streams them into shared
+    // memory while the geometry is computed (rows past the live count are still
+    // inside the capacity)
+    const long long i0 = (long long)blockIdx.x * kProjThreads;
+    const long long rows = min((long long)kProjThreads, p.cap - i0);
+    const unsigned bytes = unsigned(rows) * 12u * unsigned(K);
+    const bool bulk = p.sh_bulk && i0 < *p.count && (bytes & 15u) == 0;
+    if (bulk) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_copy_g2s(s_sh, p.sh + i0 * 3 * K, bytes, bar);
+        }
+        __syncthreads();
+    }
+    const long long i = i0 + threadIdx.x;
+    unsigned long long pairs =
+        i < p.cap ? project_one<K>(vs, p, st, i, bulk ? s_sh + threadIdx.x * 3 * K : nullptr, bar) : 0ull;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
     if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(reinterpret_cast<unsigned long long *>(st.pairs_total), pairs);
+    // the copy has landed before the block's shared memory is released
+    if (bulk && threadIdx.x == 0 && !mbar_wait(bar, 0, kDefaultSpinLimit)) set_status(p.status, GSP_ERR_TIMEOUT);
+}
+
+template <int K>
+void launch_project(const Views &vs, const Params &p, const State &S, long long cap, cudaStream_t s)
+{
+    static bool attr = false;  // once per instantiation (the size is a constant of K)
+    if (!attr) {
+        cudaFuncSetAttribute(project_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(proj_smem_bytes(K)));
+        attr = true;
+    }
+    project_kernel<K><<<div_up(cap, kProjThreads), kProjThreads, proj_smem_bytes(K), s>>>(vs, p, S);
 }
 
 // Depth-sort tiles: 8 warps x 256 keys, each warp owning a contiguous slice.
@@ -1968,15 +2021,17 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     State S = L.st;
     S.n_dev = g->count;
     Params P = make_params(g);
+    P.status = dev_status;
+    P.sh_bulk = (reinterpret_cast<uintptr_t>(g->sh) & 15) == 0;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
     GSP_CUDA_TRY(cudaMemsetAsync(S.pairs_total, 0, L.clear_bytes, s));
     stage_begin("project", s);
     switch (P.K) {
-    case 1: project_kernel<1><<<div_up(cap, 256), 256, 0, s>>>(vs, P, S); break;
-    case 4: project_kernel<4><<<div_up(cap, 256), 256, 0, s>>>(vs, P, S); break;
-    case 9: project_kernel<9><<<div_up(cap, 256), 256, 0, s>>>(vs, P, S); break;
-    default: project_kernel<16><<<div_up(cap, 256), 256, 0, s>>>(vs, P, S); break;
+    case 1: launch_project<1>(vs, P, S, cap, s); break;
+    case 4: launch_project<4>(vs, P, S, cap, s); break;
+    case 9: launch_project<9>(vs, P, S, cap, s); break;
+    default: launch_project<16>(vs, P, S, cap, s); break;
     }
     stage_end("project", s);
     GSP_LAUNCH_CHECK();
