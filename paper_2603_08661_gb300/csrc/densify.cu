@@ -1,9 +1,12 @@
 // Edge-score selection and Long-Axis-Split (paper Sec. 2.2, Alg. 1 and Alg. 2).
 //
-// Selection: exact top-k.  Scores map to order-preserving 32-bit keys; the
-// k-th largest key is found by a 3-digit radix select (11 + 11 + 10 bits),
-// every key above it is taken, and the ties at it are taken in ascending
-// index order (their ranks come from a block scan plus a scan over blocks).
+// Selection: exact top-k in one cooperative launch.  Scores map to
+// order-preserving 32-bit keys; the k-th largest key is found by a 3-digit
+// radix select (11 + 11 + 10 bits, one grid barrier per digit, every block
+// picking the same digit from the global counts), every key above it is
+// taken, and the ties at it are taken in ascending index order (ranks from a
+// block scan plus the tie counts of the lower blocks; skipped when every tie
+// is taken).
 //
 // Split: the selected Gaussians are ranked in index order by the same kind
 // of scan; one thread per selected Gaussian applies Alg. 1: the long axis l
@@ -12,6 +15,8 @@
 // the scales move in log space and the opacity in logit space.  Child 0
 // replaces the parent; child 1 is appended at slot N + rank.  The capacity
 // is checked on the device before anything is written.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gsp {
@@ -20,100 +25,10 @@ namespace {
 constexpr int kThreads = 256, kPerThread = 4, kBlockItems = kThreads * kPerThread;
 constexpr int kSelBins = 2048;
 
-struct SelState {
-    unsigned prefix;     // key bits fixed so far
-    unsigned remaining;  // how many still to take among keys matching the prefix
-    unsigned n;          // live count
-    unsigned k;          // clamped k
-};
-
 __device__ __forceinline__ unsigned order_key(float f)
 {
     unsigned b = __float_as_uint(f);
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-
-__global__ void sel_init(const int32_t *count, long long k, SelState *s, unsigned *hist)
-{
-    for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) hist[i] = 0;
-    if (threadIdx.x == 0) {
-        unsigned n = unsigned(max(*count, 0));
-        unsigned kk = k < 0 ? 0u : (k > (long long)n ? n : unsigned(k));
-        s->prefix = 0;
-        s->remaining = kk;
-        s->n = n;
-        s->k = kk;
-    }
-}
-
-// Histogram of digit `pass` over keys matching the prefix of the previous digits.
-__global__ void sel_hist(const float *scores, const SelState *s, int shift, int bits, int pass, unsigned *hist)
-{
-    __shared__ unsigned h[kSelBins];
-    const int nb = 1 << bits;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    const unsigned n = s->n;
-    const int hi = shift + bits;
-    const unsigned prefix = s->prefix;
-    if (s->remaining > 0) {
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-             i += (long long)gridDim.x * blockDim.x) {
-            unsigned key = order_key(scores[i]);
-            if (pass > 0 && (key >> hi) != (prefix >> hi)) continue;
-            atomicAdd(&h[(key >> shift) & (nb - 1)], 1u);
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += blockDim.x)
-        if (h[i]) atomicAdd(&hist[i], h[i]);
-}
-
-// Pick the digit holding the remaining-th largest key (one block): thread t
-// owns bins [nb - (t+1) per, nb - t per) counted from the top; a block scan
-// of the segment sums finds the segment, its owner walks its bins.
-__global__ void __launch_bounds__(kThreads) sel_pick(SelState *s, int shift, int bits, unsigned *hist)
-{
-    __shared__ unsigned wsum[kThreads / 32];
-    __shared__ int s_bin;
-    __shared__ unsigned s_above;
-    const int nb = 1 << bits;
-    const int per = nb / kThreads;
-    const unsigned rem = s->remaining;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned seg = 0;
-    for (int k = 0; k < per; ++k) seg += hist[nb - 1 - (threadIdx.x * per + k)];
-    unsigned inc = seg;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) wsum[wid] = inc;
-    if (threadIdx.x == 0) s_bin = -1;
-    __syncthreads();
-    unsigned base = 0;
-    for (int w = 0; w < wid; ++w) base += wsum[w];
-    const unsigned before = base + inc - seg;  // keys in higher segments
-    if (rem > 0 && before < rem && rem <= before + seg) {
-        unsigned acc = before;
-        for (int k = 0; k < per; ++k) {
-            const int b = nb - 1 - (threadIdx.x * per + k);
-            if (acc + hist[b] >= rem) {
-                s_bin = b;
-                s_above = acc;
-                break;
-            }
-            acc += hist[b];
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && s_bin >= 0) {
-        s->prefix |= unsigned(s_bin) << shift;
-        s->remaining -= s_above;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += kThreads) hist[i] = 0;
 }
 
 // Block-local exclusive scan of per-thread counts; returns the block total.
@@ -138,12 +53,6 @@ __device__ unsigned block_scan(unsigned x, unsigned *excl)
     *excl = base + inc - x;
     return tot;
 }
-
-struct TieFlag {
-    const float *scores;
-    const SelState *s;
-    __device__ bool operator()(long long i) const { return order_key(scores[i]) == s->prefix && s->k > 0; }
-};
 
 struct MaskFlag {
     const uint8_t *mask;
@@ -189,36 +98,144 @@ __global__ void __launch_bounds__(kThreads) scan_block_sums(const int32_t *count
     if (threadIdx.x == 0) sums[nb] = carry;
 }
 
-__global__ void __launch_bounds__(kThreads) sel_mark(const float *scores, const int32_t *count, long long cap,
-                                                   const SelState *s, const unsigned *tie_off, uint8_t *mask,
-                                                   int32_t *selected_out)
+struct TopkArgs {
+    const float *scores;
+    const int32_t *count;
+    long long cap, k;
+    uint8_t *mask;
+    int32_t *selected_out;
+    unsigned *hist;  // [3][kSelBins] digit counts of the three passes (zeroed before the launch)
+    unsigned *sums;  // [grid] tie counts of the blocks' index ranges
+    unsigned *bar;   // grid barrier (zeroed before the launch)
+    int32_t *status;
+};
+
+// Block-wide pick of the digit that holds the rem-th largest key, from the
+// counts hist[0 .. nb) (the top digit first): thread t owns the nb / kThreads
+// digits [nb - (t+1) per, nb - t per); a scan of the owners' sums finds the
+// owner, which walks its digits.  Returns the digit; *above = keys in higher
+// digits, *in_bin = keys in the digit.
+__device__ int pick_digit(const unsigned *hist, int nb, unsigned rem, unsigned *above, unsigned *in_bin)
 {
-    const long long n = *count;
-    const long long b0 = (long long)blockIdx.x * kBlockItems;
-    if (b0 >= cap) return;
-    const unsigned t = s->prefix, need = s->remaining, k = s->k;
-    bool tie[kPerThread], gt[kPerThread];
-    unsigned c = 0;
+    __shared__ unsigned wsum[kThreads / 32];
+    __shared__ int s_bin;
+    __shared__ unsigned s_above, s_in;
+    const int per = nb / kThreads;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned seg = 0;
+    for (int q = 0; q < per; ++q) seg += __ldcg(hist + nb - 1 - (threadIdx.x * per + q));
+    unsigned inc = seg;
 #pragma unroll
-    for (int j = 0; j < kPerThread; ++j) {
-        long long i = b0 + threadIdx.x * kPerThread + j;
-        unsigned key = i < n ? order_key(scores[i]) : 0u;
-        tie[j] = i < n && k > 0 && key == t;
-        gt[j] = i < n && k > 0 && key > t;
-        c += tie[j];
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
     }
-    unsigned ex;
-    block_scan(c, &ex);
-    unsigned r = (b0 < n ? tie_off[blockIdx.x] : 0u) + ex;
+    if (lane == 31) wsum[wid] = inc;
+    if (threadIdx.x == 0) s_bin = -1;
+    __syncthreads();
+    unsigned base = 0;
+    for (int w = 0; w < wid; ++w) base += wsum[w];
+    const unsigned before = base + inc - seg;
+    if (before < rem && rem <= before + seg) {
+        unsigned acc = before;
+        for (int q = 0; q < per; ++q) {
+            const int b = nb - 1 - (threadIdx.x * per + q);
+            const unsigned c = __ldcg(hist + b);
+            if (acc + c >= rem) {
+                s_bin = b;
+                s_above = acc;
+                s_in = c;
+                break;
+            }
+            acc += c;
+        }
+    }
+    __syncthreads();
+    const int b = s_bin;
+    *above = s_above;
+    *in_bin = s_in;
+    __syncthreads();
+    return b;
+}
+
+__global__ void __launch_bounds__(kThreads) topk_fused(TopkArgs a)
+{
+    __shared__ unsigned h[kSelBins];
+    const int tid = threadIdx.x;
+    const unsigned G = gridDim.x;
+    const long long n = max(*a.count, 0);
+    const unsigned kk = a.k < 0 ? 0u : (a.k > n ? unsigned(n) : unsigned(a.k));
+    // the same prefix / remaining in every block
+    unsigned prefix = 0, remaining = kk, eq = 0;
+    const int shifts[3] = {21, 10, 0}, bits[3] = {11, 11, 10};
+#pragma unroll 1
+    for (int pass = 0; pass < 3; ++pass) {
+        const int shift = shifts[pass], nb = 1 << bits[pass], hi = shift + bits[pass];
+        unsigned *gh = a.hist + pass * kSelBins;
+        if (remaining > 0) {
+            for (int i = tid; i < nb; i += kThreads) h[i] = 0;
+            __syncthreads();
+            for (long long i = blockIdx.x * (long long)kThreads + tid; i < n; i += (long long)G * kThreads) {
+                const unsigned key = order_key(a.scores[i]);
+                if (pass > 0 && (key >> hi) != (prefix >> hi)) continue;
+                atomicAdd(&h[(key >> shift) & unsigned(nb - 1)], 1u);
+            }
+            __syncthreads();
+            for (int i = tid; i < nb; i += kThreads)
+                if (h[i]) atomicAdd(gh + i, h[i]);
+        }
+        if (!grid_barrier(a.bar, G, kDefaultSpinLimit, a.status)) return;
+        if (remaining > 0) {
+            unsigned above, in_bin;
+            const int b = pick_digit(gh, nb, remaining, &above, &in_bin);
+            prefix |= unsigned(b) << shift;
+            remaining -= above;
+            eq = in_bin;
+        }
+    }
+    // prefix = t, the kk-th largest key; the keys above it are taken, and
+    // `remaining` of the eq keys equal to it, in ascending index order
+    const bool rank_ties = kk > 0 && remaining < eq;
+    const long long chunk = (a.cap + G - 1) / G;
+    const long long b0 = min((long long)blockIdx.x * chunk, a.cap), b1 = min(b0 + chunk, a.cap);
+    unsigned tie_base = 0;
+    if (rank_ties) {
+        unsigned c = 0;
+        for (long long i = b0 + tid; i < min(b1, n); i += kThreads) c += order_key(a.scores[i]) == prefix;
+        unsigned ex;
+        const unsigned tot = block_scan(c, &ex);
+        if (tid == 0) a.sums[blockIdx.x] = tot;
+        if (!grid_barrier(a.bar, G, kDefaultSpinLimit, a.status)) return;
+        unsigned lower = 0;
+        for (unsigned q = tid; q < blockIdx.x; q += kThreads) lower += __ldcg(a.sums + q);
+        tie_base = block_scan(lower, &ex);  // the block total: ties in the lower blocks' ranges
+    }
+    // mark the block's range, kPerThread consecutive items per thread per round
+    for (long long r0 = b0; r0 < b1; r0 += kBlockItems) {
+        bool tie[kPerThread], gt[kPerThread];
+        unsigned c = 0;
 #pragma unroll
-    for (int j = 0; j < kPerThread; ++j) {
-        long long i = b0 + threadIdx.x * kPerThread + j;
-        if (i >= cap) continue;
-        bool sel = gt[j] || (tie[j] && r < need);
-        r += tie[j];
-        mask[i] = sel;
+        for (int j = 0; j < kPerThread; ++j) {
+            const long long i = r0 + tid * kPerThread + j;
+            const unsigned key = (i < b1 && i < n) ? order_key(a.scores[i]) : 0u;
+            const bool live = i < b1 && i < n && kk > 0;
+            tie[j] = live && key == prefix;
+            gt[j] = live && key > prefix;
+            c += tie[j];
+        }
+        unsigned ex;
+        const unsigned tot = block_scan(c, &ex);
+        unsigned r = tie_base + ex;
+#pragma unroll
+        for (int j = 0; j < kPerThread; ++j) {
+            const long long i = r0 + tid * kPerThread + j;
+            if (i >= b1) continue;
+            a.mask[i] = gt[j] || (tie[j] && (!rank_ties || r < remaining));
+            r += tie[j];
+        }
+        tie_base += tot;
     }
-    if (selected_out && blockIdx.x == 0 && threadIdx.x == 0) *selected_out = int32_t(k);
+    if (a.selected_out && blockIdx.x == 0 && tid == 0) *a.selected_out = int32_t(kk);
 }
 
 struct LasArgs {
@@ -327,21 +344,27 @@ __global__ void las_commit(int32_t *count, long long cap, const unsigned *rank_o
 }
 
 struct DensifyLayout {
-    SelState *sel;
-    unsigned *hist;
+    unsigned *hist;  // [3][kSelBins], then the 2-word grid barrier: zeroed per selection
+    unsigned *bar;
     unsigned *sums;
     uint8_t *mask;
     int32_t *src;
     size_t bytes;
 };
 
+// The selection's scratch (shared by the workspace and the static array).
+void carve_topk(Carver &c, long long cap, DensifyLayout &L)
+{
+    L.hist = c.take<unsigned>(3 * kSelBins + 2);
+    L.bar = L.hist + 3 * kSelBins;
+    L.sums = c.take<unsigned>(div_up(cap, kBlockItems) + 1);
+}
+
 DensifyLayout densify_layout(void *ws, long long cap)
 {
     Carver c(ws);
     DensifyLayout L{};
-    L.sel = c.take<SelState>(1);
-    L.hist = c.take<unsigned>(kSelBins);
-    L.sums = c.take<unsigned>(div_up(cap, kBlockItems) + 1);
+    carve_topk(c, cap, L);
     L.mask = c.take<uint8_t>((size_t)cap);
     L.src = c.take<int32_t>((size_t)cap);
     L.bytes = c.size();
@@ -349,26 +372,32 @@ DensifyLayout densify_layout(void *ws, long long cap)
 }
 
 gsp_status enqueue_topk(const float *scores, const int32_t *count, long long cap, long long k, uint8_t *mask,
-                        int32_t *selected_out, const DensifyLayout &L, cudaStream_t s)
+                        int32_t *selected_out, const DensifyLayout &L, int32_t *status, cudaStream_t s)
 {
-    const unsigned nblk = div_up(cap, kBlockItems);
-    unsigned hist_blocks = div_up(cap, 256 * 8);
-    if (hist_blocks > 4u * num_sms()) hist_blocks = 4u * num_sms();
-    if (hist_blocks < 1) hist_blocks = 1;
-    stage_begin("topk", s);
-    sel_init<<<1, 256, 0, s>>>(count, k, L.sel, L.hist);
-    const int shifts[3] = {21, 10, 0}, bits[3] = {11, 11, 10};
-    for (int pass = 0; pass < 3; ++pass) {
-        sel_hist<<<hist_blocks, 256, 0, s>>>(scores, L.sel, shifts[pass], bits[pass], pass, L.hist);
-        sel_pick<<<1, kThreads, 0, s>>>(L.sel, shifts[pass], bits[pass], L.hist);
+    // co-resident blocks (grid barriers), at most two per SM and one per
+    // kBlockItems of capacity (the block sums are sized so)
+    static int per_sm = 0;
+    if (!per_sm) {
+        GSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_fused, kThreads, 0));
+        if (per_sm < 1) return GSP_ERR_UNSUPPORTED;
     }
-    TieFlag tf{scores, L.sel};
-    flag_block_sums<<<nblk, kThreads, 0, s>>>(tf, count, L.sums);
-    scan_block_sums<<<1, kThreads, 0, s>>>(count, L.sums);
-    sel_mark<<<nblk, kThreads, 0, s>>>(scores, count, cap, L.sel, L.sums, mask, selected_out);
+    long long grid = (long long)std::min(per_sm, 2) * num_sms();
+    grid = std::max(1LL, std::min(grid, (long long)div_up(cap, kBlockItems)));
+    TopkArgs a{scores, count, cap, k, mask, selected_out, L.hist, L.sums, L.bar, status};
+    stage_begin("topk", s);
+    GSP_CUDA_TRY(cudaMemsetAsync(L.hist, 0, (3 * kSelBins + 2) * sizeof(unsigned), s));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    GSP_CUDA_TRY(cudaLaunchKernelEx(&cfg, topk_fused, a));
     stage_end("topk", s);
-    note_launches(10);
-    GSP_LAUNCH_CHECK();
+    note_launches(1);
     return GSP_OK;
 }
 
@@ -402,7 +431,7 @@ extern "C" gsp_status gsp_topk_mask(const float *scores, const int32_t *count, i
     gsp_status st = check_workspace(ws, ws_bytes, L.bytes);
     if (st != GSP_OK) return st;
     L = densify_layout(ws, capacity);
-    return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L,
+    return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L, dev_status,
                         reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -426,7 +455,7 @@ extern "C" gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask,
     L = densify_layout(ws, cap);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (!mask) {
-        st = enqueue_topk(scores, g->count, cap, k, L.mask, nullptr, L, s);
+        st = enqueue_topk(scores, g->count, cap, k, L.mask, nullptr, L, dev_status, s);
         if (st != GSP_OK) return st;
         mask = L.mask;
     }
@@ -470,9 +499,9 @@ namespace gsp {
 namespace {
 
 constexpr long long kStaticTopkMaxCap = GSP_TOPK_STATIC_MAX_CAPACITY;
-constexpr size_t kStaticTopkBytes =
-    256 + 256 + kSelBins * sizeof(unsigned) + 256 +
-    sizeof(unsigned) * size_t((kStaticTopkMaxCap + kBlockItems - 1) / kBlockItems + 1) + 256;
+constexpr size_t kStaticTopkBytes = (3 * kSelBins + 2) * sizeof(unsigned) + 256 +
+                                    sizeof(unsigned) * size_t((kStaticTopkMaxCap + kBlockItems - 1) / kBlockItems + 1) +
+                                    256;
 
 static __device__ __align__(256) unsigned char g_topk_scratch[kStaticTopkBytes];
 
@@ -510,11 +539,9 @@ extern "C" gsp_status gsp_topk_mask_static(const float *scores, const int32_t *c
     // same carving as a workspace, without the mask (the caller's output)
     Carver c(scratch);
     DensifyLayout L{};
-    L.sel = c.take<SelState>(1);
-    L.hist = c.take<unsigned>(kSelBins);
-    L.sums = c.take<unsigned>(div_up(capacity, kBlockItems) + 1);
+    carve_topk(c, capacity, L);
     L.mask = nullptr;
     if (c.size() > kStaticTopkBytes) return GSP_ERR_UNSUPPORTED;
-    return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L,
+    return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L, dev_status,
                         reinterpret_cast<cudaStream_t>(stream));
 }
