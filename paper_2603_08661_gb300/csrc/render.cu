@@ -342,7 +342,8 @@ __device__ __forceinline__ unsigned long long project_one(const Views &vs, const
                 const float la = fmaxf(lim, 0.f);
                 const float ymax = sqrtf(la * P.c);
                 const float dyr = P.b * sqrtf(la / P.a);
-                const float schur = fmaxf(P.a - P.b * P.b / P.c, 0.f);
+                const float inv_c = 1.f / P.c, b_c = P.b * inv_c;  // per Gaussian, not per row
+                const float schur = fmaxf(P.a - P.b * b_c, 0.f);
                 uchar2 *ri = st.rowint + o * kRowCap;
                 const int nrows = min(ty1 - ty0 + 1, kRowCap);  // binning reads only these rows
                 const int wr = tx1 - tx0 + 1;
@@ -361,8 +362,8 @@ __device__ __forceinline__ unsigned long long project_one(const Views &vs, const
                         const float hi = fminf(float(ty * kTile + kTile - 1) + 0.5f - my, ymax);
                         if (lo <= hi) {
                             const float d1 = fminf(fmaxf(dyr, lo), hi), d2 = fminf(fmaxf(-dyr, lo), hi);
-                            const float xr = P.b / P.c * d1 + sqrtf(fmaxf(la - d1 * d1 / P.c, 0.f) * schur);
-                            const float xl = P.b / P.c * d2 - sqrtf(fmaxf(la - d2 * d2 / P.c, 0.f) * schur);
+                            const float xr = b_c * d1 + sqrtf(fmaxf(la - d1 * d1 * inv_c, 0.f) * schur);
+                            const float xl = b_c * d2 - sqrtf(fmaxf(la - d2 * d2 * inv_c, 0.f) * schur);
                             const float m = 0.01f + 1e-4f * (fabsf(xl) + fabsf(xr));
                             const int c0 = max(int(floorf((mx + xl - m - 0.5f) / kTile)), tx0);
                             const int c1 = min(int(floorf((mx + xr + m - 0.5f) / kTile)), tx1);
@@ -508,22 +509,32 @@ __global__ void __launch_bounds__(kRsThreads) ds_count(const uint32_t *keys, Sor
     __syncthreads();
     const long long n = cnt.get();
     const unsigned lt = (1u << lane) - 1u;
-    for (long long e0 = (long long)blockIdx.x * kRsThreads; e0 < n; e0 += (long long)gridDim.x * kRsThreads) {
-        const long long e = e0 + tid;
-        const bool ok = e < n;
-        const unsigned k = ok ? keys[e] : 0u;
-        // the two low digits are spread: plain shared atomics; the two high ones
-        // (exponent and leading mantissa bits of a float depth) take few values:
-        // one atomic per group of equal digits in the warp
-        if (ok) {
-            atomicAdd(&h[0][k & 255u], 1u);
-            atomicAdd(&h[1][(k >> 8) & 255u], 1u);
+    constexpr int kPer = 4;  // keys per thread per round, loaded before any is counted
+    for (long long e0 = (long long)blockIdx.x * kRsThreads * kPer; e0 < n;
+         e0 += (long long)gridDim.x * kRsThreads * kPer) {
+        unsigned kv[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const long long e = e0 + j * kRsThreads + tid;
+            kv[j] = e < n ? keys[e] : 0u;
         }
 #pragma unroll
-        for (int d = 2; d < 4; ++d) {
-            const unsigned dig = ok ? (k >> (8 * d)) & 255u : 256u;
-            const unsigned peers = __match_any_sync(0xffffffffu, dig);
-            if (ok && (peers & lt) == 0) atomicAdd(&h[d][dig], __popc(peers));
+        for (int j = 0; j < kPer; ++j) {
+            const bool ok = e0 + j * kRsThreads + tid < n;
+            const unsigned k = kv[j];
+            // the two low digits are spread: plain shared atomics; the two high ones
+            // (exponent and leading mantissa bits of a float depth) take few values:
+            // one atomic per group of equal digits in the warp
+            if (ok) {
+                atomicAdd(&h[0][k & 255u], 1u);
+                atomicAdd(&h[1][(k >> 8) & 255u], 1u);
+            }
+#pragma unroll
+            for (int d = 2; d < 4; ++d) {
+                const unsigned dig = ok ? (k >> (8 * d)) & 255u : 256u;
+                const unsigned peers = __match_any_sync(0xffffffffu, dig);
+                if (ok && (peers & lt) == 0) atomicAdd(&h[d][dig], __popc(peers));
+            }
         }
     }
     __syncthreads();
@@ -2043,7 +2054,7 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
         uint32_t *k0 = S.key, *k1 = S.key_alt;
         int32_t *v0 = S.val, *v1 = S.val_alt;
         const SortCount sc{g->count};
-        ds_count<<<dim3(num_sms(), nv), kRsThreads, 0, s>>>(k0, sc, S.sort_ghist, S.sort_state, S.nb_max, cap);
+        ds_count<<<dim3(2 * num_sms(), nv), kRsThreads, 0, s>>>(k0, sc, S.sort_ghist, S.sort_state, S.nb_max, cap);
         for (int pass = 0; pass < 4; ++pass) {
             ds_pass<<<dim3(S.nb_max, nv), kRsThreads, 0, s>>>(k0, v0, k1, v1, sc, pass, S.sort_ghist, S.sort_state,
                                                               S.sort_ticket, S.nb_max, cap, S.overflow, dev_status);
