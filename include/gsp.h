@@ -267,7 +267,7 @@ gsp_status gsp_topk_mask(const float *scores, const int32_t *count, int64_t capa
  * captured into a CUDA graph (cudaMalloc is not allowed during capture),
  * real-time loops that forbid allocation after start-up, and hosts whose
  * device memory belongs to another allocator.  Same arguments and result as
- * gsp_topk_mask, but no workspace: the scratch (about 73 KB) is a static
+ * gsp_topk_mask, but no workspace: the scratch (about 89 KB) is a static
  * device array inside the library that every GPU which loads the library
  * holds until the process exits.  The caller still passes scores, count,
  * mask_out and selected_out.
