@@ -644,16 +644,27 @@ __global__ void __launch_bounds__(kRsThreads) ds_pass(const uint32_t *kin, const
         gstart = base + inc - x;
     }
     // look-back: the keys with digit tid in the lower tiles
+    // (four lower tiles per round trip: tile 0 always holds an inclusive word)
     unsigned prefix = 0;
     if (t > 0) {
         int j = t - 1;
         long long polls = 0;
-        for (;;) {
-            const unsigned w = vlb[(size_t)j * 256 + tid];
-            if (w & (kLbInc | kLbAgg)) {
-                prefix += w & kLbVal;
-                if ((w & kLbInc) || --j < 0) break;
-            } else if (++polls > kSortSpinLimit) {
+        bool done = false;
+        while (!done) {
+            unsigned w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[q] = j - q >= 0 ? unsigned(vlb[(size_t)(j - q) * 256 + tid]) : unsigned(kLbInc);
+            int used = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (done || used < q) break;  // stopped earlier in this round
+                if (!(w[q] & (kLbInc | kLbAgg))) break;  // not published yet: poll again from here
+                prefix += w[q] & kLbVal;
+                used = q + 1;
+                if (w[q] & kLbInc) done = true;
+            }
+            j -= used;
+            if (!done && used == 0 && ++polls > kSortSpinLimit) {
                 s_fail = 1;
                 break;
             }
@@ -819,10 +830,11 @@ __global__ void __launch_bounds__(kBinThreads) l1_count(const __grid_constant__ 
     }
 }
 
-// Block-wide exclusive scan of one value per thread (256 threads); returns the
-// exclusive prefix and stores the total in *total.
-__device__ __forceinline__ unsigned long long block_excl_scan256(unsigned long long x, unsigned long long *wsum,
-                                                                 unsigned long long *total)
+// Block-wide exclusive scan of one value per thread (NT threads); returns the
+// exclusive prefix and stores the total in *total.  wsum: NT / 32 words.
+template <int NT>
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long x, unsigned long long *wsum,
+                                                              unsigned long long *total)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned long long inc = x;
@@ -834,7 +846,7 @@ __device__ __forceinline__ unsigned long long block_excl_scan256(unsigned long l
     if (lane == 31) wsum[wid] = inc;
     __syncthreads();
     unsigned long long base = 0, all = 0;
-    for (int w = 0; w < 8; ++w) {
+    for (int w = 0; w < NT / 32; ++w) {
         if (w < wid) base += wsum[w];
         all += wsum[w];
     }
@@ -844,20 +856,22 @@ __device__ __forceinline__ unsigned long long block_excl_scan256(unsigned long l
 }
 
 // One block per supertile (all views): offsets of the chunks inside its list.
-__global__ void __launch_bounds__(256) l1_scan(const __grid_constant__ Views vs, State st)
+constexpr int kScanThreads = 1024;  // l1_scan / l2_scan: one block per supertile
+
+__global__ void __launch_bounds__(kScanThreads) l1_scan(const __grid_constant__ Views vs, State st)
 {
-    __shared__ unsigned long long wsum[8];
+    __shared__ unsigned long long wsum[kScanThreads / 32];
     if (*st.overflow) return;
     const int gs = blockIdx.x;
     const int n = *st.n_dev;
     const int nch = (n + kL1Ranks - 1) / kL1Ranks;
     unsigned *row = st.count1 + (size_t)gs * st.nch1_max;
-    const int q = (nch + 255) / 256;
+    const int q = (nch + kScanThreads - 1) / kScanThreads;
     const int c0 = threadIdx.x * q, c1 = min(c0 + q, nch);
     unsigned long long sum = 0;
     for (int c = c0; c < c1; ++c) sum += row[c];
     unsigned long long total;
-    unsigned long long run = block_excl_scan256(sum, wsum, &total);
+    unsigned long long run = block_excl_scan<kScanThreads>(sum, wsum, &total);
     for (int c = c0; c < c1; ++c) {
         const unsigned x = row[c];
         row[c] = unsigned(run);
@@ -1058,9 +1072,10 @@ __device__ __forceinline__ int super_tile(const ViewP &V, int sx, int sy, int b)
 
 // One block per supertile: offsets of its chunks inside each tile's list, and
 // the tiles' list lengths.  Thread (group, b): tile b over a quarter of the chunks.
-__global__ void __launch_bounds__(256) l2_scan(const __grid_constant__ Views vs, State st)
+__global__ void __launch_bounds__(kScanThreads) l2_scan(const __grid_constant__ Views vs, State st)
 {
-    __shared__ unsigned part[4][64];
+    constexpr int kGroups = kScanThreads / 64;
+    __shared__ unsigned part[kGroups][64];
     const int gs = blockIdx.x;
     const int v = find_view_super(vs, gs);
     const ViewP &V = vs.v[v];
@@ -1069,7 +1084,7 @@ __global__ void __launch_bounds__(256) l2_scan(const __grid_constant__ Views vs,
     const int b = threadIdx.x & 63, grp = threadIdx.x >> 6;
     const bool over = *st.overflow;
     const unsigned cb0 = over ? 0u : st.chunk2_base[gs], cb1 = over ? 0u : st.chunk2_base[gs + 1];
-    const unsigned nch = cb1 - cb0, q = (nch + 3) / 4;
+    const unsigned nch = cb1 - cb0, q = (nch + kGroups - 1) / kGroups;
     const unsigned c0 = cb0 + grp * q, c1 = min(c0 + q, cb1);
     unsigned sum = 0;
     for (unsigned c = c0; c < c1; ++c) sum += st.count2[(size_t)c * 64 + b];
@@ -1082,7 +1097,7 @@ __global__ void __launch_bounds__(256) l2_scan(const __grid_constant__ Views vs,
         st.count2[(size_t)c * 64 + b] = run;
         run += x;
     }
-    if (grp == 3) {
+    if (grp == kGroups - 1) {
         const int gt = super_tile(V, sx, sy, b);
         if (gt >= 0) st.tile_len[gt] = run;
     }
@@ -2071,11 +2086,11 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
         const unsigned l1_blocks = unsigned(std::min<long long>(
             std::max<long long>(div_up((long long)nv * S.nch1_max, kBinWarps), 1), 16LL * nsm));
         l1_count<<<l1_blocks, kBinThreads, smem, s>>>(vs, S, cap);
-        l1_scan<<<vs.total_super, 256, 0, s>>>(vs, S);
+        l1_scan<<<vs.total_super, kScanThreads, 0, s>>>(vs, S);
         bin_tops<<<1, 1024, 0, s>>>(vs.total_super, S, dev_status);
         l1_scatter<<<l1_blocks, kBinThreads, smem, s>>>(vs, S, cap);
         l2_count<<<16 * nsm, kBinThreads, 0, s>>>(vs, S, cap);
-        l2_scan<<<vs.total_super, 256, 0, s>>>(vs, S);
+        l2_scan<<<vs.total_super, kScanThreads, 0, s>>>(vs, S);
         tile_scan<<<1, 1024, 0, s>>>(vs.total_tiles, S, dev_status);
         l2_scatter<<<16 * nsm, kBinThreads, 0, s>>>(vs, S);
     }
