@@ -17,6 +17,17 @@ Long-Axis-Split, Alg. 1 with the column read of Alg. 2, per selected Gaussian:
   quaternion and SH are copied.
 The paper's constants (Sec. 2.2, after Alg. 1) are k_off = alpha = 0.5,
 long_factor = alpha = 0.5, other_factor = gamma = 0.85, beta = 0.6.
+
+Gradient-threshold candidate masking (Sec. 2.3, "Global Warm-up Phase"; the
+paper names the masking but not its statistic nor its threshold).  Reading:
+the positional statistic of Gaussian i is the mean, over the (iteration,
+view) pairs in which its screen-space mean gradient is nonzero, of that
+gradient's Euclidean norm; i is a candidate when it has at least one such
+pair and the mean is >= tau.  The selection then takes the top-k edge scores
+among the candidates (fewer when there are fewer candidates).  The first
+three densification events skip the masking (the warm-up).  The candidate
+decision is an integer one taken from floating point: it is taken in FP32,
+mean = float32(sum) / float32(count), the precision of the kernel.
 """
 from __future__ import annotations
 
@@ -34,6 +45,42 @@ def topk_mask(scores: np.ndarray, k: int) -> np.ndarray:
     order = np.lexsort((np.arange(n), -s.astype(np.float64)))
     mask = np.zeros(n, dtype=bool)
     mask[order[:k]] = True
+    return mask
+
+
+def pos_grad_stats(g2d_views, sums=None, counts=None):
+    """Accumulate the positional statistic over views: g2d_views is a list of
+    (n, >= 2) arrays of screen-space gradients whose columns 0, 1 are
+    dL/d(mean2D x, y).  Returns (sum of norms, number of nonzero views)."""
+    g0 = np.asarray(g2d_views[0])
+    n = g0.shape[0]
+    s = np.zeros(n) if sums is None else np.array(sums, dtype=np.float64)
+    c = np.zeros(n, dtype=np.int64) if counts is None else np.array(counts, dtype=np.int64)
+    for g in g2d_views:
+        g = np.asarray(g, dtype=np.float64)
+        nz = (g[:, 0] != 0) | (g[:, 1] != 0)
+        s[nz] += np.hypot(g[nz, 0], g[nz, 1])
+        c[nz] += 1
+    return s, c
+
+
+def grad_candidates(sums: np.ndarray, counts: np.ndarray, tau: float) -> np.ndarray:
+    """Candidates of the gradient-threshold masking (decision in FP32)."""
+    sums32 = np.asarray(sums, dtype=np.float32)
+    c = np.asarray(counts, dtype=np.int64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        mean = sums32 / np.maximum(c, 1).astype(np.float32)
+    return (c > 0) & (mean >= np.float32(tau))
+
+
+def gated_topk_mask(scores: np.ndarray, k: int, sums: np.ndarray, counts: np.ndarray, tau: float) -> np.ndarray:
+    """Top-k by score among the gradient-threshold candidates (ties toward the
+    lower index); selects min(k, number of candidates)."""
+    cand = grad_candidates(sums, counts, tau)
+    idx = np.nonzero(cand)[0]
+    sub = topk_mask(np.asarray(scores)[idx], k)
+    mask = np.zeros(np.asarray(scores).shape[0], dtype=bool)
+    mask[idx[sub]] = True
     return mask
 
 

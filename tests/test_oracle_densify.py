@@ -109,3 +109,39 @@ def test_topk_ties_lowest_index_and_brute_force():
         ref = sorted(range(n), key=lambda i: (-float(s[i]), i))[:k]
         assert set(np.nonzero(od.topk_mask(s, k))[0]) == set(ref)
         assert od.topk_mask(s, k).sum() == k
+
+
+def test_positional_statistic_worked_example():
+    # view 1: (3, 4) -> 5, (0, 0) -> not counted; view 2: (0, -2) -> 2, (1e-30, 0) counted
+    v1 = np.array([[3.0, 4.0, 9.0], [0.0, 0.0, 7.0]])
+    v2 = np.array([[0.0, -2.0, 0.0], [1e-30, 0.0, 0.0]])
+    s, c = od.pos_grad_stats([v1, v2])
+    np.testing.assert_allclose(s, [7.0, 1e-30], rtol=0, atol=0)
+    assert list(c) == [2, 1]
+    s2, c2 = od.pos_grad_stats([v1], s, c)  # accumulates
+    np.testing.assert_allclose(s2, [12.0, 1e-30])
+    assert list(c2) == [3, 1]
+
+
+def test_gated_topk_invariants_and_brute_force():
+    rng = np.random.default_rng(3)
+    for trial in range(30):
+        n = int(rng.integers(1, 300))
+        s = rng.integers(0, 12, n).astype(np.float32)
+        cnt = rng.integers(0, 4, n)
+        sums = rng.uniform(0, 1, n) * cnt
+        k = int(rng.integers(0, n + 1))
+        # tau = 0 with every count > 0: plain top-k; tau = inf: nothing
+        full = np.maximum(cnt, 1)
+        assert np.array_equal(od.gated_topk_mask(s, k, sums, full, 0.0), od.topk_mask(s, k))
+        assert not od.gated_topk_mask(s, k, sums, cnt, np.inf).any()
+        tau = float(rng.uniform(0, 0.6))
+        m = od.gated_topk_mask(s, k, sums, cnt, tau)
+        # brute force over the candidates, in plain Python floats rounded to FP32
+        cand = [i for i in range(n) if cnt[i] > 0 and
+                float(np.float32(np.float32(sums[i]) / np.float32(cnt[i]))) >= float(np.float32(tau))]
+        ref = sorted(cand, key=lambda i: (-float(s[i]), i))[:k]
+        assert set(np.nonzero(m)[0]) == set(ref)
+        assert m.sum() == min(k, len(cand))
+    # a Gaussian never seen (count 0) is never a candidate, even at tau = 0
+    assert not od.gated_topk_mask(np.ones(3, np.float32), 3, np.zeros(3), np.zeros(3, int), 0.0).any()

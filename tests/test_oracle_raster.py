@@ -315,3 +315,35 @@ def test_region_adjoint_equals_masked_upstream_gradient():
     b = orc.render_bwd(g, cam, m)
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
         np.testing.assert_allclose(a[k], b[k], rtol=1e-12, atol=1e-300)
+
+
+def test_screen_space_mean_gradient_matches_differences_of_the_projected_mean():
+    """g2d columns 0, 1 (dL/d mean2D, the input of the positional statistic of
+    the gradient-threshold masking) against central differences that move the
+    projected mean in the record itself, for a fixed linear upstream gradient."""
+    g, cam, _ = _fd_scene()
+    proj = orc.project(g, cam)
+    rng = np.random.default_rng(21)
+    dldc = rng.normal(size=(40, 48, 3))
+    gr = orc.render_bwd(g, cam, dldc, proj=proj)
+
+    def loss(p):
+        return float(np.sum(orc.render(g, cam, proj=p)["rgb"] * dldc))
+
+    checked = 0
+    for i in range(40):
+        if proj[i, orc.P_VALID] == 0:
+            continue
+        for col, c in ((orc.P_MX, 0), (orc.P_MY, 1)):
+            fd = []
+            for h in (1e-4, 5e-5):
+                pp, pm = proj.copy(), proj.copy()
+                pp[i, col] += h
+                pm[i, col] -= h
+                fd.append((loss(pp) - loss(pm)) / (2 * h))
+            if abs(fd[0] - fd[1]) > 0.1 * max(abs(fd[0]), 1e-9):
+                continue  # a gate moved inside the step
+            an = gr["g2d"][i, c]
+            assert abs(an - fd[0]) <= 1e-5 * max(abs(fd[0]), 1e-3), (i, c, an, fd[0])
+            checked += 1
+    assert checked > 40
