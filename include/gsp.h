@@ -166,6 +166,13 @@ typedef struct gsp_render_opts {
                               block its tile rectangle touches) share the same bound */
     int32_t fwd_variant;   /* forward compositing variant, 0 .. GSP_FWD_VARIANTS - 1 (0: default) */
     int32_t bwd_variant;   /* adjoint compositing variant, 0 .. GSP_BWD_VARIANTS - 1 (0: default) */
+    /* Positional statistic of the gradient-threshold masking (Sec. 2.3, "Global Warm-up
+     * Phase"), read by gsp_render_bwd only; both NULL or both device [capacity] arrays.
+     * For every view in which Gaussian i's screen-space mean gradient g = dL/d(mean2D) is
+     * nonzero: pos_grad_sum[i] += |g| (Euclidean norm, pixel units), pos_grad_count[i] += 1.
+     * Accumulated over calls; the caller clears them (e.g. after each densification). */
+    float *pos_grad_sum;
+    int32_t *pos_grad_count;
 } gsp_render_opts;
 
 /* Compositing variants (pixels per thread, Gaussians staged per shared-memory batch,
@@ -259,6 +266,23 @@ size_t gsp_las_workspace_size(int64_t capacity);
 gsp_status gsp_topk_mask(const float *scores, const int32_t *count, int64_t capacity, int64_t k,
                          uint8_t *mask_out, int32_t *selected_out, void *workspace,
                          size_t workspace_bytes, int32_t *dev_status, gsp_stream_t stream);
+
+/*
+ * Top-k with gradient-threshold masking (Sec. 2.3, "Global Warm-up Phase": after the
+ * warm-up events the split candidates must pass the gradient threshold; the paper
+ * names neither the statistic nor the threshold).  Gaussian i < N is a candidate when
+ * pos_grad_count[i] > 0 and pos_grad_sum[i] / pos_grad_count[i] >= threshold, the
+ * quotient and comparison in FP32 (the statistic gsp_render_bwd accumulates through
+ * gsp_render_opts).  mask_out selects the min(k, candidates) largest scores among the
+ * candidates, ties in ascending index order; selected_out receives that number.
+ * pos_grad_sum / pos_grad_count: device float / int32 [capacity].  threshold: not NaN
+ * (+inf selects nothing).  Workspace: gsp_las_workspace_size(capacity) bytes, as for
+ * gsp_topk_mask.  Errors: GSP_ERR_INVALID_ARG, GSP_ERR_WORKSPACE; device: GSP_ERR_TIMEOUT.
+ */
+gsp_status gsp_topk_mask_gated(const float *scores, const float *pos_grad_sum, const int32_t *pos_grad_count,
+                               float threshold, const int32_t *count, int64_t capacity, int64_t k,
+                               uint8_t *mask_out, int32_t *selected_out, void *workspace,
+                               size_t workspace_bytes, int32_t *dev_status, gsp_stream_t stream);
 
 /*
  * Allocation-free variant of gsp_topk_mask (the paper has no counterpart).

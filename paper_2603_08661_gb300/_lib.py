@@ -42,7 +42,8 @@ class Camera(ctypes.Structure):
 
 
 class RenderOpts(ctypes.Structure):
-    _fields_ = [("pair_capacity", c_i64), ("fwd_variant", c_i32), ("bwd_variant", c_i32)]
+    _fields_ = [("pair_capacity", c_i64), ("fwd_variant", c_i32), ("bwd_variant", c_i32),
+                ("pos_grad_sum", ctypes.c_void_p), ("pos_grad_count", ctypes.c_void_p)]
 
 
 class LasParams(ctypes.Structure):
@@ -72,6 +73,7 @@ SIGNATURES = {
     "gsp_las_params_paper": (None, [P(LasParams)]),
     "gsp_las_workspace_size": (c_sz, [c_i64]),
     "gsp_topk_mask": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
+    "gsp_topk_mask_gated": (c_i32, [c_vp, c_vp, c_vp, c_f32, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
     "gsp_las_split": (c_i32, [P(Gaussians), c_vp, c_vp, c_i64, P(LasParams), c_vp, c_sz, c_vp, c_vp]),
     "gsp_topk_mask_static": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),
     "gsp_sgd_step": (c_i32, [P(Gaussians), c_vp, c_vp, c_vp, c_vp, c_vp, c_f32, c_vp]),

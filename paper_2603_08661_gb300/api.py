@@ -238,8 +238,15 @@ class Renderer:
         return {"rgb": rgb, "T": T, "last": last, "loss": loss, "status": st}
 
     def backward(self, fwd: dict, targets=None, dL_drgb=None, edge=None, score=None, grads=None,
-                 accumulate: bool = False, status=None, stream=None):
+                 accumulate: bool = False, status=None, stream=None, pos_grad=None):
+        """pos_grad: optional (sum float32 [capacity], count int32 [capacity]) device
+        tensors; the positional statistic of the gradient-threshold masking is
+        added to them (see gsp_render_opts)."""
         gs = self.gs
+        opts = self.opts
+        if pos_grad is not None:
+            opts = L.RenderOpts(self.opts.pair_capacity, self.opts.fwd_variant, self.opts.bwd_variant,
+                                _ptr(pos_grad[0]).value, _ptr(pos_grad[1]).value)
         if grads is None:
             grads = {"means": torch.zeros_like(gs.means), "log_scales": torch.zeros_like(gs.log_scales),
                      "quats": torch.zeros_like(gs.quats), "opacity_logits": torch.zeros_like(gs.opacity_logits),
@@ -249,7 +256,7 @@ class Renderer:
                                      _ptr(dL_drgb), _ptr(fwd["rgb"]), _ptr(fwd["T"]), _ptr(fwd["last"]), _ptr(edge),
                                      _ptr(score), _ptr(grads["means"]), _ptr(grads["log_scales"]),
                                      _ptr(grads["quats"]), _ptr(grads["opacity_logits"]), _ptr(grads["sh"]),
-                                     int(bool(accumulate)), ctypes.byref(self.opts), _ptr(self.ws), self.ws_bytes,
+                                     int(bool(accumulate)), ctypes.byref(opts), _ptr(self.ws), self.ws_bytes,
                                      _ptr(st), _stream_handle(stream)), "gsp_render_bwd")
         return grads
 
@@ -269,6 +276,22 @@ def topk_mask(scores: torch.Tensor, count: torch.Tensor, k: int, status=None, st
     st = status if status is not None else new_status(scores.device)
     L.check(lib().gsp_topk_mask(_ptr(scores), _ptr(count), cap, int(k), _ptr(mask), _ptr(sel), _ptr(ws), need,
                                 _ptr(st), _stream_handle(stream)), "gsp_topk_mask")
+    return mask, sel, st
+
+
+def topk_mask_gated(scores: torch.Tensor, pos_grad_sum: torch.Tensor, pos_grad_count: torch.Tensor,
+                    threshold: float, count: torch.Tensor, k: int, status=None, stream=None):
+    """Top-k among the Gaussians whose mean positional gradient reaches threshold
+    (gradient-threshold masking, gsp_topk_mask_gated)."""
+    cap = int(scores.shape[0])
+    need = lib().gsp_las_workspace_size(cap)
+    ws = _workspace(need, scores.device)
+    mask = torch.empty(cap, dtype=torch.uint8, device=scores.device)
+    sel = torch.zeros(1, dtype=torch.int32, device=scores.device)
+    st = status if status is not None else new_status(scores.device)
+    L.check(lib().gsp_topk_mask_gated(_ptr(scores), _ptr(pos_grad_sum), _ptr(pos_grad_count),
+                                      ctypes.c_float(threshold), _ptr(count), cap, int(k), _ptr(mask), _ptr(sel),
+                                      _ptr(ws), need, _ptr(st), _stream_handle(stream)), "gsp_topk_mask_gated")
     return mask, sel, st
 
 

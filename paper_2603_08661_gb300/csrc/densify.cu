@@ -108,7 +108,20 @@ struct TopkArgs {
     unsigned *sums;  // [grid] tie counts of the blocks' index ranges
     unsigned *bar;   // grid barrier (zeroed before the launch)
     int32_t *status;
+    // gradient-threshold masking (all three, or gsum == nullptr for none): Gaussian i
+    // is a candidate when gcnt[i] > 0 and gsum[i] / gcnt[i] >= tau (FP32)
+    const float *gsum;
+    const int32_t *gcnt;
+    float tau;
+    unsigned *ncand;  // candidate count (zeroed before the launch)
 };
+
+__device__ __forceinline__ bool is_candidate(const TopkArgs &a, long long i)
+{
+    if (!a.gsum) return true;
+    const int32_t c = a.gcnt[i];
+    return c > 0 && __fdiv_rn(a.gsum[i], float(c)) >= a.tau;
+}
 
 // Block-wide pick of the digit that holds the rem-th largest key, from the
 // counts hist[0 .. nb) (the top digit first): thread t owns the nb / kThreads
@@ -164,7 +177,7 @@ __global__ void __launch_bounds__(kThreads) topk_fused(TopkArgs a)
     const int tid = threadIdx.x;
     const unsigned G = gridDim.x;
     const long long n = max(*a.count, 0);
-    const unsigned kk = a.k < 0 ? 0u : (a.k > n ? unsigned(n) : unsigned(a.k));
+    unsigned kk = a.k < 0 ? 0u : (a.k > n ? unsigned(n) : unsigned(a.k));
     // the same prefix / remaining in every block
     unsigned prefix = 0, remaining = kk, eq = 0;
     const int shifts[3] = {21, 10, 0}, bits[3] = {11, 11, 10};
@@ -175,16 +188,25 @@ __global__ void __launch_bounds__(kThreads) topk_fused(TopkArgs a)
         if (remaining > 0) {
             for (int i = tid; i < nb; i += kThreads) h[i] = 0;
             __syncthreads();
+            unsigned nc = 0;
             for (long long i = blockIdx.x * (long long)kThreads + tid; i < n; i += (long long)G * kThreads) {
+                if (!is_candidate(a, i)) continue;
+                ++nc;
                 const unsigned key = order_key(a.scores[i]);
                 if (pass > 0 && (key >> hi) != (prefix >> hi)) continue;
                 atomicAdd(&h[(key >> shift) & unsigned(nb - 1)], 1u);
             }
+            nc = __reduce_add_sync(0xffffffffu, nc);
+            if (pass == 0 && a.gsum && (tid & 31) == 0 && nc) atomicAdd(a.ncand, nc);
             __syncthreads();
             for (int i = tid; i < nb; i += kThreads)
                 if (h[i]) atomicAdd(gh + i, h[i]);
         }
         if (!grid_barrier(a.bar, G, kDefaultSpinLimit, a.status)) return;
+        if (pass == 0 && a.gsum) {  // at most the candidates (the same in every block)
+            kk = min(kk, __ldcg(a.ncand));
+            remaining = kk;
+        }
         if (remaining > 0) {
             unsigned above, in_bin;
             const int b = pick_digit(gh, nb, remaining, &above, &in_bin);
@@ -201,7 +223,8 @@ __global__ void __launch_bounds__(kThreads) topk_fused(TopkArgs a)
     unsigned tie_base = 0;
     if (rank_ties) {
         unsigned c = 0;
-        for (long long i = b0 + tid; i < min(b1, n); i += kThreads) c += order_key(a.scores[i]) == prefix;
+        for (long long i = b0 + tid; i < min(b1, n); i += kThreads)
+            c += order_key(a.scores[i]) == prefix && is_candidate(a, i);
         unsigned ex;
         const unsigned tot = block_scan(c, &ex);
         if (tid == 0) a.sums[blockIdx.x] = tot;
@@ -218,7 +241,7 @@ __global__ void __launch_bounds__(kThreads) topk_fused(TopkArgs a)
         for (int j = 0; j < kPerThread; ++j) {
             const long long i = r0 + tid * kPerThread + j;
             const unsigned key = (i < b1 && i < n) ? order_key(a.scores[i]) : 0u;
-            const bool live = i < b1 && i < n && kk > 0;
+            const bool live = i < b1 && i < n && kk > 0 && is_candidate(a, i);
             tie[j] = live && key == prefix;
             gt[j] = live && key > prefix;
             c += tie[j];
@@ -343,9 +366,14 @@ __global__ void las_commit(int32_t *count, long long cap, const unsigned *rank_o
     *count = int32_t(n + total);
 }
 
+// [3][kSelBins] digit counts, the 2-word grid barrier, the candidate count:
+// zeroed before each selection
+constexpr int kTopkZeroWords = 3 * kSelBins + 3;
+
 struct DensifyLayout {
-    unsigned *hist;  // [3][kSelBins], then the 2-word grid barrier: zeroed per selection
+    unsigned *hist;
     unsigned *bar;
+    unsigned *ncand;
     unsigned *sums;
     uint8_t *mask;
     int32_t *src;
@@ -355,8 +383,9 @@ struct DensifyLayout {
 // The selection's scratch (shared by the workspace and the static array).
 void carve_topk(Carver &c, long long cap, DensifyLayout &L)
 {
-    L.hist = c.take<unsigned>(3 * kSelBins + 2);
+    L.hist = c.take<unsigned>(kTopkZeroWords);
     L.bar = L.hist + 3 * kSelBins;
+    L.ncand = L.hist + 3 * kSelBins + 2;
     L.sums = c.take<unsigned>(div_up(cap, kBlockItems) + 1);
 }
 
@@ -372,7 +401,8 @@ DensifyLayout densify_layout(void *ws, long long cap)
 }
 
 gsp_status enqueue_topk(const float *scores, const int32_t *count, long long cap, long long k, uint8_t *mask,
-                        int32_t *selected_out, const DensifyLayout &L, int32_t *status, cudaStream_t s)
+                        int32_t *selected_out, const DensifyLayout &L, int32_t *status, cudaStream_t s,
+                        const float *gsum = nullptr, const int32_t *gcnt = nullptr, float tau = 0.f)
 {
     // co-resident blocks (grid barriers), at most two per SM and one per
     // kBlockItems of capacity (the block sums are sized so)
@@ -383,9 +413,9 @@ gsp_status enqueue_topk(const float *scores, const int32_t *count, long long cap
     }
     long long grid = (long long)std::min(per_sm, 2) * num_sms();
     grid = std::max(1LL, std::min(grid, (long long)div_up(cap, kBlockItems)));
-    TopkArgs a{scores, count, cap, k, mask, selected_out, L.hist, L.sums, L.bar, status};
+    TopkArgs a{scores, count, cap, k, mask, selected_out, L.hist, L.sums, L.bar, status, gsum, gcnt, tau, L.ncand};
     stage_begin("topk", s);
-    GSP_CUDA_TRY(cudaMemsetAsync(L.hist, 0, (3 * kSelBins + 2) * sizeof(unsigned), s));
+    GSP_CUDA_TRY(cudaMemsetAsync(L.hist, 0, kTopkZeroWords * sizeof(unsigned), s));
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(unsigned(grid));
     cfg.blockDim = dim3(kThreads);
@@ -433,6 +463,22 @@ extern "C" gsp_status gsp_topk_mask(const float *scores, const int32_t *count, i
     L = densify_layout(ws, capacity);
     return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L, dev_status,
                         reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" gsp_status gsp_topk_mask_gated(const float *scores, const float *pos_grad_sum,
+                                          const int32_t *pos_grad_count, float threshold, const int32_t *count,
+                                          int64_t capacity, int64_t k, uint8_t *mask_out, int32_t *selected_out,
+                                          void *ws, size_t ws_bytes, int32_t *dev_status, gsp_stream_t stream)
+{
+    if (!scores || !pos_grad_sum || !pos_grad_count || !count || !mask_out || !dev_status || capacity < 1 ||
+        capacity > (1LL << 30) || threshold != threshold)
+        return GSP_ERR_INVALID_ARG;
+    DensifyLayout L = densify_layout(nullptr, capacity);
+    gsp_status st = check_workspace(ws, ws_bytes, L.bytes);
+    if (st != GSP_OK) return st;
+    L = densify_layout(ws, capacity);
+    return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L, dev_status,
+                        reinterpret_cast<cudaStream_t>(stream), pos_grad_sum, pos_grad_count, threshold);
 }
 
 extern "C" gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask, const float *scores, int64_t k,
@@ -499,7 +545,7 @@ namespace gsp {
 namespace {
 
 constexpr long long kStaticTopkMaxCap = GSP_TOPK_STATIC_MAX_CAPACITY;
-constexpr size_t kStaticTopkBytes = (3 * kSelBins + 2) * sizeof(unsigned) + 256 +
+constexpr size_t kStaticTopkBytes = kTopkZeroWords * sizeof(unsigned) + 256 +
                                     sizeof(unsigned) * size_t((kStaticTopkMaxCap + kBlockItems - 1) / kBlockItems + 1) +
                                     256;
 

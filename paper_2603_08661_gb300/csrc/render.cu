@@ -1673,7 +1673,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) c
 template <int K>
 __global__ void __launch_bounds__(kProjBwdThreads) project_bwd(const __grid_constant__ Views vs, Params p, State st,
                                                   float *gm, float *gls, float *gq, float *go, float *gsh,
-                                                  int accumulate)
+                                                  int accumulate, float *pg_sum, int32_t *pg_count)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= *p.count) return;
@@ -1693,10 +1693,16 @@ __global__ void __launch_bounds__(kProjBwdThreads) project_bwd(const __grid_cons
     const float qinv = __frsqrt_rn(qn2);
     const float qh[4] = {q4[0] * qinv, q4[1] * qinv, q4[2] * qinv, q4[3] * qinv};
 
+    float pg = 0.f;  // positional statistic of this call: norms of the nonzero mean gradients
+    int32_t pn = 0;
     for (int v = 0; v < vs.n; ++v) {
         const float4 *gg = st.g2d + ((size_t)v * cap + i) * 3;
         const float4 ga = gg[0], gb = gg[1], gc = gg[2];
         // ga = (mean x, mean y, A, B), gb = (C, opacity, r, g), gc = (b, -, -, -)
+        if (ga.x != 0.f || ga.y != 0.f) {
+            pg += hypotf(ga.x, ga.y);
+            ++pn;
+        }
         if (ga.x == 0.f && ga.y == 0.f && ga.z == 0.f && ga.w == 0.f && gb.x == 0.f && gb.y == 0.f &&
             gb.z == 0.f && gb.w == 0.f && gc.x == 0.f)
             continue;
@@ -1811,6 +1817,10 @@ __global__ void __launch_bounds__(kProjBwdThreads) project_bwd(const __grid_cons
         G_mu[0] += (gu[0] - ux * ud) * rn;
         G_mu[1] += (gu[1] - uy * ud) * rn;
         G_mu[2] += (gu[2] - uz * ud) * rn;
+    }
+    if (pg_sum) {  // accumulated over calls (the caller resets them)
+        pg_sum[i] += pg;
+        pg_count[i] += pn;
     }
     float *gshr = gsh + (size_t)i * 3 * K;
     if (accumulate) {
@@ -2135,6 +2145,7 @@ extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *c
     if (!dL_drgb && (!targets || !rgb)) return GSP_ERR_INVALID_ARG;
     if (opts->bwd_variant < 0 || opts->bwd_variant >= kNumBwdVariants) return GSP_ERR_INVALID_ARG;
     if (score && !edge) return GSP_ERR_INVALID_ARG;
+    if (!opts->pos_grad_sum != !opts->pos_grad_count) return GSP_ERR_INVALID_ARG;
     const long long cap = g->capacity;
     Layout L = render_layout(nullptr, cap, vs, opts->pair_capacity);
     st = check_workspace(ws, ws_bytes, L.bytes);
@@ -2164,7 +2175,8 @@ extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *c
     project_bwd<KK><<<div_up(cap, kProjBwdThreads), kProjBwdThreads,                                             \
                       sizeof(float) * kProjBwdThreads * (3 * (KK) + 1), s>>>(vs, P, S, grad_means, grad_log_scales, \
                                                                              grad_quats, grad_opacity_logits, grad_sh, \
-                                                                             accumulate)
+                                                                             accumulate, opts->pos_grad_sum,            \
+                                                                             opts->pos_grad_count)
     switch (P.K) {
     case 1: GSP_PBWD(1); break;
     case 4: GSP_PBWD(4); break;

@@ -129,3 +129,48 @@ def test_config0_pipeline_selection_and_split(gsp_lib):
     assert ((m != ref_m) & ~near).sum() == 0
     ref_las = od.las_split(g, m, **od.CONFIG_PRESET)
     _las_close(gs.means[:2200].cpu().numpy().astype(np.float64), ref_las["means"])
+
+
+def _gate_inputs(n, seed):
+    rng = np.random.default_rng(seed)
+    s = rng.integers(0, 40, n).astype(np.float32) * np.float32(0.5)  # ties
+    cnt = rng.integers(0, 5, n).astype(np.int32)  # count 0: never seen
+    sums = (rng.gamma(2.0, 1e-4, n) * cnt).astype(np.float32)
+    return s, sums, cnt
+
+
+@pytest.mark.parametrize("n,k,tau", [(1, 1, 0.0), (9, 4, 1e-4), (5000, 600, 2e-4), (5000, 5000, 1e-4),
+                                     (300000, 30000, 2.5e-4), (1000000, 100000, 1.5e-4)])
+def test_gated_topk_matches_oracle(gsp_lib, n, k, tau):
+    """Gradient-threshold masking fused into the selection: bit-exact masks and
+    counts, candidate decision in FP32 on both sides; k may exceed the candidates."""
+    import torch
+    s, sums, cnt = _gate_inputs(n, n + k)
+    cap = n + 3
+    dev = lambda a, dt: torch.from_numpy(np.concatenate([a, np.zeros(3, a.dtype)])).to("cuda", dt)
+    cnt_t = torch.tensor([n], dtype=torch.int32, device="cuda")
+    mask, sel, st = gsp_lib.topk_mask_gated(dev(s, torch.float32), dev(sums, torch.float32),
+                                            dev(cnt, torch.int32), tau, cnt_t, k)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    m = mask.cpu().numpy().astype(bool)
+    ref = od.gated_topk_mask(s, k, sums, cnt, tau)
+    assert not m[n:].any()
+    assert np.array_equal(m[:n], ref)
+    assert int(sel.item()) == int(ref.sum()) == min(k, int(od.grad_candidates(sums, cnt, tau).sum()))
+
+
+def test_gated_topk_limits(gsp_lib):
+    import torch
+    s, sums, cnt = _gate_inputs(20000, 5)
+    t = lambda a: torch.from_numpy(a).cuda()
+    n_t = torch.tensor([20000], dtype=torch.int32, device="cuda")
+    # infinite threshold: nothing; threshold 0 with every count > 0: plain top-k
+    mask, sel, _ = gsp_lib.topk_mask_gated(t(s), t(sums), t(cnt), float("inf"), n_t, 500)
+    assert int(sel.item()) == 0 and not mask.any()
+    ones = np.maximum(cnt, 1).astype(np.int32)
+    mask, _, _ = gsp_lib.topk_mask_gated(t(s), t(sums), t(ones), 0.0, n_t, 500)
+    plain, _, _ = gsp_lib.topk_mask(t(s), n_t, 500)
+    assert torch.equal(mask, plain)
+    with pytest.raises(Exception):
+        gsp_lib.topk_mask_gated(t(s), t(sums), t(cnt), float("nan"), n_t, 500)

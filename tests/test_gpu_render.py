@@ -19,6 +19,7 @@ import synth
 from conftest import grad_rel
 from oracle import edge as oe
 from oracle import raster as orc
+from oracle import densify as od
 
 pytestmark = pytest.mark.gpu
 
@@ -263,3 +264,51 @@ def test_capacity_rows_beyond_count_are_ignored(gsp_lib):
     assert np.array_equal(a["rgb"], b["rgb"])
     np.testing.assert_allclose(a["score"], b["score"][:300], rtol=1e-5, atol=1e-7)
     assert np.all(b["score"][300:] == 0)
+
+
+def test_positional_statistic_matches_oracle(gsp_lib):
+    """The positional statistic of the gradient-threshold masking, accumulated by
+    the adjoint over three uneven views and two calls, against the oracle's
+    screen-space mean gradients: counts exact and sums within 1e-4 relative
+    (floor 1e-2 x RMS), outside the gate-exempt Gaussians."""
+    import torch
+    n = 1500
+    g = synth.gaussians(n, 3, seed=31)
+    g["log_scales"] += np.float32(0.6)
+    sizes = [(80, 60), (64, 64), (97, 51)]
+    cams = [synth.camera_ring(k, 3, resolutions=sizes) for k in range(3)]
+    npix = sum(c["width"] * c["height"] for c in cams)
+    rng = np.random.default_rng(17)
+    dL = rng.normal(size=(npix, 3)) / npix
+    dL[rng.uniform(size=npix) < 0.2] = 0.0  # pixels without upstream gradient
+    gs = gsp_lib.GaussianSet.from_arrays(g)
+    r = gsp_lib.Renderer(gs, cams, 1 << 22)
+    out = r.forward()
+    psum = torch.zeros(gs.capacity, device="cuda")
+    pcnt = torch.zeros(gs.capacity, dtype=torch.int32, device="cuda")
+    dl_t = torch.from_numpy(dL.astype(np.float32)).cuda()
+    r.backward(out, dL_drgb=dl_t, pos_grad=(psum, pcnt))
+    torch.cuda.synchronize()
+    s1, c1 = psum.cpu().numpy().astype(np.float64), pcnt.cpu().numpy()
+    r.backward(out, dL_drgb=dl_t, pos_grad=(psum, pcnt))
+    torch.cuda.synchronize()
+    s2, c2 = psum.cpu().numpy().astype(np.float64), pcnt.cpu().numpy()
+    assert int(out["status"].item()) == 0
+    views, skip, off = [], set(), 0
+    for cam in cams:
+        w, h = cam["width"], cam["height"]
+        ref = orc.render(g, cam)
+        views.append(orc.render_bwd(g, cam, dL[off:off + w * h].reshape(h, w, 3), proj=ref["proj"])["g2d"])
+        skip |= exempt_gaussians(g, cam, ref)
+        off += w * h
+    s_ref, c_ref = od.pos_grad_stats(views)
+    keep = np.ones(n, bool)
+    keep[list(skip)] = False
+    assert keep.sum() > n // 2 and (c_ref[keep] > 0).sum() > 300
+    assert np.array_equal(c1[:n][keep], c_ref[keep])
+    rms = np.sqrt(np.mean(s_ref[keep] ** 2))
+    rel = np.abs(s1[:n] - s_ref) / np.maximum(np.abs(s_ref), 1e-2 * rms)
+    assert rel[keep].max() <= 1e-4, rel[keep].max()
+    # a second call adds the same statistic again
+    assert np.array_equal(c2, 2 * c1)
+    np.testing.assert_allclose(s2, 2 * s1, rtol=1e-5, atol=1e-6 * rms)
