@@ -8,6 +8,13 @@ edge score, splits them with the Long-Axis-Split (Sec. 2.2, Alg. 1-2) into
 the free capacity rows, and clears the scores.  The edge maps of the fixed
 target views (Sec. 2.1) are computed once, in one fused launch.
 
+With grad_threshold set, the adjoint also accumulates the positional
+statistic of the gradient-threshold masking, and every event after the first
+`warmup_events` (three: Sec. 2.3, "Global Warm-up Phase") selects only among
+the Gaussians whose mean positional gradient reaches the threshold; the
+statistic is cleared with the scores after each event.  The graph driver
+captures the threshold's value when it first runs.
+
 Nothing is read back to the host inside the loop: the live count stays on
 the device, every launch is sized to the capacity, and the caller reads the
 status word when it wants to.  Two drivers share the buffers:
@@ -30,8 +37,12 @@ GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 
 class DensifyLoop:
     def __init__(self, gs, cams, targets, lr: float = 1e-3, every: int = 20, k_event: int = 50_000,
-                 las: dict = LAS_CONFIG, pair_capacity: int = 1 << 26, variants=(0, 0), device="cuda"):
+                 las: dict = LAS_CONFIG, pair_capacity: int = 1 << 26, variants=(0, 0), device="cuda",
+                 grad_threshold: float | None = None, warmup_events: int = 3):
         self.gs, self.lr, self.every, self.k_event = gs, float(lr), int(every), int(k_event)
+        self.grad_threshold = None if grad_threshold is None else float(grad_threshold)
+        self.warmup_events = int(warmup_events)
+        self.events = 0
         self.device = device
         self.targets = list(targets)
         self.status = new_status(device)
@@ -39,6 +50,9 @@ class DensifyLoop:
         self.r = Renderer(gs, cams, pair_capacity, device=device, variants=variants)
         cap = gs.capacity
         self.score = torch.zeros(cap, device=device)
+        self.pos_grad = None
+        if self.grad_threshold is not None:
+            self.pos_grad = (torch.zeros(cap, device=device), torch.zeros(cap, dtype=torch.int32, device=device))
         self.grads = {k: torch.zeros_like(getattr(gs, k)) for k in GROUPS}
         npix = self.r.total_pix
         self.bufs = {"rgb": torch.empty((npix, 3), device=device), "T": torch.empty(npix, device=device),
@@ -60,27 +74,46 @@ class DensifyLoop:
         """Forward + L1 + adjoint with fused edge score + SGD (library calls only)."""
         out = self.r.forward(targets=self.targets, status=self.status, out=self.bufs, stream=stream)
         self.r.backward(out, targets=self.targets, edge=self.E, score=self.score, grads=self.grads,
-                        status=self.status, stream=stream)
+                        status=self.status, stream=stream, pos_grad=self.pos_grad)
         self._sgd(self.grads, stream)
 
-    def event(self, stream=None):
-        """Top-k by edge score, Long-Axis-Split, score reset."""
+    def gated(self) -> bool:
+        """Whether the next event applies the gradient-threshold masking."""
+        return self.pos_grad is not None and self.events >= self.warmup_events
+
+    def event(self, stream=None, gated=None, count: bool = True):
+        """Top-k by edge score (among the gradient-threshold candidates once the
+        warm-up is over), Long-Axis-Split, score and statistic reset.  count:
+        advance the event counter (not while the event is being captured)."""
         cap = self.gs.capacity
         s = _stream_handle(stream)
-        L.check(lib().gsp_topk_mask(_ptr(self.score), _ptr(self.gs.count), cap, self.k_event, _ptr(self.mask),
-                                    _ptr(self.selected), _ptr(self.ws_las), self.ws_las.numel(), _ptr(self.status),
-                                    s), "gsp_topk_mask")
+        if gated is None:
+            gated = self.gated()
+        if gated:
+            L.check(lib().gsp_topk_mask_gated(_ptr(self.score), _ptr(self.pos_grad[0]), _ptr(self.pos_grad[1]),
+                                              ctypes.c_float(self.grad_threshold), _ptr(self.gs.count), cap,
+                                              self.k_event, _ptr(self.mask), _ptr(self.selected), _ptr(self.ws_las),
+                                              self.ws_las.numel(), _ptr(self.status), s), "gsp_topk_mask_gated")
+        else:
+            L.check(lib().gsp_topk_mask(_ptr(self.score), _ptr(self.gs.count), cap, self.k_event, _ptr(self.mask),
+                                        _ptr(self.selected), _ptr(self.ws_las), self.ws_las.numel(),
+                                        _ptr(self.status), s), "gsp_topk_mask")
         L.check(lib().gsp_las_split(ctypes.byref(self.gs.struct()), _ptr(self.mask), None, 0,
                                     ctypes.byref(self.las), _ptr(self.ws_las), self.ws_las.numel(),
                                     _ptr(self.status), s), "gsp_las_split")
         self.score.zero_()
+        if self.pos_grad is not None:
+            self.pos_grad[0].zero_()
+            self.pos_grad[1].zero_()
+        if count:
+            self.events += 1
 
     def step_autograd(self):
         """One iteration through torch.autograd; the event follows every `every` iterations."""
         params = [getattr(self.gs, k) for k in GROUPS]
         for p in params:
             p.requires_grad_(True)
-        loss = GaussianRenderL1.apply(*params, self.r, self.targets, self.E, self.score)
+        loss = GaussianRenderL1.apply(*params, self.r, self.targets, self.E, self.score, self.pos_grad)
         loss.backward()
         with torch.no_grad():
             self._sgd({k: p.grad for k, p in zip(GROUPS, params)})
@@ -94,29 +127,35 @@ class DensifyLoop:
 
     # ---------------------------------------------------------- graphs
     def capture(self):
-        """CUDA graphs of one iteration and of one event (capacity-sized launches,
-        device-resident count: valid for every later state)."""
+        """CUDA graphs of one iteration and of the events (warm-up and, with a
+        gradient threshold, gated; capacity-sized launches, device-resident
+        count: valid for every later state)."""
         side = torch.cuda.Stream(device=self.device)
         side.wait_stream(torch.cuda.current_stream(self.device))
         g_it, g_ev = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        g_gated = torch.cuda.CUDAGraph() if self.pos_grad is not None else None
         with torch.cuda.stream(side):
             with torch.cuda.graph(g_it, stream=side):
                 self.iteration(stream=side)
             with torch.cuda.graph(g_ev, stream=side):
-                self.event(stream=side)
+                self.event(stream=side, gated=False, count=False)
+            if g_gated is not None:
+                with torch.cuda.graph(g_gated, stream=side):
+                    self.event(stream=side, gated=True, count=False)
         torch.cuda.current_stream(self.device).wait_stream(side)
-        self._graphs = (g_it, g_ev)
+        self._graphs = (g_it, g_ev, g_gated)
 
     def run(self, iterations: int):
         """Replay `iterations` iterations (events included) without host reads."""
         if self._graphs is None:
             self.capture()
-        g_it, g_ev = self._graphs
+        g_it, g_ev, g_gated = self._graphs
         for _ in range(iterations):
             g_it.replay()
             self.iteration_count += 1
             if self.iteration_count % self.every == 0:
-                g_ev.replay()
+                (g_gated if self.gated() else g_ev).replay()
+                self.events += 1
 
     def loss(self) -> torch.Tensor:
         return self.bufs["loss"]

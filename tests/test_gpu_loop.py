@@ -114,3 +114,51 @@ def test_graph_driver_reaches_budget_and_agrees_with_autograd(gsp_lib):
     assert int(gs_b.count.item()) == N0 + 4 * K_EVENT == CAP
     assert np.all(np.isfinite(losses))
     assert all(torch.isfinite(getattr(gs_b, k)).all() for k in GROUPS)
+
+
+def test_gated_event_after_warmup_matches_oracle(gsp_lib):
+    """Gradient-threshold masking in the loop: the first event (warm-up) selects
+    by score alone and clears the statistic; the next one selects the top-k among
+    the candidates of the statistic accumulated since, exactly as the oracle does
+    on the same score and statistic arrays.  The graph driver then replays both
+    kinds of event."""
+    import torch
+    g = synth.gaussians(N0, 3, seed=11)
+    g["log_scales"] = (g["log_scales"] + 0.8).astype(np.float32)
+    cams = [synth.camera_ring(k, V, resolutions=[(W, H)]) for k in range(V)]
+    tg = [torch.from_numpy(synth.image(H, W, 2000 + k)).cuda() for k in range(V)]
+    gs = gsp_lib.GaussianSet.from_arrays(g, capacity=CAP + 2 * K_EVENT)
+    loop = gsp_lib.DensifyLoop(gs, cams, tg, lr=LR, every=EVERY, k_event=K_EVENT, pair_capacity=1 << 22,
+                               grad_threshold=0.0, warmup_events=1)
+    for _ in range(EVERY):
+        loop.iteration()
+    assert not loop.gated()
+    loop.event()
+    torch.cuda.synchronize()
+    assert int(loop.status.item()) == 0 and loop.events == 1 and loop.gated()
+    assert int(loop.pos_grad[1].sum().item()) == 0 and float(loop.pos_grad[0].abs().sum().item()) == 0.0
+    n1 = int(gs.count.item())
+    assert n1 == N0 + K_EVENT
+    for _ in range(EVERY):
+        loop.iteration()
+    torch.cuda.synchronize()
+    sums = loop.pos_grad[0][:n1].cpu().numpy()
+    cnts = loop.pos_grad[1][:n1].cpu().numpy()
+    score = loop.score[:n1].cpu().numpy()
+    seen = cnts > 0
+    assert seen.sum() > n1 // 4
+    mean = sums[seen] / cnts[seen]
+    loop.grad_threshold = float(np.median(mean))  # about half the seen Gaussians pass
+    ref = od.gated_topk_mask(score, K_EVENT, sums, cnts, loop.grad_threshold)
+    assert 0 < ref.sum() <= K_EVENT
+    loop.event()
+    torch.cuda.synchronize()
+    assert int(loop.status.item()) == 0
+    m = loop.mask[:n1].cpu().numpy().astype(bool)
+    assert np.array_equal(m, ref)
+    assert int(gs.count.item()) == n1 + int(ref.sum()) == n1 + int(loop.selected.item())
+    # graph driver: two more events, both gated
+    loop.run(2 * EVERY)
+    torch.cuda.synchronize()
+    assert int(loop.status.item()) == 0 and loop.events == 4
+    assert int(gs.count.item()) <= CAP + 2 * K_EVENT
