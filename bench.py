@@ -429,6 +429,10 @@ def run_gsp(args, rank, world):
                                  f"{sm_max} MHz")})
     stages_roof = {st: dict(roofline(st, ms), ms=round(ms, 4)) for st, ms in breakdown.items()}
 
+    next_rows = None
+    if not args.no_extra:
+        restore(copies[0], pristine)
+        next_rows = {"gating": measure_gating(gsp, rends[0], target, E, k_split)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g, cam, tgt_np, stripes=4)
@@ -446,6 +450,7 @@ def run_gsp(args, rank, world):
         "clocks": clk.summary(), "plain": plain,
         "stages": stages_roof,
         "work_counts": {"pairs": pairs, "evaluations": evals, "composited": contrib},
+        "next_rows": next_rows,
     }
     return line
 
@@ -475,6 +480,38 @@ def _event_ms(fn, reps):
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+def measure_gating(gsp, r, target, E, k, reps=10):
+    """Gradient-threshold masking (Sec. 2.3) on the main workload: the adjoint
+    with and without the positional statistic, and the gated selection beside the
+    plain one (threshold: the median mean gradient of the Gaussians seen)."""
+    import numpy as np
+    import torch
+    dev = r.gs.means.device
+    cap = r.gs.capacity
+    score = torch.zeros(cap, device=dev)
+    psum = torch.zeros(cap, device=dev)
+    pcnt = torch.zeros(cap, dtype=torch.int32, device=dev)
+    out = r.forward(targets=[target])
+    grads = r.backward(out, targets=[target], edge=E, score=score, pos_grad=(psum, pcnt))
+    torch.cuda.synchronize()
+    s_h, c_h = psum.cpu().numpy(), pcnt.cpu().numpy()
+    seen = c_h > 0
+    tau = float(np.median(s_h[seen] / c_h[seen])) if seen.any() else 0.0
+    bwd = _event_ms(lambda: r.backward(out, targets=[target], edge=E, score=score, grads=grads), reps)
+    bwd_stat = _event_ms(lambda: r.backward(out, targets=[target], edge=E, score=score, grads=grads,
+                                            pos_grad=(psum, pcnt)), reps)
+    plain = _event_ms(lambda: gsp.topk_mask(score, r.gs.count, k), reps)
+    gated = _event_ms(lambda: gsp.topk_mask_gated(score, psum, pcnt, tau, r.gs.count, k), reps)
+    _, sel, st = gsp.topk_mask_gated(score, psum, pcnt, tau, r.gs.count, k)
+    torch.cuda.synchronize()
+    gsp.raise_on_device_status(st, "gated top-k")
+    return {"row": "gradient-threshold masking (Sec. 2.3 warm-up masking)",
+            "adjoint_ms": round(bwd, 4), "adjoint_with_statistic_ms": round(bwd_stat, 4),
+            "topk_ms": round(plain, 4), "topk_gated_ms": round(gated, 4), "k": int(k),
+            "seen": int(seen.sum()), "threshold": tau, "selected": int(sel.item()),
+            "note": "eager launches incl. host overhead; statistic fused into the adjoint's parameter pass"}
 
 
 def run_edge_batched(steps=10, warmup=3):
