@@ -84,6 +84,23 @@ def gated_topk_mask(scores: np.ndarray, k: int, sums: np.ndarray, counts: np.nda
     return mask
 
 
+def sample_mask(scores: np.ndarray, expv: np.ndarray, k: int) -> np.ndarray:
+    """Importance sampling by edge score (Sec. 1, "Edge-Score importance
+    sampling"): k Gaussians drawn without replacement with probabilities
+    proportional to their scores, by exponential clocks: Gaussian i rings at
+    expv[i] / scores[i] (expv: independent Exp(1) variates, an input), the k
+    earliest are taken (ties toward the lower index); scores <= 0 never ring.
+    The ringing times are FP32 quotients, the precision of the kernel."""
+    s = np.asarray(scores, dtype=np.float32)
+    e = np.asarray(expv, dtype=np.float32)
+    live = np.nonzero(s > 0)[0]
+    t = e[live] / s[live]  # float32 / float32: one IEEE division
+    sub = topk_mask(-t, k)
+    mask = np.zeros(s.shape[0], dtype=bool)
+    mask[live[sub]] = True
+    return mask
+
+
 def quat_rot(q: np.ndarray) -> np.ndarray:
     q = q / np.linalg.norm(q)
     w, x, y, z = q

@@ -145,3 +145,38 @@ def test_gated_topk_invariants_and_brute_force():
         assert m.sum() == min(k, len(cand))
     # a Gaussian never seen (count 0) is never a candidate, even at tau = 0
     assert not od.gated_topk_mask(np.ones(3, np.float32), 3, np.zeros(3), np.zeros(3, int), 0.0).any()
+
+
+def test_sampling_first_draw_follows_the_scores():
+    """Exponential clocks: the first Gaussian to ring is i with probability
+    s_i / sum(s) (the minimum of independent Exp(s_i) clocks); 40,000 draws
+    against the exact probabilities (chi-square, 5 degrees of freedom)."""
+    s = np.array([0.5, 1.0, 2.0, 0.25, 4.0, 0.25], dtype=np.float32)
+    p = s / s.sum()
+    rng = np.random.default_rng(8)
+    draws = 40000
+    hits = np.zeros(6)
+    for _ in range(draws // 2000):
+        e = rng.exponential(size=(2000, 6)).astype(np.float32)
+        for row in e:
+            hits[np.nonzero(od.sample_mask(s, row, 1))[0][0]] += 1
+    chi2 = np.sum((hits - draws * p) ** 2 / (draws * p))
+    assert chi2 < 20.5  # 99.9 % quantile of chi-square with 5 dof
+
+
+def test_sampling_limits_and_equal_scores():
+    rng = np.random.default_rng(9)
+    e = rng.exponential(size=500).astype(np.float32)
+    s = rng.uniform(0, 2, 500).astype(np.float32)
+    s[::7] = 0.0
+    s[::11] = -1.0
+    m = od.sample_mask(s, e, 10 ** 6)  # k beyond the positive scores: all of them
+    assert np.array_equal(m, s > 0)
+    assert not od.sample_mask(s, e, 0).any()
+    # equal scores: uniform sampling, the k smallest variates
+    eq = np.full(500, 3.0, np.float32)
+    m = od.sample_mask(eq, e, 37)
+    assert set(np.nonzero(m)[0]) == set(np.argsort(e, kind="stable")[:37])
+    # the first draw of a sample of k is also a sample of 1; larger k nests
+    for k in (1, 5, 50):
+        assert np.all(od.sample_mask(s, e, k) <= od.sample_mask(s, e, k + 20))
