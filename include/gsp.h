@@ -285,6 +285,19 @@ gsp_status gsp_topk_mask_gated(const float *scores, const float *pos_grad_sum, c
                                size_t workspace_bytes, int32_t *dev_status, gsp_stream_t stream);
 
 /*
+ * Importance sampling by edge score (Sec. 1, "Edge-Score importance sampling"): k
+ * Gaussians drawn without replacement with probabilities proportional to scores[i],
+ * by exponential clocks.  Gaussian i < N with scores[i] > 0 rings at
+ * exp_variates[i] / scores[i] (one FP32 division); mask_out selects the min(k, number
+ * of positive scores) earliest, ties in ascending index order.  exp_variates: device
+ * float [capacity] of independent Exp(1) draws supplied by the caller (fresh ones for
+ * each draw).  Workspace and errors as for gsp_topk_mask.
+ */
+gsp_status gsp_sample_mask(const float *scores, const float *exp_variates, const int32_t *count,
+                           int64_t capacity, int64_t k, uint8_t *mask_out, int32_t *selected_out,
+                           void *workspace, size_t workspace_bytes, int32_t *dev_status, gsp_stream_t stream);
+
+/*
  * Allocation-free variant of gsp_topk_mask (the paper has no counterpart).
  *
  * For callers that cannot allocate device memory when they call: code being

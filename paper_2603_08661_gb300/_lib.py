@@ -74,6 +74,7 @@ SIGNATURES = {
     "gsp_las_workspace_size": (c_sz, [c_i64]),
     "gsp_topk_mask": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
     "gsp_topk_mask_gated": (c_i32, [c_vp, c_vp, c_vp, c_f32, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
+    "gsp_sample_mask": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
     "gsp_las_split": (c_i32, [P(Gaussians), c_vp, c_vp, c_i64, P(LasParams), c_vp, c_sz, c_vp, c_vp]),
     "gsp_topk_mask_static": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),
     "gsp_sgd_step": (c_i32, [P(Gaussians), c_vp, c_vp, c_vp, c_vp, c_vp, c_f32, c_vp]),

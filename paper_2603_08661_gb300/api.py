@@ -295,6 +295,21 @@ def topk_mask_gated(scores: torch.Tensor, pos_grad_sum: torch.Tensor, pos_grad_c
     return mask, sel, st
 
 
+def sample_mask(scores: torch.Tensor, exp_variates: torch.Tensor, count: torch.Tensor, k: int, status=None,
+                stream=None):
+    """Importance sampling of k Gaussians by edge score (gsp_sample_mask);
+    exp_variates: Exp(1) draws, one per row (e.g. torch.empty_like(scores).exponential_())."""
+    cap = int(scores.shape[0])
+    need = lib().gsp_las_workspace_size(cap)
+    ws = _workspace(need, scores.device)
+    mask = torch.empty(cap, dtype=torch.uint8, device=scores.device)
+    sel = torch.zeros(1, dtype=torch.int32, device=scores.device)
+    st = status if status is not None else new_status(scores.device)
+    L.check(lib().gsp_sample_mask(_ptr(scores), _ptr(exp_variates), _ptr(count), cap, int(k), _ptr(mask), _ptr(sel),
+                                  _ptr(ws), need, _ptr(st), _stream_handle(stream)), "gsp_sample_mask")
+    return mask, sel, st
+
+
 def launch_count() -> int:
     """Kernels and memsets the library has enqueued in this process."""
     return int(lib().gsp_kernel_launch_count())

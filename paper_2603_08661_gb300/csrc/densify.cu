@@ -114,13 +114,24 @@ struct TopkArgs {
     const int32_t *gcnt;
     float tau;
     unsigned *ncand;  // candidate count (zeroed before the launch)
+    // importance sampling (expv != nullptr): Gaussian i with score > 0 rings at
+    // expv[i] / score[i] (Exp(1) variates given by the caller); the k earliest
+    // are taken, i.e. the k largest keys -expv[i] / score[i]
+    const float *expv;
 };
 
 __device__ __forceinline__ bool is_candidate(const TopkArgs &a, long long i)
 {
+    if (a.expv && !(a.scores[i] > 0.f)) return false;
     if (!a.gsum) return true;
     const int32_t c = a.gcnt[i];
     return c > 0 && __fdiv_rn(a.gsum[i], float(c)) >= a.tau;
+}
+
+// The value whose k largest are selected (for a candidate).
+__device__ __forceinline__ float select_value(const TopkArgs &a, long long i)
+{
+    return a.expv ? -__fdiv_rn(a.expv[i], a.scores[i]) : a.scores[i];
 }
 
 // Block-wide pick of the digit that holds the rem-th largest key, from the
@@ -192,18 +203,18 @@ __global__ void __launch_bounds__(kThreads) topk_fused(TopkArgs a)
             for (long long i = blockIdx.x * (long long)kThreads + tid; i < n; i += (long long)G * kThreads) {
                 if (!is_candidate(a, i)) continue;
                 ++nc;
-                const unsigned key = order_key(a.scores[i]);
+                const unsigned key = order_key(select_value(a, i));
                 if (pass > 0 && (key >> hi) != (prefix >> hi)) continue;
                 atomicAdd(&h[(key >> shift) & unsigned(nb - 1)], 1u);
             }
             nc = __reduce_add_sync(0xffffffffu, nc);
-            if (pass == 0 && a.gsum && (tid & 31) == 0 && nc) atomicAdd(a.ncand, nc);
+            if (pass == 0 && (a.gsum || a.expv) && (tid & 31) == 0 && nc) atomicAdd(a.ncand, nc);
             __syncthreads();
             for (int i = tid; i < nb; i += kThreads)
                 if (h[i]) atomicAdd(gh + i, h[i]);
         }
         if (!grid_barrier(a.bar, G, kDefaultSpinLimit, a.status)) return;
-        if (pass == 0 && a.gsum) {  // at most the candidates (the same in every block)
+        if (pass == 0 && (a.gsum || a.expv)) {  // at most the candidates (the same in every block)
             kk = min(kk, __ldcg(a.ncand));
             remaining = kk;
         }
@@ -224,7 +235,7 @@ __global__ void __launch_bounds__(kThreads) topk_fused(TopkArgs a)
     if (rank_ties) {
         unsigned c = 0;
         for (long long i = b0 + tid; i < min(b1, n); i += kThreads)
-            c += order_key(a.scores[i]) == prefix && is_candidate(a, i);
+            c += is_candidate(a, i) && order_key(select_value(a, i)) == prefix;
         unsigned ex;
         const unsigned tot = block_scan(c, &ex);
         if (tid == 0) a.sums[blockIdx.x] = tot;
@@ -240,7 +251,7 @@ __global__ void __launch_bounds__(kThreads) topk_fused(TopkArgs a)
 #pragma unroll
         for (int j = 0; j < kPerThread; ++j) {
             const long long i = r0 + tid * kPerThread + j;
-            const unsigned key = (i < b1 && i < n) ? order_key(a.scores[i]) : 0u;
+            const unsigned key = (i < b1 && i < n) ? order_key(select_value(a, i)) : 0u;
             const bool live = i < b1 && i < n && kk > 0 && is_candidate(a, i);
             tie[j] = live && key == prefix;
             gt[j] = live && key > prefix;
@@ -402,7 +413,8 @@ DensifyLayout densify_layout(void *ws, long long cap)
 
 gsp_status enqueue_topk(const float *scores, const int32_t *count, long long cap, long long k, uint8_t *mask,
                         int32_t *selected_out, const DensifyLayout &L, int32_t *status, cudaStream_t s,
-                        const float *gsum = nullptr, const int32_t *gcnt = nullptr, float tau = 0.f)
+                        const float *gsum = nullptr, const int32_t *gcnt = nullptr, float tau = 0.f,
+                        const float *expv = nullptr)
 {
     // co-resident blocks (grid barriers), at most two per SM and one per
     // kBlockItems of capacity (the block sums are sized so)
@@ -413,7 +425,8 @@ gsp_status enqueue_topk(const float *scores, const int32_t *count, long long cap
     }
     long long grid = (long long)std::min(per_sm, 2) * num_sms();
     grid = std::max(1LL, std::min(grid, (long long)div_up(cap, kBlockItems)));
-    TopkArgs a{scores, count, cap, k, mask, selected_out, L.hist, L.sums, L.bar, status, gsum, gcnt, tau, L.ncand};
+    TopkArgs a{scores, count, cap, k, mask, selected_out, L.hist, L.sums, L.bar, status, gsum, gcnt, tau, L.ncand,
+               expv};
     stage_begin("topk", s);
     GSP_CUDA_TRY(cudaMemsetAsync(L.hist, 0, kTopkZeroWords * sizeof(unsigned), s));
     cudaLaunchConfig_t cfg{};
@@ -479,6 +492,21 @@ extern "C" gsp_status gsp_topk_mask_gated(const float *scores, const float *pos_
     L = densify_layout(ws, capacity);
     return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L, dev_status,
                         reinterpret_cast<cudaStream_t>(stream), pos_grad_sum, pos_grad_count, threshold);
+}
+
+extern "C" gsp_status gsp_sample_mask(const float *scores, const float *exp_variates, const int32_t *count,
+                                      int64_t capacity, int64_t k, uint8_t *mask_out, int32_t *selected_out,
+                                      void *ws, size_t ws_bytes, int32_t *dev_status, gsp_stream_t stream)
+{
+    if (!scores || !exp_variates || !count || !mask_out || !dev_status || capacity < 1 ||
+        capacity > (1LL << 30))
+        return GSP_ERR_INVALID_ARG;
+    DensifyLayout L = densify_layout(nullptr, capacity);
+    gsp_status st = check_workspace(ws, ws_bytes, L.bytes);
+    if (st != GSP_OK) return st;
+    L = densify_layout(ws, capacity);
+    return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L, dev_status,
+                        reinterpret_cast<cudaStream_t>(stream), nullptr, nullptr, 0.f, exp_variates);
 }
 
 extern "C" gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask, const float *scores, int64_t k,

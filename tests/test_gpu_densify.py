@@ -174,3 +174,29 @@ def test_gated_topk_limits(gsp_lib):
     assert torch.equal(mask, plain)
     with pytest.raises(Exception):
         gsp_lib.topk_mask_gated(t(s), t(sums), t(cnt), float("nan"), n_t, 500)
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (50, 10), (5000, 700), (5000, 9000), (1000000, 100000)])
+def test_importance_sampling_matches_oracle(gsp_lib, n, k):
+    """Exponential-clock sampling by score: bit-exact masks for the same scores and
+    Exp(1) variates (ringing times are one FP32 division on both sides), with
+    non-positive scores, equal scores and repeated variates (tied times)."""
+    import torch
+    rng = np.random.default_rng(n * 7 + k)
+    s = rng.gamma(1.5, 1.0, n).astype(np.float32)
+    s[rng.integers(0, n, max(n // 20, 1))] = 0.0
+    s[rng.integers(0, n, max(n // 50, 1))] = -1.0
+    s[rng.integers(0, n, max(n // 10, 1))] = np.float32(2.0)
+    e = rng.exponential(size=n).astype(np.float32)
+    e[rng.integers(0, n, max(n // 10, 1))] = np.float32(0.5)
+    cap = n + 2
+    pad = lambda a: torch.from_numpy(np.concatenate([a, np.ones(2, np.float32)])).cuda()
+    cnt = torch.tensor([n], dtype=torch.int32, device="cuda")
+    mask, sel, st = gsp_lib.sample_mask(pad(s), pad(e), cnt, k)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    m = mask.cpu().numpy().astype(bool)
+    ref = od.sample_mask(s, e, k)
+    assert not m[n:].any()
+    assert np.array_equal(m[:n], ref)
+    assert int(sel.item()) == int(ref.sum()) == min(k, int((s > 0).sum()))
