@@ -507,10 +507,13 @@ def measure_gating(gsp, r, target, E, k, reps=10):
     _, sel, st = gsp.topk_mask_gated(score, psum, pcnt, tau, r.gs.count, k)
     torch.cuda.synchronize()
     gsp.raise_on_device_status(st, "gated top-k")
+    expv = torch.empty(cap, device=dev).exponential_()  # the sampling's Exp(1) inputs
+    sample = _event_ms(lambda: gsp.sample_mask(score, expv, r.gs.count, k), reps)
     return {"row": "gradient-threshold masking (Sec. 2.3 warm-up masking)",
             "adjoint_ms": round(bwd, 4), "adjoint_with_statistic_ms": round(bwd_stat, 4),
             "topk_ms": round(plain, 4), "topk_gated_ms": round(gated, 4), "k": int(k),
             "seen": int(seen.sum()), "threshold": tau, "selected": int(sel.item()),
+            "sampling_ms": round(sample, 4),
             "note": "eager launches incl. host overhead; statistic fused into the adjoint's parameter pass"}
 
 

@@ -4,7 +4,9 @@ One iteration: splatting forward over the fixed views with the L1 loss, the
 adjoint with the edge score (Sec. 1, "Edge-Score importance") accumulated in
 the same pass, and a plain SGD step on every parameter.  Every `every`
 iterations a densification event takes the top-k Gaussians by accumulated
-edge score, splits them with the Long-Axis-Split (Sec. 2.2, Alg. 1-2) into
+edge score (or samples k with probabilities proportional to it, selection =
+"sample"), splits them with the Long-Axis-Split (Sec. 2.2, Alg. 1-2; the
+paper's preset by default) into
 the free capacity rows, and clears the scores.  The edge maps of the fixed
 target views (Sec. 2.1) are computed once, in one fused launch.
 
@@ -29,7 +31,7 @@ import ctypes
 import torch
 
 from . import _lib as L
-from .api import LAS_CONFIG, Renderer, _ptr, _stream_handle, edge_map, las_params, lib, new_status
+from .api import LAS_PAPER, Renderer, _ptr, _stream_handle, edge_map, las_params, lib, new_status
 from .autograd import GaussianRenderL1
 
 GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
@@ -37,8 +39,13 @@ GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 
 class DensifyLoop:
     def __init__(self, gs, cams, targets, lr: float = 1e-3, every: int = 20, k_event: int = 50_000,
-                 las: dict = LAS_CONFIG, pair_capacity: int = 1 << 26, variants=(0, 0), device="cuda",
-                 grad_threshold: float | None = None, warmup_events: int = 3):
+                 las: dict = LAS_PAPER, pair_capacity: int = 1 << 26, variants=(0, 0), device="cuda",
+                 grad_threshold: float | None = None, warmup_events: int = 3, selection: str = "topk"):
+        if selection not in ("topk", "sample"):
+            raise ValueError("selection: 'topk' or 'sample'")
+        if selection == "sample" and grad_threshold is not None:
+            raise ValueError("the gradient threshold gates the top-k selection only")
+        self.selection = selection
         self.gs, self.lr, self.every, self.k_event = gs, float(lr), int(every), int(k_event)
         self.grad_threshold = None if grad_threshold is None else float(grad_threshold)
         self.warmup_events = int(warmup_events)
@@ -50,6 +57,7 @@ class DensifyLoop:
         self.r = Renderer(gs, cams, pair_capacity, device=device, variants=variants)
         cap = gs.capacity
         self.score = torch.zeros(cap, device=device)
+        self.expv = torch.empty(cap, device=device) if selection == "sample" else None
         self.pos_grad = None
         if self.grad_threshold is not None:
             self.pos_grad = (torch.zeros(cap, device=device), torch.zeros(cap, dtype=torch.int32, device=device))
@@ -89,7 +97,15 @@ class DensifyLoop:
         s = _stream_handle(stream)
         if gated is None:
             gated = self.gated()
-        if gated:
+        if self.selection == "sample":
+            # fresh Exp(1) variates (inputs of the sampling), drawn on the stream
+            with torch.cuda.stream(stream) if stream is not None else torch.cuda.stream(
+                    torch.cuda.current_stream(self.device)):
+                self.expv.exponential_()
+            L.check(lib().gsp_sample_mask(_ptr(self.score), _ptr(self.expv), _ptr(self.gs.count), cap, self.k_event,
+                                          _ptr(self.mask), _ptr(self.selected), _ptr(self.ws_las),
+                                          self.ws_las.numel(), _ptr(self.status), s), "gsp_sample_mask")
+        elif gated:
             L.check(lib().gsp_topk_mask_gated(_ptr(self.score), _ptr(self.pos_grad[0]), _ptr(self.pos_grad[1]),
                                               ctypes.c_float(self.grad_threshold), _ptr(self.gs.count), cap,
                                               self.k_event, _ptr(self.mask), _ptr(self.selected), _ptr(self.ws_las),

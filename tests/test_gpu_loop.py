@@ -33,7 +33,7 @@ def _make(gsp):
     tg = [synth.image(H, W, 2000 + k) for k in range(V)]
     gs = gsp.GaussianSet.from_arrays(g, capacity=CAP)
     loop = gsp.DensifyLoop(gs, cams, [torch.from_numpy(t).cuda() for t in tg], lr=LR, every=EVERY,
-                           k_event=K_EVENT, pair_capacity=1 << 22)
+                           k_event=K_EVENT, pair_capacity=1 << 22, las=gsp.LAS_CONFIG)
     return g, cams, tg, gs, loop
 
 
@@ -162,3 +162,37 @@ def test_gated_event_after_warmup_matches_oracle(gsp_lib):
     torch.cuda.synchronize()
     assert int(loop.status.item()) == 0 and loop.events == 4
     assert int(gs.count.item()) <= CAP + 2 * K_EVENT
+
+
+def test_sampling_event_matches_oracle_and_paper_preset_is_default(gsp_lib):
+    """selection = "sample": the event draws fresh Exp(1) variates and samples k
+    Gaussians by score; the mask equals the oracle's exponential-clock sample for
+    the same scores and variates, and the split uses the paper's LAS preset."""
+    import torch
+    g = synth.gaussians(N0, 3, seed=11)
+    g["log_scales"] = (g["log_scales"] + 0.8).astype(np.float32)
+    cams = [synth.camera_ring(k, V, resolutions=[(W, H)]) for k in range(V)]
+    tg = [torch.from_numpy(synth.image(H, W, 2000 + k)).cuda() for k in range(V)]
+    gs = gsp_lib.GaussianSet.from_arrays(g, capacity=CAP)
+    loop = gsp_lib.DensifyLoop(gs, cams, tg, lr=LR, every=EVERY, k_event=K_EVENT, pair_capacity=1 << 22,
+                               selection="sample")
+    for _ in range(EVERY):
+        loop.iteration()
+    torch.cuda.synchronize()
+    score = loop.score[:N0].cpu().numpy()
+    before = _host(gs, N0)
+    before["sh_degree"] = 3
+    loop.event()
+    torch.cuda.synchronize()
+    assert int(loop.status.item()) == 0
+    ref = od.sample_mask(score, loop.expv[:N0].cpu().numpy(), K_EVENT)
+    m = loop.mask[:N0].cpu().numpy().astype(bool)
+    assert np.array_equal(m, ref) and ref.sum() == min(K_EVENT, int((score > 0).sum()))
+    n1 = int(gs.count.item())
+    assert n1 == N0 + int(ref.sum())
+    p32 = {k: float(np.float32(v)) for k, v in od.PAPER_PRESET.items()}
+    split = od.las_split(before, ref, **p32)
+    after = _host(gs, n1)
+    for k in ("means", "log_scales", "opacity_logits"):
+        a, b = after[k].reshape(n1, -1), split[k].reshape(n1, -1)
+        assert (np.abs(a - b) / np.maximum(1.0, np.abs(b))).max() <= 1e-6, k
