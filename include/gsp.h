@@ -356,6 +356,30 @@ gsp_status gsp_sgd_step(const gsp_gaussians *g, float *grad_means, float *grad_l
                         float *grad_quats, float *grad_opacity_logits, float *grad_sh, float lr,
                         gsp_stream_t stream);
 
+/*
+ * Learning-rate schedule of the refinement (Sec. 2.3): per parameter group
+ * (0 means, 1 log_scales, 2 quats, 3 opacity_logits, 4 sh) an exponential decay
+ * lr(t) = lr_init * (lr_final / lr_init)^(min(t, steps) / steps); a group with
+ * lr_init == lr_final keeps that rate.  The paper's values: log_scales 0.020 -> 0.002
+ * ("Exponential Scale Scheduling", gamma = 0.1), means 1.28e-4 -> 1.28e-5
+ * ("Positional Learning Rate Optimization"); the horizon `steps` is not stated.
+ */
+typedef struct gsp_lr_schedule {
+    float lr_init[5];
+    float lr_final[5];
+    int32_t steps; /* >= 1 */
+} gsp_lr_schedule;
+
+/*
+ * gsp_sgd_step with each group's rate taken from sched at t = *step (device int32),
+ * computed on the device (FP32 expf / logf), then *step += 1: the same enqueued
+ * step (e.g. a CUDA-graph replay) follows the schedule.  Both rates of a decaying
+ * group must be > 0.  Two launches.
+ */
+gsp_status gsp_sgd_step_scheduled(const gsp_gaussians *g, float *grad_means, float *grad_log_scales,
+                                  float *grad_quats, float *grad_opacity_logits, float *grad_sh,
+                                  const gsp_lr_schedule *sched, int32_t *step, gsp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

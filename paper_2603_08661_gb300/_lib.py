@@ -46,6 +46,10 @@ class RenderOpts(ctypes.Structure):
                 ("pos_grad_sum", ctypes.c_void_p), ("pos_grad_count", ctypes.c_void_p)]
 
 
+class LrSchedule(ctypes.Structure):
+    _fields_ = [("lr_init", c_f32 * 5), ("lr_final", c_f32 * 5), ("steps", c_i32)]
+
+
 class LasParams(ctypes.Structure):
     _fields_ = [("k_off", c_f32), ("long_factor", c_f32), ("other_factor", c_f32), ("beta", c_f32)]
 
@@ -78,6 +82,7 @@ SIGNATURES = {
     "gsp_las_split": (c_i32, [P(Gaussians), c_vp, c_vp, c_i64, P(LasParams), c_vp, c_sz, c_vp, c_vp]),
     "gsp_topk_mask_static": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),
     "gsp_sgd_step": (c_i32, [P(Gaussians), c_vp, c_vp, c_vp, c_vp, c_vp, c_f32, c_vp]),
+    "gsp_sgd_step_scheduled": (c_i32, [P(Gaussians), c_vp, c_vp, c_vp, c_vp, c_vp, P(LrSchedule), c_vp, c_vp]),
 }
 
 _lib = None

@@ -180,3 +180,17 @@ def test_sampling_limits_and_equal_scores():
     # the first draw of a sample of k is also a sample of 1; larger k nests
     for k in (1, 5, 50):
         assert np.all(od.sample_mask(s, e, k) <= od.sample_mask(s, e, k + 20))
+
+
+def test_learning_rate_schedule_worked_values():
+    from oracle import optim as oo
+    l0, l1 = oo.PAPER_SCHEDULE["log_scales"]
+    assert oo.lr_at(l0, l1, 30000, 0) == 0.020
+    assert abs(oo.lr_at(l0, l1, 30000, 30000) - 0.002) < 1e-18
+    assert abs(oo.lr_at(l0, l1, 30000, 10 ** 6) - 0.002) < 1e-18  # held after the horizon
+    # half way: geometric mean of the ends (0.020 x 0.1^0.5)
+    assert abs(oo.lr_at(l0, l1, 30000, 15000) - math.sqrt(0.020 * 0.002)) < 1e-15
+    # constant ratio between consecutive steps: (final / init)^(1 / steps)
+    r = [oo.lr_at(1.28e-4, 1.28e-5, 100, t + 1) / oo.lr_at(1.28e-4, 1.28e-5, 100, t) for t in range(100)]
+    np.testing.assert_allclose(r, 0.1 ** 0.01, rtol=1e-12)
+    assert oo.lr_at(0.5, 0.5, 10, 7) == 0.5
