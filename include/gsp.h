@@ -298,6 +298,27 @@ gsp_status gsp_sample_mask(const float *scores, const float *exp_variates, const
                            void *workspace, size_t workspace_bytes, int32_t *dev_status, gsp_stream_t stream);
 
 /*
+ * One selection entry for the densification schedule: top-k (exp_variates NULL) or
+ * importance sampling (exp_variates given), optionally gated by the gradient threshold
+ * (top-k only), and capped by a Gaussian budget (Conclusion: the 1M-budget variant, and
+ * a 3M pre-allocated capacity):
+ * with budget > 0 at most max(budget - N, 0) Gaussians are selected, so that the
+ * split keeps N <= budget.  The selections are those of gsp_topk_mask,
+ * gsp_topk_mask_gated and gsp_sample_mask with k reduced accordingly.
+ */
+typedef struct gsp_select_opts {
+    const float *pos_grad_sum;     /* gating: device float [capacity], or NULL */
+    const int32_t *pos_grad_count; /* gating: device int32 [capacity], or NULL (with pos_grad_sum) */
+    float threshold;               /* gating threshold (not NaN) */
+    const float *exp_variates;     /* sampling: device Exp(1) draws [capacity], or NULL for top-k */
+    int64_t budget;                /* 0: none */
+} gsp_select_opts;
+
+gsp_status gsp_select_mask(const float *scores, const int32_t *count, int64_t capacity, int64_t k,
+                           const gsp_select_opts *opts, uint8_t *mask_out, int32_t *selected_out,
+                           void *workspace, size_t workspace_bytes, int32_t *dev_status, gsp_stream_t stream);
+
+/*
  * Allocation-free variant of gsp_topk_mask (the paper has no counterpart).
  *
  * For callers that cannot allocate device memory when they call: code being

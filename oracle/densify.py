@@ -101,6 +101,13 @@ def sample_mask(scores: np.ndarray, expv: np.ndarray, k: int) -> np.ndarray:
     return mask
 
 
+def budgeted_k(k: int, n: int, budget: int) -> int:
+    """Selections allowed under a Gaussian budget (Conclusion: 1M-budget variant):
+    the split adds one Gaussian per selection, so at most budget - n (budget 0:
+    no budget)."""
+    return int(k) if budget <= 0 else max(0, min(int(k), int(budget) - int(n)))
+
+
 def quat_rot(q: np.ndarray) -> np.ndarray:
     q = q / np.linalg.norm(q)
     w, x, y, z = q

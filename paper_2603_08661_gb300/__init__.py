@@ -18,7 +18,7 @@ _lib.load()
 
 from .api import (LAS_CONFIG, LAS_PAPER, GaussianSet, Renderer, StageTimer, camera_struct,  # noqa: E402,F401
                   edge_map, image_desc, las_split, launch_count, new_status, pitched_image,
-                  raise_on_device_status, sample_mask, topk_mask, topk_mask_gated)
+                  raise_on_device_status, sample_mask, select_mask, topk_mask, topk_mask_gated)
 from .autograd import GaussianRenderL1  # noqa: E402,F401
 from . import autotune  # noqa: E402,F401
 from .loop import DensifyLoop  # noqa: E402,F401

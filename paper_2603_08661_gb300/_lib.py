@@ -50,6 +50,11 @@ class LrSchedule(ctypes.Structure):
     _fields_ = [("lr_init", c_f32 * 5), ("lr_final", c_f32 * 5), ("steps", c_i32)]
 
 
+class SelectOpts(ctypes.Structure):
+    _fields_ = [("pos_grad_sum", c_vp), ("pos_grad_count", c_vp), ("threshold", c_f32), ("exp_variates", c_vp),
+                ("budget", c_i64)]
+
+
 class LasParams(ctypes.Structure):
     _fields_ = [("k_off", c_f32), ("long_factor", c_f32), ("other_factor", c_f32), ("beta", c_f32)]
 
@@ -79,6 +84,7 @@ SIGNATURES = {
     "gsp_topk_mask": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
     "gsp_topk_mask_gated": (c_i32, [c_vp, c_vp, c_vp, c_f32, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
     "gsp_sample_mask": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
+    "gsp_select_mask": (c_i32, [c_vp, c_vp, c_i64, c_i64, P(SelectOpts), c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
     "gsp_las_split": (c_i32, [P(Gaussians), c_vp, c_vp, c_i64, P(LasParams), c_vp, c_sz, c_vp, c_vp]),
     "gsp_topk_mask_static": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),
     "gsp_sgd_step": (c_i32, [P(Gaussians), c_vp, c_vp, c_vp, c_vp, c_vp, c_f32, c_vp]),

@@ -118,6 +118,7 @@ struct TopkArgs {
     // expv[i] / score[i] (Exp(1) variates given by the caller); the k earliest
     // are taken, i.e. the k largest keys -expv[i] / score[i]
     const float *expv;
+    long long budget;  // > 0: at most budget - N selected (the room left under a Gaussian budget)
 };
 
 __device__ __forceinline__ bool is_candidate(const TopkArgs &a, long long i)
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(kThreads) topk_fused(TopkArgs a)
     const unsigned G = gridDim.x;
     const long long n = max(*a.count, 0);
     unsigned kk = a.k < 0 ? 0u : (a.k > n ? unsigned(n) : unsigned(a.k));
+    if (a.budget > 0) kk = unsigned(min((long long)kk, max(a.budget - n, 0LL)));
     // the same prefix / remaining in every block
     unsigned prefix = 0, remaining = kk, eq = 0;
     const int shifts[3] = {21, 10, 0}, bits[3] = {11, 11, 10};
@@ -414,7 +416,7 @@ DensifyLayout densify_layout(void *ws, long long cap)
 gsp_status enqueue_topk(const float *scores, const int32_t *count, long long cap, long long k, uint8_t *mask,
                         int32_t *selected_out, const DensifyLayout &L, int32_t *status, cudaStream_t s,
                         const float *gsum = nullptr, const int32_t *gcnt = nullptr, float tau = 0.f,
-                        const float *expv = nullptr)
+                        const float *expv = nullptr, long long budget = 0)
 {
     // co-resident blocks (grid barriers), at most two per SM and one per
     // kBlockItems of capacity (the block sums are sized so)
@@ -426,7 +428,7 @@ gsp_status enqueue_topk(const float *scores, const int32_t *count, long long cap
     long long grid = (long long)std::min(per_sm, 2) * num_sms();
     grid = std::max(1LL, std::min(grid, (long long)div_up(cap, kBlockItems)));
     TopkArgs a{scores, count, cap, k, mask, selected_out, L.hist, L.sums, L.bar, status, gsum, gcnt, tau, L.ncand,
-               expv};
+               expv, budget};
     stage_begin("topk", s);
     GSP_CUDA_TRY(cudaMemsetAsync(L.hist, 0, kTopkZeroWords * sizeof(unsigned), s));
     cudaLaunchConfig_t cfg{};
@@ -507,6 +509,24 @@ extern "C" gsp_status gsp_sample_mask(const float *scores, const float *exp_vari
     L = densify_layout(ws, capacity);
     return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L, dev_status,
                         reinterpret_cast<cudaStream_t>(stream), nullptr, nullptr, 0.f, exp_variates);
+}
+
+extern "C" gsp_status gsp_select_mask(const float *scores, const int32_t *count, int64_t capacity, int64_t k,
+                                      const gsp_select_opts *opts, uint8_t *mask_out, int32_t *selected_out,
+                                      void *ws, size_t ws_bytes, int32_t *dev_status, gsp_stream_t stream)
+{
+    if (!scores || !count || !mask_out || !dev_status || !opts || capacity < 1 || capacity > (1LL << 30))
+        return GSP_ERR_INVALID_ARG;
+    if (!opts->pos_grad_sum != !opts->pos_grad_count || opts->threshold != opts->threshold || opts->budget < 0)
+        return GSP_ERR_INVALID_ARG;
+    if (opts->pos_grad_sum && opts->exp_variates) return GSP_ERR_INVALID_ARG;  // gating is for the top-k
+    DensifyLayout L = densify_layout(nullptr, capacity);
+    gsp_status st = check_workspace(ws, ws_bytes, L.bytes);
+    if (st != GSP_OK) return st;
+    L = densify_layout(ws, capacity);
+    return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L, dev_status,
+                        reinterpret_cast<cudaStream_t>(stream), opts->pos_grad_sum, opts->pos_grad_count,
+                        opts->threshold, opts->exp_variates, opts->budget);
 }
 
 extern "C" gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask, const float *scores, int64_t k,

@@ -40,7 +40,14 @@ GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 class DensifyLoop:
     def __init__(self, gs, cams, targets, lr: float = 1e-3, every: int = 20, k_event: int = 50_000,
                  las: dict = LAS_PAPER, pair_capacity: int = 1 << 26, variants=(0, 0), device="cuda",
-                 grad_threshold: float | None = None, warmup_events: int = 3, selection: str = "topk"):
+                 grad_threshold: float | None = None, warmup_events: int = 3, selection: str = "topk",
+                 schedule: dict | None = None, densify_from: int = 0, densify_until: int | None = None,
+                 budget: int = 0):
+        """schedule: {"steps": T, group: (lr_init, lr_final), ...} exponential
+        learning-rate decay per group on the device (Sec. 2.3; groups not named
+        keep lr); densify_from / densify_until: the iterations between which the
+        events run (the paper: every 500 in [500, 15000]); budget: Gaussians
+        never exceed it (the split count is capped on the device)."""
         if selection not in ("topk", "sample"):
             raise ValueError("selection: 'topk' or 'sample'")
         if selection == "sample" and grad_threshold is not None:
@@ -70,13 +77,30 @@ class DensifyLoop:
         self.selected = torch.zeros(1, dtype=torch.int32, device=device)
         self.ws_las = torch.empty(max(int(lib().gsp_las_workspace_size(cap)), 1), dtype=torch.uint8, device=device)
         self.las = las_params(las)
+        self.densify_from, self.densify_until, self.budget = int(densify_from), densify_until, int(budget)
+        self.sched = None
+        if schedule is not None:
+            rates = [tuple(schedule.get(k, (self.lr, self.lr))) for k in GROUPS]
+            self.sched = L.LrSchedule((L.c_f32 * 5)(*[r[0] for r in rates]), (L.c_f32 * 5)(*[r[1] for r in rates]),
+                                      int(schedule["steps"]))
+        self.step_dev = torch.zeros(1, dtype=torch.int32, device=device)  # the schedule's step
         self.iteration_count = 0
         self._graphs = None
 
     # ---------------------------------------------------------- pieces
     def _sgd(self, grads, stream=None):
+        if self.sched is not None:
+            L.check(lib().gsp_sgd_step_scheduled(ctypes.byref(self.gs.struct()), *[_ptr(grads[k]) for k in GROUPS],
+                                                 ctypes.byref(self.sched), _ptr(self.step_dev),
+                                                 _stream_handle(stream)), "gsp_sgd_step_scheduled")
+            return
         L.check(lib().gsp_sgd_step(ctypes.byref(self.gs.struct()), *[_ptr(grads[k]) for k in GROUPS],
                                    ctypes.c_float(self.lr), _stream_handle(stream)), "gsp_sgd_step")
+
+    def event_due(self, iteration: int) -> bool:
+        """Whether an event follows iteration `iteration` (1-based)."""
+        return (iteration % self.every == 0 and iteration >= self.densify_from and
+                (self.densify_until is None or iteration <= self.densify_until))
 
     def iteration(self, stream=None):
         """Forward + L1 + adjoint with fused edge score + SGD (library calls only)."""
@@ -97,23 +121,19 @@ class DensifyLoop:
         s = _stream_handle(stream)
         if gated is None:
             gated = self.gated()
+        expv = None
         if self.selection == "sample":
             # fresh Exp(1) variates (inputs of the sampling), drawn on the stream
             with torch.cuda.stream(stream) if stream is not None else torch.cuda.stream(
                     torch.cuda.current_stream(self.device)):
                 self.expv.exponential_()
-            L.check(lib().gsp_sample_mask(_ptr(self.score), _ptr(self.expv), _ptr(self.gs.count), cap, self.k_event,
-                                          _ptr(self.mask), _ptr(self.selected), _ptr(self.ws_las),
-                                          self.ws_las.numel(), _ptr(self.status), s), "gsp_sample_mask")
-        elif gated:
-            L.check(lib().gsp_topk_mask_gated(_ptr(self.score), _ptr(self.pos_grad[0]), _ptr(self.pos_grad[1]),
-                                              ctypes.c_float(self.grad_threshold), _ptr(self.gs.count), cap,
-                                              self.k_event, _ptr(self.mask), _ptr(self.selected), _ptr(self.ws_las),
-                                              self.ws_las.numel(), _ptr(self.status), s), "gsp_topk_mask_gated")
-        else:
-            L.check(lib().gsp_topk_mask(_ptr(self.score), _ptr(self.gs.count), cap, self.k_event, _ptr(self.mask),
-                                        _ptr(self.selected), _ptr(self.ws_las), self.ws_las.numel(),
-                                        _ptr(self.status), s), "gsp_topk_mask")
+            expv = _ptr(self.expv).value
+        pg = self.pos_grad if gated else None
+        opts = L.SelectOpts(_ptr(pg[0]).value if pg else None, _ptr(pg[1]).value if pg else None,
+                            float(self.grad_threshold or 0.0), expv, self.budget)
+        L.check(lib().gsp_select_mask(_ptr(self.score), _ptr(self.gs.count), cap, self.k_event, ctypes.byref(opts),
+                                      _ptr(self.mask), _ptr(self.selected), _ptr(self.ws_las), self.ws_las.numel(),
+                                      _ptr(self.status), s), "gsp_select_mask")
         L.check(lib().gsp_las_split(ctypes.byref(self.gs.struct()), _ptr(self.mask), None, 0,
                                     ctypes.byref(self.las), _ptr(self.ws_las), self.ws_las.numel(),
                                     _ptr(self.status), s), "gsp_las_split")
@@ -137,7 +157,7 @@ class DensifyLoop:
             p.grad = None
             p.requires_grad_(False)
         self.iteration_count += 1
-        if self.iteration_count % self.every == 0:
+        if self.event_due(self.iteration_count):
             self.event()
         return loss.detach()
 
@@ -169,7 +189,7 @@ class DensifyLoop:
         for _ in range(iterations):
             g_it.replay()
             self.iteration_count += 1
-            if self.iteration_count % self.every == 0:
+            if self.event_due(self.iteration_count):
                 (g_gated if self.gated() else g_ev).replay()
                 self.events += 1
 

@@ -200,3 +200,67 @@ def test_importance_sampling_matches_oracle(gsp_lib, n, k):
     assert not m[n:].any()
     assert np.array_equal(m[:n], ref)
     assert int(sel.item()) == int(ref.sum()) == min(k, int((s > 0).sum()))
+
+
+@pytest.mark.parametrize("mode", ["topk", "gated", "sample"])
+@pytest.mark.parametrize("budget", [0, 20300, 20000, 19000])
+def test_select_mask_budget(gsp_lib, mode, budget):
+    """gsp_select_mask: the selection of each mode with k reduced to the room left
+    under the budget (at most budget - N selected; none when N >= budget)."""
+    import torch
+    n, k = 20000, 1000
+    s, sums, cnt = _gate_inputs(n, 77)
+    e = np.random.default_rng(78).exponential(size=n).astype(np.float32)
+    t = lambda a: torch.from_numpy(a).cuda()
+    n_t = torch.tensor([n], dtype=torch.int32, device="cuda")
+    kb = od.budgeted_k(k, n, budget)
+    tau = 2e-4
+    if mode == "topk":
+        mask, sel, st = gsp_lib.select_mask(t(s), n_t, k, budget=budget)
+        ref = od.topk_mask(s, kb)
+    elif mode == "gated":
+        mask, sel, st = gsp_lib.select_mask(t(s), n_t, k, pos_grad=(t(sums), t(cnt)), threshold=tau, budget=budget)
+        ref = od.gated_topk_mask(s, kb, sums, cnt, tau)
+    else:
+        mask, sel, st = gsp_lib.select_mask(t(s), n_t, k, exp_variates=t(e), budget=budget)
+        ref = od.sample_mask(s, e, kb)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert np.array_equal(mask.cpu().numpy().astype(bool), ref)
+    assert int(sel.item()) == int(ref.sum()) <= kb
+
+
+def test_scheduled_sgd_follows_the_oracle_schedule(gsp_lib):
+    """gsp_sgd_step_scheduled: every step uses each group's rate at the device step
+    (the paper's decays for means and log-scales over 4 steps, constant rates for the
+    rest), then advances the step; held at lr_final after the horizon."""
+    import ctypes
+    import torch
+    from oracle import optim as oo
+    from paper_2603_08661_gb300 import _lib as L
+    n, steps = 3000, 4
+    g = synth.gaussians(n, 3, seed=5)
+    gs = gsp_lib.GaussianSet.from_arrays(g)
+    rng = np.random.default_rng(6)
+    grads = {k: torch.from_numpy(rng.normal(size=getattr(gs, k).shape).astype(np.float32)).cuda()
+             for k in oo.GROUPS}
+    rates = {"means": oo.PAPER_SCHEDULE["means"], "log_scales": oo.PAPER_SCHEDULE["log_scales"],
+             "quats": (1e-3, 1e-3), "opacity_logits": (5e-2, 5e-2), "sh": (2.5e-3, 2.5e-3)}
+    sched = L.LrSchedule((L.c_f32 * 5)(*[rates[k][0] for k in oo.GROUPS]),
+                         (L.c_f32 * 5)(*[rates[k][1] for k in oo.GROUPS]), steps)
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for t in range(steps + 2):
+        before = {k: getattr(gs, k).cpu().numpy().astype(np.float64) for k in oo.GROUPS}
+        L.check(gsp_lib._lib.load().gsp_sgd_step_scheduled(ctypes.byref(gs.struct()),
+                                                            *[gsp_lib.api._ptr(grads[k]) for k in oo.GROUPS],
+                                                            ctypes.byref(sched), gsp_lib.api._ptr(step), None), "sgd")
+        torch.cuda.synchronize()
+        assert int(step.item()) == t + 1
+        for k in oo.GROUPS:
+            lr = oo.lr_at(rates[k][0], rates[k][1], steps, t)
+            gk = grads[k].cpu().numpy().astype(np.float64)
+            ref = before[k] - lr * gk
+            got = getattr(gs, k).cpu().numpy().astype(np.float64)
+            # FP32 rate (1e-6 relative) times the gradient, plus one rounding of theta
+            tol = 2e-6 * lr * np.abs(gk) + np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+            assert np.all(np.abs(got - ref) <= tol), (k, t)

@@ -196,3 +196,29 @@ def test_sampling_event_matches_oracle_and_paper_preset_is_default(gsp_lib):
     for k in ("means", "log_scales", "opacity_logits"):
         a, b = after[k].reshape(n1, -1), split[k].reshape(n1, -1)
         assert (np.abs(a - b) / np.maximum(1.0, np.abs(b))).max() <= 1e-6, k
+
+
+def test_schedule_window_and_budget_in_the_graph_driver(gsp_lib):
+    """The paper's refinement set-up scaled down: events every EVERY iterations only
+    inside [2 EVERY, 4 EVERY], the Gaussian count never above the budget (the last
+    event is cut to the room left), the learning rates decaying on the device (the
+    step counter advances once per iteration, graph replays included)."""
+    import torch
+    g = synth.gaussians(N0, 3, seed=11)
+    g["log_scales"] = (g["log_scales"] + 0.8).astype(np.float32)
+    cams = [synth.camera_ring(k, V, resolutions=[(W, H)]) for k in range(V)]
+    tg = [torch.from_numpy(synth.image(H, W, 2000 + k)).cuda() for k in range(V)]
+    budget = N0 + 2 * K_EVENT + 123
+    gs = gsp_lib.GaussianSet.from_arrays(g, capacity=CAP)
+    sched = {"steps": 30, "means": (1.28e-4, 1.28e-5), "log_scales": (0.020, 0.002)}
+    loop = gsp_lib.DensifyLoop(gs, cams, tg, lr=LR, every=EVERY, k_event=K_EVENT, pair_capacity=1 << 22,
+                               schedule=sched, densify_from=2 * EVERY, densify_until=4 * EVERY, budget=budget)
+    counts = []
+    for it in range(6):  # 6 x EVERY iterations, one replay block at a time
+        loop.run(EVERY)
+        torch.cuda.synchronize()
+        assert int(loop.status.item()) == 0
+        counts.append(int(gs.count.item()))
+    assert loop.events == 3  # iterations 2 EVERY, 3 EVERY, 4 EVERY
+    assert counts == [N0, N0 + K_EVENT, N0 + 2 * K_EVENT, budget, budget, budget]
+    assert int(loop.step_dev.item()) == 6 * EVERY
