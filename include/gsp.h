@@ -5,7 +5,9 @@
  * (arXiv 2603.08661): the edge-importance map of Sec. 2.1, the tile-binned
  * Gaussian splatting pass that accumulates each Gaussian's edge score
  * (Sec. 1, "Edge-Score importance"), its adjoint, and the Long-Axis-Split of
- * Sec. 2.2 (Alg. 1 and Alg. 2).
+ * Sec. 2.2 (Alg. 1 and Alg. 2); around it, the refinement set-up of Sec. 2.3
+ * (gradient-threshold masking after a warm-up, importance sampling by edge
+ * score, the learning-rate schedule and a Gaussian budget).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -17,8 +19,9 @@
  * - Every call is asynchronous on the caller's stream and performs no host
  *   synchronisation.  Argument errors are detected on the host before any
  *   launch and returned synchronously; nothing is enqueued then.
- * - Errors that only the device can see (capacity exceeded, a grid barrier
- *   that timed out) are written as a gsp_status code to *dev_status (a
+ * - Errors that only the device can see (capacity exceeded, a bounded wait
+ *   that ran out: grid barrier, sort look-back, bulk copy) are written as a
+ *   gsp_status code to *dev_status (a
  *   device int32 the caller zeroes and reads after its own synchronisation);
  *   the first error wins.  dev_status may not be NULL.
  * - No C++ exception crosses this interface.  All floating point arithmetic
