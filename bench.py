@@ -433,6 +433,7 @@ def run_gsp(args, rank, world):
     if not args.no_extra:
         restore(copies[0], pristine)
         next_rows = {"gating": measure_gating(gsp, rends[0], target, E, k_split)}
+        restore(copies[0], pristine)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g, cam, tgt_np, stripes=4)
@@ -483,9 +484,10 @@ def _event_ms(fn, reps):
 
 
 def measure_gating(gsp, r, target, E, k, reps=10):
-    """Gradient-threshold masking (Sec. 2.3) on the main workload: the adjoint
-    with and without the positional statistic, and the gated selection beside the
-    plain one (threshold: the median mean gradient of the Gaussians seen)."""
+    """The next rows on the main workload: the adjoint with and without the
+    positional statistic and the gated selection beside the plain one
+    (threshold: the median mean gradient of the Gaussians seen), importance
+    sampling, and the plain against the scheduled SGD step."""
     import numpy as np
     import torch
     dev = r.gs.means.device
@@ -509,11 +511,24 @@ def measure_gating(gsp, r, target, E, k, reps=10):
     gsp.raise_on_device_status(st, "gated top-k")
     expv = torch.empty(cap, device=dev).exponential_()  # the sampling's Exp(1) inputs
     sample = _event_ms(lambda: gsp.sample_mask(score, expv, r.gs.count, k), reps)
+    # optimiser step: plain SGD against the device-scheduled rates (Sec. 2.3 decays); the
+    # parameters are restored afterwards by the caller's copy
+    import ctypes
+    from paper_2603_08661_gb300 import _lib as L
+    lib = L.load()
+    gp = [grads[name] for name in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+    ptrs = [ctypes.c_void_p(t.data_ptr()) for t in gp]
+    sched = L.LrSchedule((L.c_f32 * 5)(1.28e-4, 0.020, 1e-3, 5e-2, 2.5e-3),
+                         (L.c_f32 * 5)(1.28e-5, 0.002, 1e-3, 5e-2, 2.5e-3), 30000)
+    step = torch.zeros(1, dtype=torch.int32, device=dev)
+    sgd = _event_ms(lambda: lib.gsp_sgd_step(ctypes.byref(r.gs.struct()), *ptrs, ctypes.c_float(0.0), None), reps)
+    sgd_s = _event_ms(lambda: lib.gsp_sgd_step_scheduled(ctypes.byref(r.gs.struct()), *ptrs, ctypes.byref(sched),
+                                                         ctypes.c_void_p(step.data_ptr()), None), reps)
     return {"row": "gradient-threshold masking (Sec. 2.3 warm-up masking)",
             "adjoint_ms": round(bwd, 4), "adjoint_with_statistic_ms": round(bwd_stat, 4),
             "topk_ms": round(plain, 4), "topk_gated_ms": round(gated, 4), "k": int(k),
             "seen": int(seen.sum()), "threshold": tau, "selected": int(sel.item()),
-            "sampling_ms": round(sample, 4),
+            "sampling_ms": round(sample, 4), "sgd_ms": round(sgd, 4), "sgd_scheduled_ms": round(sgd_s, 4),
             "note": "eager launches incl. host overhead; statistic fused into the adjoint's parameter pass"}
 
 
