@@ -1516,7 +1516,7 @@ constexpr int kG2 = 10;  // moments dx, dy, dx^2, dx dy, dy^2 (-> mean x, y, con
 // (transpose reduction), warps meet in shared accumulators, and one global
 // atomic per (Gaussian, tile, value) leaves the block.
 template <int PPT, int BATCH, bool CULL>
-__global__ void __launch_bounds__(kTilePix / PPT, 2048 / (kTilePix / PPT) / 2) composite_bwd(const __grid_constant__ Views vs, State st,
+__global__ void __launch_bounds__(kTilePix / PPT, PPT == 2 ? 6 : 2048 / (kTilePix / PPT) / 2) composite_bwd(const __grid_constant__ Views vs, State st,
                                                                 long long cap, const float *dL_drgb, const float *rgb,
                                                                 const float *T_fin, const int32_t *last_idx,
                                                                 const float *edge, float *score, float inv_norm)
