@@ -168,7 +168,7 @@ def stage_work(stage, n, k_sh, npix, pairs, evals, contrib):
 # dominant kernel from one ncu capture of this workload
 # (profiles/composite_bwd_1M_sh3_1237x822.md): valid for the captured variant
 # while the compositing source is the one that was captured.
-NCU_TRAFFIC = {("composite_bwd", 4): (43_408_128, "91582fc351c3e937")}
+NCU_TRAFFIC = {("composite_bwd", 4): (43_537_920, "9e834e2311737c53")}
 
 
 def compositing_source_hash():
