@@ -469,8 +469,16 @@ int orc_render_bwd(int64_t n, const double *means, const double *log_scales, con
                    const double *opac_logits, const double *sh, int sh_degree, const float *viewmat,
                    const double *intr, int width, int height, const double *proj, const double *dLdC,
                    double *g_means, double *g_log_scales, double *g_quats, double *g_opac, double *g_sh,
-                   double *g2d_out, const int *region)
+                   double *g2d_out, const int *region, int mag)
 {
+    /* mag != 0: the magnitude adjoint.  Every factor of every term enters by its
+     * absolute value and every difference becomes a sum, so each output is the
+     * sum of the absolute values of the terms that the plain adjoint adds up: the
+     * condition of that sum, which bounds how far relative perturbations of the
+     * terms (rounding in a lower precision) can move the result.  mag == 0
+     * evaluates exactly the plain adjoint. */
+#define MG(x) (mag ? fabs(x) : (x))
+#define DIFF(a, b) (mag ? fabs(a) + fabs(b) : (a) - (b))
     /* region (nullable): only pixels of [x0,x1) x [y0,y1) carry dL/dC (the others are taken as 0) */
     int rx0 = 0, ry0 = 0, rx1 = width, ry1 = height;
     if (region) { rx0 = region[0]; ry0 = region[1]; rx1 = region[2]; ry1 = region[3]; }
@@ -494,25 +502,25 @@ int orc_render_bwd(int64_t n, const double *means, const double *log_scales, con
                 const double *r = proj + cb[k].id * ORC_PROJ_STRIDE;
                 double *o = g2d + 9 * cb[k].id;
                 /* dC/dc_k = alpha_k T_k */
-                for (int ch = 0; ch < 3; ch++) o[6 + ch] += g[ch] * cb[k].alpha * cb[k].T;
+                for (int ch = 0; ch < 3; ch++) o[6 + ch] += MG(g[ch]) * cb[k].alpha * cb[k].T;
                 /* dC/dalpha_k = T_k c_k - sum_{j>k} c_j alpha_j T_j / (1 - alpha_k) */
                 double dalpha = 0;
                 for (int ch = 0; ch < 3; ch++) {
                     double behind = 0;
                     for (int j = k + 1; j < nk; j++)
                         behind += proj[cb[j].id * ORC_PROJ_STRIDE + P_R + ch] * cb[j].alpha * cb[j].T;
-                    dalpha += g[ch] * (cb[k].T * r[P_R + ch] - behind / (1.0 - cb[k].alpha));
+                    dalpha += MG(g[ch]) * DIFF(cb[k].T * r[P_R + ch], behind / (1.0 - cb[k].alpha));
                 }
                 if (cb[k].raw >= 0.99) continue; /* clamped alpha: constant */
                 double G = cb[k].G;
                 double dx = x + 0.5 - r[P_MX], dy = y + 0.5 - r[P_MY];
                 o[5] += dalpha * G;
                 double dG = dalpha * r[P_OPAC];
-                o[0] += dG * G * (r[P_CON_A] * dx + r[P_CON_B] * dy);
-                o[1] += dG * G * (r[P_CON_B] * dx + r[P_CON_C] * dy);
-                o[2] += dG * G * (-0.5 * dx * dx);
-                o[3] += dG * G * (-dx * dy);
-                o[4] += dG * G * (-0.5 * dy * dy);
+                o[0] += dG * G * (MG(r[P_CON_A] * dx) + MG(r[P_CON_B] * dy));
+                o[1] += dG * G * (MG(r[P_CON_B] * dx) + MG(r[P_CON_C] * dy));
+                o[2] += dG * G * MG(-0.5 * dx * dx);
+                o[3] += dG * G * MG(-dx * dy);
+                o[4] += dG * G * MG(-0.5 * dy * dy);
             }
         }
     free(cb);
@@ -568,9 +576,9 @@ int orc_render_bwd(int64_t n, const double *means, const double *log_scales, con
         double GQ[4] = {o[2], 0.5 * o[3], 0.5 * o[3], o[4]};
         double tmp[4], GS2[4];
         for (int a = 0; a < 2; a++)
-            for (int b = 0; b < 2; b++) tmp[2 * a + b] = Q[2 * a] * GQ[b] + Q[2 * a + 1] * GQ[2 + b];
+            for (int b = 0; b < 2; b++) tmp[2 * a + b] = MG(Q[2 * a] * GQ[b]) + MG(Q[2 * a + 1] * GQ[2 + b]);
         for (int a = 0; a < 2; a++)
-            for (int b = 0; b < 2; b++) GS2[2 * a + b] = -(tmp[2 * a] * Q[b] + tmp[2 * a + 1] * Q[2 + b]);
+            for (int b = 0; b < 2; b++) GS2[2 * a + b] = MG(-tmp[2 * a] * Q[b]) + MG(-tmp[2 * a + 1] * Q[2 + b]);
 
         /* Sigma2 = T Sigma T^T + 0.3 I */
         double GSig[9], GT[6];
@@ -578,46 +586,47 @@ int orc_render_bwd(int64_t n, const double *means, const double *log_scales, con
             for (int b = 0; b < 3; b++) {
                 double acc = 0;
                 for (int k = 0; k < 2; k++)
-                    for (int l = 0; l < 2; l++) acc += T[3 * k + a] * GS2[2 * k + l] * T[3 * l + b];
+                    for (int l = 0; l < 2; l++) acc += MG(T[3 * k + a] * GS2[2 * k + l] * T[3 * l + b]);
                 GSig[3 * a + b] = acc;
             }
         for (int a = 0; a < 2; a++)
             for (int b = 0; b < 3; b++) {
                 double acc = 0;
                 for (int l = 0; l < 2; l++)
-                    for (int k = 0; k < 3; k++) acc += GS2[2 * a + l] * T[3 * l + k] * Sig[3 * k + b];
+                    for (int k = 0; k < 3; k++) acc += MG(GS2[2 * a + l] * T[3 * l + k] * Sig[3 * k + b]);
                 GT[3 * a + b] = 2.0 * acc;
             }
         /* T = J W  ->  dL/dJ = GT W^T */
         double GJ[6];
         for (int a = 0; a < 2; a++)
-            for (int b = 0; b < 3; b++) GJ[3 * a + b] = GT[3 * a] * W[3 * b] + GT[3 * a + 1] * W[3 * b + 1] + GT[3 * a + 2] * W[3 * b + 2];
+            for (int b = 0; b < 3; b++)
+                GJ[3 * a + b] = MG(GT[3 * a] * W[3 * b]) + MG(GT[3 * a + 1] * W[3 * b + 1]) + MG(GT[3 * a + 2] * W[3 * b + 2]);
         double gt[3] = {0, 0, 0};
         /* J entries */
-        gt[2] += GJ[0] * (-fx / (tz * tz));
-        gt[0] += GJ[2] * (-fx / (tz * tz));
-        gt[2] += GJ[2] * (2.0 * fx * t[0] / (tz * tz * tz));
-        gt[2] += GJ[4] * (-fy / (tz * tz));
-        gt[1] += GJ[5] * (-fy / (tz * tz));
-        gt[2] += GJ[5] * (2.0 * fy * t[1] / (tz * tz * tz));
+        gt[2] += MG(GJ[0] * (-fx / (tz * tz)));
+        gt[0] += MG(GJ[2] * (-fx / (tz * tz)));
+        gt[2] += MG(GJ[2] * (2.0 * fx * t[0] / (tz * tz * tz)));
+        gt[2] += MG(GJ[4] * (-fy / (tz * tz)));
+        gt[1] += MG(GJ[5] * (-fy / (tz * tz)));
+        gt[2] += MG(GJ[5] * (2.0 * fy * t[1] / (tz * tz * tz)));
         /* mean2 */
-        gt[0] += o[0] * fx / tz;
-        gt[2] += o[0] * (-fx * t[0] / (tz * tz));
-        gt[1] += o[1] * fy / tz;
-        gt[2] += o[1] * (-fy * t[1] / (tz * tz));
-        for (int j = 0; j < 3; j++) g_means[3 * i + j] = W[j] * gt[0] + W[3 + j] * gt[1] + W[6 + j] * gt[2];
+        gt[0] += MG(o[0] * fx / tz);
+        gt[2] += MG(o[0] * (-fx * t[0] / (tz * tz)));
+        gt[1] += MG(o[1] * fy / tz);
+        gt[2] += MG(o[1] * (-fy * t[1] / (tz * tz)));
+        for (int j = 0; j < 3; j++) g_means[3 * i + j] = MG(W[j] * gt[0]) + MG(W[3 + j] * gt[1]) + MG(W[6 + j] * gt[2]);
 
         /* Sigma = M M^T: dL/dM = 2 GSig M (GSig symmetric) */
         double GM[9];
         for (int a = 0; a < 3; a++)
             for (int b = 0; b < 3; b++) {
                 double acc = 0;
-                for (int k = 0; k < 3; k++) acc += (GSig[3 * a + k] + GSig[3 * k + a]) * Mm[3 * k + b];
+                for (int k = 0; k < 3; k++) acc += MG((GSig[3 * a + k] + GSig[3 * k + a]) * Mm[3 * k + b]);
                 GM[3 * a + b] = acc;
             }
         for (int b = 0; b < 3; b++) {
             double gs = 0;
-            for (int a = 0; a < 3; a++) gs += GM[3 * a + b] * R[3 * a + b];
+            for (int a = 0; a < 3; a++) gs += MG(GM[3 * a + b] * R[3 * a + b]);
             g_log_scales[3 * i + b] = gs * s[b];
         }
         double GR[9];
@@ -627,9 +636,9 @@ int orc_render_bwd(int64_t n, const double *means, const double *log_scales, con
         quat_to_rot_jac(q, dR);
         double gqn[4] = {0, 0, 0, 0};
         for (int e = 0; e < 9; e++)
-            for (int j = 0; j < 4; j++) gqn[j] += GR[e] * dR[e][j];
-        double dotq = gqn[0] * q[0] + gqn[1] * q[1] + gqn[2] * q[2] + gqn[3] * q[3];
-        for (int j = 0; j < 4; j++) g_quats[4 * i + j] = (gqn[j] - q[j] * dotq) / nq;
+            for (int j = 0; j < 4; j++) gqn[j] += MG(GR[e] * dR[e][j]);
+        double dotq = MG(gqn[0] * q[0]) + MG(gqn[1] * q[1]) + MG(gqn[2] * q[2]) + MG(gqn[3] * q[3]);
+        for (int j = 0; j < 4; j++) g_quats[4 * i + j] = DIFF(gqn[j], q[j] * dotq) / nq;
 
         g_opac[i] = o[5] * r[P_OPAC] * (1.0 - r[P_OPAC]);
 
@@ -645,14 +654,16 @@ int orc_render_bwd(int64_t n, const double *means, const double *log_scales, con
             if (r[P_RAW_R + ch] < 0) continue;
             double gc = o[6 + ch];
             for (int k = 0; k < K; k++) {
-                g_sh[(i * K + k) * 3 + ch] = gc * Y[k];
-                for (int a = 0; a < 3; a++) gu[a] += gc * sh[(i * K + k) * 3 + ch] * dY[k][a];
+                g_sh[(i * K + k) * 3 + ch] = MG(gc * Y[k]);
+                for (int a = 0; a < 3; a++) gu[a] += MG(gc * sh[(i * K + k) * 3 + ch] * dY[k][a]);
             }
         }
-        double udot = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
-        for (int a = 0; a < 3; a++) g_means[3 * i + a] += (gu[a] - u[a] * udot) / dn;
+        double udot = MG(gu[0] * u[0]) + MG(gu[1] * u[1]) + MG(gu[2] * u[2]);
+        for (int a = 0; a < 3; a++) g_means[3 * i + a] += DIFF(gu[a], u[a] * udot) / dn;
     }
     if (g2d_out) memcpy(g2d_out, g2d, sizeof(double) * 9 * n);
     free(g2d);
     return 0;
+#undef MG
+#undef DIFF
 }

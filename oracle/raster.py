@@ -38,7 +38,7 @@ def lib():
         _lib.orc_gate_affected.argtypes = [i64, _i64p, _dp, i64, _i32p, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_uint8)]
         _lib.orc_render_bwd.argtypes = [i64, _dp, _dp, _dp, _dp, _dp, ci, _fp, _dp, ci, ci, _dp,
-                                        _dp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_int)]
+                                        _dp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_int), ci]
         _lib.orc_sh_basis.argtypes = [i64, _dp, _dp]
         _lib.orc_quat_to_rot.argtypes = [i64, _dp, _dp]
     return _lib
@@ -54,8 +54,11 @@ def _params64(g: dict):
 
 
 def _cam(cam: dict):
+    """The camera as the library receives it: the view matrix and the pinhole
+    intrinsics are the FP32 numbers of its camera record (both sides then
+    compute the same function of the same inputs; the arithmetic stays FP64)."""
     vm = np.ascontiguousarray(cam["viewmat"], dtype=np.float32).reshape(12)
-    intr = np.array([cam["fx"], cam["fy"], cam["cx"], cam["cy"]], dtype=np.float64)
+    intr = np.array([cam["fx"], cam["fy"], cam["cx"], cam["cy"]], dtype=np.float32).astype(np.float64)
     return vm, intr, int(cam["width"]), int(cam["height"])
 
 
@@ -128,10 +131,15 @@ def render(g: dict, cam: dict, edge=None, brute: bool = False, region=None, proj
             "gate_gap": gap, "proj": proj}
 
 
-def render_bwd(g: dict, cam: dict, dLdC: np.ndarray, proj=None, region=None) -> dict:
+def render_bwd(g: dict, cam: dict, dLdC: np.ndarray, proj=None, region=None, magnitude: bool = False) -> dict:
     """Analytic adjoint: parameter gradients of sum(dLdC * C).
 
-    region (x0, y0, x1, y1), optional: dLdC is taken as zero outside it."""
+    region (x0, y0, x1, y1), optional: dLdC is taken as zero outside it.
+    magnitude=True returns the magnitude adjoint instead: for every gradient
+    entry, the sum of the absolute values of the terms the adjoint adds up
+    (every factor by its absolute value, every difference as a sum).  It is
+    the condition of each entry: a result computed from terms that each carry
+    a relative error e is off by at most e times it."""
     m, s, q, o, sh = _params64(g)
     vm, intr, w, h = _cam(cam)
     proj = project(g, cam) if proj is None else proj
@@ -144,7 +152,8 @@ def render_bwd(g: dict, cam: dict, dLdC: np.ndarray, proj=None, region=None) -> 
                          _p(intr), w, h, _p(np.ascontiguousarray(proj)), _p(d), _p(out["means"]),
                          _p(out["log_scales"]), _p(out["quats"]), _p(out["opacity_logits"]),
                          _p(out["sh"]), _p(out["g2d"]),
-                         None if region is None else (ctypes.c_int * 4)(*[int(r) for r in region]))
+                         None if region is None else (ctypes.c_int * 4)(*[int(r) for r in region]),
+                         1 if magnitude else 0)
     return out
 
 

@@ -347,3 +347,52 @@ def test_screen_space_mean_gradient_matches_differences_of_the_projected_mean():
             assert abs(an - fd[0]) <= 1e-5 * max(abs(fd[0]), 1e-3), (i, c, an, fd[0])
             checked += 1
     assert checked > 40
+
+
+# ---- magnitude adjoint (the condition of each gradient entry, used to bound
+# what FP32 rounding can do to sums whose terms cancel)
+
+def _mag_scene():
+    g, cam, _ = _fd_scene()
+    h, w = int(cam["height"]), int(cam["width"])
+    dl = np.random.default_rng(21).normal(size=(h, w, 3)) / (h * w)
+    return g, cam, dl
+
+
+def test_magnitude_adjoint_bounds_the_adjoint_and_is_homogeneous():
+    g, cam, dl = _mag_scene()
+    gr = orc.render_bwd(g, cam, dl)
+    gm = orc.render_bwd(g, cam, dl, magnitude=True)
+    gm3 = orc.render_bwd(g, cam, -3.0 * dl, magnitude=True)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        assert np.all(gm[k] >= 0)
+        assert np.all(gm[k] >= np.abs(gr[k]) * (1 - 1e-12))  # |sum| <= sum of |terms|
+        np.testing.assert_allclose(gm3[k], 3.0 * gm[k], rtol=1e-12, atol=0)
+    # the upstream gradient cancels across pixels: some entries are far below their magnitude
+    assert (gm["opacity_logits"] > 10 * np.abs(gr["opacity_logits"])).any()
+
+
+def test_magnitude_adjoint_of_sh_is_the_adjoint_of_the_absolute_upstream_gradient():
+    """dL/dsh[k, ch] = Y_k(dir) sum_p alpha T g_ch(p): one product per pixel, so
+    its magnitude is |Y_k| sum_p alpha T |g_ch(p)|, the plain adjoint of |g|
+    up to the sign of Y_k (for the colour channels that are not clamped)."""
+    g, cam, dl = _mag_scene()
+    gm = orc.render_bwd(g, cam, dl, magnitude=True)
+    ga = orc.render_bwd(g, cam, np.abs(dl))
+    proj = orc.project(g, cam)
+    for ch in range(3):
+        live = (proj[:, orc.P_VALID] > 0) & (proj[:, orc.P_RAW_R + ch] >= 0)
+        np.testing.assert_allclose(gm["sh"][live, :, ch], np.abs(ga["sh"][live, :, ch]), rtol=1e-12, atol=0)
+
+
+def test_magnitude_adjoint_equals_the_adjoint_when_no_term_changes_sign():
+    """With one Gaussian and a single pixel of positive upstream gradient, the
+    colour and opacity entries are single products of positive factors."""
+    g, cam = _single(0.08, 0.3, 0.4)
+    h, w = int(cam["height"]), int(cam["width"])
+    dl = np.zeros((h, w, 3))
+    dl[h // 2, w // 2] = (1.0, 0.5, 0.25)
+    gr = orc.render_bwd(g, cam, dl)
+    gm = orc.render_bwd(g, cam, dl, magnitude=True)
+    np.testing.assert_allclose(gm["sh"][0, 0], np.abs(gr["sh"][0, 0]), rtol=1e-14)
+    np.testing.assert_allclose(gm["opacity_logits"], np.abs(gr["opacity_logits"]), rtol=1e-14)
