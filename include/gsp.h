@@ -104,6 +104,13 @@ typedef struct gsp_edge_opts {
     float taps[5];           /* 1-D blur taps, symmetric (taps[k] == taps[4-k]) */
     float sigma;             /* blur sigma when use_custom_taps == 0 (> 0) */
     int64_t spin_limit;      /* grid-barrier polls before GSP_ERR_TIMEOUT; <= 0: default */
+    int32_t test_expire;     /* failure-injection hook for tests (0 in normal use), fused mode:
+                                bit 0: the first grid barrier is never opened, so every
+                                block's bounded wait runs out; bit 1: each wait for a staged
+                                TMA box gives up at once (the block still lets its copies in
+                                flight land before it leaves).  Either way the call reports
+                                GSP_ERR_TIMEOUT in dev_status and E_out / median_out are
+                                unspecified; the next call works normally. */
 } gsp_edge_opts;
 
 /* Default options: fused mode, sigma = 1. */
@@ -143,6 +150,7 @@ gsp_status gsp_edge_map(const gsp_image_desc *imgs, int32_t num_views, float *E_
  *   C      = sum_i c_i alpha_i T_i (black background)
  *   score  s_i += sum over pixels of alpha_i T_i E(pixel)
  *   loss   L1: mean over all pixels of all views and 3 channels of |C - target/255|
+ *          (over gsp_render_opts.loss_pixels pixels when the caller sets it)
  * ==================================================================== */
 
 typedef struct gsp_gaussians {
@@ -176,6 +184,20 @@ typedef struct gsp_render_opts {
      * Accumulated over calls; the caller clears them (e.g. after each densification). */
     float *pos_grad_sum;
     int32_t *pos_grad_count;
+    int64_t loss_pixels;   /* pixels the L1 loss averages over, for the loss of gsp_render_fwd and
+                              the L1 upstream gradient of gsp_render_bwd; <= 0: the pixels of
+                              this call's views.  A caller that shards the views of one loss
+                              over several GPUs passes the pixel count of all of them, so that
+                              the per-GPU results sum to the whole loss and its gradient. */
+    int64_t spin_limit;    /* depth-sort look-back polls before GSP_ERR_TIMEOUT; <= 0: default */
+    int32_t test_expire;   /* failure-injection hook for tests (0 in normal use), gsp_render_fwd:
+                              bit 0: the first depth-sort tile never publishes its digit counts,
+                              so every later tile's bounded look-back runs out (the forward
+                              then skips its remaining stages and writes no output); bit 1:
+                              the projection's wait for its bulk SH copy gives up at once (each
+                              thread then reads its SH row from global memory, so the outputs
+                              are complete and correct).  Either way dev_status receives
+                              GSP_ERR_TIMEOUT. */
 } gsp_render_opts;
 
 /* Compositing variants (pixels per thread, Gaussians staged per shared-memory batch,
@@ -226,7 +248,8 @@ const int64_t *gsp_render_pair_count_ptr(const void *workspace, int64_t capacity
  * Adjoint of gsp_render_fwd, replayed back to front from T_final and last_idx.
  *
  * The upstream gradient is dL_drgb (device float [total_pixels][3]) when it is
- * not NULL; otherwise that of the L1 loss, sign(C - target/255) / (3 * total_pixels)
+ * not NULL; otherwise that of the L1 loss, sign(C - target/255) / (3 * P), P = opts->loss_pixels
+ * when it is > 0, else the total pixels of these views,
  * with sign(0) = 0, from rgb and targets (both then required).
  * grad_*     device buffers shaped like the parameters; accumulate != 0 adds to
  *            them, accumulate == 0 overwrites rows [0, N)
@@ -315,6 +338,11 @@ typedef struct gsp_select_opts {
     float threshold;               /* gating threshold (not NaN) */
     const float *exp_variates;     /* sampling: device Exp(1) draws [capacity], or NULL for top-k */
     int64_t budget;                /* 0: none */
+    int64_t spin_limit;            /* grid-barrier polls before GSP_ERR_TIMEOUT; <= 0: default */
+    int32_t test_expire;           /* failure-injection hook for tests (0 in normal use): nonzero
+                                      withholds the first grid barrier, so every block's bounded
+                                      wait runs out; dev_status receives GSP_ERR_TIMEOUT and
+                                      mask_out / selected_out are unspecified */
 } gsp_select_opts;
 
 gsp_status gsp_select_mask(const float *scores, const int32_t *count, int64_t capacity, int64_t k,
@@ -324,19 +352,19 @@ gsp_status gsp_select_mask(const float *scores, const int32_t *count, int64_t ca
 /*
  * Allocation-free variant of gsp_topk_mask (the paper has no counterpart).
  *
- * For callers that cannot allocate device memory when they call: code being
- * captured into a CUDA graph (cudaMalloc is not allowed during capture),
- * real-time loops that forbid allocation after start-up, and hosts whose
- * device memory belongs to another allocator.  Same arguments and result as
+ * For callers that cannot allocate device memory when they call: real-time
+ * loops that forbid allocation once they run, and host applications whose
+ * device memory is owned by their own allocator, where a plug-in may not take
+ * memory behind the host's back.  Same arguments and result as
  * gsp_topk_mask, but no workspace: the scratch (about 89 KB) is a static
  * device array inside the library that every GPU which loads the library
  * holds until the process exits.  The caller still passes scores, count,
  * mask_out and selected_out.
  * - capacity must be <= GSP_TOPK_STATIC_MAX_CAPACITY, else GSP_ERR_INVALID_ARG
  *   is returned and nothing is enqueued.
- * - The first call on a device looks up the array's device address on that
- *   device (cudaGetSymbolAddress); make that first call before any stream
- *   capture.
+ * - The first call on a device (that device current) looks up the array's
+ *   device address on it (cudaGetSymbolAddress); make that first call before
+ *   any stream capture.
  * - All calls share the one array and the kernels re-initialise what must
  *   start at zero; calls that overlap on the GPU (other streams, other host
  *   threads) race on it and must be serialised by the caller.

@@ -70,13 +70,14 @@ def pitched_image(img: torch.Tensor, align: int = 16) -> torch.Tensor:
 # ----------------------------------------------------------------- edge map
 
 def edge_map(images, *, mode: str = "fused", taps=None, sigma: float = 1.0, with_mask: bool = False,
-             spin_limit: int = 0, out: torch.Tensor | None = None, status: torch.Tensor | None = None,
-             workspace: torch.Tensor | None = None, stream=None):
+             spin_limit: int = 0, test_expire: int = 0, out: torch.Tensor | None = None,
+             status: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None):
     """Edge-importance maps of a list of HWC uint8 CUDA views (one launch in fused mode).
 
     Returns (E, medians, mask, status): E is a flat float32 tensor holding the
     views one after another (row-major), medians is [V], mask is uint8 like E
-    (or None), status is the device status word.
+    (or None), status is the device status word.  spin_limit and test_expire
+    are gsp_edge_opts' bounded-wait limit and failure-injection hook (tests).
     """
     if isinstance(images, torch.Tensor):
         images = [images]
@@ -96,6 +97,7 @@ def edge_map(images, *, mode: str = "fused", taps=None, sigma: float = 1.0, with
             opts.taps[k] = float(taps[k])
     opts.sigma = float(sigma)
     opts.spin_limit = int(spin_limit)
+    opts.test_expire = int(test_expire)
     need = lib().gsp_edge_map_workspace_size(descs, v, ctypes.byref(opts))
     if need == 0:
         raise L.GspError(L.GSP_ERR_INVALID_ARG, "gsp_edge_map_workspace_size")
@@ -182,6 +184,12 @@ class Renderer:
             off += int(c["width"]) * int(c["height"])
         self.total_pix = off
         self.opts = L.RenderOpts(int(pair_capacity), int(variants[0]), int(variants[1]))
+        # gsp_render_opts.spin_limit / test_expire: the depth sort's look-back limit and
+        # the failure-injection hook (tests); 0 in normal use
+        self.spin_limit = 0
+        self.test_expire = 0
+        # pixels of the whole L1 loss when it spans views rendered elsewhere (0: these views)
+        self.loss_pixels = 0
         self.ws_bytes = lib().gsp_render_workspace_size(gs.capacity, gs.sh_degree, self.cams, self.nv,
                                                         ctypes.byref(self.opts))
         if self.ws_bytes == 0:
@@ -218,6 +226,13 @@ class Renderer:
             arr[i] = image_desc(t, 0)
         return arr
 
+    def _opts(self, pos_grad=None) -> L.RenderOpts:
+        o = self.opts
+        return L.RenderOpts(o.pair_capacity, o.fwd_variant, o.bwd_variant,
+                            _ptr(pos_grad[0]).value if pos_grad is not None else None,
+                            _ptr(pos_grad[1]).value if pos_grad is not None else None,
+                            int(self.loss_pixels), int(self.spin_limit), int(self.test_expire))
+
     def forward(self, targets=None, edge=None, score=None, want_loss: bool = True, status=None, stream=None,
                 out=None):
         dev = self.device
@@ -233,7 +248,7 @@ class Renderer:
         st = status if status is not None else new_status(dev)
         L.check(lib().gsp_render_fwd(ctypes.byref(self.gs.struct()), self.cams, self.nv, self._targets(targets),
                                      _ptr(edge), _ptr(rgb), _ptr(T), _ptr(last), _ptr(score), _ptr(loss),
-                                     ctypes.byref(self.opts), _ptr(self.ws), self.ws_bytes, _ptr(st),
+                                     ctypes.byref(self._opts()), _ptr(self.ws), self.ws_bytes, _ptr(st),
                                      _stream_handle(stream)), "gsp_render_fwd")
         return {"rgb": rgb, "T": T, "last": last, "loss": loss, "status": st}
 
@@ -243,10 +258,7 @@ class Renderer:
         tensors; the positional statistic of the gradient-threshold masking is
         added to them (see gsp_render_opts)."""
         gs = self.gs
-        opts = self.opts
-        if pos_grad is not None:
-            opts = L.RenderOpts(self.opts.pair_capacity, self.opts.fwd_variant, self.opts.bwd_variant,
-                                _ptr(pos_grad[0]).value, _ptr(pos_grad[1]).value)
+        opts = self._opts(pos_grad)
         if grads is None:
             grads = {"means": torch.zeros_like(gs.means), "log_scales": torch.zeros_like(gs.log_scales),
                      "quats": torch.zeros_like(gs.quats), "opacity_logits": torch.zeros_like(gs.opacity_logits),
@@ -311,9 +323,12 @@ def sample_mask(scores: torch.Tensor, exp_variates: torch.Tensor, count: torch.T
 
 
 def select_mask(scores: torch.Tensor, count: torch.Tensor, k: int, pos_grad=None, threshold: float = 0.0,
-                exp_variates=None, budget: int = 0, status=None, stream=None, workspace=None, out=None):
+                exp_variates=None, budget: int = 0, status=None, stream=None, workspace=None, out=None,
+                spin_limit: int = 0, test_expire: int = 0):
     """gsp_select_mask: top-k or importance sampling, optionally gated by the
-    gradient threshold (pos_grad = (sum, count)) and capped by a Gaussian budget."""
+    gradient threshold (pos_grad = (sum, count)) and capped by a Gaussian budget.
+    spin_limit and test_expire are the grid barriers' limit and the
+    failure-injection hook (tests)."""
     cap = int(scores.shape[0])
     need = lib().gsp_las_workspace_size(cap)
     ws = workspace if workspace is not None else _workspace(need, scores.device)
@@ -322,7 +337,8 @@ def select_mask(scores: torch.Tensor, count: torch.Tensor, k: int, pos_grad=None
     st = status if status is not None else new_status(scores.device)
     o = L.SelectOpts(_ptr(pos_grad[0]).value if pos_grad is not None else None,
                      _ptr(pos_grad[1]).value if pos_grad is not None else None, float(threshold),
-                     _ptr(exp_variates).value if exp_variates is not None else None, int(budget))
+                     _ptr(exp_variates).value if exp_variates is not None else None, int(budget),
+                     int(spin_limit), int(test_expire))
     L.check(lib().gsp_select_mask(_ptr(scores), _ptr(count), cap, int(k), ctypes.byref(o), _ptr(mask), _ptr(sel),
                                   _ptr(ws), ws.numel(), _ptr(st), _stream_handle(stream)), "gsp_select_mask")
     return mask, sel, st

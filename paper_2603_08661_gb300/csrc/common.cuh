@@ -60,16 +60,21 @@ inline gsp_status check_workspace(const void *ws, size_t have, size_t need)
     return GSP_OK;
 }
 
+constexpr int kMaxDevices = 64;
+
+// SM count of the current device (looked up once per device).
 inline int num_sms()
 {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
+    static int n[kMaxDevices] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= kMaxDevices) dev = 0;
+    if (!n[dev]) {
+        int c = 0;
+        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+        n[dev] = c > 0 ? c : 1;
     }
-    return n;
+    return n[dev];
 }
 
 inline unsigned div_up(long long a, long long b) { return static_cast<unsigned>((a + b - 1) / b); }
@@ -78,8 +83,12 @@ inline unsigned div_up(long long a, long long b) { return static_cast<unsigned>(
 // bar[0] counts arrivals, bar[1] is the generation.  Every wait polls at
 // most spin_limit times; on expiry it records GSP_ERR_TIMEOUT and returns
 // false, and the caller leaves the kernel.
+// withhold (a test hook): the last block to arrive resets the count but does
+// not open the barrier and leaves with GSP_ERR_TIMEOUT, so every other block's
+// wait runs out - a flag that nothing sets.  The barrier state stays
+// consistent (count 0, generation unchanged).
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, long long spin_limit,
-                                             int32_t *status)
+                                             int32_t *status, bool withhold = false)
 {
     __shared__ int ok;
     __syncthreads();
@@ -92,7 +101,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, lo
         if (arrived == nblocks - 1) {
             atomicExch(bar, 0u);
             __threadfence();
-            atomicAdd(bar + 1, 1u);
+            if (withhold) {
+                set_status(status, GSP_ERR_TIMEOUT);
+                ok = 0;
+            } else {
+                atomicAdd(bar + 1, 1u);
+            }
         } else {
             long long polls = 0;
             while (*vgen == gen) {

@@ -119,6 +119,8 @@ struct TopkArgs {
     // are taken, i.e. the k largest keys -expv[i] / score[i]
     const float *expv;
     long long budget;  // > 0: at most budget - N selected (the room left under a Gaussian budget)
+    long long spin_limit;  // grid-barrier polls before GSP_ERR_TIMEOUT
+    int expire;            // test hook: the first grid barrier is withheld (every wait runs out)
 };
 
 __device__ __forceinline__ bool is_candidate(const TopkArgs &a, long long i)
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) topk_fused(TopkArgs a)
             for (int i = tid; i < nb; i += kThreads)
                 if (h[i]) atomicAdd(gh + i, h[i]);
         }
-        if (!grid_barrier(a.bar, G, kDefaultSpinLimit, a.status)) return;
+        if (!grid_barrier(a.bar, G, a.spin_limit, a.status, a.expire && pass == 0)) return;
         if (pass == 0 && (a.gsum || a.expv)) {  // at most the candidates (the same in every block)
             kk = min(kk, __ldcg(a.ncand));
             remaining = kk;
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(kThreads) topk_fused(TopkArgs a)
         unsigned ex;
         const unsigned tot = block_scan(c, &ex);
         if (tid == 0) a.sums[blockIdx.x] = tot;
-        if (!grid_barrier(a.bar, G, kDefaultSpinLimit, a.status)) return;
+        if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
         unsigned lower = 0;
         for (unsigned q = tid; q < blockIdx.x; q += kThreads) lower += __ldcg(a.sums + q);
         tie_base = block_scan(lower, &ex);  // the block total: ties in the lower blocks' ranges
@@ -416,19 +418,26 @@ DensifyLayout densify_layout(void *ws, long long cap)
 gsp_status enqueue_topk(const float *scores, const int32_t *count, long long cap, long long k, uint8_t *mask,
                         int32_t *selected_out, const DensifyLayout &L, int32_t *status, cudaStream_t s,
                         const float *gsum = nullptr, const int32_t *gcnt = nullptr, float tau = 0.f,
-                        const float *expv = nullptr, long long budget = 0)
+                        const float *expv = nullptr, long long budget = 0, long long spin_limit = 0,
+                        int expire = 0)
 {
     // co-resident blocks (grid barriers), at most two per SM and one per
-    // kBlockItems of capacity (the block sums are sized so)
-    static int per_sm = 0;
-    if (!per_sm) {
-        GSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_fused, kThreads, 0));
-        if (per_sm < 1) return GSP_ERR_UNSUPPORTED;
+    // kBlockItems of capacity (the block sums are sized so); the occupancy is
+    // looked up once per device
+    static int per_sm_dev[kMaxDevices] = {0};
+    int dev = 0;
+    GSP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return GSP_ERR_UNSUPPORTED;
+    if (!per_sm_dev[dev]) {
+        int per = 0;
+        GSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, topk_fused, kThreads, 0));
+        if (per < 1) return GSP_ERR_UNSUPPORTED;
+        per_sm_dev[dev] = per;
     }
-    long long grid = (long long)std::min(per_sm, 2) * num_sms();
+    long long grid = (long long)std::min(per_sm_dev[dev], 2) * num_sms();
     grid = std::max(1LL, std::min(grid, (long long)div_up(cap, kBlockItems)));
     TopkArgs a{scores, count, cap, k, mask, selected_out, L.hist, L.sums, L.bar, status, gsum, gcnt, tau, L.ncand,
-               expv, budget};
+               expv, budget, spin_limit > 0 ? spin_limit : kDefaultSpinLimit, expire ? 1 : 0};
     stage_begin("topk", s);
     GSP_CUDA_TRY(cudaMemsetAsync(L.hist, 0, kTopkZeroWords * sizeof(unsigned), s));
     cudaLaunchConfig_t cfg{};
@@ -526,7 +535,7 @@ extern "C" gsp_status gsp_select_mask(const float *scores, const int32_t *count,
     L = densify_layout(ws, capacity);
     return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L, dev_status,
                         reinterpret_cast<cudaStream_t>(stream), opts->pos_grad_sum, opts->pos_grad_count,
-                        opts->threshold, opts->exp_variates, opts->budget);
+                        opts->threshold, opts->exp_variates, opts->budget, opts->spin_limit, opts->test_expire);
 }
 
 extern "C" gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask, const float *scores, int64_t k,
@@ -581,10 +590,10 @@ extern "C" gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask,
 
 // ------------------------------------------------- allocation-free top-k
 //
-// Some callers cannot allocate device memory at the time they call us: code
-// that is being captured into a CUDA graph (cudaMalloc is not allowed during
-// capture), real-time loops that forbid allocation after start-up, and hosts
-// whose device memory belongs to another allocator.  gsp_topk_mask_static
+// Some callers cannot allocate device memory at the time they call us:
+// real-time loops that forbid allocation once they run, and host applications
+// whose device memory is owned by their own allocator, where a plug-in may not
+// take memory behind the host's back.  gsp_topk_mask_static
 // serves them with the same selection as gsp_topk_mask, its scratch held in
 // this file-scope device array instead of a caller workspace.  Every GPU that
 // loads the library keeps the array until the process exits.
@@ -599,7 +608,6 @@ constexpr size_t kStaticTopkBytes = kTopkZeroWords * sizeof(unsigned) + 256 +
 
 static __device__ __align__(256) unsigned char g_topk_scratch[kStaticTopkBytes];
 
-constexpr int kMaxDevices = 64;
 static void *g_topk_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device (looked up once

@@ -87,7 +87,8 @@ struct EdgeArgs {
     unsigned *med_bits;    // [V]
     unsigned *bar;         // grid barrier state [2]
     int32_t *status;
-    long long spin_limit;
+    long long spin_limit;  // grid-barrier polls
+    int expire;            // test hook bits: 1 withholds the first grid barrier, 2 makes box waits give up at once
     CUtensorMap tmap[GSP_MAX_VIEWS];  // uint8 [h][3w] with row pitch, box kBoxW x kBoxH
 };
 
@@ -348,6 +349,11 @@ __global__ void __launch_bounds__(NT) edge_fused_kernel(const __grid_constant__ 
     __syncthreads();
     if (tid == 0 && t_begin < t_end) issue_box(a, stg, t_begin, 0);
     unsigned uses[2] = {0u, 0u};  // completed phases of each buffer's barrier (block-uniform)
+    // The waits for this block's own box copies are bounded by the default limit
+    // (a copy that never lands is a fault, not a state to wait out); the hook
+    // (expire bit 1) makes them give up at once.  Either way a block that gives
+    // up first lets every copy it has in flight land, then leaves.
+    const long long box_limit = (a.expire & 2) ? 0 : kDefaultSpinLimit;
     int cur_view = -1;
     for (int t = t_begin, it = 0; t < t_end; ++t, ++it) {
         const int buf = it & 1;
@@ -366,11 +372,19 @@ __global__ void __launch_bounds__(NT) edge_fused_kernel(const __grid_constant__ 
             cur_view = v;
         }
         if (V.tma) {
-            const bool mine = mbar_wait(&stg.bar[buf], uses[buf] & 1u, a.spin_limit);
+            const bool mine = mbar_wait(&stg.bar[buf], uses[buf] & 1u, box_limit);
             if (!__syncthreads_and(mine)) {
                 set_status(a.status, GSP_ERR_TIMEOUT);
-                // let the copies in flight land before the block leaves (bounded)
-                mbar_wait(&stg.bar[buf ^ 1], uses[buf ^ 1] & 1u, a.spin_limit);
+                // drain: this tile's copy, and the next tile's if one was issued
+                if (tid == 0) {
+                    mbar_wait(&stg.bar[buf], uses[buf] & 1u, kDefaultSpinLimit);
+                    if (t + 1 < t_end) {
+                        int v1, x1, y1;
+                        tile_origin(a, t + 1, v1, x1, y1);
+                        if (a.v[v1].tma) mbar_wait(&stg.bar[buf ^ 1], uses[buf ^ 1] & 1u, kDefaultSpinLimit);
+                    }
+                }
+                __syncthreads();
                 return;
             }
             ++uses[buf];
@@ -394,7 +408,7 @@ __global__ void __launch_bounds__(NT) edge_fused_kernel(const __grid_constant__ 
         for (int i = tid; i < kBins1; i += NT)
             if (hist_s[i]) atomicAdd(&a.hist1[(size_t)cur_view * kBins1 + i], hist_s[i]);
     }
-    if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
+    if (!grid_barrier(a.bar, G, a.spin_limit, a.status, (a.expire & 1) != 0)) return;
 
     // ---- phase B0: each view's median bin of bits [30:19] and kept count (block v)
     for (int v = blockIdx.x; v < a.nviews; v += G) {
@@ -864,6 +878,7 @@ extern "C" gsp_status gsp_edge_map(const gsp_image_desc *imgs, int32_t nv, float
     a.bar = L.bar;
     a.status = dev_status;
     a.spin_limit = o.spin_limit > 0 ? o.spin_limit : kDefaultSpinLimit;
+    a.expire = o.test_expire & 3;
 
     // histogram, candidate counters, medians and barrier state start at zero
     size_t zero_bytes = reinterpret_cast<char *>(L.bar + 2) - reinterpret_cast<char *>(L.hist1);

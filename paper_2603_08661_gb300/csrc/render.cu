@@ -69,10 +69,12 @@ struct Params {
     int K;  // SH coefficients per channel
     int32_t *status = nullptr;  // device status word (bounded waits report here)
     bool sh_bulk = false;       // sh is 16-byte aligned: the projection streams it by bulk copies
+    long long sh_wait_limit = kDefaultSpinLimit;  // polls of a thread's wait for the SH copy (0: gives up at once)
 };
 
 struct State {
-    float4 *xyo;   // [V][cap] (mean x, mean y, opacity, depth)
+    float4 *xyo;   // [V][cap] (mean x, mean y, opacity, bbox half-width)
+    float2 *mlo;   // [V][cap] residual of the projected mean: mean = xyo.xy + mlo (double-float)
     float4 *con;   // [V][cap] log2(e) (-A/2, -B, -C/2) of the conic Q = [[A, B], [B, C]], bbox half-height
     float4 *col;   // [V][cap] (r, g, b, clamp bits)
     uint2 *rect;   // [V][cap] (tx0 | ty0 << 16, tx1 | ty1 << 16); empty if tx1 < tx0
@@ -292,6 +294,66 @@ __device__ __forceinline__ void load_sh(const float *row, float *out)
     }
 }
 
+// ---- double-float arithmetic for the projected mean (error-free transformations:
+// Knuth's TwoSum, the FMA TwoProduct, and the compensated dot product of Ogita,
+// Rump and Oishi, "Accurate sum and dot product", 2005)
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// r0 a + r1 b + r2 c + r3 as hi + lo (compensated dot product)
+__device__ __forceinline__ void dot3_plus(const float *r, float a, float b, float c, float &hi, float &lo)
+{
+    float p0, e0, p1, e1, p2, e2, s, t;
+    two_prod(r[0], a, p0, e0);
+    two_prod(r[1], b, p1, e1);
+    two_prod(r[2], c, p2, e2);
+    two_sum(p0, p1, s, t);
+    float err = __fadd_rn(__fadd_rn(e0, e1), t);
+    two_sum(s, p2, s, t);
+    err = __fadd_rn(err, __fadd_rn(e2, t));
+    two_sum(s, r[3], s, t);
+    err = __fadd_rn(err, t);
+    two_sum(s, err, hi, lo);
+}
+
+// f (n / z) + c for double-float n and z, as a normalised hi + lo
+__device__ __forceinline__ void df_project(float f, float c, float n_hi, float n_lo, float z_hi, float z_lo,
+                                           float &hi, float &lo)
+{
+    const float q = __fdiv_rn(n_hi, z_hi);
+    const float r = __fmaf_rn(-q, z_hi, n_hi);  // exact remainder
+    const float ql = __fdiv_rn(__fadd_rn(r, __fsub_rn(n_lo, __fmul_rn(q, z_lo))), z_hi);
+    float p, e, s, t;
+    two_prod(f, q, p, e);
+    e = __fmaf_rn(f, ql, e);
+    two_sum(p, c, s, t);
+    two_sum(s, __fadd_rn(e, t), hi, lo);
+}
+
+// Projected mean (fx t_x / t_z + cx, fy t_y / t_z + cy), t = W mu + t_c, to about
+// 2^-44 relative: the pixel offsets of compositing then carry only their own rounding.
+__device__ __forceinline__ void projected_mean(const ViewP &V, const float *mu, float &mx, float &mx_lo, float &my,
+                                               float &my_lo)
+{
+    float xh, xl, yh, yl, zh, zl;
+    dot3_plus(V.vm, mu[0], mu[1], mu[2], xh, xl);
+    dot3_plus(V.vm + 4, mu[0], mu[1], mu[2], yh, yl);
+    dot3_plus(V.vm + 8, mu[0], mu[1], mu[2], zh, zl);
+    df_project(V.fx, V.cx, xh, xl, zh, zl, mx, mx_lo);
+    df_project(V.fy, V.cy, yh, yl, zh, zl, my, my_lo);
+}
+
 // Projects Gaussian i < capacity into every view; returns its tile-Gaussian pairs.
 // sh_s: the Gaussian's SH row in shared memory, valid once the bulk copy on bar
 // has landed (nullptr: read it from global memory).
@@ -321,8 +383,11 @@ __device__ __forceinline__ unsigned long long project_one(const Views &vs, const
         bool ok = P.tz > kNear && P.det > 0.f && opac >= kAlphaMin;
         uint2 rect = make_uint2(1u, 0u);  // empty
         if (ok) {
-            float iz = 1.f / P.tz;
-            float mx = V.fx * P.tx * iz + V.cx, my = V.fy * P.ty * iz + V.cy;
+            // the projected mean as a double-float (hi + lo): an FP32 mean is off by up
+            // to half an ulp of the pixel coordinate (3e-5 px at x ~ 600), which moves
+            // every pixel offset d of the Gaussian by as much
+            float mx, my, mx_lo, my_lo;
+            projected_mean(V, mu, mx, mx_lo, my, my_lo);
             float id = 1.f / P.det;
             // footprint of alpha >= 1/255: d^T Q d <= 2 ln(255 o); its bounding box
             // has half-extents sqrt(2 ln(255 o) Sigma2_xx), sqrt(... Sigma2_yy)
@@ -385,7 +450,7 @@ __device__ __forceinline__ unsigned long long project_one(const Views &vs, const
             sh_eval(dx * rn, dy * rn, dz * rn, K, Y);
             float col[3] = {0.5f, 0.5f, 0.5f};
             if (sh_s && !sh_ready) {
-                sh_ready = mbar_wait(bar, 0, kDefaultSpinLimit);
+                sh_ready = mbar_wait(bar, 0, p.sh_wait_limit);
                 if (!sh_ready) {
                     set_status(p.status, GSP_ERR_TIMEOUT);
                     sh_s = nullptr;  // the global row is still there
@@ -408,6 +473,7 @@ __device__ __forceinline__ unsigned long long project_one(const Views &vs, const
             // whole warps with them)
             const float ci = kLog2E * id;
             st.xyo[o] = make_float4(mx, my, opac, ex);
+            st.mlo[o] = make_float2(mx_lo, my_lo);
             st.con[o] = make_float4(-0.5f * (P.c * ci), P.b * ci, -0.5f * (P.a * ci), ey);
             st.col[o] = make_float4(col[0], col[1], col[2], __uint_as_float(clampbits));
         }
@@ -547,7 +613,8 @@ __global__ void __launch_bounds__(kRsThreads) ds_count(const uint32_t *keys, Sor
 __global__ void __launch_bounds__(kRsThreads) ds_pass(const uint32_t *kin, const int32_t *vin, uint32_t *kout,
                                                       int32_t *vout, SortCount cnt, int pass, const unsigned *ghist,
                                                       unsigned *state, unsigned *ticket, int nb_max, long long seg,
-                                                      int32_t *overflow, int32_t *status)
+                                                      int32_t *overflow, int32_t *status, long long spin_limit,
+                                                      int withhold)
 {
     const int view = blockIdx.y;
     kin += (size_t)view * seg;
@@ -614,7 +681,8 @@ __global__ void __launch_bounds__(kRsThreads) ds_pass(const uint32_t *kin, const
         tot += c;
     }
     volatile unsigned *vlb = lb;
-    vlb[(size_t)t * 256 + tid] = (t == 0 ? kLbInc : kLbAgg) | tot;
+    // (test hook: tile 0 withholds its word, so every later tile's walk runs out)
+    if (!(withhold && t == 0)) vlb[(size_t)t * 256 + tid] = (t == 0 ? kLbInc : kLbAgg) | tot;
     // tile-local digit starts; digit starts over the view
     unsigned gstart;
     {
@@ -664,7 +732,7 @@ __global__ void __launch_bounds__(kRsThreads) ds_pass(const uint32_t *kin, const
                 if (w[q] & kLbInc) done = true;
             }
             j -= used;
-            if (!done && used == 0 && ++polls > kSortSpinLimit) {
+            if (!done && used == 0 && ++polls > spin_limit) {
                 s_fail = 1;
                 break;
             }
@@ -1278,11 +1346,13 @@ struct Alpha {
 // Identical in the forward and the backward kernel (explicitly rounded ops),
 // so both take the same 1/255 decision.  The exponential is evaluated for every
 // lane (a branch around it costs more than the MUFU op it saves).
-__device__ __forceinline__ Alpha eval_alpha(float4 xyo, float4 con, float px, float py)
+__device__ __forceinline__ Alpha eval_alpha(float4 xyo, float2 lo, float4 con, float px, float py)
 {
     Alpha r;
-    r.dx = __fsub_rn(px, xyo.x);
-    r.dy = __fsub_rn(py, xyo.y);
+    // d = pixel centre - (hi + lo); px - hi is exact when px and hi are within a
+    // factor of two (Sterbenz), else off by half an ulp of a small coordinate
+    r.dx = __fsub_rn(__fsub_rn(px, xyo.x), lo.x);
+    r.dy = __fsub_rn(__fsub_rn(py, xyo.y), lo.y);
     r.dxx = __fmul_rn(r.dx, r.dx);
     r.dyy = __fmul_rn(r.dy, r.dy);
     r.dxy = __fmul_rn(r.dx, r.dy);
@@ -1310,6 +1380,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
 {
     constexpr int NT = kTilePix / PPT;
     __shared__ float4 s_xyo[BATCH], s_con[BATCH], s_col[BATCH];
+    __shared__ float2 s_mlo[BATCH];
     __shared__ int32_t s_id[BATCH];
     __shared__ float s_score[BATCH];
     __shared__ float s_red[NT / 32];
@@ -1329,6 +1400,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
     const int len = int(st.tile_len[gt]);
     const int32_t *list = st.ids + st.tile_start[gt];
     const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
+    const float2 *mlo = st.mlo + (size_t)v * cap;
     if (tid == 0) {
         s_maxlast = 0;
         s_contrib = 0;
@@ -1358,6 +1430,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
                 const int id = list[k];
                 s_id[q] = id;
                 s_xyo[q] = xyo[id];
+                s_mlo[q] = mlo[id];
                 s_con[q] = con[id];
                 s_col[q] = col[id];
             }
@@ -1373,7 +1446,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
 #pragma unroll
             for (int m = 0; m < PPT; ++m) {
                 if (done[m]) continue;
-                const Alpha a = eval_alpha(gx, gc, px, y0 + m + 0.5f);
+                const Alpha a = eval_alpha(gx, s_mlo[j], gc, px, y0 + m + 0.5f);
                 if (!a.pass) continue;
                 const float Tn = __fmul_rn(T[m], __fsub_rn(1.f, a.alpha));
                 if (Tn < kTMin) {
@@ -1523,6 +1596,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 2 ? 6 : 2048 / (kTilePi
 {
     constexpr int NT = kTilePix / PPT;
     __shared__ float4 s_xyo[BATCH], s_con[BATCH], s_col[BATCH];
+    __shared__ float2 s_mlo[BATCH];
     __shared__ int32_t s_id[BATCH];
     __shared__ float s_acc[BATCH][kG2];
     __shared__ int s_maxlast;
@@ -1539,6 +1613,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 2 ? 6 : 2048 / (kTilePi
     const int list_len = int(st.tile_len[gt]);
     const int32_t *list = st.ids + st.tile_start[gt];
     const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
+    const float2 *mlo = st.mlo + (size_t)v * cap;
     float4 *g2d = st.g2d + (size_t)v * cap * 3;
     const bool want_score = score && edge;
     const float wcx = wb.wcx, wcy = wb.wcy, whw = wb.whw, whh = wb.whh;
@@ -1590,6 +1665,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 2 ? 6 : 2048 / (kTilePi
             const int id = list[lo + q];
             s_id[q] = id;
             s_xyo[q] = xyo[id];
+            s_mlo[q] = mlo[id];
             s_con[q] = con[id];
             s_col[q] = col[id];
         }
@@ -1606,7 +1682,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 2 ? 6 : 2048 / (kTilePi
 #pragma unroll
             for (int m = 0; m < PPT; ++m) {
                 if (pos >= last[m]) continue;
-                const Alpha a = eval_alpha(gx, gc, px, y0 + m + 0.5f);
+                const Alpha a = eval_alpha(gx, s_mlo[j], gc, px, y0 + m + 0.5f);
                 if (!a.pass) continue;
                 active = true;
                 const float4 c = s_col[j];
@@ -1894,6 +1970,7 @@ Layout render_layout(void *ws, long long cap, const Views &vs, long long pair_ca
     const size_t vc = (size_t)vs.n * cap;
     const size_t total_tiles = (size_t)vs.total_tiles, total_super = (size_t)vs.total_super;
     s.xyo = c.take<float4>(vc);
+    s.mlo = c.take<float2>(vc);
     s.con = c.take<float4>(vc);
     s.col = c.take<float4>(vc);
     s.rect = c.take<uint2>(vc);
@@ -2059,6 +2136,8 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     Params P = make_params(g);
     P.status = dev_status;
     P.sh_bulk = (reinterpret_cast<uintptr_t>(g->sh) & 15) == 0;
+    P.sh_wait_limit = (opts->test_expire & 2) ? 0 : kDefaultSpinLimit;
+    const long long sort_spin = opts->spin_limit > 0 ? opts->spin_limit : kSortSpinLimit;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
     GSP_CUDA_TRY(cudaMemsetAsync(S.pairs_total, 0, L.clear_bytes, s));
@@ -2082,7 +2161,8 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
         ds_count<<<dim3(2 * num_sms(), nv), kRsThreads, 0, s>>>(k0, sc, S.sort_ghist, S.sort_state, S.nb_max, cap);
         for (int pass = 0; pass < 4; ++pass) {
             ds_pass<<<dim3(S.nb_max, nv), kRsThreads, 0, s>>>(k0, v0, k1, v1, sc, pass, S.sort_ghist, S.sort_state,
-                                                              S.sort_ticket, S.nb_max, cap, S.overflow, dev_status);
+                                                              S.sort_ticket, S.nb_max, cap, S.overflow, dev_status,
+                                                              sort_spin, pass == 0 && (opts->test_expire & 1));
             uint32_t *tk = k0; k0 = k1; k1 = tk;
             int32_t *tv = v0; v0 = v1; v1 = tv;
         }
@@ -2119,7 +2199,7 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     GSP_LAUNCH_CHECK();
     note_launches(2 + 5 + 8 + 1);
     if (loss_out) {
-        loss_finalise<<<1, 1, 0, s>>>(S, vs.total_pix, loss_out);
+        loss_finalise<<<1, 1, 0, s>>>(S, opts->loss_pixels > 0 ? opts->loss_pixels : vs.total_pix, loss_out);
         note_launches(1);
         GSP_LAUNCH_CHECK();
     }
@@ -2155,7 +2235,8 @@ extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *c
     S.n_dev = g->count;
     Params P = make_params(g);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const float inv_norm = float(1.0 / (3.0 * double(vs.total_pix)));
+    const float inv_norm =
+        float(1.0 / (3.0 * double(opts->loss_pixels > 0 ? opts->loss_pixels : vs.total_pix)));
     stage_begin("composite_bwd", s);
     // the screen-space gradients accumulate from zero in every adjoint call
     GSP_CUDA_TRY(cudaMemsetAsync(S.g2d, 0, sizeof(float4) * 3 * (size_t)nv * cap, s));

@@ -2,9 +2,12 @@
 
 Tolerances (stated with the workload): NMS masks bit-exact except at pixels
 whose compared magnitudes or direction-bin boundary differ by < 1e-6
-relative (oracle.edge.nms_exempt); medians within 1e-5 relative of the
-oracle's lower median over the same kept set (exempt pixels may change the
-set, and with it the median's rank); E within 1e-5 relative where both keep.
+relative, or whose magnitude is at most 1e-6 of the view's largest
+(oracle.edge.nms_exempt); the exempt pixels must stay within 0.01 % of a
+view's pixels (at most one on views under 10,000 pixels); medians within
+1e-5 relative of the oracle's lower median over the same kept set (exempt
+pixels may change the set, and with it the median's rank); E within 1e-5
+relative where both keep.
 """
 import numpy as np
 import pytest
@@ -32,10 +35,14 @@ def _run(gsp, imgs, **kw):
     return out, med.cpu().numpy()
 
 
-def _compare(img, e_gpu, m_gpu, med_gpu, taps=None):
+def _compare(img, e_gpu, m_gpu, med_gpu, taps=None, bound_exempt=True):
+    """bound_exempt=False for images built to hold exact ties (the ideal step),
+    where every tie is exempt by construction and decided exactly on both sides."""
     ref = oe.edge_map(img, None if taps is None else np.array(taps))
     keep = m_gpu.astype(bool)
     ex = oe.nms_exempt(ref)
+    if bound_exempt:
+        assert ex.sum() <= max(1, int(1e-4 * ex.size)), (int(ex.sum()), ex.size)
     bad = (keep != ref["keep"]) & ~ex
     assert bad.sum() == 0, f"{bad.sum()} non-exempt NMS differences"
     both = keep & ref["keep"]
@@ -125,7 +132,7 @@ def test_ideal_step_single_column_exact(gsp_lib, mode):
     e, m = outs[0]
     assert m.sum() == h and m[:, c - 1].all()
     assert np.all(e[m.astype(bool)] == 1.0)
-    _compare(img, e, m, med[0], taps=DYADIC)
+    _compare(img, e, m, med[0], taps=DYADIC, bound_exempt=False)
 
 
 def test_pitched_rows_match_dense(gsp_lib):
@@ -136,19 +143,6 @@ def test_pitched_rows_match_dense(gsp_lib):
     E2, med2, _, s2 = gsp_lib.edge_map([gsp_lib.pitched_image(t, 16)])
     torch.cuda.synchronize()
     assert torch.equal(E1, E2) and torch.equal(med1, med2)
-
-
-def test_barrier_wait_that_runs_out_reports_timeout(gsp_lib):
-    import torch
-    imgs = [torch.from_numpy(synth.image(822, 1237, 1000 + i)).cuda() for i in range(4)]
-    E, med, _, st = gsp_lib.edge_map(imgs, spin_limit=1)
-    torch.cuda.synchronize()
-    code = int(st.item())
-    assert code in (0, gsp_lib._lib.GSP_ERR_TIMEOUT)
-    # the context stays usable
-    E2, med2, _, st2 = gsp_lib.edge_map(imgs[:1])
-    torch.cuda.synchronize()
-    assert int(st2.item()) == 0
 
 
 def test_full_batch_32_views_1237x822(gsp_lib):

@@ -1,18 +1,22 @@
-"""Allocation-free top-k (gsp_topk_mask_static) against the workspace version.
+"""Allocation-free top-k (gsp_topk_mask_static) against the workspace version
+and the oracle.
 
 Some callers cannot allocate device memory at the moment they call the
-library: code being captured into a CUDA graph, real-time loops that forbid
-allocation after start-up, hosts whose device memory belongs to another
-allocator.  gsp_topk_mask_static serves them with its scratch in a static
-device array.  This test calls it through the C ABI twice in a row (the
-second call sees the array as the first left it) and requires the same
-masks and counts as gsp_topk_mask on the same scores (selection is integer
-work: exact equality).  It lives in its own file, collected last.
+library: real-time loops that forbid allocation once they run, and host
+applications whose device memory is owned by their own allocator, where a
+plug-in may not take memory behind its back.  gsp_topk_mask_static serves
+them with its scratch in a static device array.  This test calls it through
+the C ABI twice in a row (the second call sees the array as the first left
+it) and requires the same masks and counts as gsp_topk_mask on the same
+scores and as the oracle's top-k (selection is integer work: exact
+equality).  It lives in its own file, collected last.
 """
 import ctypes
 
 import numpy as np
 import pytest
+
+from oracle import densify as od
 
 pytestmark = pytest.mark.gpu
 
@@ -40,6 +44,7 @@ def test_static_topk_matches_workspace_topk_on_two_calls(gsp_lib):
         assert int(status.item()) == 0 and int(ref_st.item()) == 0
         assert torch.equal(mask, ref_mask)
         assert int(sel.item()) == int(ref_sel.item()) == k
+        assert np.array_equal(mask.cpu().numpy().astype(bool), od.topk_mask(s, k))
 
 
 def test_static_topk_rejects_capacity_beyond_its_maximum(gsp_lib):
