@@ -24,35 +24,56 @@ def build_gsp() -> str:
     return mod.build()
 
 
-# Gradient groups compared per Gaussian as vectors: their components mix under
-# rotations (world and camera axes, the quaternion's tangent projection), so a
-# single component can be small by cancellation (e.g. a quaternion entry of a
-# nearly isotropic Gaussian) while the vector is well determined.
-VECTOR_GROUPS = ("means", "log_scales", "quats")
+# Gradient parity (CUDA adjoint against the oracle's analytic adjoint), per
+# entry: |gpu - oracle| <= GRAD_TOL * max(|oracle|, GRAD_FLOOR * RMS) +
+# GRAD_ROUND * u * A, with u = 2^-24 and A the oracle's magnitude adjoint of
+# that entry (the sum of the absolute values of the terms the adjoint adds up).
+# The first part is the stated 1e-4 relative tolerance with a floor of 1e-3 x
+# the RMS of the parameter group.  The second is the rounding bound of an
+# FP32 evaluation: where an entry is a sum whose terms cancel (A >> |entry|),
+# terms computed in FP32 with relative errors of a few u, summed in FP32 over
+# the n tiles and views a Gaussian covers (about sqrt(n) u A for that sum),
+# move it by tens of u A whatever the implementation.  Measured beyond the
+# relative part: at most 0.82 u A on 32x32-pixel regions of 1M and 3M-Gaussian
+# scenes (8 views), 17 u A on whole-view L1 gradients summed over 8 views;
+# GRAD_ROUND = 64 keeps a margin of almost 4 over the largest.
+U32 = 2.0 ** -24
+GRAD_TOL, GRAD_FLOOR, GRAD_ROUND = 1e-4, 1e-3, 64.0
 
 
-def grad_rel(name, a, b, floor):
-    """Relative gradient error per row (Gaussian): for the vector groups
-    max_j |a_ij - b_ij| / max(max_j |b_ij|, floor), else elementwise
-    |a - b| / max(|b|, floor).  floor is absolute (callers pass a multiple of
-    the group's RMS)."""
-    a = np.asarray(a, dtype=np.float64).reshape(a.shape[0], -1)
-    b = np.asarray(b, dtype=np.float64).reshape(b.shape[0], -1)
-    if name in VECTOR_GROUPS:
-        return np.abs(a - b).max(axis=1) / np.maximum(np.abs(b).max(axis=1), floor)
-    return np.abs(a - b) / np.maximum(np.abs(b), floor)
+def grad_bound(b, mag, rms):
+    """Allowed |gpu - oracle| per entry (see above); b and mag shaped alike."""
+    return GRAD_TOL * np.maximum(np.abs(b), GRAD_FLOOR * rms) + GRAD_ROUND * U32 * mag
 
 
-def assert_grads_close(name, a, b, floor, tol=1e-4, tail_tol=1e-3, tail_frac=1e-3):
-    """Gradient parity on a large scene: all but max(2, tail_frac x rows) rows
-    within tol (grad_rel), every row within tail_tol.  FP32 back-to-front
-    replay (transmittance by division, colour behind by recursion) leaves a
-    tail of entries dominated by cancellation."""
-    rel = grad_rel(name, a, b, floor)
-    rows = rel.reshape(rel.shape[0], -1).max(axis=1) if rel.size else rel
-    beyond = int((rows > tol).sum())
-    allowed = max(2, int(tail_frac * rows.size))
-    assert beyond <= allowed and rel.max(initial=0) <= tail_tol, (name, beyond, rows.size, float(rel.max(initial=0)))
+def assert_grads_match(name, a, b, mag, rms=None):
+    """Every entry of a (CUDA) within grad_bound of b (oracle), elementwise.
+    mag: the oracle's magnitude adjoint; rms: the group RMS (default: of b).
+    Returns the largest error / bound ratio."""
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    mag = np.asarray(mag, dtype=np.float64).reshape(-1)
+    if b.size == 0:
+        return 0.0
+    if rms is None:
+        rms = float(np.sqrt(np.mean(b ** 2)))
+    err = np.abs(a - b)
+    ratio = err / np.maximum(grad_bound(b, mag, rms), 1e-300)
+    w = int(np.argmax(ratio))
+    assert ratio[w] <= 1.0, (name, int((ratio > 1).sum()), b.size, float(ratio[w]), float(err[w]), float(b[w]),
+                             float(mag[w]), rms)
+    return float(ratio[w])
+
+
+# Gate exemption (rendering): a pixel whose oracle evaluation meets a gate
+# (alpha = 1/255, or T (1 - alpha) = 1e-4) within GATE_REL relative may take
+# that decision differently in FP32: alpha carries about (4 |power| + 3) u of
+# rounding from the FP32 conic, pixel offset and exponential (|power| <= ln 255
+# at the 1/255 gate), 25 u = 1.5e-6.  Such pixels, and the Gaussians whose
+# results a flip there would move, are exempt; their number must stay below
+# EXEMPT_FRAC of the pixels compared.
+GATE_REL = 2e-6
+EXEMPT_FRAC = 1e-4
 
 
 @pytest.fixture(scope="session")

@@ -9,13 +9,15 @@ whole view), checked on sampled outputs the FP64 oracle computes directly.
   is exactly the sum the oracle's region renders give.
 * The score invariant at full size: with E = 1 the scores sum to sum(1 - T).
 * Gradients of every Gaussian against the oracle's analytic adjoint for an
-  upstream gradient that lives on one region: 1e-4 relative for all but
-  max(2, 0.1 %) of the Gaussians, 1e-3 for all (conftest.assert_grads_close).
+  upstream gradient that lives on one region, entry by entry: 1e-4 relative
+  (floor 1e-3 x the group RMS) plus the FP32 rounding bound of cancelling
+  sums (conftest.grad_bound).
 * Central finite differences of the L1 loss restricted to 25 separated
   regions, on a 1,000-Gaussian subset x 8 scalars, within 1e-3 relative
   (kinks excluded).
 Pixels at which the oracle meets a gate within GATE_REL are exempt, and so
-are the Gaussians whose results such a flip would move.
+are the Gaussians whose results such a flip would move; they must stay within
+EXEMPT_FRAC of the pixels compared.
 """
 import concurrent.futures as cf
 import multiprocessing as mp
@@ -25,7 +27,7 @@ import numpy as np
 import pytest
 
 import synth
-from conftest import assert_grads_close
+from conftest import EXEMPT_FRAC, GATE_REL, assert_grads_match
 from oracle import edge as oe
 from oracle import raster as orc
 
@@ -33,7 +35,6 @@ pytestmark = pytest.mark.gpu
 
 N, W, H = 1_000_000, 1237, 822
 CAP = N + N // 10
-GATE_REL = 2e-5
 REGIONS = [(608, 400, 640, 432), (477, 253, 509, 285), (1205, 790, 1237, 822)]
 GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 FD_SCALARS = [("means", 0), ("means", 2), ("log_scales", 0), ("quats", 0), ("quats", 2), ("opacity_logits", 0),
@@ -86,16 +87,19 @@ def test_1m_regions_rgb_T_and_every_score(gsp_lib, scene):
     T = out["T"].cpu().numpy().reshape(H, W)
     s_ref = np.zeros(N)
     gap = np.full((H, W), np.inf)
+    n_ex = n_px = 0
     for reg in REGIONS:
         x0, y0, x1, y1 = reg
         ref = orc.render(g, cam, edge=e32.astype(np.float64), region=reg, proj=proj, order=order)
         ok = ref["gate_gap"][y0:y1, x0:x1] >= GATE_REL
-        assert (~ok).sum() <= 2
+        n_ex += int((~ok).sum())
+        n_px += ok.size
         err = np.abs(rgb[y0:y1, x0:x1] - ref["rgb"][y0:y1, x0:x1]).max(axis=2)
         assert err[ok].max(initial=0) <= 1e-4
         assert np.abs(T[y0:y1, x0:x1] - ref["T"][y0:y1, x0:x1])[ok].max(initial=0) <= 1e-4
         s_ref += ref["score"]
         gap[y0:y1, x0:x1] = ref["gate_gap"][y0:y1, x0:x1]
+    assert n_ex <= EXEMPT_FRAC * n_px, (n_ex, n_px)
     assert np.all(rgb[790:, 1205:] == 0) and np.all(T[790:, 1205:] == 1)  # outside the scene
     skip = _exempt_gaussians(proj, order, gap)
     s_gpu = score.cpu().numpy()[:N].astype(np.float64)
@@ -129,7 +133,11 @@ def test_1m_region_gradients_match_oracle_adjoint(gsp_lib, scene):
     grads = r.backward(out, dL_drgb=torch.from_numpy(dl.astype(np.float32).reshape(-1, 3)).cuda())
     torch.cuda.synchronize()
     ref = orc.render(g, cam, region=REGIONS[0], proj=proj, order=order)
-    gr = orc.render_bwd(g, cam, dl.astype(np.float32).astype(np.float64), proj=proj, region=REGIONS[0])
+    dl64 = dl.astype(np.float32).astype(np.float64)
+    gr = orc.render_bwd(g, cam, dl64, proj=proj, region=REGIONS[0])
+    gm = orc.render_bwd(g, cam, dl64, proj=proj, region=REGIONS[0], magnitude=True)
+    x0, y0, x1, y1 = REGIONS[0]
+    assert (ref["gate_gap"][y0:y1, x0:x1] < GATE_REL).sum() <= EXEMPT_FRAC * (x1 - x0) * (y1 - y0)
     skip = _exempt_gaussians(proj, order, ref["gate_gap"])
     touched = np.abs(gr["opacity_logits"]) > 0
     assert touched.sum() > 100
@@ -138,8 +146,7 @@ def test_1m_region_gradients_match_oracle_adjoint(gsp_lib, scene):
         a = grads[name][:N].cpu().numpy().astype(np.float64).reshape(N, -1)
         b = gr[name].reshape(N, -1)
         assert np.all(a[~touched & ~skip] == 0)
-        rms = np.sqrt(np.mean(b[keep] ** 2))
-        assert_grads_close(name, a[keep], b[keep], 1e-2 * rms)
+        assert_grads_match(name, a[keep], b[keep], gm[name].reshape(N, -1)[keep])
 
 
 def _fd_chunk(args):
@@ -239,6 +246,7 @@ def test_1m_finite_differences_on_a_1000_gaussian_subset(gsp_lib, scene):
         gap[y0:y1, x0:x1] = ref["gate_gap"][y0:y1, x0:x1]
         # pixels whose colour is within 1e-5 of the target: their L1 sign is not fixed
         mask[y0:y1, x0:x1] &= ~(np.abs(ref["rgb"][y0:y1, x0:x1] - t[y0:y1, x0:x1]) < 1e-5).any(axis=2)
+    assert (gap[mask] < GATE_REL).sum() <= EXEMPT_FRAC * mask.sum()
     mask &= gap >= GATE_REL
     skip = _exempt_gaussians(proj, order, gap)
     gs, r = _renderer(gsp_lib, g, cam)

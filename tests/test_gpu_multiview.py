@@ -5,27 +5,26 @@ captured as a CUDA graph, with the compositing variants the autotuner picks.
 Checked on sampled outputs the FP64 oracle computes directly: RGB and T_final
 (1e-4 absolute) on a 32x32 region of every view, the per-Gaussian edge score
 summed over the views (1e-4 relative, every Gaussian; the edge map lives on
-the regions), and every gradient for an upstream gradient on those regions
-(1e-4 relative for all but max(2, 0.1 %) of the Gaussians, 1e-3 for all, floor 1e-2 x the
-RMS of the group, vector groups per Gaussian: conftest.assert_grads_close)
-view by view, the
+the regions), and every gradient entry for an upstream gradient on those
+regions (1e-4 relative, floor 1e-3 x the RMS of the group, plus the FP32
+rounding bound of cancelling sums: conftest.grad_bound) view by view, the
 batched launch given an upstream gradient on one view at a time; the
 all-view gradient must then match the sum of the per-view ones by the same
-criterion (both are FP32 sums of the same terms in different orders).  Also: the compositing variants agree with each other, and
+criterion (both are FP32 sums of the same terms in different orders).  Gate-
+exempt pixels stay within EXEMPT_FRAC of the pixels compared.  Also: the compositing variants agree with each other, and
 a graph replay reproduces the eager results bit for bit.
 """
 import numpy as np
 import pytest
 
 import synth
-from conftest import assert_grads_close
+from conftest import EXEMPT_FRAC, GATE_REL, assert_grads_match
 from oracle import raster as orc
 
 pytestmark = pytest.mark.gpu
 
 N_MV = 3_000_000
 V = 8
-GATE_REL = 2e-5
 GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 
 
@@ -111,7 +110,8 @@ def test_3m_eight_uneven_views_graph_autotuned(gsp_lib, mv_scene):
     grads_all = {k: v.clone() for k, v in grads.items()}
     s_ref = np.zeros(N_MV)
     skip = np.zeros(N_MV, bool)
-    per_view = []
+    per_view, per_mag = [], []
+    n_ex = n_px = 0
     for v, (cam, off, proj, order) in enumerate(zip(cams, offs, projs, orders)):
         w, h = int(cam["width"]), int(cam["height"])
         reg = _region(cam)
@@ -119,6 +119,8 @@ def test_3m_eight_uneven_views_graph_autotuned(gsp_lib, mv_scene):
         ev = e[off:off + w * h].reshape(h, w).astype(np.float64)
         ref = orc.render(g, cam, edge=ev, region=reg, proj=proj, order=order)
         ok = ref["gate_gap"][y0:y1, x0:x1] >= GATE_REL
+        n_ex += int((~ok).sum())
+        n_px += ok.size
         got = rgb[off:off + w * h].reshape(h, w, 3)[y0:y1, x0:x1]
         assert np.abs(got - ref["rgb"][y0:y1, x0:x1]).max(axis=2)[ok].max(initial=0) <= 1e-4
         gotT = T[off:off + w * h].reshape(h, w)[y0:y1, x0:x1]
@@ -126,9 +128,11 @@ def test_3m_eight_uneven_views_graph_autotuned(gsp_lib, mv_scene):
         s_ref += ref["score"]
         dlv = dl[off:off + w * h].reshape(h, w, 3).astype(np.float64)
         gr = orc.render_bwd(g, cam, dlv, proj=proj, region=reg)
+        per_mag.append(orc.render_bwd(g, cam, dlv, proj=proj, region=reg, magnitude=True))
         if (~ok).any():
             skip |= orc.gate_affected(proj, ref["gate_gap"] < GATE_REL, GATE_REL, order)
         per_view.append(gr)
+    assert n_ex <= EXEMPT_FRAC * n_px, (n_ex, n_px)
     floor = 1e-3 * np.abs(s_ref).max()
     rel = np.abs(s_gpu - s_ref) / np.maximum(np.abs(s_ref), floor)
     assert (s_ref > 0).sum() > 500
@@ -142,7 +146,8 @@ def test_3m_eight_uneven_views_graph_autotuned(gsp_lib, mv_scene):
     rows = np.nonzero(touched)[0]
     rows_t = torch.from_numpy(rows).cuda()
     sum_v = {k: 0.0 for k in GROUPS}
-    for v, (off, gr) in enumerate(zip(offs, per_view)):
+    mag_v = {k: 0.0 for k in GROUPS}
+    for v, (off, gr, gm) in enumerate(zip(offs, per_view, per_mag)):
         w, h = int(cams[v]["width"]), int(cams[v]["height"])
         dlv = torch.zeros_like(dL)
         dlv[off:off + w * h] = dL[off:off + w * h]
@@ -152,13 +157,14 @@ def test_3m_eight_uneven_views_graph_autotuned(gsp_lib, mv_scene):
         for k in GROUPS:
             a = gv[k][rows_t].cpu().numpy().reshape(rows.size, -1).astype(np.float64)
             b = gr[k][rows].reshape(rows.size, -1)
+            m = gm[k][rows].reshape(rows.size, -1)
             kv = tv[rows]
-            rms = np.sqrt(np.mean(b[kv] ** 2))
-            assert_grads_close(k, a[kv], b[kv], 1e-2 * rms)
+            assert_grads_match(k, a[kv], b[kv], m[kv])
             sum_v[k] = sum_v[k] + a
+            mag_v[k] = mag_v[k] + m
     for k in GROUPS:
         a = grads_all[k][rows_t].cpu().numpy().reshape(rows.size, -1).astype(np.float64)
-        assert_grads_close(k, a, sum_v[k], 1e-2 * np.sqrt(np.mean(sum_v[k] ** 2)))
+        assert_grads_match(k, a, sum_v[k], mag_v[k])
         mask = torch.ones(N_MV, dtype=torch.bool, device="cuda")
         mask[rows_t] = False
         assert bool((grads_all[k][mask] == 0).all())
