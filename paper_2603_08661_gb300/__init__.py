@@ -9,6 +9,8 @@ The compute lives in libgsp.so (C ABI, include/gsp.h), built for sm_103a by
 * GaussianRenderL1    - torch.autograd.Function over the forward / adjoint
 * autotune.tune       - picks the fastest compositing variants for a workload
 * DensifyLoop         - device-resident loop: fwd/L1/bwd+score/SGD, top-k + LAS events
+* ShardedRenderer     - view-sharded forward/adjoint over the ranks of a process
+                        group, one all-reduce of gradients, scores and loss
 
 Importing fails loudly when libgsp.so is missing; there is no CPU fallback.
 """
@@ -22,3 +24,4 @@ from .api import (LAS_CONFIG, LAS_PAPER, GaussianSet, Renderer, StageTimer, came
 from .autograd import GaussianRenderL1  # noqa: E402,F401
 from . import autotune  # noqa: E402,F401
 from .loop import DensifyLoop  # noqa: E402,F401
+from .sharded import FlatGrads, ShardedRenderer, all_reduce_flat, partition_views  # noqa: E402,F401
