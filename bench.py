@@ -14,8 +14,9 @@ rewrites them in place), so every step sees the identical scene; a copy is
 needed.  The plain path (edge map one launch per stage, score accumulated in
 the forward, no CUDA graph) is timed beside it on the same GPU.
 
-`--impl reference` times the FP64 CPU oracle on the host cores instead, each
-step a bounded pixel-region sample of the same workload scaled to the view.
+`--impl reference` times the FP64 CPU oracle on the host cores instead: every
+step is one whole step of the same workload, the view's pixel rows spread
+over one process per host core.
 """
 from __future__ import annotations
 
@@ -436,8 +437,7 @@ def run_gsp(args, rank, world):
         restore(copies[0], pristine)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(g, cam, tgt_np, stripes=4)
-        cpu.pop("fixed", None)
+        cpu = cpu_baseline(n)
 
     line = {
         "metric": METRIC, "value": round(ms_step / world, 4), "unit": "ms/iter", "n_gpus": world,
@@ -643,6 +643,46 @@ def run_multiview(steps=5, warmup=3):
             "steps": steps}
 
 
+def run_multiview_sharded(rank, world, steps=5, warmup=3):
+    """The 3M-Gaussian, 8-view workload sharded over the ranks by view
+    (paper_2603_08661_gb300.sharded): each rank renders its share (forward + L1 +
+    adjoint with the edge score), then one all-reduce (sum) of gradients, scores
+    and loss.  Total work is fixed as the ranks grow (strong scaling); the time
+    is the max over ranks."""
+    import torch
+
+    import paper_2603_08661_gb300 as gsp
+    import synth
+    n, nv = 3_000_000, 8
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    g = synth.gaussians(n, 3, seed=1)
+    cams = [synth.camera_ring(k, nv) for k in range(nv)]
+    gs = gsp.GaussianSet.from_arrays(g, capacity=n, device=dev)
+    del g
+    targets = [torch.from_numpy(synth.image(c["height"], c["width"], 2000 + k)).to(dev) for k, c in enumerate(cams)]
+    E, _, _, _ = gsp.edge_map(targets)
+    views = gsp.partition_views([c["width"] * c["height"] for c in cams], world)[rank]
+    pairs = _probe_pairs(gsp, gs, [cams[v] for v in views]) if views else 1
+    sr = gsp.ShardedRenderer(gs, cams, pair_capacity=int(pairs * 1.02) + 4096, device=dev)
+    for _ in range(warmup):
+        sr.step(targets, edge=E)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        sr.step(targets, edge=E)
+    b.record()
+    torch.cuda.synchronize()
+    ms = dist_max(a.elapsed_time(b) / steps, world)
+    if sr.r is not None:
+        gsp.raise_on_device_status(sr.status, "multiview sharded")
+    return {"workload": "3M Gaussians SH3, 8 ring views 640x480..1920x1080 sharded by view over the ranks: "
+                        "fwd + L1 + bwd + edge score, one all-reduce of gradients, scores and loss",
+            "ranks": world, "views_of_rank0": views if rank == 0 else None, "ms_per_iter": round(ms, 3),
+            "allreduce_bytes": int(sr.out.flat.numel() * 4), "scaling": "strong", "steps": steps}
+
+
 def run_densify_loop(iterations=200, warmup=3):
     """500K -> 1M Gaussians (SH degree 0, as the tiny configuration) on 4 ring
     views of 1237x822: 200 graph-replayed iterations of fwd + L1 + bwd with the
@@ -684,128 +724,200 @@ def run_densify_loop(iterations=200, warmup=3):
 
 # --------------------------------------------------------------- oracle
 
-def oracle_projection(g, cam):
-    """Projection and compositing order of all Gaussians in the oracle, and its time."""
-    from oracle import raster as orc
-    a = time.perf_counter()
-    proj = orc.project(g, cam)
-    order = orc.order(proj)
-    return proj, order, time.perf_counter() - a
+_ORC = {}  # per-process inputs of the oracle step (set in pool workers and in the serial path)
 
 
-def cpu_baseline(g, cam, tgt_np, stripes=4, proj_order=None, phase=0.5, fixed=None):
-    """Time the FP64 oracle on a bounded sample of one step.
+def _orc_init(n_gauss):
+    """Pool worker: the step's inputs, made from the same seeds as the GPU leg."""
+    import synth
+    _ORC["g"] = synth.gaussians(n_gauss, SH_DEGREE, seed=1)
+    _ORC["cam"] = synth.camera_front(WIDTH, HEIGHT)
+    _ORC["t"] = synth.image(HEIGHT, WIDTH, 2000) / 255.0
 
-    Whole view or all Gaussians: the projection, the compositing order, the
-    top-k and the edge map.  Sampled: the forward composite and the analytic
-    adjoint on `stripes` full-width pixel stripes at evenly spaced rows, each
-    call made at two stripe heights (2 and 10 rows): the difference gives the
-    cost per pixel, the rest is the call's fixed cost (the oracle sorts and
-    bins all Gaussians per call), counted once for the whole view.  The LAS
-    runs on 1000 and 20000 of the selected the same way (its fixed cost is a
-    copy of every parameter array).  proj_order: the oracle's
-    projection, order and their time, when already computed; fixed: the
-    measured times (s) of the edge map, top-k and LAS, when already measured
-    (they do not depend on the sampled rows)."""
+
+def _orc_attach(spec):
+    from multiprocessing import shared_memory
+
+    import numpy as np
+    shm = shared_memory.SharedMemory(name=spec[0])
+    return shm, np.ndarray(spec[1], dtype=spec[2], buffer=shm.buf)
+
+
+def _orc_stripe(task):
+    """Rows [y0, y1) of the view through the oracle as it stands: forward
+    composite with the edge score, L1 sign, analytic adjoint.  Returns the
+    gradient rows of the Gaussians the stripe touches, its score entries and
+    its part of the L1 sum."""
     import numpy as np
 
-    from oracle import densify as od
-    from oracle import edge as oe
     from oracle import raster as orc
-
-    h, w = tgt_np.shape[:2]
-    t = tgt_np / 255.0
-    proj, order, t_proj = proj_order if proj_order is not None else oracle_projection(g, cam)
-    rows = [min(int((j + phase) * h / stripes), h - 10) for j in range(stripes)]
-
-    def sample(hs):
-        tf = tb = 0.0
-        for y0 in rows:
-            reg = (0, y0, w, min(h, y0 + hs))
-            b = time.perf_counter()
-            out = orc.render(g, cam, region=reg, proj=proj, order=order)
-            c = time.perf_counter()
-            dl = np.zeros((h, w, 3))
-            dl[reg[1]:reg[3]] = np.sign(out["rgb"][reg[1]:reg[3]] - t[reg[1]:reg[3]]) / (3.0 * w * h)
-            d = time.perf_counter()
-            orc.render_bwd(g, cam, dl, proj=proj, region=reg)
-            tb += time.perf_counter() - d
-            tf += c - b
-        return tf / stripes, tb / stripes
-
-    if fixed is None:
-        a = time.perf_counter()
-        oe.edge_map(tgt_np)
-        t_edge = time.perf_counter() - a
-    h1, h2 = 2, 10
-    f1, b1 = sample(h1)
-    f2, b2 = sample(h2)
-    npix = w * h
-
-    def whole(c1, c2):
-        per_px = max(c2 - c1, 0.0) / ((h2 - h1) * w)
-        fixed = max(c1 - per_px * h1 * w, 0.0)
-        return fixed + per_px * npix
-
-    t_fwd, t_bwd = whole(f1, f2), whole(b1, b2)
+    y0, y1, specs = task
+    t_begin = time.perf_counter()
+    g, cam, t = _ORC["g"], _ORC["cam"], _ORC["t"]
+    held = [_orc_attach(sp) for sp in specs]
+    proj, order, E = (a for _, a in held)
+    try:
+        reg = (0, y0, WIDTH, y1)
+        out = orc.render(g, cam, edge=E, region=reg, proj=proj, order=order)
+        d = out["rgb"][y0:y1] - t[y0:y1]
+        dl = np.zeros((HEIGHT, WIDTH, 3))
+        dl[y0:y1] = np.sign(d) / (3.0 * WIDTH * HEIGHT)
+        gr = orc.render_bwd(g, cam, dl, proj=proj, region=reg)
+    finally:
+        for shm, _ in held:
+            shm.close()
     n = g["means"].shape[0]
-    k = int(SPLIT_FRACTION * n)
-    sub = min(20000, k)
-    if fixed is None:
-        scores = np.random.default_rng(0).gamma(2.0, 1.0, n)
-        a = time.perf_counter()
-        m = od.topk_mask(scores, k)
-        t_topk = time.perf_counter() - a
-        picked = np.nonzero(m)[0]
-        las_t = []
-        for sz in (min(1000, k), sub):
-            sel = np.zeros(n, bool)
-            sel[picked[:sz]] = True
-            a = time.perf_counter()
-            od.las_split(g, sel, **od.CONFIG_PRESET)
-            las_t.append(time.perf_counter() - a)
-        per_item = max(las_t[1] - las_t[0], 0.0) / max(sub - min(1000, k), 1)
-        t_las = max(las_t[0] - per_item * min(1000, k), 0.0) + per_item * k
-    else:
-        t_edge, t_topk, t_las = fixed
-    ms = 1e3 * (t_edge + t_proj + t_fwd + t_bwd + t_topk + t_las)
-    return {"value": round(ms, 1), "unit": "ms/iter", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle, one core: projection, order, top-k and edge map over all Gaussians and the "
-                      f"whole view; forward composite and analytic adjoint on {stripes} full-width stripes of 2 and "
-                      f"10 rows (per-pixel "
-                      f"cost from the difference, fixed per-call cost counted once), scaled to {w}x{h}; LAS of "
-                      f"{sub} of {k} selected, scaled",
-            "parts_s": {"edge": round(t_edge, 3), "project_order": round(t_proj, 3), "forward": round(t_fwd, 3),
-                        "adjoint": round(t_bwd, 3), "topk": round(t_topk, 3), "las": round(t_las, 3)},
-            "fixed": (t_edge, t_topk, t_las)}
+    touched = np.zeros(n, bool)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        touched |= (gr[k].reshape(n, -1) != 0).any(axis=1)
+    idx = np.flatnonzero(touched)
+    sidx = np.flatnonzero(out["score"])
+    return (idx, {k: gr[k].reshape(n, -1)[idx] for k in ("means", "log_scales", "quats", "opacity_logits", "sh")},
+            sidx, out["score"][sidx], float(np.abs(d).sum()), time.perf_counter() - t_begin)
+
+
+class OracleStep:
+    """One whole step of the hot path through the FP64 oracle, on `workers`
+    host processes: the edge map of the target, projection and compositing
+    order of all Gaussians, the forward composite with the edge score, the L1
+    loss and the analytic adjoint over every pixel of the view (full-width row
+    stripes spread over the workers, their gradient rows and scores summed),
+    the top-10 % selection and the Long-Axis-Split.  The oracle's code runs as
+    it stands; only the pixel rows are divided among processes (spawned, so
+    that a process that has used the GPU can host them)."""
+
+    def __init__(self, n_gauss, workers, stripes_per_worker=1):
+        import multiprocessing as mp
+
+        import numpy as np
+        _orc_init(n_gauss)
+        self.n = n_gauss
+        self.workers = max(1, int(workers))
+        self.stripes_per_worker = int(stripes_per_worker)
+        self.pool = None
+        if self.workers > 1:
+            self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_orc_init, initargs=(n_gauss,))
+            self.pool.map(abs, range(self.workers))  # every worker has made its inputs
+        k_sh = (SH_DEGREE + 1) ** 2
+        self.cols = {"means": 3, "log_scales": 3, "quats": 4, "opacity_logits": 1, "sh": 3 * k_sh}
+        self.grads = {k: np.zeros((n_gauss, c)) for k, c in self.cols.items()}
+        self.score = np.zeros(n_gauss)
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+
+    def step(self):
+        """Seconds of one whole step (all of its parts measured, nothing scaled)."""
+        from multiprocessing import shared_memory
+
+        import numpy as np
+
+        import synth
+        from oracle import densify as od
+        from oracle import edge as oe
+        from oracle import raster as orc
+        parallel = self.pool is not None
+        g, cam = _ORC["g"], _ORC["cam"]
+        tgt_u8 = synth.image(HEIGHT, WIDTH, 2000)
+        t0 = time.perf_counter()
+        E = oe.edge_map(tgt_u8)["E"]
+        proj = orc.project(g, cam)
+        order = orc.order(proj)
+        t1 = time.perf_counter()
+        shms, specs = [], []
+        for arr in (proj, order, E):
+            shm = shared_memory.SharedMemory(create=True, size=max(arr.nbytes, 1))
+            np.ndarray(arr.shape, dtype=arr.dtype, buffer=shm.buf)[...] = arr
+            shms.append(shm)
+            specs.append((shm.name, arr.shape, arr.dtype.str))
+        nstripes = self.stripes_per_worker * self.workers if parallel else 1
+        edges = [round(i * HEIGHT / nstripes) for i in range(nstripes + 1)]
+        tasks = [(edges[i], edges[i + 1], specs) for i in range(nstripes) if edges[i + 1] > edges[i]]
+        try:
+            parts = (self.pool.map(_orc_stripe, tasks, chunksize=1) if parallel
+                     else [_orc_stripe(tk) for tk in tasks])
+        finally:
+            for shm in shms:
+                shm.close()
+                shm.unlink()
+        for k in self.grads:
+            self.grads[k].fill(0.0)
+        self.score.fill(0.0)
+        loss = 0.0
+        busy = 0.0
+        for idx, rows, sidx, svals, l1, dt in parts:
+            for k in self.grads:
+                self.grads[k][idx] += rows[k]
+            self.score[sidx] += svals
+            loss += l1
+            busy += dt
+        t2 = time.perf_counter()
+        k_split = int(SPLIT_FRACTION * self.n)
+        mask = od.topk_mask(self.score, k_split)
+        od.las_split(g, mask, **od.CONFIG_PRESET)
+        t3 = time.perf_counter()
+        self.loss = loss / (3.0 * WIDTH * HEIGHT)
+        # busy seconds of every process: the step's CPU time, i.e. one core's share of work
+        self.cpu_seconds = (t1 - t0) + busy + (t3 - t2)
+        return t3 - t0, {"edge_project_order": round(t1 - t0, 3), "render_adjoint": round(t2 - t1, 3),
+                         "topk_las": round(t3 - t2, 3), "stripes": len(tasks),
+                         "stripe_busy_s": round(busy, 3)}
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(n_gauss):
+    """The FP64 oracle timed on the host cores in the GPU run: one whole step on
+    every core (the value) and its CPU time, the busy seconds of all processes
+    summed (what one core spends on the step)."""
+    cores = host_cores()
+    o = OracleStep(n_gauss, cores)
+    try:
+        t_all, parts_all = o.step()
+    finally:
+        o.close()
+    return {"value": round(1e3 * t_all, 1), "unit": "ms/iter", "cores": cores, "kind": "oracle",
+            "sample": f"one whole step (edge map, projection, forward composite with edge score, L1, analytic "
+                      f"adjoint over all {WIDTH}x{HEIGHT} pixels, top-10% selection, LAS) of the FP64 oracle on "
+                      f"{cores} host processes (one pixel-row stripe each), measured, nothing scaled",
+            "cpu_seconds_per_step": round(o.cpu_seconds, 1), "parts_s": parts_all}
 
 
 def run_reference(args, rank, world):
-    """The reference arm: the FP64 oracle as it stands, one bounded sample of
-    the workload per step (one stripe at two heights), on one host core,
-    rank 0 only."""
+    """The reference arm: the FP64 oracle as it stands, one whole step of the
+    workload per step, on every host core (rank 0 only)."""
     if rank != 0:
         return None
-    g, cam, tgt = make_inputs(args.gaussians)
-    # the projection and order of all Gaussians, and the whole-view parts
-    # (edge map, top-k, LAS), are measured once; their time is part of every
-    # step's estimate
-    po = oracle_projection(g, cam)
-    vals, last, fixed = [], None, None
-    for i in range(args.warmup + args.steps):
-        # one stripe per step, cycling through 8 evenly spaced rows
-        last = cpu_baseline(g, cam, tgt, stripes=1, proj_order=po, phase=((i % 8) + 0.5) / 8.0, fixed=fixed)
-        fixed = last["fixed"]
-        if i >= args.warmup:
-            vals.append(last["value"])
+    cores = host_cores()
+    o = OracleStep(args.gaussians, cores)
+    vals = []
+    try:
+        for i in range(args.warmup + args.steps):
+            t, parts = o.step()
+            if i >= args.warmup:
+                vals.append(1e3 * t)
+    finally:
+        o.close()
     v = statistics.mean(vals)
+    sample = (f"whole steps of the FP64 oracle (edge map, projection, forward composite with edge score, L1, "
+              f"analytic adjoint over all {WIDTH}x{HEIGHT} pixels, top-10% selection, LAS) on {cores} host "
+              f"processes, each step measured")
     return {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms/iter", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "gaussians": args.gaussians, "sh_degree": SH_DEGREE,
                        "view": f"{WIDTH}x{HEIGHT}"},
-            "cpu_baseline": {"value": round(v, 1), "unit": "ms/iter", "cores": 1, "kind": "oracle",
-                             "sample": last["sample"] + "; edge map, top-k and LAS measured once for all steps"},
+            "cpu_baseline": {"value": round(v, 1), "unit": "ms/iter", "cores": cores, "kind": "oracle",
+                             "sample": sample, "parts_s_last_step": parts,
+                             "cpu_seconds_last_step": round(o.cpu_seconds, 1)},
             "e2e": {"value": round(v, 1), "unit": "ms/iter", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -813,8 +925,9 @@ def run_reference(args, rank, world):
 
 def dist_setup():
     """One process per GPU (torchrun env); NCCL on GPUs, gloo without them.
-    The path has no data exchange (replicas), so the group only carries the
-    barriers and the max-over-ranks of the timed region."""
+    The main workload (one view) runs as independent replicas, so for it the
+    group only carries the barriers and the max-over-ranks of the timed region;
+    the multi-view leg runs view-sharded with one all-reduce per iteration."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:
@@ -863,6 +976,11 @@ def main():
                 if name in legs:
                     torch.cuda.empty_cache()
                     line[key] = fn()
+        elif world > 1 and not args.no_extra and "multiview" in legs:
+            # N > 1: the multi-view workload runs view-sharded (one all-reduce per iteration)
+            import torch
+            torch.cuda.empty_cache()
+            line["multiview_sharded"] = run_multiview_sharded(rank, world)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:
