@@ -106,11 +106,12 @@ typedef struct gsp_edge_opts {
     int64_t spin_limit;      /* grid-barrier polls before GSP_ERR_TIMEOUT; <= 0: default */
     int32_t test_expire;     /* failure-injection hook for tests (0 in normal use), fused mode:
                                 bit 0: the first grid barrier is never opened, so every
-                                block's bounded wait runs out; bit 1: each wait for a staged
-                                TMA box gives up at once (the block still lets its copies in
-                                flight land before it leaves).  Either way the call reports
-                                GSP_ERR_TIMEOUT in dev_status and E_out / median_out are
-                                unspecified; the next call works normally. */
+                                block's bounded wait runs out; bit 1 (batches under 4 Mi
+                                pixels, which stage their halo boxes by TMA): each wait for
+                                a staged box gives up at once (the block still lets its
+                                copies in flight land before it leaves).  Either way the
+                                call reports GSP_ERR_TIMEOUT in dev_status and E_out /
+                                median_out are unspecified; the next call works normally. */
 } gsp_edge_opts;
 
 /* Default options: fused mode, sigma = 1. */

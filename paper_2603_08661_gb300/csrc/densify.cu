@@ -351,21 +351,27 @@ __global__ void __launch_bounds__(kThreads) las_kernel(LasArgs a)
     }
 }
 
-// SH rows of the appended children: one warp per row, consecutive lanes on
-// consecutive floats (the parent index is read once per row).
-__global__ void __launch_bounds__(256) las_copy_sh(LasArgs a)
+// SH rows of the appended children: one thread per (child, chunk), chunks of
+// 16 bytes when the rows allow it (every copy independent: no per-row loop).
+__global__ void __launch_bounds__(256) las_copy_sh(LasArgs a, int vec4)
 {
     const long long n = *a.count;
     const int nb = int((n + kBlockItems - 1) / kBlockItems);
     const long long total = n > 0 ? a.rank_off[nb] : 0;
     if (n + total > a.cap) return;
     const int row = 3 * a.K;
-    const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
-    for (long long c = blockIdx.x * (long long)(blockDim.x / 32) + (threadIdx.x >> 5); c < total; c += warps) {
-        const float *src = a.sh + (size_t)a.src[c] * row;
-        float *dst = a.sh + (size_t)(n + c) * row;
-        for (int k = lane; k < row; k += 32) dst[k] = src[k];
+    const int chunks = vec4 ? row / 4 : row;
+    const long long work = total * chunks;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < work;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long c = t / chunks;
+        const int q = int(t - c * chunks);
+        const long long src = a.src[c], dst = n + c;
+        if (vec4)
+            reinterpret_cast<float4 *>(a.sh + (size_t)dst * row)[q] =
+                reinterpret_cast<const float4 *>(a.sh + (size_t)src * row)[q];
+        else
+            a.sh[(size_t)dst * row + q] = a.sh[(size_t)src * row + q];
     }
 }
 
@@ -580,7 +586,8 @@ extern "C" gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask,
     a.src = L.src;
     a.status = dev_status;
     las_kernel<<<nblk, kThreads, 0, s>>>(a);
-    las_copy_sh<<<4 * num_sms(), 256, 0, s>>>(a);
+    const int vec4 = (3 * a.K) % 4 == 0 && (reinterpret_cast<uintptr_t>(g->sh) & 15) == 0;
+    las_copy_sh<<<4 * num_sms(), 256, 0, s>>>(a, vec4);
     las_commit<<<1, 1, 0, s>>>(g->count, cap, L.sums, dev_status);
     stage_end("las", s);
     note_launches(5);

@@ -1719,7 +1719,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 2 ? 6 : 2048 / (kTilePi
         __syncthreads();
         for (int q = tid; q < cnt; q += NT) {
             float *a = s_acc[q];
-            float *gp = reinterpret_cast<float *>(g2d + (long long)s_id[q] * 3);
+            float4 *gp4 = g2d + (long long)s_id[q] * 3;
             // power = A' dx^2 + B' dx dy + C' dy^2 with (A', B', C') = s_con and
             // dx = px - mean x: d power / d mean = -(2 A' dx + B' dy, B' dx + 2 C' dy),
             // d power / d(A', B', C') = (dx^2, dx dy, dy^2) (the conic's own gradient
@@ -1731,9 +1731,11 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 2 ? 6 : 2048 / (kTilePi
             a[2] = -0.5f * a[2];
             a[3] = -a[3];
             a[4] = -0.5f * a[4];
-#pragma unroll
-            for (int k = 0; k < 9; ++k)
-                if (a[k] != 0.f) atomicAdd(gp + k, a[k]);
+            // 16-byte vector atomics: three operations instead of nine
+            const float4 v0 = make_float4(a[0], a[1], a[2], a[3]), v1 = make_float4(a[4], a[5], a[6], a[7]);
+            if (v0.x != 0.f || v0.y != 0.f || v0.z != 0.f || v0.w != 0.f) atomicAdd(gp4, v0);
+            if (v1.x != 0.f || v1.y != 0.f || v1.z != 0.f || v1.w != 0.f) atomicAdd(gp4 + 1, v1);
+            if (a[8] != 0.f) atomicAdd(reinterpret_cast<float *>(gp4 + 2), a[8]);
             if (want_score && a[9] != 0.f) atomicAdd(&score[s_id[q]], a[9]);
 #pragma unroll
             for (int k = 0; k < kG2; ++k) a[k] = 0.f;

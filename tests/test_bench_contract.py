@@ -1,12 +1,20 @@
 """The reference arm of bench.py (the FP64 oracle on the host) keeps the
 JSON-line contract: one line with the metric, value, unit, cpu_baseline and
-e2e objects.  Run on a small scene so that it takes seconds (CPU only)."""
+e2e objects, the oracle timed on every host core.  Run on a small scene so
+that it takes seconds (CPU only)."""
 import json
 import os
 import subprocess
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def bench_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
 def test_reference_arm_prints_one_contract_line():
@@ -20,5 +28,5 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["unit"] == "ms/iter" and d["higher_is_better"] is False
     assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == bench_cores() and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "ms/iter", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -94,9 +94,10 @@ def test_fused_equals_plain_bitwise(gsp_lib):
     assert np.array_equal(ma, mb)
 
 
-def test_tma_staged_views_equal_plain_bitwise(gsp_lib):
-    """Views with 16-byte aligned rows are staged by TMA in fused mode (clamped
-    borders read from the staged box); ragged sizes, tiny views, one tile."""
+def test_pitched_views_equal_plain_bitwise(gsp_lib):
+    """Views with 16-byte aligned rows (the fused kernel loads their rows as
+    aligned words) and packed views (rows realigned by funnel shifts); ragged
+    sizes, tiny views, one warp item."""
     import torch
     shapes = [(822, 1237), (1, 1), (5, 7), (16, 64), (17, 65), (203, 347), (40, 130)]
     imgs = [synth.image(h, w, 900 + i) for i, (h, w) in enumerate(shapes)]

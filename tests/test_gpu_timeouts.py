@@ -33,10 +33,12 @@ def _views(gsp, pitched, n=6):
     return [gsp.pitched_image(t, 16) for t in imgs] if pitched else imgs
 
 
-@pytest.mark.parametrize("pitched", [False, True])
-def test_edge_grid_barrier_that_is_never_opened(gsp_lib, pitched):
+@pytest.mark.parametrize("pitched,n", [(False, 6), (True, 6), (True, 64)])
+def test_edge_grid_barrier_that_is_never_opened(gsp_lib, pitched, n):
+    """Both fused schedules: 6 views (tile kernel) and 64 views of 203 x 347
+    (4.5M pixels: walk kernel)."""
     import torch
-    ts = _views(gsp_lib, pitched)
+    ts = _views(gsp_lib, pitched, n)
     E0, m0, _, s0 = gsp_lib.edge_map(ts)
     torch.cuda.synchronize()
     assert int(s0.item()) == 0
@@ -49,8 +51,8 @@ def test_edge_grid_barrier_that_is_never_opened(gsp_lib, pitched):
 
 
 def test_edge_tma_box_wait_that_gives_up(gsp_lib):
-    """Pitched (16-byte aligned) views are staged by TMA; each block's wait
-    for its box gives up at once, drains its copies and leaves."""
+    """Pitched (16-byte aligned) views of a small batch are staged by TMA; each
+    block's wait for its box gives up at once, drains its copies and leaves."""
     import torch
     ts = _views(gsp_lib, True, n=32)
     E0, m0, _, s0 = gsp_lib.edge_map(ts)
