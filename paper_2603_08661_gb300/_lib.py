@@ -95,11 +95,14 @@ SIGNATURES = {
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libgsp.so and declare every entry point; raises if it is missing."""
+def load(path: str | None = None):
+    """Load libgsp.so (or the build GSP_LIBRARY names, e.g. the bounds-checked
+    libgsp_debug.so) and declare every entry point; raises if it is missing."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = os.environ.get("GSP_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"libgsp.so not built at {path}; run `python paper_2603_08661_gb300/build.py`")
     lib = ctypes.CDLL(path)

@@ -37,6 +37,23 @@ __device__ __forceinline__ void set_status(int32_t *st, int32_t code)
     atomicCAS(st, 0, code);
 }
 
+// Bounds-checked build (compiled with -DGSP_DEBUG, libgsp_debug.so): every index
+// guarded by GSP_BOUND is compared with its bound before the access; an index
+// out of bounds records GSP_ERR_CAPACITY in the status word and the access is
+// skipped (nothing traps).  The release build compiles the guard away.
+__device__ __forceinline__ bool bound_ok(unsigned long long i, unsigned long long n, int32_t *status)
+{
+    if (i < n) return true;
+    if (status) set_status(status, GSP_ERR_CAPACITY);
+    return false;
+}
+#ifdef GSP_DEBUG
+#define GSP_BOUND(idx, bound, status) \
+    gsp::bound_ok(static_cast<unsigned long long>(idx), static_cast<unsigned long long>(bound), (status))
+#else
+#define GSP_BOUND(idx, bound, status) true
+#endif
+
 // Bump allocator over a caller workspace; the same code sizes and carves.
 struct Carver {
     char *base;

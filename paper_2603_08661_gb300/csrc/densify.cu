@@ -313,6 +313,7 @@ __global__ void __launch_bounds__(kThreads) las_kernel(LasArgs a)
         const long long i = b0 + threadIdx.x * kPerThread + j;
         const long long dst = n + r;
         ++r;
+        if (!GSP_BOUND(dst, a.cap, a.status)) continue;
         float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
         int l = 0;
         if (ls[1] > ls[l]) l = 1;
@@ -367,6 +368,7 @@ __global__ void __launch_bounds__(256) las_copy_sh(LasArgs a, int vec4)
         const long long c = t / chunks;
         const int q = int(t - c * chunks);
         const long long src = a.src[c], dst = n + c;
+        if (!GSP_BOUND(src, n, a.status)) continue;
         if (vec4)
             reinterpret_cast<float4 *>(a.sh + (size_t)dst * row)[q] =
                 reinterpret_cast<const float4 *>(a.sh + (size_t)src * row)[q];

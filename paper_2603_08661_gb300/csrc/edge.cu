@@ -385,11 +385,12 @@ __device__ void item_stencil(const EdgeArgs &a, int it, WarpSmem &ws)
         else if (x0 + kStrip > V.w) keep &= (1u << (V.w - x0)) - 1u;
         unsigned excl;
         const unsigned tot = warp_exclusive_scan(__popc(keep), &excl);
-        float *dst = slot + run + excl;
+        unsigned o = run + excl;
 #pragma unroll
         for (int j = 0; j < kStrip; ++j) {
             if (keep >> j & 1u) {
-                *dst++ = vals[j];
+                if (GSP_BOUND(o, (unsigned)(kItemCols * a.rb), a.status)) slot[o] = vals[j];
+                ++o;
                 atomicAdd(&whist[__float_as_uint(vals[j]) >> kShift1], 1u);
             }
         }
@@ -838,7 +839,8 @@ __global__ void __launch_bounds__(NT) edge_tile_kernel(const __grid_constant__ T
             if (tid == 0) s_base = atomicAdd(a.cand_count + v, total);
             __syncthreads();
             float *dst = a.cand + V.out_off + s_base;
-            for (unsigned i = tid; i < total; i += NT) dst[i] = cbuf[i];
+            for (unsigned i = tid; i < total; i += NT)
+                if (GSP_BOUND(s_base + i, (long long)V.w * V.h, a.status)) dst[i] = cbuf[i];
             __syncthreads();
         }
     }
@@ -994,7 +996,8 @@ __global__ void __launch_bounds__(NT, 1) edge_walk_kernel(const __grid_constant_
                 unsigned at = 0;
                 if (lane == 0 && nc) at = atomicAdd(a.cand_count + v, nc);
                 at = __shfl_sync(0xffffffffu, at, 0);
-                for (unsigned j = lane; j < nc; j += 32) cand[at + j] = cbuf[j];
+                for (unsigned j = lane; j < nc; j += 32)
+                    if (GSP_BOUND(at + j, (long long)a.v[v].w * a.v[v].h, a.status)) cand[at + j] = cbuf[j];
                 nc = 0;
                 __syncwarp();
             };

@@ -103,6 +103,7 @@ struct State {
     float4 *g2d;              // [V][cap][3]
     double *loss_acc;         // [1]
     int32_t *overflow;        // [1]
+    int32_t *status = nullptr;  // the caller's device status word (bounds-checked build)
     const int32_t *n_dev;     // the caller's device count of live Gaussians
     int nb_max;               // depth-sort blocks for cap
     int nch1_max;             // level-1 chunks for cap
@@ -763,6 +764,7 @@ __global__ void __launch_bounds__(kRsThreads) ds_pass(const uint32_t *kin, const
         const uint32_t k = sk[i];
         const unsigned d = (k >> shift) & 255u;
         const long long pos = (long long)gbase[d] + (i - lstart[d]);
+        if (!GSP_BOUND(pos, n, status)) continue;
         kout[pos] = k;
         vout[pos] = sv[i];
     }
@@ -886,7 +888,8 @@ __global__ void __launch_bounds__(kBinThreads) l1_count(const __grid_constant__ 
             rect_unpack(rc, tx0, ty0, tx1, ty1);
             if (tx1 < tx0) continue;
             for (int sy = ty0 / kSuper; sy <= ty1 / kSuper; ++sy)
-                for (int sx = tx0 / kSuper; sx <= tx1 / kSuper; ++sx) atomicAdd(&tab[sy * V.sx + sx], 1u);
+                for (int sx = tx0 / kSuper; sx <= tx1 / kSuper; ++sx)
+                    if (GSP_BOUND(sy * V.sx + sx, vs.smax, st.status)) atomicAdd(&tab[sy * V.sx + sx], 1u);
         }
         __syncwarp();
         const int S = V.sx * V.sy;
@@ -1042,13 +1045,13 @@ __global__ void __launch_bounds__(kBinThreads) l1_scatter(const __grid_constant_
                 const bool mine = key == smin;
                 const unsigned bal = __ballot_sync(0xffffffffu, mine);
                 unsigned base = 0;
-                if (lane == 0) {
+                if (lane == 0 && GSP_BOUND(smin, vs.smax, st.status)) {
                     base = cur[smin];
                     cur[smin] = base + __popc(bal);
                 }
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (mine) {
-                    st.id1[base + __popc(bal & lt)] = g;
+                    if (GSP_BOUND(base + __popc(bal & lt), st.pair_cap, st.status)) st.id1[base + __popc(bal & lt)] = g;
                     if (++csx > sx1) {
                         csx = sx0;
                         if (++csy > sy1) live = false;
@@ -1112,10 +1115,12 @@ __global__ void __launch_bounds__(kBinThreads) l2_count(const __grid_constant__ 
         for (int k = 0; k < kBinRounds; ++k) {
             const unsigned e = e0 + 32 * k + lane;
             m[k] = 0;
-            if (e < e1) {
+            if (e < e1 && GSP_BOUND(e, st.pair_cap, st.status)) {
                 const int g = st.id1[e];
-                m[k] = entry_mask(rect[g], rowint + (size_t)g * kRowCap, sx, sy);
-                st.mask1[e] = m[k];
+                if (GSP_BOUND(g, cap, st.status)) {
+                    m[k] = entry_mask(rect[g], rowint + (size_t)g * kRowCap, sx, sy);
+                    st.mask1[e] = m[k];
+                }
             }
         }
         // per-tile counts: after the transpose lane L holds, per round, the
@@ -1280,7 +1285,7 @@ __global__ void __launch_bounds__(kBinThreads) l2_scatter(const __grid_constant_
             const unsigned e = e0 + 32 * k + lane;
             g[k] = 0;
             m[k] = 0;
-            if (e < e1) {
+            if (e < e1 && GSP_BOUND(e, st.pair_cap, st.status)) {
                 g[k] = st.id1[e];
                 m[k] = st.mask1[e];
             }
@@ -1308,7 +1313,8 @@ __global__ void __launch_bounds__(kBinThreads) l2_scatter(const __grid_constant_
                 for (int k = 0; k < kBinRounds; ++k) {
                     const bool bit = (mh[k] >> b) & 1u;
                     const unsigned bal = __ballot_sync(0xffffffffu, bit);
-                    if (bit) st.ids[base + __popc(bal & lt)] = g[k];
+                    if (bit && GSP_BOUND(base + __popc(bal & lt), st.pair_cap, st.status))
+                        st.ids[base + __popc(bal & lt)] = g[k];
                     base += __popc(bal);
                 }
             }
@@ -1427,7 +1433,9 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
         for (int q = tid; q < BATCH; q += NT) {
             const int k = b + q;
             if (k < len) {
-                const int id = list[k];
+                int id = 0;
+                if (GSP_BOUND((long long)st.tile_start[gt] + k, st.pair_cap, st.status)) id = list[k];
+                if (!GSP_BOUND(id, cap, st.status)) id = 0;
                 s_id[q] = id;
                 s_xyo[q] = xyo[id];
                 s_mlo[q] = mlo[id];
@@ -1662,7 +1670,9 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 2 ? 6 : 2048 / (kTilePi
         const int lo = max(hi - BATCH, 0);
         const int cnt = hi - lo;
         for (int q = tid; q < cnt; q += NT) {
-            const int id = list[lo + q];
+            int id = 0;
+            if (GSP_BOUND((long long)st.tile_start[gt] + lo + q, st.pair_cap, st.status)) id = list[lo + q];
+            if (!GSP_BOUND(id, cap, st.status)) id = 0;
             s_id[q] = id;
             s_xyo[q] = xyo[id];
             s_mlo[q] = mlo[id];
@@ -2135,6 +2145,7 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     L = render_layout(ws, cap, vs, opts->pair_capacity);
     State S = L.st;
     S.n_dev = g->count;
+    S.status = dev_status;
     Params P = make_params(g);
     P.status = dev_status;
     P.sh_bulk = (reinterpret_cast<uintptr_t>(g->sh) & 15) == 0;
@@ -2235,6 +2246,7 @@ extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *c
     L = render_layout(ws, cap, vs, opts->pair_capacity);
     State S = L.st;
     S.n_dev = g->count;
+    S.status = dev_status;
     Params P = make_params(g);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const float inv_norm =

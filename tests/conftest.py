@@ -15,13 +15,14 @@ def pytest_configure(config):
 
 
 def build_gsp() -> str:
-    """Build libgsp.so (load the build script by path: the package needs the library)."""
+    """Build libgsp.so and the bounds-checked libgsp_debug.so (load the build
+    script by path: the package needs the library); returns libgsp.so's path."""
     import importlib.util
     path = os.path.join(ROOT, "paper_2603_08661_gb300", "build.py")
     spec = importlib.util.spec_from_file_location("_gsp_build", path)
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
-    return mod.build()
+    return mod.build(debug=True)
 
 
 # Gradient parity (CUDA adjoint against the oracle's analytic adjoint), per

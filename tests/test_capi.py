@@ -33,6 +33,12 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), name
 
 
+def test_bounds_checked_build_exports_the_same_symbols(lib):
+    dbg = ctypes.CDLL(os.path.join(ROOT, "paper_2603_08661_gb300", "libgsp_debug.so"))
+    for name in declared_functions():
+        assert hasattr(dbg, name), name
+
+
 def test_binding_declares_exactly_the_header(lib):
     from paper_2603_08661_gb300 import _lib
     assert sorted(_lib.SIGNATURES) == declared_functions()
