@@ -874,21 +874,30 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(n_gauss):
+def cpu_baseline(n_gauss, one_core=True):
     """The FP64 oracle timed on the host cores in the GPU run: one whole step on
-    every core (the value) and its CPU time, the busy seconds of all processes
-    summed (what one core spends on the step)."""
+    every core (the value), its CPU time (the busy seconds of all processes
+    summed), and one whole step on one core."""
     cores = host_cores()
     o = OracleStep(n_gauss, cores)
     try:
         t_all, parts_all = o.step()
     finally:
         o.close()
-    return {"value": round(1e3 * t_all, 1), "unit": "ms/iter", "cores": cores, "kind": "oracle",
-            "sample": f"one whole step (edge map, projection, forward composite with edge score, L1, analytic "
-                      f"adjoint over all {WIDTH}x{HEIGHT} pixels, top-10% selection, LAS) of the FP64 oracle on "
-                      f"{cores} host processes (one pixel-row stripe each), measured, nothing scaled",
-            "cpu_seconds_per_step": round(o.cpu_seconds, 1), "parts_s": parts_all}
+    out = {"value": round(1e3 * t_all, 1), "unit": "ms/iter", "cores": cores, "kind": "oracle",
+           "sample": f"one whole step (edge map, projection, forward composite with edge score, L1, analytic "
+                     f"adjoint over all {WIDTH}x{HEIGHT} pixels, top-10% selection, LAS) of the FP64 oracle on "
+                     f"{cores} host processes (one pixel-row stripe each), measured, nothing scaled",
+           "cpu_seconds_per_step": round(o.cpu_seconds, 1), "parts_s": parts_all}
+    if one_core and cores > 1:
+        o1 = OracleStep(n_gauss, 1)
+        try:
+            t1, parts1 = o1.step()
+        finally:
+            o1.close()
+        out["one_core"] = {"value": round(1e3 * t1, 1), "unit": "ms/iter", "cores": 1,
+                           "sample": "the same whole step in one process", "parts_s": parts1}
+    return out
 
 
 def run_reference(args, rank, world):

@@ -1,0 +1,134 @@
+"""The device-resident densification loop at full size, in the configuration
+the benchmark times: 500,000 SH-0 Gaussians (capacity 1,000,000), four ring
+views of 1237x822 with pitched targets, SGD with lr 1e-3, top 50,000 + LAS
+(the paper's preset) every 20 iterations.
+
+* First iteration: the gradients the loop's L1 path produces equal those of
+  the explicit upstream gradient sign(rgb - target) / (3 * pixels) - same
+  kernels, atomics in another order: within 1e-5 of each group's 2-norm - and,
+  for that upstream gradient restricted to a 32x32 region of each of two
+  views, every Gaussian's gradient matches the oracle's analytic adjoint of
+  the region entry by entry (conftest.grad_bound), outside the gate-exempt
+  Gaussians.
+* First event (after 20 iterations, 19 of them graph-replayed): the selection
+  mask equals the oracle's top-k of the device scores bit for bit - fewer
+  than k Gaussians have a positive score, so the ties at zero are broken in
+  index order - and the split equals the oracle's Long-Axis-Split of the
+  pre-event state within 1e-6.
+"""
+import numpy as np
+import pytest
+
+import synth
+from conftest import EXEMPT_FRAC, GATE_REL, assert_grads_match
+from oracle import densify as od
+from oracle import raster as orc
+
+pytestmark = pytest.mark.gpu
+
+N0, CAP, V, W, H = 500_000, 1_000_000, 4, 1237, 822
+K_EVENT, EVERY, LR = 50_000, 20, 1e-3
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+REGIONS = {0: (608, 400, 640, 432), 2: (477, 253, 509, 285)}  # a tile-aligned and an unaligned region
+
+
+@pytest.fixture(scope="module")
+def setup(gsp_lib):
+    import torch
+    g = synth.gaussians(N0, 0, seed=1)
+    cams = [synth.camera_ring(k, V, resolutions=[(W, H)]) for k in range(V)]
+    tg = [synth.image(H, W, 2000 + k) for k in range(V)]
+    gs = gsp_lib.GaussianSet.from_arrays(g, capacity=CAP)
+    targets = [gsp_lib.pitched_image(torch.from_numpy(t).cuda(), 16) for t in tg]
+    probe = gsp_lib.Renderer(gs, cams, pair_capacity=1 << 27)
+    probe.forward()
+    torch.cuda.synchronize()
+    pairs = int(probe.pair_count().item())
+    del probe
+    loop = gsp_lib.DensifyLoop(gs, cams, targets, lr=LR, every=EVERY, k_event=K_EVENT,
+                               pair_capacity=int(pairs * 2.5) + 4096)
+    return g, cams, tg, gs, loop
+
+
+def _norm_close(a, b, name):
+    a = a.astype(np.float64).ravel()
+    b = b.astype(np.float64).ravel()
+    assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b), name
+
+
+def test_first_iteration_gradients(gsp_lib, setup):
+    import torch
+    g, cams, tg, gs, loop = setup
+    assert int(gs.count.item()) == N0
+    r = loop.r
+    out = r.forward(targets=loop.targets, status=loop.status, out=loop.bufs)
+    r.backward(out, targets=loop.targets, grads=loop.grads, status=loop.status)
+    torch.cuda.synchronize()
+    assert int(loop.status.item()) == 0
+    l1 = {k: loop.grads[k][:N0].cpu().numpy() for k in GROUPS}
+    rgb = out["rgb"].cpu().numpy().astype(np.float64)
+    t32 = np.concatenate([(t.astype(np.float32) / np.float32(255.0)).reshape(-1, 3) for t in tg]).astype(np.float64)
+    dl = (np.sign(rgb - t32) / (3.0 * r.total_pix)).astype(np.float32)
+    explicit = r.backward(out, dL_drgb=torch.from_numpy(dl).cuda())
+    torch.cuda.synchronize()
+    for k in GROUPS:
+        _norm_close(l1[k], explicit[k][:N0].cpu().numpy(), k)
+
+    for v, reg in REGIONS.items():
+        x0, y0, x1, y1 = reg
+        off = r.offsets[v]
+        dl_reg = np.zeros((r.total_pix, 3), np.float32)
+        view = dl.reshape(-1, 3)[off:off + W * H].reshape(H, W, 3)
+        dl_reg[off:off + W * H].reshape(H, W, 3)[y0:y1, x0:x1] = view[y0:y1, x0:x1]
+        got = r.backward(out, dL_drgb=torch.from_numpy(dl_reg).cuda())
+        torch.cuda.synchronize()
+        assert int(out["status"].item()) == 0
+        cam = cams[v]
+        proj = orc.project(g, cam)
+        order = orc.order(proj)
+        ref = orc.render(g, cam, region=reg, proj=proj, order=order)
+        dl64 = dl_reg[off:off + W * H].reshape(H, W, 3).astype(np.float64)
+        gr = orc.render_bwd(g, cam, dl64, proj=proj, region=reg)
+        gm = orc.render_bwd(g, cam, dl64, proj=proj, region=reg, magnitude=True)
+        gap = ref["gate_gap"]
+        assert (gap[y0:y1, x0:x1] < GATE_REL).sum() <= max(1, EXEMPT_FRAC * (x1 - x0) * (y1 - y0))
+        ex = gap < GATE_REL
+        skip = orc.gate_affected(proj, ex, GATE_REL, order) if ex.any() else np.zeros(N0, bool)
+        touched = np.abs(gr["opacity_logits"]).reshape(N0) > 0
+        assert touched.sum() > 20, (v, int(touched.sum()))
+        keep = touched & ~skip
+        for k in GROUPS:
+            a = got[k][:N0].cpu().numpy().astype(np.float64).reshape(N0, -1)
+            b = gr[k].reshape(N0, -1)
+            assert np.all(a[~touched & ~skip] == 0), (v, k)
+            assert_grads_match(k, a[keep], b[keep], gm[k].reshape(N0, -1)[keep])
+
+
+def test_first_event_topk_and_split(gsp_lib, setup):
+    import torch
+    g, cams, tg, gs, loop = setup
+    loop.score.zero_()
+    loop.run(EVERY - 1)  # graph-replayed iterations; no event yet
+    loop.iteration()
+    torch.cuda.synchronize()
+    assert int(loop.status.item()) == 0 and loop.events == 0
+    n = int(gs.count.item())
+    assert n == N0
+    before = {k: getattr(gs, k)[:n].cpu().numpy().astype(np.float64) for k in GROUPS}
+    before["sh_degree"] = 0
+    scores = loop.score[:n].cpu().numpy()
+    # fewer Gaussians than k reach a pixel in 20 iterations: the selection takes
+    # every positive score, then zero scores in index order
+    assert 0 < (scores > 0).sum() < K_EVENT
+    loop.event()
+    torch.cuda.synchronize()
+    assert int(loop.status.item()) == 0 and int(gs.count.item()) == N0 + K_EVENT
+    mask = loop.mask[:n].cpu().numpy().astype(bool)
+    assert np.array_equal(mask, od.topk_mask(scores.astype(np.float64), K_EVENT))
+    p32 = {k: float(np.float32(v)) for k, v in od.PAPER_PRESET.items()}
+    ref = od.las_split(before, mask, **p32)
+    m = N0 + K_EVENT
+    for k in GROUPS:
+        got = getattr(gs, k)[:m].cpu().numpy().astype(np.float64).reshape(m, -1)
+        want = ref[k].reshape(m, -1)
+        assert (np.abs(got - want) / np.maximum(1.0, np.abs(want))).max() <= 1e-6, k
