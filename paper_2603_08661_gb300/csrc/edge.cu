@@ -29,31 +29,33 @@
 //      E_out, per-view histogram of bits [30:19]
 //   then B0, B, C as below, streaming M^2_thin from E_out; D divides in place.
 //
-// Walk kernel (edge_walk_kernel): one block of 8 warps per SM.  The unit of
-// work is a warp item: 32 strips of 8 columns side by side (256 columns) over
-// a band of rows of one view.
-//   A  each thread walks its strip down the band, keeping a sliding window of
-//      the stencil chain in registers (blurred-Sobel rows (5), squared-magnitude
-//      rows (3)) and in shared memory (luma rows (3)); the warp streams its
-//      rows' bytes into a ring of shared-memory row buffers by cp.async, three
-//      rows ahead, and forms each row's luma once per column.  Per row a thread
-//      emits the NMS decision of 8 pixels.  Kept M^2 values are compacted per
-//      warp row into the item's scratch slot with a per-lane 8-bit keep mask,
-//      and counted in a warp-private histogram of bits [30:19].
+// Walk kernel (edge_walk_kernel): four blocks of 4 warps per SM.  The unit of
+// work is a warp item: 120 output columns over a band of rows of one view.
+//   A  lane L walks the 4 columns xg - 4 + 4 L .. + 3 down the band (lanes 0
+//      and 31 hold the halo columns on either side): it loads its pixels'
+//      bytes one row ahead, forms their luma, the vertical Sobel parts from
+//      the last three luma rows, takes the neighbours' edge columns by warp
+//      shuffles for the horizontal Sobel parts and the horizontal blur (both
+//      gradient components in one packed FP32x2 operation), keeps five
+//      blurred rows in registers for the vertical blur, and decides NMS from
+//      the last three M^2 rows (their ring columns by shuffles).  Kept M^2
+//      values are compacted per row pair into the item's slot, with a keep
+//      byte per lane and pair, and counted in a warp histogram of bits
+//      [30:19] (two 16-bit counts a word, flushed before they can overflow).
 //   -- grid barrier --
 //   B0 block v finds view v's median bin of bits [30:19]
 //   -- grid barrier --
-//   B  every warp streams its items' compacted values (staged by cp.async),
-//      collects those in the median bin and counts them on bits [18:9] in
-//      shared memory, and appends them to the view's list with one reservation
+//   B  every warp streams its items' kept values, collects those in the
+//      median bin and counts them on bits [18:9], and appends them to the
+//      view's candidate list with one reservation per buffer
 //   -- grid barrier --
 //   C  block v resolves view v's median: the bin of bits [18:9] from that
 //      count, bits [8:0] from one pass over the candidates in it
 //   -- grid barrier --
-//   D  every warp re-walks its items in chunks of rows: the chunk's masks and
-//      compacted values come in at once, the values are converted to E =
+//   D  every warp re-walks its items in chunks of row pairs: the chunk's keep
+//      bytes come in at once, its kept values are converted to E =
 //      sqrt(M^2) / median by all lanes together, and each E row (zeros and
-//      those values) is transposed through shared memory for coalesced stores.
+//      those values) is staged in shared memory for contiguous stores.
 // Plain mode launches one kernel per stage and per view, with every
 // intermediate in global memory (the unfused reference path); both modes
 // perform the same FP32 operations and agree bit for bit.
@@ -66,64 +68,13 @@
 namespace gsp {
 namespace {
 
-constexpr int NT = 256;                  // threads of the fused kernel's block (8 warps)
-constexpr int kWarps = NT / 32;
-constexpr int kStrip = 8;                // output columns per thread
-constexpr int kLumaW = kStrip + 8;       // luma columns per thread (4-column halo each side)
-constexpr int kSobW = kStrip + 6;        // Sobel columns per thread
-constexpr int kHW = kStrip + 2;          // blurred / magnitude columns (1-column ring)
-constexpr int kItemCols = 32 * kStrip;   // columns of a warp item
+constexpr int NT = 256;                  // threads of a tile-kernel block (8 warps)
 constexpr int kBins1 = 4096, kShift1 = 19;
 constexpr int kBins2 = 1024, kShift2 = 9;
 constexpr int kBins3 = 512;
 constexpr float kTan22 = 0.41421356237309503f;  // tan(22.5 deg) = sqrt(2) - 1
 
-struct EdgeView {
-    const uint8_t *rgb;
-    long long pitch;
-    long long out_off;
-    int w, h;
-    int groups;     // warp items across the width (256 columns each)
-    int bands;      // warp items down the height
-    int item_base;  // first item of the view
-};
-
-struct EdgeArgs {
-    EdgeView v[GSP_MAX_VIEWS];
-    int nviews;
-    int total_items;
-    int rb;                // rows per band
-    float w0, w1, w2;      // blur taps: centre, +-1, +-2
-    float *E;
-    uint8_t *mask;
-    float *median_out;
-    unsigned *hist1;       // [V][kBins1]
-    unsigned *hist2;       // [V][kBins2] bits [18:9] of the candidates
-    unsigned *sel;         // [V][4]: kept count, median bin of bits [30:19], count below that bin
-    unsigned *cand_count;  // [V]
-    float *cand;           // candidate values, laid out like E
-    unsigned *med_bits;    // [V]: bits of the median of M^2
-    float *kept;           // [item][kItemCols * rb]: compacted kept M^2, row after row
-    uint8_t *kmask;        // [item][rb][32]: keep mask of each lane's 8 columns
-    unsigned *kcount;      // [item]: kept values of the item
-    unsigned *bar;         // grid barrier state [2]
-    int32_t *status;
-    long long spin_limit;  // grid-barrier polls
-    int expire;            // test hook: bit 0 withholds the first grid barrier
-};
-
 __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
-
-__device__ __forceinline__ void item_origin(const EdgeArgs &a, int it, int &v, int &x0, int &y0)
-{
-    v = 0;
-    while (v + 1 < a.nviews && a.v[v + 1].item_base <= it) ++v;
-    const EdgeView &V = a.v[v];
-    const int li = it - V.item_base;
-    const int band = li / V.groups;
-    x0 = (li - band * V.groups) * kItemCols;
-    y0 = band * a.rb;
-}
 
 // Exact integer to float for |i| < 2^22: place i in the mantissa of 1.5 * 2^23
 // and subtract (two full-rate operations instead of a conversion).
@@ -132,101 +83,12 @@ __device__ __forceinline__ float i2f_exact(int i)
     return __fsub_rn(__int_as_float(i + 0x4B400000), 12582912.0f);
 }
 
-// The luma 299 R + 587 G + 114 B of a pixel is formed from a word holding its
-// bytes (R, G, B, x) as 256 (R + 2 G) + (43 R + 75 G + 114 B): two byte dot
-// products whose weights fit in 8 bits.
-
-// ---- input rows: each warp streams the bytes of its item's rows into a ring of
-// shared-memory row buffers by cp.async, kRing - 1 rows ahead of use, then forms
-// the luma of the item's 264 columns (256 and a 4-column halo each side, clamped
-// to the image) once into a shared row, from which every lane reads its 16.
-constexpr int kRing = 4;
-constexpr int kLumaCols = kItemCols + 8;                  // 264
-constexpr int kRowWords = (3 * kLumaCols + 8 + 3) / 4 + 1;  // bytes of a row span + alignment slack, in words
-
-struct WarpSmem {
-    unsigned hist[kBins1];                 // warp-private histogram (phase A)
-    unsigned ring[kRing][kRowWords];       // row bytes (word-aligned span)
-    alignas(16) int luma[3][kLumaCols];    // luma of the last three rows (slot = row mod 3)
-};
-
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+// The luma 299 R + 587 G + 114 B of a pixel whose bytes are the low three of
+// px (R, G, B, any), as an exact float: 256 (R + 2 G) + (43 R + 75 G + 114 B),
+// two byte dot products whose weights fit in 8 bits.
+__device__ __forceinline__ float luma_exact(unsigned px)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Byte span of the item's row y: columns [xa, xb) of the image, from the word
-// containing its first byte.
-struct RowSpan {
-    const uint8_t *row;
-    int xa, xb;
-    uintptr_t gstart;  // word-aligned address of the first copied byte
-};
-
-__device__ __forceinline__ RowSpan row_span(const EdgeView &V, int xg, int y)
-{
-    RowSpan r;
-    r.row = V.rgb + (long long)y * V.pitch;
-    r.xa = max(xg - 4, 0);
-    r.xb = min(xg + kItemCols + 4, V.w);
-    r.gstart = reinterpret_cast<uintptr_t>(r.row + 3 * r.xa) & ~uintptr_t(3);
-    return r;
-}
-
-// Every lane: queue its share of the words of row y (clamped) into ring slot `slot`.
-__device__ __forceinline__ void issue_row(const EdgeView &V, int xg, int y, unsigned *slot)
-{
-    const RowSpan r = row_span(V, xg, y);
-    const uintptr_t gend = (reinterpret_cast<uintptr_t>(r.row + 3 * r.xb) + 3) & ~uintptr_t(3);
-    const int nw = int((gend - r.gstart) >> 2);
-    const int lane = threadIdx.x & 31;
-    for (int w = lane; w < nw; w += 32) cp_async4(slot + w, reinterpret_cast<const void *>(r.gstart + 4u * w));
-}
-
-// Luma of the item's columns xg - 4 + c (c < kLumaCols, clamped to the image) from
-// ring slot `slot` (row y) into the warp's luma row `dst`.
-__device__ __forceinline__ void luma_row(const EdgeView &V, int xg, int y, const unsigned *slot, int *dst)
-{
-    const RowSpan r = row_span(V, xg, y);
-    const int lane = threadIdx.x & 31;
-    const int lead = int(reinterpret_cast<uintptr_t>(r.row + 3 * r.xa) - r.gstart);  // 0..3
-    if (xg - 4 >= 0 && xg + kItemCols + 4 <= V.w) {
-        // interior item: column c sits at byte 3 c + lead of the span
-#pragma unroll
-        for (int k = 0; k < (kLumaCols + 31) / 32; ++k) {
-            const int c = lane + 32 * k;
-            if (c < kLumaCols) {
-                const int b = 3 * c + lead, wi = b >> 2, sh = b & 3;
-                const unsigned x = __byte_perm(slot[wi], slot[wi + 1], 0x3210 + sh * 0x1111);
-                dst[c] = int(__dp4a(x, 0x00724B2Bu, __dp4a(x, 0x00000201u, 0u) << 8));
-            }
-        }
-    } else {
-        for (int c = lane; c < kLumaCols; c += 32) {
-            const int xc = clampi(xg - 4 + c, 0, V.w - 1);
-            const int b = 3 * (xc - r.xa) + lead, wi = b >> 2, sh = b & 3;
-            const unsigned x = __byte_perm(slot[wi], slot[wi + 1], 0x3210 + sh * 0x1111);
-            dst[c] = int(__dp4a(x, 0x00724B2Bu, __dp4a(x, 0x00000201u, 0u) << 8));
-        }
-    }
-    __syncwarp();
-}
-
-// The lane's 16 luma values of one luma row.
-__device__ __forceinline__ void read_luma(const int *row, int L[kLumaW])
-{
-    const int4 *q = reinterpret_cast<const int4 *>(row + kStrip * (threadIdx.x & 31));
-#pragma unroll
-    for (int t = 0; t < kLumaW / 4; ++t) {
-        const int4 u = q[t];
-        L[4 * t] = u.x; L[4 * t + 1] = u.y; L[4 * t + 2] = u.z; L[4 * t + 3] = u.w;
-    }
+    return i2f_exact(int(__dp4a(px, 0x00724B2Bu, __dp4a(px, 0x00000201u, 0u) << 8)));
 }
 
 // Exclusive warp scan of one value per lane; returns the warp total.
@@ -243,179 +105,11 @@ __device__ __forceinline__ unsigned warp_exclusive_scan(unsigned x, unsigned *ex
     return __shfl_sync(0xffffffffu, inc, 31);
 }
 
-// State of a strip's walk: sliding windows of the stencil chain (the luma
-// rows live in shared memory).
-struct Walk {
-    float Hx[5][kHW], Hy[5][kHW];      // blurred-Sobel rows, slot = Sobel row mod 5
-    float M0[kHW], M1[kHW];            // squared magnitudes of rows q-1, q (q: the next NMS row)
-    float gx1[kStrip], gy1[kStrip];    // gradient of row q at the strip's own columns
-};
-
-// Input step i of a strip (luma row y0 - 4 + i); P = i mod 5, the H slot
-// written is (i - 2) mod 5 = (P + 3) mod 5.  Returns through keep / vals the
-// NMS row q = y0 + i - 8 when i >= 8.
-template <int P>
-__device__ __forceinline__ bool walk_step(const EdgeArgs &a, const EdgeView &V, int xg, int y0, int i, int nin,
-                                          WarpSmem &ws, Walk &s, unsigned &keep, float vals[kStrip])
-{
-    // queue row i + kRing - 1 into the slot row i - 1 used, then wait for row i
-    __syncwarp();
-    if (i + kRing - 1 < nin)
-        issue_row(V, xg, clampi(y0 - 4 + i + kRing - 1, 0, V.h - 1), ws.ring[(i + kRing - 1) % kRing]);
-    cp_async_commit();
-    cp_async_wait<kRing - 1>();
-    __syncwarp();
-    luma_row(V, xg, clampi(y0 - 4 + i, 0, V.h - 1), ws.ring[i % kRing], ws.luma[i % 3]);
-    const int x0 = xg + kStrip * (threadIdx.x & 31);
-    constexpr int hs = (P + 3) % 5;
-    if (i >= 2) {
-        // Sobel row y - 1 from luma rows y - 2, y - 1, y (exact integers)
-        int v121[kLumaW], vd[kLumaW];
-        {
-            int La[kLumaW], Lb[kLumaW];
-            read_luma(ws.luma[(i + 1) % 3], La);  // row i - 2
-            read_luma(ws.luma[i % 3], Lb);        // row i
-#pragma unroll
-            for (int p = 0; p < kLumaW; ++p) {
-                v121[p] = La[p] + Lb[p];
-                vd[p] = Lb[p] - La[p];
-            }
-            read_luma(ws.luma[(i + 2) % 3], La);  // row i - 1
-#pragma unroll
-            for (int p = 0; p < kLumaW; ++p) v121[p] += 2 * La[p];
-        }
-        float fx[kSobW], fy[kSobW];
-#pragma unroll
-        for (int j = 0; j < kSobW; ++j) {
-            fx[j] = i2f_exact(v121[j + 2] - v121[j]);
-            fy[j] = i2f_exact(vd[j] + 2 * vd[j + 1] + vd[j + 2]);
-        }
-        // horizontal blur: H column k (image x = x0 - 1 + k) uses Sobel columns k .. k + 4
-#pragma unroll
-        for (int k = 0; k < kHW; ++k) {
-            s.Hx[hs][k] = __fmaf_rn(a.w2, __fadd_rn(fx[k], fx[k + 4]),
-                                    __fmaf_rn(a.w1, __fadd_rn(fx[k + 1], fx[k + 3]), __fmul_rn(a.w0, fx[k + 2])));
-            s.Hy[hs][k] = __fmaf_rn(a.w2, __fadd_rn(fy[k], fy[k + 4]),
-                                    __fmaf_rn(a.w1, __fadd_rn(fy[k + 1], fy[k + 3]), __fmul_rn(a.w0, fy[k + 2])));
-        }
-    }
-    if (i < 6) return false;
-    // vertical blur of row m = y - 3 from H rows m - 2 .. m + 2 (slots, oldest first)
-    constexpr int h0 = (P + 4) % 5, h1 = P, h2 = (P + 1) % 5, h3 = (P + 2) % 5, h4 = (P + 3) % 5;
-    const int m = y0 - 7 + i;
-    const bool row_in = m >= 0 && m < V.h;
-    float M2[kHW], gx[kHW], gy[kHW];
-#pragma unroll
-    for (int k = 0; k < kHW; ++k) {
-        gx[k] = __fmaf_rn(a.w2, __fadd_rn(s.Hx[h0][k], s.Hx[h4][k]),
-                          __fmaf_rn(a.w1, __fadd_rn(s.Hx[h1][k], s.Hx[h3][k]), __fmul_rn(a.w0, s.Hx[h2][k])));
-        gy[k] = __fmaf_rn(a.w2, __fadd_rn(s.Hy[h0][k], s.Hy[h4][k]),
-                          __fmaf_rn(a.w1, __fadd_rn(s.Hy[h1][k], s.Hy[h3][k]), __fmul_rn(a.w0, s.Hy[h2][k])));
-        const int x = x0 - 1 + k;
-        M2[k] = (row_in && x >= 0 && x < V.w) ? __fmaf_rn(gx[k], gx[k], __fmul_rn(gy[k], gy[k])) : 0.f;
-    }
-    bool have = false;
-    if (i >= 8) {
-        // NMS of row q = m - 1 (rows M0 = q - 1, M1 = q, M2 = q + 1); pixel j is column k = j + 1
-        keep = 0u;
-#pragma unroll
-        for (int j = 0; j < kStrip; ++j) {
-            const int k = j + 1;
-            const float mq = s.M1[k], g_x = s.gx1[j], g_y = s.gy1[j];
-            const float ax = fabsf(g_x), ay = fabsf(g_y);
-            const bool horiz = ay <= __fmul_rn(kTan22, ax);
-            const bool vert = !horiz && ax <= __fmul_rn(kTan22, ay);
-            const bool same = (g_x > 0.f) == (g_y > 0.f);
-            // canonical neighbour pair (A: + direction, B: - direction) of the direction class
-            float A, B;
-            bool up;
-            if (horiz) {
-                A = s.M1[k + 1]; B = s.M1[k - 1]; up = g_x > 0.f;
-            } else if (vert) {
-                A = M2[k]; B = s.M0[k]; up = g_y > 0.f;
-            } else if (same) {
-                A = M2[k + 1]; B = s.M0[k - 1]; up = g_x > 0.f;   // (+x, +y)
-            } else {
-                A = s.M0[k + 1]; B = M2[k - 1]; up = g_x > 0.f;   // (+x, -y)
-            }
-            const float mp = up ? A : B, mm = up ? B : A;
-            const bool kp = mq > 0.f && mq >= mp && mq > mm;
-            keep |= unsigned(kp) << j;
-            vals[j] = mq;
-        }
-        have = true;
-    }
-#pragma unroll
-    for (int k = 0; k < kHW; ++k) {
-        s.M0[k] = s.M1[k];
-        s.M1[k] = M2[k];
-    }
-#pragma unroll
-    for (int j = 0; j < kStrip; ++j) {
-        s.gx1[j] = gx[j + 1];
-        s.gy1[j] = gy[j + 1];
-    }
-    return have;
-}
-
-// Phase A of one warp item: walk, compact the kept values, count them.
-__device__ void item_stencil(const EdgeArgs &a, int it, WarpSmem &ws)
-{
-    unsigned *whist = ws.hist;
-    int v, xg, y0;
-    item_origin(a, it, v, xg, y0);
-    const EdgeView &V = a.v[v];
-    const int lane = threadIdx.x & 31;
-    const int x0 = xg + kStrip * lane;
-    const int nout = min(a.rb, V.h - y0);
-    float *slot = a.kept + (size_t)it * kItemCols * a.rb;
-    uint8_t *km = a.kmask + (size_t)it * a.rb * 32;
-    Walk s;
-    unsigned run = 0;
-    const int nin = nout + 8;
-    // the first kRing - 1 rows are queued ahead of the walk
-#pragma unroll
-    for (int r = 0; r < kRing - 1; ++r) {
-        if (r < nin) issue_row(V, xg, clampi(y0 - 4 + r, 0, V.h - 1), ws.ring[r]);
-        cp_async_commit();
-    }
-    auto emit = [&](int i, unsigned keep, const float *vals) {
-        const int q = i - 8;  // output row within the band
-        if (x0 >= V.w) keep = 0u;
-        else if (x0 + kStrip > V.w) keep &= (1u << (V.w - x0)) - 1u;
-        unsigned excl;
-        const unsigned tot = warp_exclusive_scan(__popc(keep), &excl);
-        unsigned o = run + excl;
-#pragma unroll
-        for (int j = 0; j < kStrip; ++j) {
-            if (keep >> j & 1u) {
-                if (GSP_BOUND(o, (unsigned)(kItemCols * a.rb), a.status)) slot[o] = vals[j];
-                ++o;
-                atomicAdd(&whist[__float_as_uint(vals[j]) >> kShift1], 1u);
-            }
-        }
-        km[q * 32 + lane] = uint8_t(keep);
-        run += tot;
-    };
-#pragma unroll 1
-    for (int i = 0; i < nin; i += 5) {
-        unsigned keep;
-        float vals[kStrip];
-        if (walk_step<0>(a, V, xg, y0, i, nin, ws, s, keep, vals)) emit(i, keep, vals);
-        if (i + 1 < nin && walk_step<1>(a, V, xg, y0, i + 1, nin, ws, s, keep, vals)) emit(i + 1, keep, vals);
-        if (i + 2 < nin && walk_step<2>(a, V, xg, y0, i + 2, nin, ws, s, keep, vals)) emit(i + 2, keep, vals);
-        if (i + 3 < nin && walk_step<3>(a, V, xg, y0, i + 3, nin, ws, s, keep, vals)) emit(i + 3, keep, vals);
-        if (i + 4 < nin && walk_step<4>(a, V, xg, y0, i + 4, nin, ws, s, keep, vals)) emit(i + 4, keep, vals);
-    }
-    cp_async_wait<0>();
-    __syncwarp();
-    if (lane == 0) a.kcount[it] = run;
-}
-
-// Exclusive block scan of one value per thread (NT threads); returns the total.
+// Exclusive block scan of one value per thread (BT threads); returns the total.
+template <int BT = NT>
 __device__ unsigned block_exclusive_scan(unsigned x, unsigned *out)
 {
-    __shared__ unsigned warp_tot[NT / 32];
+    __shared__ unsigned warp_tot[BT / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned inc = x;
 #pragma unroll
@@ -426,7 +120,7 @@ __device__ unsigned block_exclusive_scan(unsigned x, unsigned *out)
     if (lane == 31) warp_tot[wid] = inc;
     __syncthreads();
     unsigned base = 0, total = 0;
-    for (int w = 0; w < NT / 32; ++w) {
+    for (int w = 0; w < BT / 32; ++w) {
         if (w < wid) base += warp_tot[w];
         total += warp_tot[w];
     }
@@ -436,17 +130,19 @@ __device__ unsigned block_exclusive_scan(unsigned x, unsigned *out)
 }
 
 // Find the bin of the element of ascending rank `rank` in a histogram (any
-// address space).  Every thread receives (bin, count below the bin).
+// address space; nbins a multiple of BT).  Every thread receives (bin, count
+// below the bin).
+template <int BT = NT>
 __device__ void block_find_bin(const unsigned *hist, int nbins, unsigned rank, int *bin_out,
                                unsigned *below_out)
 {
     __shared__ int s_bin;
     __shared__ unsigned s_below;
-    const int per = nbins / NT;
+    const int per = nbins / BT;
     unsigned seg = 0;
     for (int k = 0; k < per; ++k) seg += hist[threadIdx.x * per + k];
     unsigned before;
-    block_exclusive_scan(seg, &before);
+    block_exclusive_scan<BT>(seg, &before);
     if (rank >= before && rank < before + seg) {
         unsigned acc = before;
         for (int k = 0; k < per; ++k) {
@@ -907,58 +603,422 @@ __global__ void __launch_bounds__(NT) edge_tile_kernel(const __grid_constant__ T
 
 
 // ================================================================ walk kernel
+//
+// A warp item is 128 image columns over a band of rb rows: lane L holds the 4
+// columns cx = xg - 4 + 4 L .. cx + 3; lanes 1..30 produce the item's 120
+// output columns xg .. xg + 119 and lanes 0 and 31 compute the 4-column halo
+// on either side.  Values a lane needs from its neighbours' columns (Sobel and
+// blur halos, the NMS ring) come by warp shuffles.
+constexpr int WNT = 128;                      // threads of a walk block (4 warps)
+constexpr int kWWarps = WNT / 32;
+constexpr int kWalkBlocksPerSM = 4;           // resident walk blocks per SM the plan assumes
+constexpr int kQ = 4;                         // columns per lane
+constexpr int kItemCols = 32 * kQ - 2 * kQ;   // 120 output columns per item
+constexpr int kDPairs = 8;                    // row pairs per phase-D chunk
+constexpr int kBCand = 512;                   // phase-B candidate buffer per warp
+constexpr unsigned kFull = 0xffffffffu;
+constexpr bool kWalkRotate = true;            // one step per loop trip, the blurred-row window moved by copies
 
-// Flush a warp-private histogram into view v's global histogram and clear it.
+struct EdgeView {
+    const uint8_t *rgb;
+    long long pitch;
+    long long out_off;
+    int w, h;
+    int groups;     // warp items across the width (120 columns each)
+    int bands;      // warp items down the height
+    int item_base;  // first item of the view
+};
+
+struct EdgeArgs {
+    EdgeView v[GSP_MAX_VIEWS];
+    int nviews;
+    int total_items;
+    int rb;                // rows per band (even)
+    float w0, w1, w2;      // blur taps: centre, +-1, +-2
+    float *E;
+    uint8_t *mask;
+    float *median_out;
+    unsigned *hist1;       // [V][kBins1]
+    unsigned *hist2;       // [V][kBins2] bits [18:9] of the candidates
+    unsigned *sel;         // [V][4]: kept count, median bin of bits [30:19], count below that bin
+    unsigned *cand_count;  // [V]
+    float *cand;           // candidate values, laid out like E
+    unsigned *med_bits;    // [V]: bits of the median of M^2
+    float *kept;           // [item][kItemCols * rb]: kept M^2, row pair after row pair (lane, row, column)
+    uint8_t *kmask;        // [item][rb / 2][32]: keep bits of each lane's 4 columns x 2 rows
+    unsigned *kcount;      // [item]: kept values of the item
+    unsigned *bar;         // grid barrier state [2]
+    int32_t *status;
+    long long spin_limit;  // grid-barrier polls
+    int expire;            // test hook: bit 0 withholds the first grid barrier
+};
+
+// Shared memory of a walk block, one layout per phase.
+union alignas(16) WalkSmem {
+    unsigned hist[kWWarps][kBins1 / 2];  // A: warp histograms of bits [30:19], two 16-bit counts a word
+    struct {
+        unsigned h2[kWWarps][kBins2];    // B: warp counts of bits [18:9] of the candidates
+        float cbuf[kWWarps][kBCand];     //    candidates waiting for their reservation
+    } b;
+    unsigned hist3[kBins3];              // C: count of bits [8:0]
+    struct {
+        float vals[kWWarps][kDPairs * 2 * kItemCols];  // D: E of a chunk's kept values
+        float row[kWWarps][2][32 * kQ];                //    E rows of a pair, for coalesced stores
+        uint8_t mrow[kWWarps][2][32 * kQ];             //    NMS mask rows of a pair
+    } d;
+};
+
+__device__ __forceinline__ void item_origin(const EdgeArgs &a, int it, int &v, int &xg, int &y0)
+{
+    v = 0;
+    while (v + 1 < a.nviews && a.v[v + 1].item_base <= it) ++v;
+    const EdgeView &V = a.v[v];
+    const int li = it - V.item_base;
+    const int band = li / V.groups;
+    xg = (li - band * V.groups) * kItemCols;
+    y0 = band * a.rb;
+}
+
+// Per-lane constants of an item's walk.
+struct QLane {
+    const uint8_t *rgb;
+    long long pitch;
+    int w, h;
+    int cx;             // first of the lane's 4 columns (may lie outside the image)
+    int y0, nout, nin;  // first output row, output rows, input rows (nout + 8)
+    bool fast;          // all 4 columns inside the image: word loads
+    unsigned colmask;   // columns inside the image
+    unsigned outmask;   // columns this lane outputs (lanes 1..30, inside the image)
+};
+
+// The raw words of the lane's 4 pixels of input row i (image row y0 - 4 + i,
+// clamped).  Fast lanes: the aligned words covering their 12 bytes and the
+// byte shift of the first; other lanes: one word per pixel (clamped column).
+__device__ __forceinline__ void load_row(const QLane &q, int i, unsigned (&w)[4], unsigned &shift)
+{
+    const int y = clampi(q.y0 - 4 + i, 0, q.h - 1);
+    const uint8_t *row = q.rgb + (long long)y * q.pitch;
+    if (q.fast) {
+        const uintptr_t p = reinterpret_cast<uintptr_t>(row + 3 * q.cx);
+        const unsigned *wp = reinterpret_cast<const unsigned *>(p & ~uintptr_t(3));
+        shift = unsigned(p & 3) * 8u;
+        w[0] = __ldg(wp);
+        w[1] = __ldg(wp + 1);
+        w[2] = __ldg(wp + 2);
+        // the fourth word holds the last byte only when the span is not word aligned
+        w[3] = shift ? __ldg(wp + 3) : 0u;
+    } else {
+        shift = 0u;
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) {
+            const uint8_t *b = row + 3 * clampi(q.cx + j, 0, q.w - 1);
+            w[j] = unsigned(b[0]) | unsigned(b[1]) << 8 | unsigned(b[2]) << 16;
+        }
+    }
+}
+
+__device__ __forceinline__ void row_luma(const QLane &q, const unsigned (&w)[4], unsigned shift, float (&I)[kQ])
+{
+    unsigned px[kQ];
+    if (q.fast) {
+        const unsigned u0 = __funnelshift_r(w[0], w[1], shift);
+        const unsigned u1 = __funnelshift_r(w[1], w[2], shift);
+        const unsigned u2 = __funnelshift_r(w[2], w[3], shift);
+        px[0] = u0;
+        px[1] = __byte_perm(u0, u1, 0x6543);
+        px[2] = __byte_perm(u1, u2, 0x5432);
+        px[3] = u2 >> 8;
+    } else {
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) px[j] = w[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kQ; ++j) I[j] = luma_exact(px[j]);
+}
+
+// Walk state of a lane.
+struct QState {
+    float I0[kQ], I1[kQ];      // luma of input rows i - 2, i - 1
+    float2 H[5][kQ];           // (x, y) horizontally blurred Sobel rows, slot = Sobel row mod 5
+    float M0[kQ + 2];          // M^2 of NMS row q - 1 (index 0: column -1, kQ + 1: column kQ)
+    float M1[kQ + 2];          // M^2 of NMS row q
+    float2 g1[kQ];             // blurred gradient of row q
+    unsigned w[4], shift;      // words of the next input row
+    unsigned keep0;            // first row of a pair, waiting for the second
+    float v0[kQ];
+};
+
+// Output of phase A for one item.
+struct QOut {
+    float *slot;       // the item's kept values
+    uint8_t *km;       // the item's keep masks
+    unsigned *whist;   // the warp's histogram
+    unsigned run;      // kept values so far
+    unsigned cap;      // kItemCols * rb
+    int32_t *status;
+};
+
+__device__ __forceinline__ void emit_pair(QOut &o, int pair, unsigned k8, const float (&vv)[2 * kQ])
+{
+    const int lane = threadIdx.x & 31;
+    unsigned excl;
+    const unsigned tot = warp_exclusive_scan(__popc(k8), &excl);
+    unsigned at = o.run + excl;
+#pragma unroll
+    for (int b = 0; b < 2 * kQ; ++b) {
+        const bool kb = (k8 >> b & 1u) != 0u;
+        if (kb) {
+            if (GSP_BOUND(at, o.cap, o.status)) o.slot[at] = vv[b];
+            const unsigned bin = __float_as_uint(vv[b]) >> kShift1;
+            atomicAdd(&o.whist[bin >> 1], 1u << ((bin & 1u) << 4));
+        }
+        at += kb;
+    }
+    o.km[pair * 32 + lane] = uint8_t(k8);
+    o.run += tot;
+}
+
+// Input step i of the walk: luma row i, Sobel row i - 1, horizontal blur,
+// then (i >= 6) vertical blur of row m = y0 - 7 + i and its M^2, then (i >= 8)
+// NMS of output row q = i - 8.  The five blurred rows sit in slots: with
+// P = i mod 5 (a walk unrolled by five steps) the slots are chosen statically,
+// with P = -1 the window moves down one slot per step (slot 4 the newest).
+template <int P>
+__device__ __forceinline__ void qstep(const QLane &q, const float2 w0v, const float2 w1v, const float2 w2v,
+                                      QState &s, QOut &o, int i)
+{
+    float Ic[kQ];
+    row_luma(q, s.w, s.shift, Ic);
+    if (i + 1 < q.nin) load_row(q, i + 1, s.w, s.shift);
+    constexpr int hs = P < 0 ? 4 : (P + 3) % 5;  // slot of Sobel row i - 1 (its index i - 2 from the first)
+    if (P < 0) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int j = 0; j < kQ; ++j) s.H[t][j] = s.H[t + 1][j];
+    }
+    if (i >= 2) {
+        // vertical parts of Sobel row i - 1 (exact integers in FP32), the lane's
+        // columns at index 1..4, the neighbours' edge columns at 0 and 5
+        float v121[kQ + 2], vd[kQ + 2];
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) {
+            v121[j + 1] = __fadd_rn(__fmaf_rn(2.f, s.I1[j], s.I0[j]), Ic[j]);
+            vd[j + 1] = __fsub_rn(Ic[j], s.I0[j]);
+        }
+        v121[0] = __shfl_up_sync(kFull, v121[kQ], 1);
+        vd[0] = __shfl_up_sync(kFull, vd[kQ], 1);
+        v121[kQ + 1] = __shfl_down_sync(kFull, v121[1], 1);
+        vd[kQ + 1] = __shfl_down_sync(kFull, vd[1], 1);
+        // (Sx, Sy) at columns -2 .. kQ + 1 (index + 2)
+        float2 f[kQ + 4];
+#pragma unroll
+        for (int j = 0; j < kQ; ++j)
+            f[j + 2] = make_float2(__fsub_rn(v121[j + 2], v121[j]),
+                                   __fadd_rn(__fmaf_rn(2.f, vd[j + 1], vd[j]), vd[j + 2]));
+        f[0].x = __shfl_up_sync(kFull, f[kQ].x, 1);
+        f[0].y = __shfl_up_sync(kFull, f[kQ].y, 1);
+        f[1].x = __shfl_up_sync(kFull, f[kQ + 1].x, 1);
+        f[1].y = __shfl_up_sync(kFull, f[kQ + 1].y, 1);
+        f[kQ + 2].x = __shfl_down_sync(kFull, f[2].x, 1);
+        f[kQ + 2].y = __shfl_down_sync(kFull, f[2].y, 1);
+        f[kQ + 3].x = __shfl_down_sync(kFull, f[3].x, 1);
+        f[kQ + 3].y = __shfl_down_sync(kFull, f[3].y, 1);
+        // horizontal blur, taps paired (both components at once)
+#pragma unroll
+        for (int j = 0; j < kQ; ++j)
+            s.H[hs][j] = __ffma2_rn(w2v, __fadd2_rn(f[j], f[j + 4]),
+                                    __ffma2_rn(w1v, __fadd2_rn(f[j + 1], f[j + 3]), __fmul2_rn(w0v, f[j + 2])));
+    }
+#pragma unroll
+    for (int j = 0; j < kQ; ++j) {
+        s.I0[j] = s.I1[j];
+        s.I1[j] = Ic[j];
+    }
+    if (i < 6) return;
+    // vertical blur of row m = y0 - 7 + i from Sobel rows m - 2 .. m + 2 (slots, oldest first)
+    constexpr int h0 = P < 0 ? 0 : (P + 4) % 5, h1 = P < 0 ? 1 : P, h2 = P < 0 ? 2 : (P + 1) % 5,
+                  h3 = P < 0 ? 3 : (P + 2) % 5, h4 = P < 0 ? 4 : (P + 3) % 5;
+    const int m = q.y0 - 7 + i;
+    const bool row_in = m >= 0 && m < q.h;
+    float2 g[kQ];
+    float M2[kQ + 2];
+#pragma unroll
+    for (int j = 0; j < kQ; ++j) {
+        g[j] = __ffma2_rn(w2v, __fadd2_rn(s.H[h0][j], s.H[h4][j]),
+                          __ffma2_rn(w1v, __fadd2_rn(s.H[h1][j], s.H[h3][j]), __fmul2_rn(w0v, s.H[h2][j])));
+        M2[j + 1] = (row_in && (q.colmask >> j & 1u)) ? __fmaf_rn(g[j].x, g[j].x, __fmul_rn(g[j].y, g[j].y)) : 0.f;
+    }
+    M2[0] = __shfl_up_sync(kFull, M2[kQ], 1);
+    M2[kQ + 1] = __shfl_down_sync(kFull, M2[1], 1);
+    if (i >= 8) {
+        // NMS of row q (M0 = q - 1, M1 = q, M2 = q + 1); column j is index j + 1.
+        // The neighbour in the + direction of the gradient (compared with >=)
+        // and the one in the - direction (compared with >): along the row for
+        // the horizontal class (+ is +x when gx > 0); otherwise in row q + 1
+        // exactly when gy > 0, at the column offset of the class.
+        unsigned keep = 0u;
+        float vals[kQ];
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) {
+            const int k = j + 1;
+            const float mq = s.M1[k], gxq = s.g1[j].x, gyq = s.g1[j].y;
+            const float ax = fabsf(gxq), ay = fabsf(gyq);
+            const bool gxp = gxq > 0.f, gyp = gyq > 0.f;
+            const bool horiz = ay <= __fmul_rn(kTan22, ax);
+            const bool vert = ax <= __fmul_rn(kTan22, ay);  // read only when not horizontal
+            const bool same = gxp == gyp;
+            const float n0 = vert ? s.M0[k] : (same ? s.M0[k - 1] : s.M0[k + 1]);
+            const float n2 = vert ? M2[k] : (same ? M2[k + 1] : M2[k - 1]);
+            const float lo = horiz ? s.M1[k - 1] : n0, hi = horiz ? s.M1[k + 1] : n2;
+            const bool pos = horiz ? gxp : gyp;
+            const float mp = pos ? hi : lo, mm = pos ? lo : hi;
+            keep |= unsigned(mq > 0.f && mq >= mp && mq > mm) << j;
+            vals[j] = mq;
+        }
+        keep &= q.outmask;
+        const int r = i - 8;
+        if ((r & 1) == 0 && r + 1 < q.nout) {
+            s.keep0 = keep;
+#pragma unroll
+            for (int j = 0; j < kQ; ++j) s.v0[j] = vals[j];
+        } else {
+            float vv[2 * kQ];
+            unsigned k8;
+            if (r & 1) {
+                k8 = s.keep0 | keep << kQ;
+#pragma unroll
+                for (int j = 0; j < kQ; ++j) {
+                    vv[j] = s.v0[j];
+                    vv[kQ + j] = vals[j];
+                }
+            } else {
+                k8 = keep;
+#pragma unroll
+                for (int j = 0; j < kQ; ++j) {
+                    vv[j] = vals[j];
+                    vv[kQ + j] = 0.f;
+                }
+            }
+            emit_pair(o, r >> 1, k8, vv);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kQ + 2; ++k) {
+        s.M0[k] = s.M1[k];
+        s.M1[k] = M2[k];
+    }
+#pragma unroll
+    for (int j = 0; j < kQ; ++j) s.g1[j] = g[j];
+}
+
+// Phase A of one warp item: walk the band, compact the kept values per row
+// pair, count them in the warp histogram.  Returns the item's kept count.
+__device__ unsigned walk_item(const EdgeArgs &a, int it, unsigned *whist)
+{
+    int v, xg, y0;
+    item_origin(a, it, v, xg, y0);
+    const EdgeView &V = a.v[v];
+    const int lane = threadIdx.x & 31;
+    QLane q;
+    q.rgb = V.rgb;
+    q.pitch = V.pitch;
+    q.w = V.w;
+    q.h = V.h;
+    q.cx = xg - kQ + kQ * lane;
+    q.y0 = y0;
+    q.nout = min(a.rb, V.h - y0);
+    q.nin = q.nout + 8;
+    q.fast = q.cx >= 0 && q.cx + kQ <= V.w;
+    q.colmask = 0u;
+#pragma unroll
+    for (int j = 0; j < kQ; ++j) q.colmask |= unsigned(q.cx + j >= 0 && q.cx + j < V.w) << j;
+    q.outmask = (lane >= 1 && lane <= 30) ? q.colmask : 0u;
+    QOut o;
+    o.slot = a.kept + (size_t)it * kItemCols * a.rb;
+    o.km = a.kmask + (size_t)it * (a.rb / 2) * 32;
+    o.whist = whist;
+    o.run = 0;
+    o.cap = unsigned(kItemCols * a.rb);
+    o.status = a.status;
+    const float2 w0v = make_float2(a.w0, a.w0), w1v = make_float2(a.w1, a.w1), w2v = make_float2(a.w2, a.w2);
+    QState s;
+    s.keep0 = 0u;
+    load_row(q, 0, s.w, s.shift);
+    if (kWalkRotate) {
+#pragma unroll 1
+        for (int i = 0; i < q.nin; ++i) qstep<-1>(q, w0v, w1v, w2v, s, o, i);
+    } else {
+#pragma unroll 1
+        for (int i = 0; i < q.nin; i += 5) {
+            qstep<0>(q, w0v, w1v, w2v, s, o, i);
+            if (i + 1 < q.nin) qstep<1>(q, w0v, w1v, w2v, s, o, i + 1);
+            if (i + 2 < q.nin) qstep<2>(q, w0v, w1v, w2v, s, o, i + 2);
+            if (i + 3 < q.nin) qstep<3>(q, w0v, w1v, w2v, s, o, i + 3);
+            if (i + 4 < q.nin) qstep<4>(q, w0v, w1v, w2v, s, o, i + 4);
+        }
+    }
+    if (lane == 0) a.kcount[it] = o.run;
+    return o.run;
+}
+
+// Add a warp histogram (two 16-bit counts a word) to view v's global
+// histogram and clear it.
 __device__ __forceinline__ void flush_whist(unsigned *whist, unsigned *gh)
 {
     const int lane = threadIdx.x & 31;
     __syncwarp();
-    for (int b = lane; b < kBins1; b += 32) {
+    for (int b = lane; b < kBins1 / 2; b += 32) {
         const unsigned c = whist[b];
         if (c) {
-            atomicAdd(gh + b, c);
+            if (c & 0xffffu) atomicAdd(gh + 2 * b, c & 0xffffu);
+            if (c >> 16) atomicAdd(gh + 2 * b + 1, c >> 16);
             whist[b] = 0u;
         }
     }
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(NT, 1) edge_walk_kernel(const __grid_constant__ EdgeArgs a)
+__global__ void __launch_bounds__(WNT, kWalkBlocksPerSM) edge_walk_kernel(const __grid_constant__ EdgeArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    __shared__ WalkSmem sm;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    WarpSmem &ws = reinterpret_cast<WarpSmem *>(smem_dyn)[wid];
-    unsigned *whist = ws.hist;
     const int G = gridDim.x;
-    const long long gw = (long long)blockIdx.x * kWarps + wid, nw = (long long)G * kWarps;
+    const long long gw = (long long)blockIdx.x * kWWarps + wid, nw = (long long)G * kWWarps;
     const int it_begin = int(a.total_items * gw / nw), it_end = int(a.total_items * (gw + 1) / nw);
 
     // ---- phase A: stencil walk, NMS, compacted kept M^2, warp histograms of bits [30:19]
-    for (int b = lane; b < kBins1; b += 32) whist[b] = 0u;
-    __syncwarp();
-    int cur_view = -1;
-    for (int it = it_begin; it < it_end; ++it) {
-        int v = 0;
-        while (v + 1 < a.nviews && a.v[v + 1].item_base <= it) ++v;
-        if (v != cur_view) {
-            if (cur_view >= 0) flush_whist(whist, a.hist1 + (size_t)cur_view * kBins1);
-            cur_view = v;
+    {
+        unsigned *whist = sm.hist[wid];
+        for (int b = lane; b < kBins1 / 2; b += 32) whist[b] = 0u;
+        __syncwarp();
+        int cur_view = -1;
+        unsigned since = 0;  // kept values counted since the last flush (16-bit counts)
+        const unsigned item_cap = unsigned(kItemCols * a.rb);
+        for (int it = it_begin; it < it_end; ++it) {
+            int v = 0;
+            while (v + 1 < a.nviews && a.v[v + 1].item_base <= it) ++v;
+            if (v != cur_view || since + item_cap > 0xffffu) {
+                if (cur_view >= 0) flush_whist(whist, a.hist1 + (size_t)cur_view * kBins1);
+                cur_view = v;
+                since = 0;
+            }
+            since += walk_item(a, it, whist);
         }
-        item_stencil(a, it, ws);
+        if (cur_view >= 0) flush_whist(whist, a.hist1 + (size_t)cur_view * kBins1);
     }
-    if (cur_view >= 0) flush_whist(whist, a.hist1 + (size_t)cur_view * kBins1);
     if (!grid_barrier(a.bar, G, a.spin_limit, a.status, (a.expire & 1) != 0)) return;
 
     // ---- phase B0: each view's median bin of bits [30:19] and kept count (block v)
     for (int v = blockIdx.x; v < a.nviews; v += G) {
         const unsigned *h = a.hist1 + (size_t)v * kBins1;
         unsigned seg = 0;
-        for (int k = 0; k < kBins1 / NT; ++k) seg += h[tid * (kBins1 / NT) + k];
+        for (int k = 0; k < kBins1 / WNT; ++k) seg += h[tid * (kBins1 / WNT) + k];
         unsigned before;
-        const unsigned n = block_exclusive_scan(seg, &before);
+        const unsigned n = block_exclusive_scan<WNT>(seg, &before);
         int b1 = 0;
         unsigned below = 0;
-        if (n > 0) block_find_bin(h, kBins1, (n - 1) / 2, &b1, &below);
+        if (n > 0) block_find_bin<WNT>(h, kBins1, (n - 1) / 2, &b1, &below);
         if (tid == 0) {
             a.sel[4 * v + 0] = n;
             a.sel[4 * v + 1] = unsigned(b1);
@@ -968,78 +1028,91 @@ __global__ void __launch_bounds__(NT, 1) edge_walk_kernel(const __grid_constant_
     }
     if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
 
-    // ---- phase B: each warp streams its items' kept values (in chunks brought to
-    // shared memory by cp.async, all loads in flight), collects the candidates
-    // (values in the median bin) in shared memory with their count on bits
-    // [18:9], and appends them to the view's list with one reservation per item
+    // ---- phase B: each warp streams its items' kept values, collects the
+    // candidates (values in the median bin) with their count on bits [18:9],
+    // and appends them to the view's list with one reservation per buffer
     {
-        constexpr int kBChunk = 2048;                          // values per staged chunk
-        constexpr int kBCand = 1024;                           // candidate buffer
-        unsigned char *wb = smem_dyn + (size_t)wid * sizeof(WarpSmem);
-        float *bstage = reinterpret_cast<float *>(wb);
-        float *cbuf = bstage + kBChunk;
-        unsigned *h2s = reinterpret_cast<unsigned *>(cbuf + kBCand);  // warp-private count on bits [18:9]
-        static_assert(sizeof(float) * (kBChunk + kBCand) + sizeof(unsigned) * kBins2 <= sizeof(WarpSmem),
-                      "phase B staging");
+        unsigned *h2s = sm.b.h2[wid];
+        float *cbuf = sm.b.cbuf[wid];
         for (int b = lane; b < kBins2; b += 32) h2s[b] = 0u;
         __syncwarp();
+        int cur_view = -1;
         for (int it = it_begin; it < it_end; ++it) {
             int v = 0;
             while (v + 1 < a.nviews && a.v[v + 1].item_base <= it) ++v;
+            if (v != cur_view) {
+                if (cur_view >= 0) {
+                    unsigned *h2 = a.hist2 + (size_t)cur_view * kBins2;
+                    for (int b = lane; b < kBins2; b += 32) {
+                        const unsigned c = h2s[b];
+                        if (c) {
+                            atomicAdd(h2 + b, c);
+                            h2s[b] = 0u;
+                        }
+                    }
+                    __syncwarp();
+                }
+                cur_view = v;
+            }
             const unsigned b1 = __ldcg(a.sel + 4 * v + 1);
             const unsigned n = __ldcg(a.kcount + it);
             const float *src = a.kept + (size_t)it * kItemCols * a.rb;
             float *cand = a.cand + a.v[v].out_off;
-            unsigned *h2 = a.hist2 + (size_t)v * kBins2;
+            [[maybe_unused]] const long long vpx = (long long)a.v[v].w * a.v[v].h;
             unsigned nc = 0;  // candidates buffered
-            auto drain = [&]() {
-                unsigned at = 0;
-                if (lane == 0 && nc) at = atomicAdd(a.cand_count + v, nc);
-                at = __shfl_sync(0xffffffffu, at, 0);
-                for (unsigned j = lane; j < nc; j += 32)
-                    if (GSP_BOUND(at + j, (long long)a.v[v].w * a.v[v].h, a.status)) cand[at + j] = cbuf[j];
-                nc = 0;
-                __syncwarp();
-            };
-            for (unsigned c0 = 0; c0 < n; c0 += kBChunk) {
-                const unsigned cn = min(n - c0, unsigned(kBChunk));
-                __syncwarp();
-                for (unsigned j = lane; j < cn; j += 32) cp_async4(bstage + j, src + c0 + j);
-                cp_async_commit();
-                cp_async_wait<0>();
-                __syncwarp();
-                for (unsigned base = 0; base < cn; base += 32) {
-                    const unsigned e = base + lane;
-                    const float val = e < cn ? bstage[e] : 0.f;
-                    const unsigned bits = __float_as_uint(val);
-                    const bool pick = e < cn && (bits >> kShift1) == b1;
-                    const unsigned m = __ballot_sync(0xffffffffu, pick);
+            for (unsigned c0 = 0; c0 < n; c0 += 8 * 32) {
+                float val[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const unsigned e = c0 + 32 * k + lane;
+                    val[k] = e < n ? __ldcg(src + e) : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const unsigned e = c0 + 32 * k + lane;
+                    const unsigned bits = __float_as_uint(val[k]);
+                    const bool pick = e < n && (bits >> kShift1) == b1;
+                    const unsigned m = __ballot_sync(kFull, pick);
                     if (!m) continue;
-                    if (nc + 32 > unsigned(kBCand)) drain();
+                    if (nc + 32 > unsigned(kBCand)) {
+                        unsigned at = 0;
+                        if (lane == 0) at = atomicAdd(a.cand_count + v, nc);
+                        at = __shfl_sync(kFull, at, 0);
+                        __syncwarp();
+                        for (unsigned j = lane; j < nc; j += 32)
+                            if (GSP_BOUND(at + j, vpx, a.status)) cand[at + j] = cbuf[j];
+                        nc = 0;
+                        __syncwarp();
+                    }
                     if (pick) {
-                        cbuf[nc + __popc(m & ((1u << lane) - 1u))] = val;
+                        cbuf[nc + __popc(m & ((1u << lane) - 1u))] = val[k];
                         atomicAdd(&h2s[(bits >> kShift2) & (kBins2 - 1)], 1u);
                     }
                     nc += __popc(m);
                 }
             }
             __syncwarp();
-            drain();
+            if (nc) {
+                unsigned at = 0;
+                if (lane == 0) at = atomicAdd(a.cand_count + v, nc);
+                at = __shfl_sync(kFull, at, 0);
+                for (unsigned j = lane; j < nc; j += 32)
+                    if (GSP_BOUND(at + j, vpx, a.status)) cand[at + j] = cbuf[j];
+                __syncwarp();
+            }
+        }
+        if (cur_view >= 0) {
+            unsigned *h2 = a.hist2 + (size_t)cur_view * kBins2;
             for (int b = lane; b < kBins2; b += 32) {
                 const unsigned c = h2s[b];
-                if (c) {
-                    atomicAdd(h2 + b, c);
-                    h2s[b] = 0u;
-                }
+                if (c) atomicAdd(h2 + b, c);
             }
-            __syncwarp();
         }
     }
     if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
 
     // ---- phase C: exact median of each view (block v): the level-2 bin from
-    // the candidates' histogram, then bits [8:0] among the candidates in it
-    unsigned *hist_s = reinterpret_cast<unsigned *>(smem_dyn);  // the warp histograms are free
+    // the candidates' count, then bits [8:0] among the candidates in it
     for (int v = blockIdx.x; v < a.nviews; v += G) {
         const unsigned n = a.sel[4 * v + 0];
         unsigned bits = 0;
@@ -1048,20 +1121,20 @@ __global__ void __launch_bounds__(NT, 1) edge_walk_kernel(const __grid_constant_
             unsigned rank = (n - 1) / 2 - a.sel[4 * v + 2];
             int b2;
             unsigned below2;
-            block_find_bin(a.hist2 + (size_t)v * kBins2, kBins2, rank, &b2, &below2);
+            block_find_bin<WNT>(a.hist2 + (size_t)v * kBins2, kBins2, rank, &b2, &below2);
             rank -= below2;
-            for (int i = tid; i < kBins3; i += NT) hist_s[i] = 0;
+            for (int i = tid; i < kBins3; i += WNT) sm.hist3[i] = 0;
             __syncthreads();
             const float *cand = a.cand + a.v[v].out_off;
             const unsigned count = a.cand_count[v];
-            for (unsigned i = tid; i < count; i += NT) {
+            for (unsigned i = tid; i < count; i += WNT) {
                 const unsigned cb = __float_as_uint(cand[i]);
-                if (((cb >> kShift2) & (kBins2 - 1)) == unsigned(b2)) atomicAdd(&hist_s[cb & (kBins3 - 1)], 1u);
+                if (((cb >> kShift2) & (kBins2 - 1)) == unsigned(b2)) atomicAdd(&sm.hist3[cb & (kBins3 - 1)], 1u);
             }
             __syncthreads();
             int b3;
             unsigned below3;
-            block_find_bin(hist_s, kBins3, rank, &b3, &below3);
+            block_find_bin<WNT>(sm.hist3, kBins3, rank, &b3, &below3);
             bits = (b1 << kShift1) | (unsigned(b2) << kShift2) | unsigned(b3);
         }
         if (tid == 0) {
@@ -1072,84 +1145,99 @@ __global__ void __launch_bounds__(NT, 1) edge_walk_kernel(const __grid_constant_
     }
     if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
 
-    // ---- phase D: every warp writes its items' E rows: zeros and sqrt(M^2) /
-    // median.  Rows go in chunks of kDRows: the chunk's keep masks and its
-    // compacted values are loaded at once (all loads in flight), the values
-    // staged in shared memory; each row is then transposed through shared
-    // memory so that every store instruction covers 128 contiguous bytes.
-    constexpr int kDRows = 16;
-    unsigned char *wbase = smem_dyn + (size_t)wid * sizeof(WarpSmem);  // this warp's region (phase A state is dead)
-    float *vstage = reinterpret_cast<float *>(wbase);                      // kDRows * kItemCols values
-    float *stage = vstage + kDRows * kItemCols;                            // one E row
-    uint8_t *mstage = reinterpret_cast<uint8_t *>(stage + kItemCols);      // one mask row
-    static_assert(sizeof(float) * (kDRows + 1) * kItemCols + kItemCols <= sizeof(WarpSmem), "phase D staging");
-    for (int it = it_begin; it < it_end; ++it) {
-        int v, xg, y0;
-        item_origin(a, it, v, xg, y0);
-        const EdgeView &V = a.v[v];
-        const float med2 = __uint_as_float(__ldcg(a.med_bits + v));
-        const float smed = __fsqrt_rn(med2);
-        const int nout = min(a.rb, V.h - y0);
-        const float *src = a.kept + (size_t)it * kItemCols * a.rb;
-        const uint8_t *km = a.kmask + (size_t)it * a.rb * 32;
-        unsigned run = 0;
-        for (int q0 = 0; q0 < nout; q0 += kDRows) {
-            const int nr = min(kDRows, nout - q0);
-            unsigned keepr[kDRows], excl[kDRows], offr[kDRows];
+    // ---- phase D: every warp writes its items' E rows, zeros and sqrt(M^2) /
+    // median.  Row pairs go in chunks of kDPairs: the chunk's keep masks are
+    // loaded at once, its kept values converted to E by all lanes together
+    // (no lane idles on a pixel it does not keep), then each row is staged in
+    // shared memory so that every store instruction covers contiguous columns.
+    {
+        float *vals = sm.d.vals[wid];
+        for (int it = it_begin; it < it_end; ++it) {
+            int v, xg, y0;
+            item_origin(a, it, v, xg, y0);
+            const EdgeView &V = a.v[v];
+            const float med2 = __uint_as_float(__ldcg(a.med_bits + v));
+            const float smed = __fsqrt_rn(med2);
+            const int nout = min(a.rb, V.h - y0);
+            const int npairs = (nout + 1) / 2;
+            const float *src = a.kept + (size_t)it * kItemCols * a.rb;
+            const uint8_t *km = a.kmask + (size_t)it * (a.rb / 2) * 32;
+            unsigned run = 0;
+            for (int t0 = 0; t0 < npairs; t0 += kDPairs) {
+                const int np = min(kDPairs, npairs - t0);
+                unsigned k8[kDPairs], excl[kDPairs], off[kDPairs];
 #pragma unroll
-            for (int r = 0; r < kDRows; ++r) keepr[r] = r < nr ? km[(q0 + r) * 32 + lane] : 0u;
-            unsigned ctot = 0;
+                for (int r = 0; r < kDPairs; ++r) k8[r] = r < np ? unsigned(__ldcg(km + (t0 + r) * 32 + lane)) : 0u;
+                unsigned ctot = 0;
 #pragma unroll
-            for (int r = 0; r < kDRows; ++r) {
-                offr[r] = ctot;
-                ctot += warp_exclusive_scan(__popc(keepr[r]), &excl[r]);
-            }
-            __syncwarp();
-            for (unsigned j = lane; j < ctot; j += 32) cp_async4(vstage + j, src + run + j);
-            cp_async_commit();
-            cp_async_wait<0>();
-            // E = sqrt(M^2) / median of every staged value, lanes on consecutive values
-            // (no lane idles on a pixel it does not keep)
-            for (unsigned j = lane; j < ctot; j += 32)
-                vstage[j] = med2 > 0.f ? __fdiv_rn(__fsqrt_rn(vstage[j]), smed) : 0.f;
-            __syncwarp();
-            for (int r = 0; r < nr; ++r) {
-                const unsigned keep = keepr[r];
-                const float *p = vstage + offr[r] + excl[r];
-                float e[kStrip];
-#pragma unroll
-                for (int j = 0; j < kStrip; ++j) {
-                    e[j] = 0.f;
-                    if (keep >> j & 1u) e[j] = *p++;
-                }
-                reinterpret_cast<float4 *>(stage)[2 * lane] = make_float4(e[0], e[1], e[2], e[3]);
-                reinterpret_cast<float4 *>(stage)[2 * lane + 1] = make_float4(e[4], e[5], e[6], e[7]);
-                if (a.mask) {
-                    unsigned lo = 0, hi = 0;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        lo |= (keep >> j & 1u) << (8 * j);
-                        hi |= (keep >> (j + 4) & 1u) << (8 * j);
-                    }
-                    reinterpret_cast<uint2 *>(mstage)[lane] = make_uint2(lo, hi);
+                for (int r = 0; r < kDPairs; ++r) {
+                    off[r] = ctot;
+                    ctot += warp_exclusive_scan(__popc(k8[r]), &excl[r]);
                 }
                 __syncwarp();
-                float *out = a.E + V.out_off + (long long)(y0 + q0 + r) * V.w + xg;
-                uint8_t *mout = a.mask ? a.mask + V.out_off + (long long)(y0 + q0 + r) * V.w + xg : nullptr;
+                for (unsigned j0 = 0; j0 < ctot; j0 += 4 * 32) {
+                    float m2[4];
 #pragma unroll
-                for (int k = 0; k < kStrip; ++k) {
-                    const int c = 32 * k + lane;
-                    if (xg + c < V.w) {
-                        out[c] = stage[c];
-                        if (mout) mout[c] = mstage[c];
+                    for (int u = 0; u < 4; ++u) {
+                        const unsigned j = j0 + 32 * u + lane;
+                        m2[u] = j < ctot ? __ldcg(src + run + j) : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const unsigned j = j0 + 32 * u + lane;
+                        if (j < ctot) vals[j] = med2 > 0.f ? __fdiv_rn(__fsqrt_rn(m2[u]), smed) : 0.f;
                     }
                 }
                 __syncwarp();
+#pragma unroll
+                for (int r = 0; r < kDPairs; ++r) {
+                    if (r >= np) break;
+                    const float *p = vals + off[r] + excl[r];
+                    float e[2 * kQ];
+#pragma unroll
+                    for (int b = 0; b < 2 * kQ; ++b) {
+                        e[b] = 0.f;
+                        if (k8[r] >> b & 1u) e[b] = *p++;
+                    }
+                    float *row0 = sm.d.row[wid][0], *row1 = sm.d.row[wid][1];
+                    reinterpret_cast<float4 *>(row0)[lane] = make_float4(e[0], e[1], e[2], e[3]);
+                    reinterpret_cast<float4 *>(row1)[lane] = make_float4(e[4], e[5], e[6], e[7]);
+                    if (a.mask) {
+                        unsigned lo = 0, hi = 0;
+#pragma unroll
+                        for (int j = 0; j < kQ; ++j) {
+                            lo |= (k8[r] >> j & 1u) << (8 * j);
+                            hi |= (k8[r] >> (j + kQ) & 1u) << (8 * j);
+                        }
+                        reinterpret_cast<unsigned *>(sm.d.mrow[wid][0])[lane] = lo;
+                        reinterpret_cast<unsigned *>(sm.d.mrow[wid][1])[lane] = hi;
+                    }
+                    __syncwarp();
+                    for (int rr = 0; rr < 2; ++rr) {
+                        const int qrow = 2 * (t0 + r) + rr;
+                        if (qrow >= nout) break;
+                        const long long rowoff = V.out_off + (long long)(y0 + qrow) * V.w + xg;
+                        float *out = a.E + rowoff;
+                        uint8_t *mout = a.mask ? a.mask + rowoff : nullptr;
+                        const float *st = sm.d.row[wid][rr];
+                        const uint8_t *mst = sm.d.mrow[wid][rr];
+#pragma unroll
+                        for (int k = 0; k < kQ; ++k) {
+                            const int c = 32 * k + lane - kQ;  // output column xg + c, staged at c + kQ
+                            if (c >= 0 && c < kItemCols && xg + c < V.w) {
+                                out[c] = st[c + kQ];
+                                if (mout) mout[c] = mst[c + kQ];
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+                run += ctot;
             }
-            run += ctot;
         }
     }
 }
+
 // ------------------------------------------------------------ plain path
 
 struct PlainBufs {
@@ -1318,13 +1406,13 @@ void fill_taps(const gsp_edge_opts &o, float &w0, float &w1, float &w2)
     w2 = float(e2 / z);
 }
 
-// Work plan of the fused kernel: one block of NT threads per SM; warp items of
-// 256 columns x rb rows.  rb minimises the rounds of items over the warps times
-// the rows a round walks (each band re-walks 8 halo rows).
+// Work plan of the walk kernel: kWalkBlocksPerSM blocks of WNT threads per SM;
+// warp items of 120 output columns x rb rows (rb even).  rb minimises the
+// rounds of items over the warps times the rows a round walks (each band
+// re-walks 8 halo rows).
 struct EdgePlan {
     int rb = 0;
     long long items = 0;
-    int grid = 0;
 };
 
 long long plan_items(const gsp_image_desc *imgs, int nv, int rb)
@@ -1338,10 +1426,9 @@ long long plan_items(const gsp_image_desc *imgs, int nv, int rb)
 EdgePlan edge_plan(const gsp_image_desc *imgs, int nv)
 {
     EdgePlan p;
-    p.grid = num_sms();
-    const long long warps = (long long)p.grid * kWarps;
+    const long long warps = (long long)num_sms() * kWalkBlocksPerSM * kWWarps;
     double best = 1e300;
-    for (int rb = 8; rb <= 128; ++rb) {
+    for (int rb = 8; rb <= 128; rb += 2) {
         const long long items = plan_items(imgs, nv, rb);
         const double cost = double((items + warps - 1) / warps) * double(rb + 8);
         if (cost < best) {
@@ -1353,7 +1440,6 @@ EdgePlan edge_plan(const gsp_image_desc *imgs, int nv)
     return p;
 }
 
-constexpr size_t kWalkSmem = size_t(kWarps) * sizeof(WarpSmem);  // per warp: histogram, row ring, luma rows
 constexpr size_t kTileSmem = 128 + sizeof(StageSmem) + sizeof(TileSmem) + kBins1 * sizeof(unsigned);
 
 // The walk kernel from this many pixels on (measured: 32 views of 1237 x 822 in
@@ -1396,7 +1482,7 @@ EdgeLayout edge_layout(void *ws, const gsp_image_desc *imgs, int nv, int mode, c
         L.cand = c.take<float>((size_t)total);
         if (use_walk(imgs, nv)) {
             L.kept = c.take<float>((size_t)P.items * kItemCols * P.rb);
-            L.kmask = c.take<uint8_t>((size_t)P.items * P.rb * 32);
+            L.kmask = c.take<uint8_t>((size_t)P.items * (P.rb / 2) * 32);
             L.kcount = c.take<unsigned>((size_t)P.items);
         }
     } else {
@@ -1573,19 +1659,13 @@ extern "C" gsp_status gsp_edge_map(const gsp_image_desc *imgs, int32_t nv, float
         a.status = dev_status;
         a.spin_limit = spin;
         a.expire = o.test_expire & 1;
-        static bool attr_set[kMaxDevices] = {false};
-        if (!attr_set[dev]) {
-            GSP_CUDA_TRY(cudaFuncSetAttribute(edge_walk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              int(kWalkSmem)));
-            attr_set[dev] = true;
-        }
         int per_sm = 0;
-        GSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_walk_kernel, NT, kWalkSmem));
+        GSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_walk_kernel, WNT, 0));
         if (per_sm < 1) return GSP_ERR_UNSUPPORTED;
         cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(P.grid);
-        cfg.blockDim = dim3(NT);
-        cfg.dynamicSmemBytes = kWalkSmem;
+        cfg.gridDim = dim3(num_sms() * (per_sm < kWalkBlocksPerSM ? per_sm : kWalkBlocksPerSM));
+        cfg.blockDim = dim3(WNT);
+        cfg.dynamicSmemBytes = 0;
         cfg.stream = s;
         cfg.attrs = coop;
         cfg.numAttrs = 1;
