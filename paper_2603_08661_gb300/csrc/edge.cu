@@ -5,8 +5,9 @@
 // (= 255000 x the [0, 1] luma).  Blur and Sobel are linear and act on the
 // clamp-extended image, so they commute: the Sobel differences are taken first
 // on the exact integers (|S| < 2^21, exact in FP32) and the 5x5 blur is applied
-// to them in FP32 with its symmetric taps paired (pair sums stay exact in the
-// horizontal pass).  NMS compares squared magnitudes M^2 = gx^2 + gy^2 (the
+// to them in FP32: horizontally with its symmetric taps paired (the pair sums
+// of integers are exact), vertically as one FMA chain from the top row down.
+// NMS compares squared magnitudes M^2 = gx^2 + gy^2 (the
 // comparisons of M and of M^2 agree except at FP32 near-ties), and only kept
 // pixels take a square root.  Magnitudes stay in units of 255000 x luma; E =
 // M / median is unit-free.
@@ -89,6 +90,15 @@ __device__ __forceinline__ float i2f_exact(int i)
 __device__ __forceinline__ float luma_exact(unsigned px)
 {
     return i2f_exact(int(__dp4a(px, 0x00724B2Bu, __dp4a(px, 0x00000201u, 0u) << 8)));
+}
+
+// Vertical 5-tap blur of one column, rows h0 (top) .. h4: the chain
+// w2 h0 (+) w1 h1 (+) w0 h2 (+) w1 h3 (+) w2 h4, each step one rounding (the
+// walk kernel advances the same chains in place as rows arrive).
+__device__ __forceinline__ float vblur5(float h0, float h1, float h2, float h3, float h4, float w0, float w1,
+                                        float w2)
+{
+    return __fmaf_rn(w2, h4, __fmaf_rn(w1, h3, __fmaf_rn(w0, h2, __fmaf_rn(w1, h1, __fmul_rn(w2, h0)))));
 }
 
 // Exclusive warp scan of one value per lane; returns the warp total.
@@ -317,10 +327,8 @@ __device__ void tile_stencil(const TileView &V, int x0, int y0, float w0, float 
 #pragma unroll
         for (int j = 0; j < kSegV; ++j) {
             const int r = r0 + j;
-            const float bx1 = __fadd_rn(hx[j + 1], hx[j + 3]), bx2 = __fadd_rn(hx[j], hx[j + 4]);
-            const float by1 = __fadd_rn(hy[j + 1], hy[j + 3]), by2 = __fadd_rn(hy[j], hy[j + 4]);
-            const float gx = __fmaf_rn(w2, bx2, __fmaf_rn(w1, bx1, __fmul_rn(w0, hx[j + 2])));
-            const float gy = __fmaf_rn(w2, by2, __fmaf_rn(w1, by1, __fmul_rn(w0, hy[j + 2])));
+            const float gx = vblur5(hx[j], hx[j + 1], hx[j + 2], hx[j + 3], hx[j + 4], w0, w1, w2);
+            const float gy = vblur5(hy[j], hy[j + 1], hy[j + 2], hy[j + 3], hy[j + 4], w0, w1, w2);
             const int yy = y0 - 1 + r;
             const bool inside = yy >= 0 && yy < V.h && xx >= 0 && xx < V.w;
             s.M[r][c] = inside ? __fmaf_rn(gx, gx, __fmul_rn(gy, gy)) : 0.0f;  // squared magnitude
@@ -617,7 +625,6 @@ constexpr int kItemCols = 32 * kQ - 2 * kQ;   // 120 output columns per item
 constexpr int kDPairs = 8;                    // row pairs per phase-D chunk
 constexpr int kBCand = 512;                   // phase-B candidate buffer per warp
 constexpr unsigned kFull = 0xffffffffu;
-constexpr bool kWalkRotate = true;            // one step per loop trip, the blurred-row window moved by copies
 
 struct EdgeView {
     const uint8_t *rgb;
@@ -739,7 +746,7 @@ __device__ __forceinline__ void row_luma(const QLane &q, const unsigned (&w)[4],
 // Walk state of a lane.
 struct QState {
     float I0[kQ], I1[kQ];      // luma of input rows i - 2, i - 1
-    float2 H[5][kQ];           // (x, y) horizontally blurred Sobel rows, slot = Sobel row mod 5
+    float2 acc[4][kQ];         // vertical blur chains: acc[d] lacks the d + 1 newest blurred rows
     float M0[kQ + 2];          // M^2 of NMS row q - 1 (index 0: column -1, kQ + 1: column kQ)
     float M1[kQ + 2];          // M^2 of NMS row q
     float2 g1[kQ];             // blurred gradient of row q
@@ -778,25 +785,20 @@ __device__ __forceinline__ void emit_pair(QOut &o, int pair, unsigned k8, const 
     o.run += tot;
 }
 
-// Input step i of the walk: luma row i, Sobel row i - 1, horizontal blur,
-// then (i >= 6) vertical blur of row m = y0 - 7 + i and its M^2, then (i >= 8)
-// NMS of output row q = i - 8.  The five blurred rows sit in slots: with
-// P = i mod 5 (a walk unrolled by five steps) the slots are chosen statically,
-// with P = -1 the window moves down one slot per step (slot 4 the newest).
-template <int P>
+// Input step i of the walk (PAR = i mod 2): luma row i, Sobel row i - 1 and its
+// horizontal blur, which completes the vertical blur of row m = y0 - 7 + i
+// (i >= 6) and its M^2, then (i >= 8) NMS of output row r = i - 8, emitted
+// with the row before it when r is odd.  The vertical blur of a row is the
+// chain w2 h0 (+) w1 h1 (+) w0 h2 (+) w1 h3 (+) w2 h4 over its five blurred
+// rows, oldest first: four partial chains advance in place as rows arrive.
+template <int PAR>
 __device__ __forceinline__ void qstep(const QLane &q, const float2 w0v, const float2 w1v, const float2 w2v,
                                       QState &s, QOut &o, int i)
 {
     float Ic[kQ];
     row_luma(q, s.w, s.shift, Ic);
     if (i + 1 < q.nin) load_row(q, i + 1, s.w, s.shift);
-    constexpr int hs = P < 0 ? 4 : (P + 3) % 5;  // slot of Sobel row i - 1 (its index i - 2 from the first)
-    if (P < 0) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-#pragma unroll
-            for (int j = 0; j < kQ; ++j) s.H[t][j] = s.H[t + 1][j];
-    }
+    float2 g[kQ];
     if (i >= 2) {
         // vertical parts of Sobel row i - 1 (exact integers in FP32), the lane's
         // columns at index 1..4, the neighbours' edge columns at 0 and 5
@@ -824,11 +826,18 @@ __device__ __forceinline__ void qstep(const QLane &q, const float2 w0v, const fl
         f[kQ + 2].y = __shfl_down_sync(kFull, f[2].y, 1);
         f[kQ + 3].x = __shfl_down_sync(kFull, f[3].x, 1);
         f[kQ + 3].y = __shfl_down_sync(kFull, f[3].y, 1);
-        // horizontal blur, taps paired (both components at once)
 #pragma unroll
-        for (int j = 0; j < kQ; ++j)
-            s.H[hs][j] = __ffma2_rn(w2v, __fadd2_rn(f[j], f[j + 4]),
-                                    __ffma2_rn(w1v, __fadd2_rn(f[j + 1], f[j + 3]), __fmul2_rn(w0v, f[j + 2])));
+        for (int j = 0; j < kQ; ++j) {
+            // horizontal blur, taps paired (both components at once)
+            const float2 h = __ffma2_rn(w2v, __fadd2_rn(f[j], f[j + 4]),
+                                        __ffma2_rn(w1v, __fadd2_rn(f[j + 1], f[j + 3]), __fmul2_rn(w0v, f[j + 2])));
+            // the newest row ends the oldest chain and enters the others
+            g[j] = __ffma2_rn(w2v, h, s.acc[3][j]);
+            s.acc[3][j] = __ffma2_rn(w1v, h, s.acc[2][j]);
+            s.acc[2][j] = __ffma2_rn(w0v, h, s.acc[1][j]);
+            s.acc[1][j] = __ffma2_rn(w1v, h, s.acc[0][j]);
+            s.acc[0][j] = __fmul2_rn(w2v, h);
+        }
     }
 #pragma unroll
     for (int j = 0; j < kQ; ++j) {
@@ -836,19 +845,12 @@ __device__ __forceinline__ void qstep(const QLane &q, const float2 w0v, const fl
         s.I1[j] = Ic[j];
     }
     if (i < 6) return;
-    // vertical blur of row m = y0 - 7 + i from Sobel rows m - 2 .. m + 2 (slots, oldest first)
-    constexpr int h0 = P < 0 ? 0 : (P + 4) % 5, h1 = P < 0 ? 1 : P, h2 = P < 0 ? 2 : (P + 1) % 5,
-                  h3 = P < 0 ? 3 : (P + 2) % 5, h4 = P < 0 ? 4 : (P + 3) % 5;
     const int m = q.y0 - 7 + i;
     const bool row_in = m >= 0 && m < q.h;
-    float2 g[kQ];
     float M2[kQ + 2];
 #pragma unroll
-    for (int j = 0; j < kQ; ++j) {
-        g[j] = __ffma2_rn(w2v, __fadd2_rn(s.H[h0][j], s.H[h4][j]),
-                          __ffma2_rn(w1v, __fadd2_rn(s.H[h1][j], s.H[h3][j]), __fmul2_rn(w0v, s.H[h2][j])));
+    for (int j = 0; j < kQ; ++j)
         M2[j + 1] = (row_in && (q.colmask >> j & 1u)) ? __fmaf_rn(g[j].x, g[j].x, __fmul_rn(g[j].y, g[j].y)) : 0.f;
-    }
     M2[0] = __shfl_up_sync(kFull, M2[kQ], 1);
     M2[kQ + 1] = __shfl_down_sync(kFull, M2[1], 1);
     if (i >= 8) {
@@ -878,14 +880,14 @@ __device__ __forceinline__ void qstep(const QLane &q, const float2 w0v, const fl
         }
         keep &= q.outmask;
         const int r = i - 8;
-        if ((r & 1) == 0 && r + 1 < q.nout) {
+        if (PAR == 0 && r + 1 < q.nout) {
             s.keep0 = keep;
 #pragma unroll
             for (int j = 0; j < kQ; ++j) s.v0[j] = vals[j];
         } else {
             float vv[2 * kQ];
             unsigned k8;
-            if (r & 1) {
+            if (PAR == 1) {
                 k8 = s.keep0 | keep << kQ;
 #pragma unroll
                 for (int j = 0; j < kQ; ++j) {
@@ -945,18 +947,10 @@ __device__ unsigned walk_item(const EdgeArgs &a, int it, unsigned *whist)
     QState s;
     s.keep0 = 0u;
     load_row(q, 0, s.w, s.shift);
-    if (kWalkRotate) {
 #pragma unroll 1
-        for (int i = 0; i < q.nin; ++i) qstep<-1>(q, w0v, w1v, w2v, s, o, i);
-    } else {
-#pragma unroll 1
-        for (int i = 0; i < q.nin; i += 5) {
-            qstep<0>(q, w0v, w1v, w2v, s, o, i);
-            if (i + 1 < q.nin) qstep<1>(q, w0v, w1v, w2v, s, o, i + 1);
-            if (i + 2 < q.nin) qstep<2>(q, w0v, w1v, w2v, s, o, i + 2);
-            if (i + 3 < q.nin) qstep<3>(q, w0v, w1v, w2v, s, o, i + 3);
-            if (i + 4 < q.nin) qstep<4>(q, w0v, w1v, w2v, s, o, i + 4);
-        }
+    for (int i = 0; i < q.nin; i += 2) {
+        qstep<0>(q, w0v, w1v, w2v, s, o, i);
+        if (i + 1 < q.nin) qstep<1>(q, w0v, w1v, w2v, s, o, i + 1);
     }
     if (lane == 0) a.kcount[it] = o.run;
     return o.run;
@@ -1294,8 +1288,8 @@ __global__ void plain_vblur_mag(TileView V, const float *Hx, const float *Hy, fl
     int r = int(i / W), c = int(i - (long long)r * W);
     long long s = (long long)W;
     const float *x = Hx + (long long)r * W + c, *y = Hy + (long long)r * W + c;
-    float gx = __fmaf_rn(w2, __fadd_rn(x[0], x[4 * s]), __fmaf_rn(w1, __fadd_rn(x[s], x[3 * s]), __fmul_rn(w0, x[2 * s])));
-    float gy = __fmaf_rn(w2, __fadd_rn(y[0], y[4 * s]), __fmaf_rn(w1, __fadd_rn(y[s], y[3 * s]), __fmul_rn(w0, y[2 * s])));
+    float gx = vblur5(x[0], x[s], x[2 * s], x[3 * s], x[4 * s], w0, w1, w2);
+    float gy = vblur5(y[0], y[s], y[2 * s], y[3 * s], y[4 * s], w0, w1, w2);
     bool inside = r >= 1 && r <= V.h && c >= 1 && c <= V.w;
     Gx[i] = gx;
     Gy[i] = gy;
