@@ -165,11 +165,13 @@ def stage_work(stage, n, k_sh, npix, pairs, evals, contrib):
     return table.get(stage)
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel from one ncu capture of this workload
-# (profiles/composite_bwd_1M_sh3_1237x822.md): valid for the captured variant
-# while the compositing source is the one that was captured.
-NCU_TRAFFIC = {("composite_bwd", 4): (43_537_920, "9e834e2311737c53")}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) and warp
+# instructions per launch (sm__inst_executed.sum) of the dominant kernel from
+# one ncu capture of this workload (profiles/composite_bwd_1M_sh3_1237x822.md):
+# valid for the captured variant while the compositing source is the one that
+# was captured.
+NCU_TRAFFIC = {("composite_bwd", 4): (46_372_352, "72140bd405d14970")}
+NCU_INST = {("composite_bwd", 4): (323_373_585, "72140bd405d14970")}
 
 
 def compositing_source_hash():
@@ -186,6 +188,25 @@ def captured_traffic(stage, variants):
         return None
     nbytes, src = NCU_TRAFFIC[key]
     return nbytes if src == compositing_source_hash() else None
+
+
+def issue_roofline(stage, variants, n_sm, sm_mhz, avg_ms):
+    """The instruction-issue bound of a compositing kernel: its warp instructions
+    per launch (ncu sm__inst_executed.sum, taken while the source was the one
+    hashed) at one warp instruction per cycle on each of the 4 schedulers of
+    every SM; frac = that time / the measured launch time.  None once the
+    source has changed since the capture."""
+    key = (stage, variants[1] if stage == "composite_bwd" else variants[0])
+    if key not in NCU_INST:
+        return None
+    inst, src = NCU_INST[key]
+    if src != compositing_source_hash():
+        return None
+    peak = 4 * n_sm * sm_mhz * 1e6
+    min_ms = inst / peak * 1e3
+    return {"warp_inst_per_launch": inst, "peak_warp_inst_per_s": peak, "min_ms": round(min_ms, 4),
+            "frac": round(min_ms / avg_ms, 4),
+            "source": "ncu sm__inst_executed.sum; 4 schedulers x SMs x max SM clock"}
 
 
 def alu_peak_tflops(n_sm, sm_max_mhz):
@@ -424,6 +445,7 @@ def run_gsp(args, rank, world):
 
     roof = roofline(dominant, dom_avg_ms)
     roof.update({"kernel": dominant, "traffic": captured_traffic(dominant, variants),
+                 "issue": issue_roofline(dominant, variants, props.multi_processor_count, sm_max, dom_avg_ms),
                  "avg_launch_ms": round(dom_avg_ms, 5), "launches": dom_cnt,
                  "peak_source": (f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if roof["bound"] == "hbm" else
                                  f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "

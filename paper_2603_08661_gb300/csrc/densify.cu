@@ -77,15 +77,12 @@ __global__ void __launch_bounds__(kThreads) flag_block_sums(F f, const int32_t *
 }
 
 // Exclusive scan of the block sums (one block); total goes to sums[nblocks].
-__global__ void __launch_bounds__(kThreads) scan_block_sums(const int32_t *count, unsigned *sums, unsigned *ticket)
+__global__ void __launch_bounds__(kThreads) scan_block_sums(const int32_t *count, unsigned *sums)
 {
     __shared__ unsigned carry;
     const long long n = *count;
     const int nb = int((n + kBlockItems - 1) / kBlockItems);
-    if (threadIdx.x == 0) {
-        carry = 0;
-        *ticket = 0u;  // the split's completion ticket
-    }
+    if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int b0 = 0; b0 < nb; b0 += kThreads) {
         int b = b0 + threadIdx.x;
@@ -284,109 +281,112 @@ struct LasArgs {
     int32_t *count;
     long long cap;
     int K;
-    int vec4;                  // SH rows copied in 16-byte chunks
     float k_off, log_long, log_other, beta;
     const uint8_t *mask;
     const unsigned *rank_off;  // block offsets; [nblocks] = total selected
-    unsigned *ticket;          // blocks finished (zeroed by scan_block_sums)
+    int32_t *src;              // [cap]: parent of appended child slot n + r
     int32_t *status;
 };
 
-// Alg. 1 for the selected Gaussians of one block of kBlockItems: child 0
-// replaces the parent, child 1 is appended at n + its rank.  The block then
-// copies its appended children's SH rows (one thread per 16-byte chunk), and
-// the last block to finish commits the new count, or reports a capacity
-// overflow (then nothing has been written).
 __global__ void __launch_bounds__(kThreads) las_kernel(LasArgs a)
 {
-    __shared__ int32_t s_src[kBlockItems];  // parent of the block's r-th appended child
     const long long n = *a.count;
     const long long b0 = (long long)blockIdx.x * kBlockItems;
+    if (b0 >= n) return;
+    const int nb = int((n + kBlockItems - 1) / kBlockItems);
+    const long long total = a.rank_off[nb];
+    if (n + total > a.cap) return;  // reported by las_commit; nothing is written
+    bool f[kPerThread];
+    unsigned c = 0;
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        long long i = b0 + threadIdx.x * kPerThread + j;
+        f[j] = i < n && a.mask[i] != 0;
+        c += f[j];
+    }
+    unsigned ex;
+    block_scan(c, &ex);
+    unsigned r = a.rank_off[blockIdx.x] + ex;
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        if (!f[j]) continue;
+        const long long i = b0 + threadIdx.x * kPerThread + j;
+        const long long dst = n + r;
+        ++r;
+        if (!GSP_BOUND(dst, a.cap, a.status)) continue;
+        float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
+        int l = 0;
+        if (ls[1] > ls[l]) l = 1;
+        if (ls[2] > ls[l]) l = 2;
+        const float off = a.k_off * expf(ls[l]);
+        float q[4] = {a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]};
+        const float qi = __frsqrt_rn(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const float w = q[0] * qi, x = q[1] * qi, y = q[2] * qi, z = q[3] * qi;
+        // column l of the row-major rotation matrix: entries l, l + 3, l + 6 (Alg. 2)
+        float cx, cy, cz;
+        if (l == 0) {
+            cx = 1.f - 2.f * (y * y + z * z); cy = 2.f * (x * y + w * z); cz = 2.f * (x * z - w * y);
+        } else if (l == 1) {
+            cx = 2.f * (x * y - w * z); cy = 1.f - 2.f * (x * x + z * z); cz = 2.f * (y * z + w * x);
+        } else {
+            cx = 2.f * (x * z + w * y); cy = 2.f * (y * z - w * x); cz = 1.f - 2.f * (x * x + y * y);
+        }
+        const float dx = cx * off, dy = cy * off, dz = cz * off;
+        float nls[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) nls[k] = ls[k] + (k == l ? a.log_long : a.log_other);
+        const float sig = 1.f / (1.f + expf(-a.opac[i]));
+        const float p = a.beta * sig;
+        const float nop = logf(p) - log1pf(-p);
+        const float m0 = a.means[3 * i], m1 = a.means[3 * i + 1], m2 = a.means[3 * i + 2];
+        // child 1 (appended)
+        a.means[3 * dst] = m0 - dx; a.means[3 * dst + 1] = m1 - dy; a.means[3 * dst + 2] = m2 - dz;
+        for (int k = 0; k < 3; ++k) a.log_scales[3 * dst + k] = nls[k];
+        for (int k = 0; k < 4; ++k) a.quats[4 * dst + k] = q[k];
+        a.opac[dst] = nop;
+        a.src[dst - n] = int32_t(i);
+        // child 0 (in place)
+        a.means[3 * i] = m0 + dx; a.means[3 * i + 1] = m1 + dy; a.means[3 * i + 2] = m2 + dz;
+        for (int k = 0; k < 3; ++k) a.log_scales[3 * i + k] = nls[k];
+        a.opac[i] = nop;
+    }
+}
+
+// SH rows of the appended children: one thread per (child, chunk), chunks of
+// 16 bytes when the rows allow it (every copy independent: no per-row loop).
+__global__ void __launch_bounds__(256) las_copy_sh(LasArgs a, int vec4)
+{
+    const long long n = *a.count;
     const int nb = int((n + kBlockItems - 1) / kBlockItems);
     const long long total = n > 0 ? a.rank_off[nb] : 0;
-    const bool fits = n + total <= a.cap;
-    if (b0 < n && fits) {
-        bool f[kPerThread];
-        unsigned c = 0;
-#pragma unroll
-        for (int j = 0; j < kPerThread; ++j) {
-            long long i = b0 + threadIdx.x * kPerThread + j;
-            f[j] = i < n && a.mask[i] != 0;
-            c += f[j];
-        }
-        unsigned ex;
-        const unsigned mine = block_scan(c, &ex);  // the block's children
-        const unsigned base = a.rank_off[blockIdx.x];
-        unsigned r = base + ex;
-#pragma unroll
-        for (int j = 0; j < kPerThread; ++j) {
-            if (!f[j]) continue;
-            const long long i = b0 + threadIdx.x * kPerThread + j;
-            const long long dst = n + r;
-            s_src[r - base] = int32_t(i);
-            ++r;
-            if (!GSP_BOUND(dst, a.cap, a.status)) continue;
-            float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
-            int l = 0;
-            if (ls[1] > ls[l]) l = 1;
-            if (ls[2] > ls[l]) l = 2;
-            const float off = a.k_off * expf(ls[l]);
-            float q[4] = {a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]};
-            const float qi = __frsqrt_rn(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-            const float w = q[0] * qi, x = q[1] * qi, y = q[2] * qi, z = q[3] * qi;
-            // column l of the row-major rotation matrix: entries l, l + 3, l + 6 (Alg. 2)
-            float cx, cy, cz;
-            if (l == 0) {
-                cx = 1.f - 2.f * (y * y + z * z); cy = 2.f * (x * y + w * z); cz = 2.f * (x * z - w * y);
-            } else if (l == 1) {
-                cx = 2.f * (x * y - w * z); cy = 1.f - 2.f * (x * x + z * z); cz = 2.f * (y * z + w * x);
-            } else {
-                cx = 2.f * (x * z + w * y); cy = 2.f * (y * z - w * x); cz = 1.f - 2.f * (x * x + y * y);
-            }
-            const float dx = cx * off, dy = cy * off, dz = cz * off;
-            float nls[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) nls[k] = ls[k] + (k == l ? a.log_long : a.log_other);
-            const float sig = 1.f / (1.f + expf(-a.opac[i]));
-            const float p = a.beta * sig;
-            const float nop = logf(p) - log1pf(-p);
-            const float m0 = a.means[3 * i], m1 = a.means[3 * i + 1], m2 = a.means[3 * i + 2];
-            // child 1 (appended)
-            a.means[3 * dst] = m0 - dx; a.means[3 * dst + 1] = m1 - dy; a.means[3 * dst + 2] = m2 - dz;
-            for (int k = 0; k < 3; ++k) a.log_scales[3 * dst + k] = nls[k];
-            for (int k = 0; k < 4; ++k) a.quats[4 * dst + k] = q[k];
-            a.opac[dst] = nop;
-            // child 0 (in place)
-            a.means[3 * i] = m0 + dx; a.means[3 * i + 1] = m1 + dy; a.means[3 * i + 2] = m2 + dz;
-            for (int k = 0; k < 3; ++k) a.log_scales[3 * i + k] = nls[k];
-            a.opac[i] = nop;
-        }
-        __syncthreads();
-        // SH rows of the block's appended children (parents' rows are not written)
-        const int row = 3 * a.K;
-        const int chunks = a.vec4 ? row / 4 : row;
-        for (int t = threadIdx.x; t < int(mine) * chunks; t += kThreads) {
-            const int c = t / chunks, qk = t - c * chunks;
-            const long long src = s_src[c], dst = n + base + c;
-            if (!GSP_BOUND(src, n, a.status) || !GSP_BOUND(dst, a.cap, a.status)) continue;
-            if (a.vec4)
-                reinterpret_cast<float4 *>(a.sh + (size_t)dst * row)[qk] =
-                    reinterpret_cast<const float4 *>(a.sh + (size_t)src * row)[qk];
-            else
-                a.sh[(size_t)dst * row + qk] = a.sh[(size_t)src * row + qk];
-        }
+    if (n + total > a.cap) return;
+    const int row = 3 * a.K;
+    const int chunks = vec4 ? row / 4 : row;
+    const long long work = total * chunks;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < work;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long c = t / chunks;
+        const int q = int(t - c * chunks);
+        const long long src = a.src[c], dst = n + c;
+        if (!GSP_BOUND(src, n, a.status)) continue;
+        if (vec4)
+            reinterpret_cast<float4 *>(a.sh + (size_t)dst * row)[q] =
+                reinterpret_cast<const float4 *>(a.sh + (size_t)src * row)[q];
+        else
+            a.sh[(size_t)dst * row + q] = a.sh[(size_t)src * row + q];
     }
-    // every block has read the count once the last one arrives here
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(a.ticket, 1u) == gridDim.x - 1) {
-            if (!fits)
-                set_status(a.status, GSP_ERR_CAPACITY);
-            else
-                *a.count = int32_t(n + total);
-        }
+}
+
+__global__ void las_commit(int32_t *count, long long cap, const unsigned *rank_off, int32_t *status)
+{
+    const long long n = *count;
+    const int nb = int((n + kBlockItems - 1) / kBlockItems);
+    const long long total = n > 0 ? rank_off[nb] : 0;
+    if (n + total > cap) {
+        set_status(status, GSP_ERR_CAPACITY);
+        return;
     }
+    *count = int32_t(n + total);
 }
 
 // [3][kSelBins] digit counts, the 2-word grid barrier, the candidate count:
@@ -399,7 +399,7 @@ struct DensifyLayout {
     unsigned *ncand;
     unsigned *sums;
     uint8_t *mask;
-    unsigned *ticket;
+    int32_t *src;
     size_t bytes;
 };
 
@@ -418,7 +418,7 @@ DensifyLayout densify_layout(void *ws, long long cap)
     DensifyLayout L{};
     carve_topk(c, cap, L);
     L.mask = c.take<uint8_t>((size_t)cap);
-    L.ticket = c.take<unsigned>(1);
+    L.src = c.take<int32_t>((size_t)cap);
     L.bytes = c.size();
     return L;
 }
@@ -574,7 +574,7 @@ extern "C" gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask,
     MaskFlag mf{mask};
     stage_begin("las", s);
     flag_block_sums<<<nblk, kThreads, 0, s>>>(mf, g->count, L.sums);
-    scan_block_sums<<<1, kThreads, 0, s>>>(g->count, L.sums, L.ticket);
+    scan_block_sums<<<1, kThreads, 0, s>>>(g->count, L.sums);
     LasArgs a;
     a.means = g->means; a.log_scales = g->log_scales; a.quats = g->quats; a.opac = g->opacity_logits;
     a.sh = g->sh; a.count = g->count; a.cap = cap;
@@ -585,12 +585,14 @@ extern "C" gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask,
     a.beta = p->beta;
     a.mask = mask;
     a.rank_off = L.sums;
-    a.ticket = L.ticket;
-    a.vec4 = (3 * a.K) % 4 == 0 && (reinterpret_cast<uintptr_t>(g->sh) & 15) == 0;
+    a.src = L.src;
     a.status = dev_status;
     las_kernel<<<nblk, kThreads, 0, s>>>(a);
+    const int vec4 = (3 * a.K) % 4 == 0 && (reinterpret_cast<uintptr_t>(g->sh) & 15) == 0;
+    las_copy_sh<<<4 * num_sms(), 256, 0, s>>>(a, vec4);
+    las_commit<<<1, 1, 0, s>>>(g->count, cap, L.sums, dev_status);
     stage_end("las", s);
-    note_launches(3);
+    note_launches(5);
     GSP_LAUNCH_CHECK();
     return GSP_OK;
 }

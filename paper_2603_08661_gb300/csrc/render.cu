@@ -85,6 +85,7 @@ struct State {
     unsigned *sort_state;     // [V][4][nb_max][256] look-back words of the depth sort
     unsigned *sort_ghist;     // [V][4][256] digit counts of the four passes
     unsigned *sort_ticket;    // [V][4] tile tickets of the four passes
+    unsigned *scan_ticket;    // [2] blocks done in l1_scan, l2_scan (the last one scans the totals)
     unsigned *count1;         // [total_super][nch1_max] level-1 chunk counts, then offsets
     unsigned *len1;           // [total_super] supertile list lengths
     unsigned *list1_start;    // [total_super] supertile list starts in id1
@@ -929,30 +930,52 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
 // One block per supertile (all views): offsets of the chunks inside its list.
 constexpr int kScanThreads = 1024;  // l1_scan / l2_scan: one block per supertile
 
-__global__ void __launch_bounds__(kScanThreads) l1_scan(const __grid_constant__ Views vs, State st)
+// Whether this block is the last of the grid to arrive (its writes, and all
+// earlier blocks', are then visible to it).
+__device__ __forceinline__ bool last_block(unsigned *ticket)
 {
-    __shared__ unsigned long long wsum[kScanThreads / 32];
-    if (*st.overflow) return;
-    const int gs = blockIdx.x;
-    const int n = *st.n_dev;
-    const int nch = (n + kL1Ranks - 1) / kL1Ranks;
-    unsigned *row = st.count1 + (size_t)gs * st.nch1_max;
-    const int q = (nch + kScanThreads - 1) / kScanThreads;
-    const int c0 = threadIdx.x * q, c1 = min(c0 + q, nch);
-    unsigned long long sum = 0;
-    for (int c = c0; c < c1; ++c) sum += row[c];
-    unsigned long long total;
-    unsigned long long run = block_excl_scan<kScanThreads>(sum, wsum, &total);
-    for (int c = c0; c < c1; ++c) {
-        const unsigned x = row[c];
-        row[c] = unsigned(run);
-        run += x;
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
-    if (threadIdx.x == 0) st.len1[gs] = unsigned(total);
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
 }
 
-// One block: starts of the supertile lists, level-2 chunk bases, capacity check.
-__global__ void __launch_bounds__(1024) bin_tops(int total_super, State st, int32_t *status)
+__device__ void bin_tops(int total_super, State st, int32_t *status);
+__device__ void tile_scan(int total_tiles, State st, int32_t *status);
+
+__global__ void __launch_bounds__(kScanThreads) l1_scan(const __grid_constant__ Views vs, State st, int32_t *status)
+{
+    __shared__ unsigned long long wsum[kScanThreads / 32];
+    if (!*st.overflow) {
+        const int gs = blockIdx.x;
+        const int n = *st.n_dev;
+        const int nch = (n + kL1Ranks - 1) / kL1Ranks;
+        unsigned *row = st.count1 + (size_t)gs * st.nch1_max;
+        const int q = (nch + kScanThreads - 1) / kScanThreads;
+        const int c0 = threadIdx.x * q, c1 = min(c0 + q, nch);
+        unsigned long long sum = 0;
+        for (int c = c0; c < c1; ++c) sum += row[c];
+        unsigned long long total;
+        unsigned long long run = block_excl_scan<kScanThreads>(sum, wsum, &total);
+        for (int c = c0; c < c1; ++c) {
+            const unsigned x = row[c];
+            row[c] = unsigned(run);
+            run += x;
+        }
+        if (threadIdx.x == 0) st.len1[gs] = unsigned(total);
+    }
+    // the last block: starts of the supertile lists, level-2 chunk bases
+    if (last_block(st.scan_ticket)) bin_tops(vs.total_super, st, status);
+}
+
+// Starts of the supertile lists, level-2 chunk bases, capacity check (one
+// block of kScanThreads, the last of l1_scan).
+__device__ void bin_tops(int total_super, State st, int32_t *status)
 {
     __shared__ unsigned long long wsum[2][32];
     __shared__ unsigned long long carry[2];
@@ -962,7 +985,7 @@ __global__ void __launch_bounds__(1024) bin_tops(int total_super, State st, int3
     const bool over0 = *st.overflow;
     for (int b0 = 0; b0 < total_super; b0 += 1024) {
         const int gs = b0 + threadIdx.x;
-        const unsigned long long len = (!over0 && gs < total_super) ? st.len1[gs] : 0;
+        const unsigned long long len = (!over0 && gs < total_super) ? __ldcg(st.len1 + gs) : 0;
         const unsigned long long nc = (len + kBinRanks - 1) / kBinRanks;
         unsigned long long a = len, b = nc;
 #pragma unroll
@@ -1145,7 +1168,7 @@ __device__ __forceinline__ int super_tile(const ViewP &V, int sx, int sy, int b)
 
 // One block per supertile: offsets of its chunks inside each tile's list, and
 // the tiles' list lengths.  Thread (group, b): tile b over a quarter of the chunks.
-__global__ void __launch_bounds__(kScanThreads) l2_scan(const __grid_constant__ Views vs, State st)
+__global__ void __launch_bounds__(kScanThreads) l2_scan(const __grid_constant__ Views vs, State st, int32_t *status)
 {
     constexpr int kGroups = kScanThreads / 64;
     __shared__ unsigned part[kGroups][64];
@@ -1174,6 +1197,8 @@ __global__ void __launch_bounds__(kScanThreads) l2_scan(const __grid_constant__ 
         const int gt = super_tile(V, sx, sy, b);
         if (gt >= 0) st.tile_len[gt] = run;
     }
+    // the last block: starts of the tile lists and the forward's tile order
+    if (last_block(st.scan_ticket + 1)) tile_scan(vs.total_tiles, st, status);
 }
 
 // 8-bit logarithmic bucket of a work estimate: 3 bits of mantissa under the
@@ -1196,7 +1221,7 @@ __device__ void order_tiles_desc(const unsigned *work, int total_tiles, int32_t 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid < 256) hist[tid] = 0;
     __syncthreads();
-    for (int t = tid; t < total_tiles; t += blockDim.x) atomicAdd(&hist[255u - work_bucket(work[t])], 1u);
+    for (int t = tid; t < total_tiles; t += blockDim.x) atomicAdd(&hist[255u - work_bucket(__ldcg(work + t))], 1u);
     __syncthreads();
     unsigned x = 0, inc = 0;
     if (tid < 256) {
@@ -1216,12 +1241,14 @@ __device__ void order_tiles_desc(const unsigned *work, int total_tiles, int32_t 
         hist[tid] = base + inc - x;
     }
     __syncthreads();
-    for (int t = tid; t < total_tiles; t += blockDim.x) order[atomicAdd(&hist[255u - work_bucket(work[t])], 1u)] = t;
+    for (int t = tid; t < total_tiles; t += blockDim.x)
+        order[atomicAdd(&hist[255u - work_bucket(__ldcg(work + t))], 1u)] = t;
 }
 
-// One block: exclusive scan of the tile list lengths into list starts; the
-// total is checked against the pair capacity once more before any id is written.
-__global__ void __launch_bounds__(1024) tile_scan(int total_tiles, State st, int32_t *status)
+// Exclusive scan of the tile list lengths into list starts (one block of
+// kScanThreads, the last of l2_scan); the total is checked against the pair
+// capacity once more before any id is written.
+__device__ void tile_scan(int total_tiles, State st, int32_t *status)
 {
     __shared__ unsigned long long wsum[32];
     __shared__ unsigned long long carry;
@@ -1230,7 +1257,7 @@ __global__ void __launch_bounds__(1024) tile_scan(int total_tiles, State st, int
     __syncthreads();
     for (int b0 = 0; b0 < total_tiles; b0 += 1024) {
         const int i = b0 + threadIdx.x;
-        const unsigned long long x = i < total_tiles ? st.tile_len[i] : 0;
+        const unsigned long long x = i < total_tiles ? __ldcg(st.tile_len + i) : 0;
         unsigned long long inc = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -2011,7 +2038,7 @@ Layout render_layout(void *ws, long long cap, const Views &vs, long long pair_ca
     s.g2d = c.take<float4>(vc * 3);
     // cleared by one memset per forward pass (from pairs_total to clear_end):
     // pair total, composited pairs, loss sum, overflow flag; the depth sort's
-    // digit counts and tickets
+    // digit counts and tickets, the binning scans' tickets
     const size_t clear0 = c.size();  // where the counters start
     long long *ctr = c.take<long long>(kCounters);
     s.pairs_total = ctr;
@@ -2020,6 +2047,7 @@ Layout render_layout(void *ws, long long cap, const Views &vs, long long pair_ca
     s.overflow = reinterpret_cast<int32_t *>(ctr + 3);
     s.sort_ghist = c.take<unsigned>((size_t)vs.n * 4 * 256);
     s.sort_ticket = c.take<unsigned>((size_t)vs.n * 4);
+    s.scan_ticket = c.take<unsigned>(2);
     L.clear_bytes = c.size() - clear0;
     s.pair_cap = pair_cap;
     L.bytes = c.size();
@@ -2189,12 +2217,10 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
         const unsigned l1_blocks = unsigned(std::min<long long>(
             std::max<long long>(div_up((long long)nv * S.nch1_max, kBinWarps), 1), 16LL * nsm));
         l1_count<<<l1_blocks, kBinThreads, smem, s>>>(vs, S, cap);
-        l1_scan<<<vs.total_super, kScanThreads, 0, s>>>(vs, S);
-        bin_tops<<<1, 1024, 0, s>>>(vs.total_super, S, dev_status);
+        l1_scan<<<vs.total_super, kScanThreads, 0, s>>>(vs, S, dev_status);
         l1_scatter<<<l1_blocks, kBinThreads, smem, s>>>(vs, S, cap);
         l2_count<<<16 * nsm, kBinThreads, 0, s>>>(vs, S, cap);
-        l2_scan<<<vs.total_super, kScanThreads, 0, s>>>(vs, S);
-        tile_scan<<<1, 1024, 0, s>>>(vs.total_tiles, S, dev_status);
+        l2_scan<<<vs.total_super, kScanThreads, 0, s>>>(vs, S, dev_status);
         l2_scatter<<<16 * nsm, kBinThreads, 0, s>>>(vs, S);
     }
     stage_end("bin", s);
@@ -2210,7 +2236,7 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     }
     stage_end("composite_fwd", s);
     GSP_LAUNCH_CHECK();
-    note_launches(2 + 5 + 8 + 1);
+    note_launches(2 + 5 + 6 + 1);
     if (loss_out) {
         loss_finalise<<<1, 1, 0, s>>>(S, opts->loss_pixels > 0 ? opts->loss_pixels : vs.total_pix, loss_out);
         note_launches(1);
