@@ -1,6 +1,10 @@
-// Status strings, the per-thread CUDA error record and the version query.
+// Status strings, the per-thread CUDA error record, the version query and the
+// stage instrumentation: an NVTX range per stage of every call (host-side
+// enqueue ranges named after the stage, for profilers that filter on them;
+// free when no tool is attached) and the armed CUDA-event stage timer.
 #include "common.cuh"
 
+#include <nvtx3/nvToolsExt.h>
 #include <string.h>
 
 #include <vector>
@@ -34,6 +38,7 @@ static void record(cudaEvent_t e, cudaStream_t s)
 
 void stage_begin(const char *stage, cudaStream_t s)
 {
+    nvtxRangePushA(stage);
     if (!g_timer.name[0] || strcmp(g_timer.name, stage) != 0) return;
     if (2 * (g_timer.used + 1) > int(g_timer.ev.size())) return;
     record(g_timer.ev[2 * g_timer.used], s);
@@ -42,6 +47,7 @@ void stage_begin(const char *stage, cudaStream_t s)
 
 void stage_end(const char *stage, cudaStream_t s)
 {
+    nvtxRangePop();
     if (!g_timer.open || strcmp(g_timer.name, stage) != 0) return;
     record(g_timer.ev[2 * g_timer.used + 1], s);
     g_timer.used++;

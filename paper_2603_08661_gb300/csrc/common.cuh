@@ -15,7 +15,8 @@ constexpr int kTilePix = kTile * kTile;   // pixels per tile = threads per compo
 // Host-side record of the last CUDA error (per host thread).
 void note_cuda_error(cudaError_t e);
 
-// Instrumentation: launch counter and the armed stage timer.
+// Instrumentation: launch counter, an NVTX range per stage (pushed by
+// stage_begin, popped by stage_end) and the armed stage timer.
 void note_launches(int n);
 void stage_begin(const char *stage, cudaStream_t s);
 void stage_end(const char *stage, cudaStream_t s);
