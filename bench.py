@@ -282,16 +282,46 @@ def run_gsp(args, rank, world):
     fwd_bufs = {"rgb": torch.empty((npix, 3), device=dev), "T": torch.empty(npix, device=dev),
                 "last": torch.empty(npix, dtype=torch.int32, device=dev), "loss": torch.empty(1, device=dev)}
 
-    def step(j, plain=False, tgt=None):
+    edge_stream = torch.cuda.Stream(device=dev)
+    score_ev = torch.cuda.Event()
+    ws_sel = torch.empty_like(ws_las)
+    sel_mask = torch.empty(cap, dtype=torch.uint8, device=dev)
+    edge_bps = 1  # one edge-map block per SM beside the forward (measured 1.18 ms per step; 2: 1.19, all: 1.20)
+
+    def step(j, plain=False, tgt=None, overlap=True):
         r = rends[j]
         tgt = target if tgt is None else tgt
-        gsp.edge_map([tgt], mode="plain" if plain else "fused", out=E, status=status, workspace=ws_e)
-        if plain:
+        if not plain and not overlap:
+            # the same launches one after another (the per-stage timings)
+            gsp.edge_map([tgt], mode="fused", out=E, status=status, workspace=ws_e)
+            out = r.forward(targets=[tgt], status=status, out=fwd_bufs)
+            r.backward(out, targets=[tgt], edge=E, score=scores[j], grads=grads, status=status)
+        elif plain:
+            gsp.edge_map([tgt], mode="plain", out=E, status=status, workspace=ws_e)
             out = r.forward(targets=[tgt], edge=E, score=scores[j], status=status, out=fwd_bufs)
             r.backward(out, targets=[tgt], grads=grads, status=status)
         else:
+            # the edge map needs only the target and the forward pass does not read
+            # it: it runs on a second stream beside projection, sort, binning and
+            # forward compositing, and the adjoint (which takes the edge score) waits
+            cur = torch.cuda.current_stream(dev)
+            edge_stream.wait_stream(cur)
+            with torch.cuda.stream(edge_stream):
+                gsp.edge_map([tgt], mode="fused", out=E, status=status, workspace=ws_e, blocks_per_sm=edge_bps)
             out = r.forward(targets=[tgt], status=status, out=fwd_bufs)
-            r.backward(out, targets=[tgt], edge=E, score=scores[j], grads=grads, status=status)
+            cur.wait_stream(edge_stream)
+            r.backward(out, targets=[tgt], edge=E, score=scores[j], grads=grads, status=status,
+                       score_event=score_ev)
+            # the selection needs only the edge score: it runs on the second stream
+            # while the adjoint chains the gradients to the parameters; the split
+            # (which rewrites parameters the chain reads) waits for both
+            edge_stream.wait_event(score_ev)
+            with torch.cuda.stream(edge_stream):
+                gsp.select_mask(scores[j], copies[j].count, k_split, status=status, workspace=ws_sel,
+                                out=sel_mask)
+            cur.wait_stream(edge_stream)
+            gsp.las_split(copies[j], mask=sel_mask, params=gsp.LAS_CONFIG, status=status, workspace=ws_las)
+            return out
         gsp.las_split(copies[j], scores=scores[j], k=k_split, params=gsp.LAS_CONFIG, status=status,
                       workspace=ws_las)
         return out
@@ -309,7 +339,7 @@ def run_gsp(args, rank, world):
     breakdown = {}
     for st in STAGES:
         timer = gsp.StageTimer(st, 8)
-        step(0)
+        step(0, overlap=False)
         ms, cnt = timer.read()
         breakdown[st] = ms / max(cnt, 1)
         restore(copies[0], pristine)
@@ -402,7 +432,8 @@ def run_gsp(args, rank, world):
     # end to end: pinned host parameters and image in, loss and count out, every step
     e2e = None
     if not args.no_e2e:
-        host = {name: getattr(pristine, name).cpu().pin_memory()
+        # the step's inputs: the N live Gaussians (rows past N are room for the split's children)
+        host = {name: (getattr(pristine, name) if name == "count" else getattr(pristine, name)[:n]).cpu().pin_memory()
                 for name in ("means", "log_scales", "quats", "opacity_logits", "sh", "count")}
         host_img = target.cpu().pin_memory()
         res_host = torch.empty(2, dtype=torch.float32).pin_memory()
@@ -418,7 +449,7 @@ def run_gsp(args, rank, world):
             for j in range(m):
                 c = copies[j]
                 for name, t in host.items():
-                    getattr(c, name).copy_(t, non_blocking=True)
+                    getattr(c, name)[:t.shape[0]].copy_(t, non_blocking=True)
                 target.copy_(host_img, non_blocking=True)
                 scores[j].zero_()
                 out = step(j)
@@ -450,7 +481,7 @@ def run_gsp(args, rank, world):
                         cs.wait_event(ev_free[j % 2])
                     c = copies[j]
                     for name, t in host.items():
-                        getattr(c, name).copy_(t, non_blocking=True)
+                        getattr(c, name)[:t.shape[0]].copy_(t, non_blocking=True)
                     tbuf[j % 2].copy_(host_img, non_blocking=True)
                     ev_in[j].record(cs)
 
@@ -475,7 +506,7 @@ def run_gsp(args, rank, world):
         ms_pipe = pipelined()
         e2e = {"value": round(ms_pipe, 4), "unit": "ms/iter", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": 8, "steps": m, "serial_ms_per_iter": round(ms_serial, 4),
-               "note": "parameters and target image copied from pinned host memory every step (step j + 1's "
+               "note": "the N live Gaussians' parameters and the target image copied from pinned host memory every step (step j + 1's "
                        "copies on a second stream overlap step j), loss and count read back every step; "
                        "serial_ms_per_iter: copies, step and read-back one after another"}
 

@@ -112,6 +112,10 @@ typedef struct gsp_edge_opts {
                                 copies in flight land before it leaves).  Either way the
                                 call reports GSP_ERR_TIMEOUT in dev_status and E_out /
                                 median_out are unspecified; the next call works normally. */
+    int32_t blocks_per_sm;   /* fused mode: at most this many blocks of the launch per SM
+                                (<= 0: as many as fit).  A caller that runs the edge map
+                                on a second stream beside other kernels leaves them room
+                                with 1; the result does not depend on it. */
 } gsp_edge_opts;
 
 /* Default options: fused mode, sigma = 1. */
@@ -199,6 +203,11 @@ typedef struct gsp_render_opts {
                               thread then reads its SH row from global memory, so the outputs
                               are complete and correct).  Either way dev_status receives
                               GSP_ERR_TIMEOUT. */
+    void *score_event;     /* a cudaEvent_t, or NULL; read by gsp_render_bwd only, which records
+                              it on its stream once the adjoint compositing has finished: the
+                              edge score (and every screen-space gradient) is then complete,
+                              while the chain to the parameters still runs.  A caller can start
+                              the selection on another stream from it. */
 } gsp_render_opts;
 
 /* Compositing variants (pixels per thread, Gaussians staged per shared-memory batch,

@@ -28,7 +28,7 @@ class ImageDesc(ctypes.Structure):
 
 class EdgeOpts(ctypes.Structure):
     _fields_ = [("mode", c_i32), ("use_custom_taps", c_i32), ("taps", c_f32 * 5), ("sigma", c_f32),
-                ("spin_limit", c_i64), ("test_expire", c_i32)]
+                ("spin_limit", c_i64), ("test_expire", c_i32), ("blocks_per_sm", c_i32)]
 
 
 class Gaussians(ctypes.Structure):
@@ -44,7 +44,8 @@ class Camera(ctypes.Structure):
 class RenderOpts(ctypes.Structure):
     _fields_ = [("pair_capacity", c_i64), ("fwd_variant", c_i32), ("bwd_variant", c_i32),
                 ("pos_grad_sum", ctypes.c_void_p), ("pos_grad_count", ctypes.c_void_p),
-                ("loss_pixels", c_i64), ("spin_limit", c_i64), ("test_expire", c_i32)]
+                ("loss_pixels", c_i64), ("spin_limit", c_i64), ("test_expire", c_i32),
+                ("score_event", ctypes.c_void_p)]
 
 
 class LrSchedule(ctypes.Structure):

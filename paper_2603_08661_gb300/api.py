@@ -34,6 +34,16 @@ def _ptr(t) -> ctypes.c_void_p | None:
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _event_handle(ev) -> int | None:
+    """The cudaEvent_t of a torch.cuda.Event (created on the current stream if it
+    has not been yet), or None."""
+    if ev is None:
+        return None
+    if not ev.cuda_event:
+        ev.record()
+    return int(ev.cuda_event)
+
+
 def _workspace(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
 
@@ -70,14 +80,15 @@ def pitched_image(img: torch.Tensor, align: int = 16) -> torch.Tensor:
 # ----------------------------------------------------------------- edge map
 
 def edge_map(images, *, mode: str = "fused", taps=None, sigma: float = 1.0, with_mask: bool = False,
-             spin_limit: int = 0, test_expire: int = 0, out: torch.Tensor | None = None,
+             spin_limit: int = 0, test_expire: int = 0, blocks_per_sm: int = 0, out: torch.Tensor | None = None,
              status: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None):
     """Edge-importance maps of a list of HWC uint8 CUDA views (one launch in fused mode).
 
     Returns (E, medians, mask, status): E is a flat float32 tensor holding the
     views one after another (row-major), medians is [V], mask is uint8 like E
     (or None), status is the device status word.  spin_limit and test_expire
-    are gsp_edge_opts' bounded-wait limit and failure-injection hook (tests).
+    are gsp_edge_opts' bounded-wait limit and failure-injection hook (tests);
+    blocks_per_sm caps the fused launch's blocks per SM (0: as many as fit).
     """
     if isinstance(images, torch.Tensor):
         images = [images]
@@ -98,6 +109,7 @@ def edge_map(images, *, mode: str = "fused", taps=None, sigma: float = 1.0, with
     opts.sigma = float(sigma)
     opts.spin_limit = int(spin_limit)
     opts.test_expire = int(test_expire)
+    opts.blocks_per_sm = int(blocks_per_sm)
     need = lib().gsp_edge_map_workspace_size(descs, v, ctypes.byref(opts))
     if need == 0:
         raise L.GspError(L.GSP_ERR_INVALID_ARG, "gsp_edge_map_workspace_size")
@@ -226,12 +238,13 @@ class Renderer:
             arr[i] = image_desc(t, 0)
         return arr
 
-    def _opts(self, pos_grad=None) -> L.RenderOpts:
+    def _opts(self, pos_grad=None, score_event=None) -> L.RenderOpts:
         o = self.opts
         return L.RenderOpts(o.pair_capacity, o.fwd_variant, o.bwd_variant,
                             _ptr(pos_grad[0]).value if pos_grad is not None else None,
                             _ptr(pos_grad[1]).value if pos_grad is not None else None,
-                            int(self.loss_pixels), int(self.spin_limit), int(self.test_expire))
+                            int(self.loss_pixels), int(self.spin_limit), int(self.test_expire),
+                            _event_handle(score_event))
 
     def forward(self, targets=None, edge=None, score=None, want_loss: bool = True, status=None, stream=None,
                 out=None):
@@ -253,12 +266,14 @@ class Renderer:
         return {"rgb": rgb, "T": T, "last": last, "loss": loss, "status": st}
 
     def backward(self, fwd: dict, targets=None, dL_drgb=None, edge=None, score=None, grads=None,
-                 accumulate: bool = False, status=None, stream=None, pos_grad=None):
+                 accumulate: bool = False, status=None, stream=None, pos_grad=None, score_event=None):
         """pos_grad: optional (sum float32 [capacity], count int32 [capacity]) device
         tensors; the positional statistic of the gradient-threshold masking is
-        added to them (see gsp_render_opts)."""
+        added to them (see gsp_render_opts).  score_event: optional
+        torch.cuda.Event, recorded once the edge score is complete (before the
+        chain to the parameters has finished)."""
         gs = self.gs
-        opts = self._opts(pos_grad)
+        opts = self._opts(pos_grad, score_event)
         if grads is None:
             grads = {"means": torch.zeros_like(gs.means), "log_scales": torch.zeros_like(gs.log_scales),
                      "quats": torch.zeros_like(gs.quats), "opacity_logits": torch.zeros_like(gs.opacity_logits),

@@ -1656,6 +1656,7 @@ extern "C" gsp_status gsp_edge_map(const gsp_image_desc *imgs, int32_t nv, float
         int per_sm = 0;
         GSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_walk_kernel, WNT, 0));
         if (per_sm < 1) return GSP_ERR_UNSUPPORTED;
+        if (o.blocks_per_sm > 0 && per_sm > o.blocks_per_sm) per_sm = o.blocks_per_sm;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(num_sms() * (per_sm < kWalkBlocksPerSM ? per_sm : kWalkBlocksPerSM));
         cfg.blockDim = dim3(WNT);
@@ -1713,6 +1714,7 @@ extern "C" gsp_status gsp_edge_map(const gsp_image_desc *imgs, int32_t nv, float
         int per_sm = 0;
         GSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_tile_kernel, NT, kTileSmem));
         if (per_sm < 1) return GSP_ERR_UNSUPPORTED;
+        if (o.blocks_per_sm > 0 && per_sm > o.blocks_per_sm) per_sm = o.blocks_per_sm;
         int grid = per_sm * num_sms();
         if (grid > tiles) grid = tiles;
         if (grid < nv && nv <= per_sm * num_sms()) grid = nv;

@@ -2291,6 +2291,8 @@ extern "C" gsp_status gsp_render_bwd(const gsp_gaussians *g, const gsp_camera *c
     }
     stage_end("composite_bwd", s);
     GSP_LAUNCH_CHECK();
+    // the edge score is complete: a caller may start the selection from here
+    if (opts->score_event) GSP_CUDA_TRY(cudaEventRecord(reinterpret_cast<cudaEvent_t>(opts->score_event), s));
     stage_begin("project_bwd", s);
 #define GSP_PBWD(KK)                                                                                           \
     project_bwd<KK><<<div_up(cap, kProjBwdThreads), kProjBwdThreads,                                             \

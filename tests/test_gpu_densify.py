@@ -264,3 +264,33 @@ def test_scheduled_sgd_follows_the_oracle_schedule(gsp_lib):
             # FP32 rate (1e-6 relative) times the gradient, plus one rounding of theta
             tol = 2e-6 * lr * np.abs(gk) + np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
             assert np.all(np.abs(got - ref) <= tol), (k, t)
+
+
+def test_selection_started_from_the_score_event(gsp_lib):
+    """gsp_render_bwd records the score event once the edge score is complete: a
+    selection started from it on a second stream, while the adjoint still chains
+    the gradients to the parameters, equals the oracle's top-k of the final
+    scores."""
+    import torch
+    n, k = 60000, 6000
+    g = synth.gaussians(n, 3, seed=31)
+    cam = synth.camera_front(320, 240)
+    t = torch.from_numpy(synth.image(240, 320, 77)).cuda()
+    E, _, _, _ = gsp_lib.edge_map([t])
+    gs = gsp_lib.GaussianSet.from_arrays(g)
+    r = gsp_lib.Renderer(gs, [cam], pair_capacity=1 << 24)
+    score = torch.zeros(n, device="cuda")
+    ev = torch.cuda.Event()
+    side = torch.cuda.Stream()
+    out = r.forward(targets=[t])
+    r.backward(out, targets=[t], edge=E, score=score, score_event=ev)
+    side.wait_event(ev)
+    with torch.cuda.stream(side):
+        mask, sel, st = gsp_lib.select_mask(score, gs.count, k)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    assert int(out["status"].item()) == 0 and int(st.item()) == 0
+    s = score.cpu().numpy()
+    assert (s > 0).sum() > k
+    assert np.array_equal(mask.cpu().numpy().astype(bool), od.topk_mask(s.astype(np.float64), k))
+    assert int(sel.item()) == k

@@ -168,3 +168,19 @@ def test_full_batch_32_views_1237x822(gsp_lib):
     for v in (0, 17):
         _compare(imgs[v], Ec[v], Mc[v], med.cpu().numpy()[v])
     assert E.numel() == 32 * npx
+
+
+@pytest.mark.parametrize("nviews", [1, 6])
+def test_blocks_per_sm_cap_changes_nothing(gsp_lib, nviews):
+    """A launch capped at one or two blocks per SM (for running beside other
+    work on a second stream) gives the map of the full launch bit for bit:
+    one view of 1237x822 and six of them (over 4 Mi pixels: walk kernel)."""
+    import torch
+    ts = [gsp_lib.pitched_image(torch.from_numpy(synth.image(822, 1237, 950 + i)).cuda(), 16)
+          for i in range(nviews)]
+    E0, m0, k0, s0 = gsp_lib.edge_map(ts, with_mask=True)
+    for bps in (1, 2):
+        E1, m1, k1, s1 = gsp_lib.edge_map(ts, with_mask=True, blocks_per_sm=bps)
+        torch.cuda.synchronize()
+        assert int(s0.item()) == 0 and int(s1.item()) == 0
+        assert torch.equal(E0, E1) and torch.equal(m0, m1) and torch.equal(k0, k1)

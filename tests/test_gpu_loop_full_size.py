@@ -74,6 +74,7 @@ def test_first_iteration_gradients(gsp_lib, setup):
     for k in GROUPS:
         _norm_close(l1[k], explicit[k][:N0].cpu().numpy(), k)
 
+    n_ex = n_px = 0
     for v, reg in REGIONS.items():
         x0, y0, x1, y1 = reg
         off = r.offsets[v]
@@ -91,7 +92,8 @@ def test_first_iteration_gradients(gsp_lib, setup):
         gr = orc.render_bwd(g, cam, dl64, proj=proj, region=reg)
         gm = orc.render_bwd(g, cam, dl64, proj=proj, region=reg, magnitude=True)
         gap = ref["gate_gap"]
-        assert (gap[y0:y1, x0:x1] < GATE_REL).sum() <= max(1, EXEMPT_FRAC * (x1 - x0) * (y1 - y0))
+        n_ex += int((gap[y0:y1, x0:x1] < GATE_REL).sum())
+        n_px += (x1 - x0) * (y1 - y0)
         ex = gap < GATE_REL
         skip = orc.gate_affected(proj, ex, GATE_REL, order) if ex.any() else np.zeros(N0, bool)
         touched = np.abs(gr["opacity_logits"]).reshape(N0) > 0
@@ -102,6 +104,7 @@ def test_first_iteration_gradients(gsp_lib, setup):
             b = gr[k].reshape(N0, -1)
             assert np.all(a[~touched & ~skip] == 0), (v, k)
             assert_grads_match(k, a[keep], b[keep], gm[k].reshape(N0, -1)[keep])
+    assert n_ex <= EXEMPT_FRAC * n_px, (n_ex, n_px)
 
 
 def test_first_event_topk_and_split(gsp_lib, setup):
