@@ -749,11 +749,26 @@ struct QState {
     float2 acc[4][kQ];         // vertical blur chains: acc[d] lacks the d + 1 newest blurred rows
     float M0[kQ + 2];          // M^2 of NMS row q - 1 (index 0: column -1, kQ + 1: column kQ)
     float M1[kQ + 2];          // M^2 of NMS row q
-    float2 g1[kQ];             // blurred gradient of row q
+    unsigned dir1;             // direction class of row q: 4 bits per column (see dir_bits)
     unsigned w[4], shift;      // words of the next input row
-    unsigned keep0;            // first row of a pair, waiting for the second
-    float v0[kQ];
+    unsigned keep0;            // keep bits of the first row of a pair, waiting for the second
 };
+
+// Direction class of a blurred gradient for NMS, 4 bits: horizontal (|gy| <=
+// tan 22.5 |gx|), vertical (|gx| <= tan 22.5 |gy|; read only when not
+// horizontal), same signs (gx > 0 == gy > 0), and whether the + direction
+// neighbour (compared with >=) is the right one (horizontal: gx > 0) or the
+// one in the row below (otherwise: gy > 0).
+__device__ __forceinline__ unsigned dir_bits(float2 g)
+{
+    const float ax = fabsf(g.x), ay = fabsf(g.y);
+    const bool gxp = g.x > 0.f, gyp = g.y > 0.f;
+    const bool horiz = ay <= __fmul_rn(kTan22, ax);
+    const bool vert = ax <= __fmul_rn(kTan22, ay);
+    const bool same = gxp == gyp;
+    const bool pos = horiz ? gxp : gyp;
+    return unsigned(horiz) | unsigned(vert) << 1 | unsigned(same) << 2 | unsigned(pos) << 3;
+}
 
 // Output of phase A for one item.
 struct QOut {
@@ -860,45 +875,39 @@ __device__ __forceinline__ void qstep(const QLane &q, const float2 w0v, const fl
         // the horizontal class (+ is +x when gx > 0); otherwise in row q + 1
         // exactly when gy > 0, at the column offset of the class.
         unsigned keep = 0u;
-        float vals[kQ];
 #pragma unroll
         for (int j = 0; j < kQ; ++j) {
             const int k = j + 1;
-            const float mq = s.M1[k], gxq = s.g1[j].x, gyq = s.g1[j].y;
-            const float ax = fabsf(gxq), ay = fabsf(gyq);
-            const bool gxp = gxq > 0.f, gyp = gyq > 0.f;
-            const bool horiz = ay <= __fmul_rn(kTan22, ax);
-            const bool vert = ax <= __fmul_rn(kTan22, ay);  // read only when not horizontal
-            const bool same = gxp == gyp;
+            const unsigned d = s.dir1 >> (4 * j);
+            const bool horiz = d & 1u, vert = d & 2u, same = d & 4u, pos = d & 8u;
+            const float mq = s.M1[k];
             const float n0 = vert ? s.M0[k] : (same ? s.M0[k - 1] : s.M0[k + 1]);
             const float n2 = vert ? M2[k] : (same ? M2[k + 1] : M2[k - 1]);
             const float lo = horiz ? s.M1[k - 1] : n0, hi = horiz ? s.M1[k + 1] : n2;
-            const bool pos = horiz ? gxp : gyp;
             const float mp = pos ? hi : lo, mm = pos ? lo : hi;
             keep |= unsigned(mq > 0.f && mq >= mp && mq > mm) << j;
-            vals[j] = mq;
         }
         keep &= q.outmask;
         const int r = i - 8;
         if (PAR == 0 && r + 1 < q.nout) {
             s.keep0 = keep;
-#pragma unroll
-            for (int j = 0; j < kQ; ++j) s.v0[j] = vals[j];
         } else {
+            // the pair's values: the first row's M^2 is row q - 1 (M0) on the
+            // second step of the pair, the second row's is row q (M1)
             float vv[2 * kQ];
             unsigned k8;
             if (PAR == 1) {
                 k8 = s.keep0 | keep << kQ;
 #pragma unroll
                 for (int j = 0; j < kQ; ++j) {
-                    vv[j] = s.v0[j];
-                    vv[kQ + j] = vals[j];
+                    vv[j] = s.M0[j + 1];
+                    vv[kQ + j] = s.M1[j + 1];
                 }
             } else {
                 k8 = keep;
 #pragma unroll
                 for (int j = 0; j < kQ; ++j) {
-                    vv[j] = vals[j];
+                    vv[j] = s.M1[j + 1];
                     vv[kQ + j] = 0.f;
                 }
             }
@@ -910,8 +919,10 @@ __device__ __forceinline__ void qstep(const QLane &q, const float2 w0v, const fl
         s.M0[k] = s.M1[k];
         s.M1[k] = M2[k];
     }
+    unsigned dir = 0u;
 #pragma unroll
-    for (int j = 0; j < kQ; ++j) s.g1[j] = g[j];
+    for (int j = 0; j < kQ; ++j) dir |= dir_bits(g[j]) << (4 * j);
+    s.dir1 = dir;
 }
 
 // Phase A of one warp item: walk the band, compact the kept values per row
