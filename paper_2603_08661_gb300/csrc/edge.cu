@@ -693,9 +693,8 @@ struct QLane {
     int w, h;
     int cx;             // first of the lane's 4 columns (may lie outside the image)
     int y0, nout, nin;  // first output row, output rows, input rows (nout + 8)
-    bool fast;          // all 4 columns inside the image: word loads
-    unsigned colmask;   // columns inside the image
-    unsigned outmask;   // columns this lane outputs (lanes 1..30, inside the image)
+    unsigned bits;      // bits 0-3: columns inside the image; 4-7: columns this lane outputs
+                        // (lanes 1..30, inside the image); 8: all 4 inside (word loads)
 };
 
 // The raw words of the lane's 4 pixels of input row i (image row y0 - 4 + i,
@@ -705,7 +704,7 @@ __device__ __forceinline__ void load_row(const QLane &q, int i, unsigned (&w)[4]
 {
     const int y = clampi(q.y0 - 4 + i, 0, q.h - 1);
     const uint8_t *row = q.rgb + (long long)y * q.pitch;
-    if (q.fast) {
+    if (q.bits & 0x100u) {
         const uintptr_t p = reinterpret_cast<uintptr_t>(row + 3 * q.cx);
         const unsigned *wp = reinterpret_cast<const unsigned *>(p & ~uintptr_t(3));
         shift = unsigned(p & 3) * 8u;
@@ -727,7 +726,7 @@ __device__ __forceinline__ void load_row(const QLane &q, int i, unsigned (&w)[4]
 __device__ __forceinline__ void row_luma(const QLane &q, const unsigned (&w)[4], unsigned shift, float (&I)[kQ])
 {
     unsigned px[kQ];
-    if (q.fast) {
+    if (q.bits & 0x100u) {
         const unsigned u0 = __funnelshift_r(w[0], w[1], shift);
         const unsigned u1 = __funnelshift_r(w[1], w[2], shift);
         const unsigned u2 = __funnelshift_r(w[2], w[3], shift);
@@ -865,7 +864,7 @@ __device__ __forceinline__ void qstep(const QLane &q, const float2 w0v, const fl
     float M2[kQ + 2];
 #pragma unroll
     for (int j = 0; j < kQ; ++j)
-        M2[j + 1] = (row_in && (q.colmask >> j & 1u)) ? __fmaf_rn(g[j].x, g[j].x, __fmul_rn(g[j].y, g[j].y)) : 0.f;
+        M2[j + 1] = (row_in && (q.bits >> j & 1u)) ? __fmaf_rn(g[j].x, g[j].x, __fmul_rn(g[j].y, g[j].y)) : 0.f;
     M2[0] = __shfl_up_sync(kFull, M2[kQ], 1);
     M2[kQ + 1] = __shfl_down_sync(kFull, M2[1], 1);
     if (i >= 8) {
@@ -887,7 +886,7 @@ __device__ __forceinline__ void qstep(const QLane &q, const float2 w0v, const fl
             const float mp = pos ? hi : lo, mm = pos ? lo : hi;
             keep |= unsigned(mq > 0.f && mq >= mp && mq > mm) << j;
         }
-        keep &= q.outmask;
+        keep &= (q.bits >> 4) & 0xfu;
         const int r = i - 8;
         if (PAR == 0 && r + 1 < q.nout) {
             s.keep0 = keep;
@@ -942,11 +941,11 @@ __device__ unsigned walk_item(const EdgeArgs &a, int it, unsigned *whist)
     q.y0 = y0;
     q.nout = min(a.rb, V.h - y0);
     q.nin = q.nout + 8;
-    q.fast = q.cx >= 0 && q.cx + kQ <= V.w;
-    q.colmask = 0u;
+    unsigned colmask = 0u;
 #pragma unroll
-    for (int j = 0; j < kQ; ++j) q.colmask |= unsigned(q.cx + j >= 0 && q.cx + j < V.w) << j;
-    q.outmask = (lane >= 1 && lane <= 30) ? q.colmask : 0u;
+    for (int j = 0; j < kQ; ++j) colmask |= unsigned(q.cx + j >= 0 && q.cx + j < V.w) << j;
+    q.bits = colmask | ((lane >= 1 && lane <= 30) ? colmask : 0u) << 4 |
+             unsigned(q.cx >= 0 && q.cx + kQ <= V.w) << 8;
     QOut o;
     o.slot = a.kept + (size_t)it * kItemCols * a.rb;
     o.km = a.kmask + (size_t)it * (a.rb / 2) * 32;
