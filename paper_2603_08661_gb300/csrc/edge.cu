@@ -675,6 +675,17 @@ union alignas(16) WalkSmem {
     } d;
 };
 
+// 4-byte asynchronous copies into shared memory (phase D stages a chunk's kept
+// values with every copy in flight at once).
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void item_origin(const EdgeArgs &a, int it, int &v, int &xg, int &y0)
 {
     v = 0;
@@ -1179,19 +1190,13 @@ __global__ void __launch_bounds__(WNT, kWalkBlocksPerSM) edge_walk_kernel(const 
                     ctot += warp_exclusive_scan(__popc(k8[r]), &excl[r]);
                 }
                 __syncwarp();
-                for (unsigned j0 = 0; j0 < ctot; j0 += 4 * 32) {
-                    float m2[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const unsigned j = j0 + 32 * u + lane;
-                        m2[u] = j < ctot ? __ldcg(src + run + j) : 0.f;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const unsigned j = j0 + 32 * u + lane;
-                        if (j < ctot) vals[j] = med2 > 0.f ? __fdiv_rn(__fsqrt_rn(m2[u]), smed) : 0.f;
-                    }
-                }
+                // the chunk's kept values arrive in shared memory with one round trip,
+                // then become E in place
+                for (unsigned j = lane; j < ctot; j += 32) cp_async4(vals + j, src + run + j);
+                cp_async_wait_all();
+                __syncwarp();
+                for (unsigned j = lane; j < ctot; j += 32)
+                    vals[j] = med2 > 0.f ? __fdiv_rn(__fsqrt_rn(vals[j]), smed) : 0.f;
                 __syncwarp();
 #pragma unroll
                 for (int r = 0; r < kDPairs; ++r) {
