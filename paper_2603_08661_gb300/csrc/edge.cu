@@ -1025,19 +1025,44 @@ __global__ void __launch_bounds__(WNT, kWalkBlocksPerSM) edge_walk_kernel(const 
     if (!grid_barrier(a.bar, G, a.spin_limit, a.status, (a.expire & 1) != 0)) return;
 
     // ---- phase B0: each view's median bin of bits [30:19] and kept count (block v)
+    // (thread t holds bins [32 t, 32 t + 32) in registers: eight 16-byte loads,
+    // one block scan, and the thread whose range holds the median rank walks it)
     for (int v = blockIdx.x; v < a.nviews; v += G) {
-        const unsigned *h = a.hist1 + (size_t)v * kBins1;
+        static_assert(kBins1 == 32 * WNT, "32 bins per thread");
+        const uint4 *h4 = reinterpret_cast<const uint4 *>(a.hist1 + (size_t)v * kBins1) + tid * 8;
+        unsigned hb[32];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint4 u = __ldcg(h4 + k);
+            hb[4 * k] = u.x; hb[4 * k + 1] = u.y; hb[4 * k + 2] = u.z; hb[4 * k + 3] = u.w;
+        }
         unsigned seg = 0;
-        for (int k = 0; k < kBins1 / WNT; ++k) seg += h[tid * (kBins1 / WNT) + k];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) seg += hb[k];
         unsigned before;
         const unsigned n = block_exclusive_scan<WNT>(seg, &before);
-        int b1 = 0;
-        unsigned below = 0;
-        if (n > 0) block_find_bin<WNT>(h, kBins1, (n - 1) / 2, &b1, &below);
-        if (tid == 0) {
-            a.sel[4 * v + 0] = n;
+        const unsigned rank = n > 0 ? (n - 1) / 2 : 0u;
+        if (tid == 0) a.sel[4 * v + 0] = n;
+        if (n > 0 && rank >= before && rank < before + seg) {
+            unsigned acc = before;
+            int b1 = 0;
+            unsigned below = 0;
+            bool found = false;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                if (!found && rank < acc + hb[k]) {
+                    b1 = 32 * tid + k;
+                    below = acc;
+                    found = true;
+                }
+                acc += hb[k];
+            }
             a.sel[4 * v + 1] = unsigned(b1);
             a.sel[4 * v + 2] = below;
+        }
+        if (n == 0 && tid == 0) {
+            a.sel[4 * v + 1] = 0u;
+            a.sel[4 * v + 2] = 0u;
         }
         __syncthreads();
     }
@@ -1075,15 +1100,16 @@ __global__ void __launch_bounds__(WNT, kWalkBlocksPerSM) edge_walk_kernel(const 
             float *cand = a.cand + a.v[v].out_off;
             [[maybe_unused]] const long long vpx = (long long)a.v[v].w * a.v[v].h;
             unsigned nc = 0;  // candidates buffered
-            for (unsigned c0 = 0; c0 < n; c0 += 8 * 32) {
-                float val[8];
+            constexpr int kBLoads = 16;  // values per lane in flight
+            for (unsigned c0 = 0; c0 < n; c0 += kBLoads * 32) {
+                float val[kBLoads];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                for (int k = 0; k < kBLoads; ++k) {
                     const unsigned e = c0 + 32 * k + lane;
                     val[k] = e < n ? __ldcg(src + e) : 0.f;
                 }
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                for (int k = 0; k < kBLoads; ++k) {
                     const unsigned e = c0 + 32 * k + lane;
                     const unsigned bits = __float_as_uint(val[k]);
                     const bool pick = e < n && (bits >> kShift1) == b1;
