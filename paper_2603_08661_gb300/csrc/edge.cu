@@ -1168,9 +1168,18 @@ __global__ void __launch_bounds__(WNT, kWalkBlocksPerSM) edge_walk_kernel(const 
             __syncthreads();
             const float *cand = a.cand + a.v[v].out_off;
             const unsigned count = a.cand_count[v];
-            for (unsigned i = tid; i < count; i += WNT) {
-                const unsigned cb = __float_as_uint(cand[i]);
-                if (((cb >> kShift2) & (kBins2 - 1)) == unsigned(b2)) atomicAdd(&sm.hist3[cb & (kBins3 - 1)], 1u);
+            constexpr int kCLoads = 8;  // candidates per thread in flight
+            for (unsigned i0 = 0; i0 < count; i0 += kCLoads * WNT) {
+                unsigned cb[kCLoads];
+#pragma unroll
+                for (int u = 0; u < kCLoads; ++u) {
+                    const unsigned i = i0 + u * WNT + tid;
+                    cb[u] = i < count ? __float_as_uint(__ldcg(cand + i)) : 0xffffffffu;
+                }
+#pragma unroll
+                for (int u = 0; u < kCLoads; ++u)
+                    if (cb[u] != 0xffffffffu && ((cb[u] >> kShift2) & (kBins2 - 1)) == unsigned(b2))
+                        atomicAdd(&sm.hist3[cb[u] & (kBins3 - 1)], 1u);
             }
             __syncthreads();
             int b3;
