@@ -167,9 +167,9 @@ def stage_work(stage, n, k_sh, npix, pairs, evals, contrib):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) and warp
 # instructions per launch (sm__inst_executed.sum) of the dominant kernel from
-# one ncu capture of this workload (profiles/composite_bwd_1M_sh3_1237x822.md):
-# valid for the captured variant while the compositing source is the one that
-# was captured.
+# one ncu capture of this workload (--set full, the kernel's first launch after
+# the pair-count probe): valid for the captured variant while the compositing
+# source is the one that was captured.
 NCU_TRAFFIC = {("composite_bwd", 4): (46_372_352, "72140bd405d14970")}
 NCU_INST = {("composite_bwd", 4): (323_373_585, "72140bd405d14970")}
 
@@ -713,6 +713,15 @@ def run_multiview(steps=5, warmup=3):
     ms_graph = _event_ms(graph.replay, steps)
     torch.cuda.synchronize()
     gsp.raise_on_device_status(status, "multiview")
+    # per-stage CUDA-event times (eager iterations, one armed stage at a time)
+    stages = {}
+    for stg in ("project", "depth_sort", "bin", "composite_fwd", "composite_bwd", "project_bwd"):
+        timer = gsp.StageTimer(stg, 4)
+        for _ in range(2):
+            it()
+        ms, cnt = timer.read()
+        stages[stg] = round(ms / max(cnt, 1), 3)
+    gsp.StageTimer.disarm()
     # plain path: one single-view call per view and pass, default variants, eager
     del r
     torch.cuda.empty_cache()
@@ -745,7 +754,7 @@ def run_multiview(steps=5, warmup=3):
     return {"workload": "3M Gaussians SH3, 8 ring views 640x480..1920x1080 (8.76 Mpix): fwd + L1 + bwd + edge score",
             "pairs": pairs, "variants": list(variants), "ms_per_iter_batched_graph": round(ms_graph, 3),
             "ms_per_iter_plain_per_view": round(ms_plain, 3), "mpix_per_s_batched": round(npix / ms_graph / 1e3, 1),
-            "steps": steps}
+            "steps": steps, "stages_ms": stages}
 
 
 def run_multiview_sharded(rank, world, steps=5, warmup=3):
