@@ -37,9 +37,10 @@
 //      bytes one row ahead, forms their luma, the vertical Sobel parts from
 //      the last three luma rows, takes the neighbours' edge columns by warp
 //      shuffles for the horizontal Sobel parts and the horizontal blur (both
-//      gradient components in one packed FP32x2 operation), keeps five
-//      blurred rows in registers for the vertical blur, and decides NMS from
-//      the last three M^2 rows (their ring columns by shuffles).  Kept M^2
+//      gradient components in one packed FP32x2 operation), advances four
+//      partial vertical-blur chains in registers, and decides NMS from the
+//      last three M^2 rows (their ring columns by shuffles) and the previous
+//      row's direction class (4 bits per column).  Kept M^2
 //      values are compacted per row pair into the item's slot, with a keep
 //      byte per lane and pair, and counted in a warp histogram of bits
 //      [30:19] (two 16-bit counts a word, flushed before they can overflow).
@@ -54,7 +55,8 @@
 //      count, bits [8:0] from one pass over the candidates in it
 //   -- grid barrier --
 //   D  every warp re-walks its items in chunks of row pairs: the chunk's keep
-//      bytes come in at once, its kept values are converted to E =
+//      bytes come in at once, its kept values arrive in shared memory by
+//      cp.async (all in flight together) and are converted to E =
 //      sqrt(M^2) / median by all lanes together, and each E row (zeros and
 //      those values) is staged in shared memory for contiguous stores.
 // Plain mode launches one kernel per stage and per view, with every
