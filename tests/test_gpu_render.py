@@ -320,3 +320,36 @@ def test_positional_statistic_matches_oracle(gsp_lib):
     # a second call adds the same statistic again
     assert np.array_equal(c2, 2 * c1)
     np.testing.assert_allclose(s2, 2 * s1, rtol=1e-5, atol=1e-6 * rms)
+
+
+def test_footprints_wider_than_255_tiles_and_taller_than_16_rows(gsp_lib):
+    """A 4400 x 320 view (275 x 20 tiles) with Gaussians whose footprints span
+    more than 255 tiles across (their per-row column intervals are not stored:
+    every row keeps the full rectangle) and more than 16 tile rows (rows past
+    the 16 stored intervals keep the full width), beside small ones: RGB, T
+    and every gradient against the oracle."""
+    rng = np.random.default_rng(17)
+    n_big, n_small = 12, 48
+    n = n_big + n_small
+    g = synth.gaussians(n, 1, seed=23)
+    g["means"][:n_big] = rng.uniform([-0.3, -0.05, -0.3], [0.3, 0.05, 0.3], (n_big, 3)).astype(np.float32)
+    g["log_scales"][:n_big] = np.stack([rng.uniform(-0.1, 0.15, n_big), rng.uniform(-2.6, -1.6, n_big),
+                                        rng.uniform(-2.0, -1.0, n_big)], axis=1).astype(np.float32)
+    g["opacity_logits"][:n_big] = rng.uniform(-2.5, -1.0, g["opacity_logits"][:n_big].shape).astype(np.float32)
+    cam = synth.camera_front(4400, 320)
+    w, h = cam["width"], cam["height"]
+    dL = rng.normal(size=(h * w, 3)) / (h * w)
+    res = gpu_render(gsp_lib, g, [cam], dL=dL, pair_capacity=1 << 22)
+    assert res["status"] == 0
+    ref = orc.render(g, cam)
+    proj = ref["proj"]
+    tiles_x = (w + 15) // 16
+    wide = np.minimum(proj[:n_big, orc.P_TX1], tiles_x - 1) - np.maximum(proj[:n_big, orc.P_TX0], 0) + 1
+    tall = np.minimum(proj[:n_big, orc.P_TY1], (h + 15) // 16 - 1) - np.maximum(proj[:n_big, orc.P_TY0], 0) + 1
+    valid = proj[:n_big, orc.P_VALID] > 0
+    assert (valid & (wide > 255)).sum() >= 3, wide  # rectangles wider than 255 tiles
+    assert (valid & (tall > 16)).sum() >= 3, tall   # and taller than 16 tile rows
+    check_image(res, [ref], [cam])
+    gr = orc.render_bwd(g, cam, dL.reshape(h, w, 3))
+    gm = orc.render_bwd(g, cam, dL.reshape(h, w, 3), magnitude=True)
+    check_grads(res["grads"], gr, gm, n, exempt_gaussians(g, cam, ref))
