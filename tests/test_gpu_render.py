@@ -353,3 +353,38 @@ def test_footprints_wider_than_255_tiles_and_taller_than_16_rows(gsp_lib):
     gr = orc.render_bwd(g, cam, dL.reshape(h, w, 3))
     gm = orc.render_bwd(g, cam, dL.reshape(h, w, 3), magnitude=True)
     check_grads(res["grads"], gr, gm, n, exempt_gaussians(g, cam, ref))
+
+
+def test_degenerate_view_shapes_in_one_batch(gsp_lib):
+    """One launch over views of 1 x 1, 3 x 250, 250 x 3, 17 x 17 and 160 x 120
+    pixels (single tiles, single tile rows and columns, ragged tails): RGB, T,
+    edge scores and every gradient against the oracle, summed over the views."""
+    sizes = [(1, 1), (250, 3), (3, 250), (17, 17), (160, 120)]
+    g = synth.gaussians(400, 2, seed=29)
+    g["log_scales"] += np.float32(0.5)
+    n = 400
+    cams = [synth.camera_ring(k, len(sizes), resolutions=sizes) for k in range(len(sizes))]
+    rng = np.random.default_rng(5)
+    edges = [rng.uniform(0, 2, (c["height"], c["width"])) for c in cams]
+    npix = sum(c["width"] * c["height"] for c in cams)
+    dL = rng.normal(size=(npix, 3)) / npix
+    res = gpu_render(gsp_lib, g, cams, edges=edges, dL=dL, score_in="bwd")
+    assert res["status"] == 0
+    refs = oracle_views(g, cams, edges)
+    check_image(res, refs, cams)
+    skip = set()
+    gr = {k: 0.0 for k in GROUPS}
+    gm = {k: 0.0 for k in GROUPS}
+    off = 0
+    for c, r in zip(cams, refs):
+        h, w = c["height"], c["width"]
+        skip |= exempt_gaussians(g, c, r)
+        d = dL[off:off + h * w].reshape(h, w, 3)
+        a = orc.render_bwd(g, c, d, proj=r["proj"])
+        m = orc.render_bwd(g, c, d, proj=r["proj"], magnitude=True)
+        for k in GROUPS:
+            gr[k] = gr[k] + a[k].reshape(n, -1)
+            gm[k] = gm[k] + m[k].reshape(n, -1)
+        off += h * w
+    check_scores(res["score"], sum(r["score"] for r in refs), skip)
+    check_grads(res["grads"], gr, gm, n, skip)
