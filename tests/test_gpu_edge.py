@@ -215,3 +215,25 @@ def test_walk_kernel_tiny_and_ragged_views(gsp_lib):
             _compare(imgs[i], Ec[off:off + h * w].reshape(h, w), Mc[off:off + h * w].reshape(h, w), med[i],
                      bound_exempt=min(h, w) >= 8)
         off += h * w
+
+
+def test_walk_kernel_views_without_edges_beside_textured_ones(gsp_lib):
+    """A walk-kernel batch (over 4 Mi pixels) of constant views, which keep no
+    pixel (median 0, E all zero), beside textured ones: every view's map and
+    median equal those of the view computed alone."""
+    import torch
+    h, w = 822, 1237
+    imgs = [np.full((h, w, 3), 40 * i + 7, np.uint8) if i % 2 == 0 else synth.image(h, w, 970 + i)
+            for i in range(5)]
+    ts = [torch.from_numpy(i).cuda() for i in imgs]
+    E, med, mask, st = gsp_lib.edge_map(ts, with_mask=True)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    for i, t in enumerate(ts):
+        Ei, mi, ki, si = gsp_lib.edge_map([t], with_mask=True)
+        torch.cuda.synchronize()
+        assert int(si.item()) == 0
+        sl = slice(i * h * w, (i + 1) * h * w)
+        assert torch.equal(E[sl], Ei) and torch.equal(mask[sl], ki) and float(med[i]) == float(mi[0])
+        if i % 2 == 0:
+            assert float(mi[0]) == 0.0 and not bool(Ei.any()) and not bool(ki.any())
