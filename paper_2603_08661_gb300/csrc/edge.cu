@@ -624,7 +624,7 @@ constexpr int kWWarps = WNT / 32;
 constexpr int kWalkBlocksPerSM = 4;           // resident walk blocks per SM the plan assumes
 constexpr int kQ = 4;                         // columns per lane
 constexpr int kItemCols = 32 * kQ - 2 * kQ;   // 120 output columns per item
-constexpr int kDPairs = 8;                    // row pairs per phase-D chunk
+constexpr int kDPairs = 4;                    // row pairs per phase-D chunk (two chunks staged at once)
 constexpr int kBCand = 512;                   // phase-B candidate buffer per warp
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -671,21 +671,27 @@ union alignas(16) WalkSmem {
     } b;
     unsigned hist3[kBins3];              // C: count of bits [8:0]
     struct {
-        float vals[kWWarps][kDPairs * 2 * kItemCols];  // D: E of a chunk's kept values
+        float vals[kWWarps][2 * kDPairs * 2 * kItemCols];  // D: E of two chunks' kept values
         float row[kWWarps][2][32 * kQ];                //    E rows of a pair, for coalesced stores
         uint8_t mrow[kWWarps][2][32 * kQ];             //    NMS mask rows of a pair
     } d;
 };
 
 // 4-byte asynchronous copies into shared memory (phase D stages a chunk's kept
-// values with every copy in flight at once).
+// values with every copy in flight at once, one commit group per chunk).
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all()
+__device__ __forceinline__ void cp_async_commit()
 {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// waits until at most N of this thread's commit groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ void item_origin(const EdgeArgs &a, int it, int &v, int &xg, int &y0)
@@ -1198,12 +1204,15 @@ __global__ void __launch_bounds__(WNT, kWalkBlocksPerSM) edge_walk_kernel(const 
     if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
 
     // ---- phase D: every warp writes its items' E rows, zeros and sqrt(M^2) /
-    // median.  Row pairs go in chunks of kDPairs: the chunk's keep masks are
-    // loaded at once, its kept values converted to E by all lanes together
-    // (no lane idles on a pixel it does not keep), then each row is staged in
-    // shared memory so that every store instruction covers contiguous columns.
+    // median.  Row pairs go in chunks of kDPairs, pipelined: while chunk c is
+    // written, the kept values of chunk c + 1 are on their way into the other
+    // shared buffer (cp.async) and the keep bytes of chunk c + 2 are loading.
+    // A chunk's kept values are converted to E by all lanes together (no lane
+    // idles on a pixel it does not keep), then each row is staged in shared
+    // memory so that every store instruction covers contiguous columns.
     {
-        float *vals = sm.d.vals[wid];
+        float *vbuf = sm.d.vals[wid];  // two buffers of kDPairs * 2 * kItemCols values
+        constexpr int kDBuf = kDPairs * 2 * kItemCols;
         for (int it = it_begin; it < it_end; ++it) {
             int v, xg, y0;
             item_origin(a, it, v, xg, y0);
@@ -1212,38 +1221,64 @@ __global__ void __launch_bounds__(WNT, kWalkBlocksPerSM) edge_walk_kernel(const 
             const float smed = __fsqrt_rn(med2);
             const int nout = min(a.rb, V.h - y0);
             const int npairs = (nout + 1) / 2;
+            const int nch = (npairs + kDPairs - 1) / kDPairs;
             const float *src = a.kept + (size_t)it * kItemCols * a.rb;
             const uint8_t *km = a.kmask + (size_t)it * (a.rb / 2) * 32;
-            unsigned run = 0;
-            for (int t0 = 0; t0 < npairs; t0 += kDPairs) {
-                const int np = min(kDPairs, npairs - t0);
-                unsigned k8[kDPairs], excl[kDPairs], off[kDPairs];
-#pragma unroll
-                for (int r = 0; r < kDPairs; ++r) k8[r] = r < np ? unsigned(__ldcg(km + (t0 + r) * 32 + lane)) : 0u;
-                unsigned ctot = 0;
+            auto load_masks = [&](int c, unsigned (&k8)[kDPairs]) {
 #pragma unroll
                 for (int r = 0; r < kDPairs; ++r) {
-                    off[r] = ctot;
-                    ctot += warp_exclusive_scan(__popc(k8[r]), &excl[r]);
+                    const int t = c * kDPairs + r;
+                    k8[r] = t < npairs ? unsigned(__ldcg(km + t * 32 + lane)) : 0u;
                 }
+            };
+            auto scan = [&](const unsigned (&k8)[kDPairs], unsigned (&excl)[kDPairs], unsigned (&off)[kDPairs]) {
+                unsigned tot = 0;
+#pragma unroll
+                for (int r = 0; r < kDPairs; ++r) {
+                    off[r] = tot;
+                    tot += warp_exclusive_scan(__popc(k8[r]), &excl[r]);
+                }
+                return tot;
+            };
+            auto issue = [&](float *dst, unsigned from, unsigned n) {
                 __syncwarp();
-                // the chunk's kept values arrive in shared memory with one round trip,
-                // then become E in place
-                for (unsigned j = lane; j < ctot; j += 32) cp_async4(vals + j, src + run + j);
-                cp_async_wait_all();
+                for (unsigned j = lane; j < n; j += 32) cp_async4(dst + j, src + from + j);
+                cp_async_commit();
+            };
+            unsigned ck8[kDPairs], cex[kDPairs], cof[kDPairs], nk8[kDPairs];
+            load_masks(0, ck8);
+            unsigned ctot = scan(ck8, cex, cof);
+            unsigned run = 0;
+            issue(vbuf, 0, ctot);
+            if (nch > 1) load_masks(1, nk8);
+            for (int c = 0; c < nch; ++c) {
+                float *cur = vbuf + (c & 1) * kDBuf;
+                unsigned xex[kDPairs], xof[kDPairs], xtot = 0;
+                if (c + 1 < nch) {
+                    xtot = scan(nk8, xex, xof);
+                    issue(vbuf + ((c + 1) & 1) * kDBuf, run + ctot, xtot);
+                    cp_async_wait<1>();  // chunk c has landed, chunk c + 1 may still fly
+                } else {
+                    cp_async_wait<0>();
+                }
+                unsigned xk8[kDPairs];
+#pragma unroll
+                for (int r = 0; r < kDPairs; ++r) xk8[r] = nk8[r];
+                if (c + 2 < nch) load_masks(c + 2, nk8);
                 __syncwarp();
                 for (unsigned j = lane; j < ctot; j += 32)
-                    vals[j] = med2 > 0.f ? __fdiv_rn(__fsqrt_rn(vals[j]), smed) : 0.f;
+                    cur[j] = med2 > 0.f ? __fdiv_rn(__fsqrt_rn(cur[j]), smed) : 0.f;
                 __syncwarp();
 #pragma unroll
                 for (int r = 0; r < kDPairs; ++r) {
-                    if (r >= np) break;
-                    const float *p = vals + off[r] + excl[r];
+                    const int t = c * kDPairs + r;
+                    if (t >= npairs) break;
+                    const float *p = cur + cof[r] + cex[r];
                     float e[2 * kQ];
 #pragma unroll
                     for (int b = 0; b < 2 * kQ; ++b) {
                         e[b] = 0.f;
-                        if (k8[r] >> b & 1u) e[b] = *p++;
+                        if (ck8[r] >> b & 1u) e[b] = *p++;
                     }
                     float *row0 = sm.d.row[wid][0], *row1 = sm.d.row[wid][1];
                     reinterpret_cast<float4 *>(row0)[lane] = make_float4(e[0], e[1], e[2], e[3]);
@@ -1252,15 +1287,15 @@ __global__ void __launch_bounds__(WNT, kWalkBlocksPerSM) edge_walk_kernel(const 
                         unsigned lo = 0, hi = 0;
 #pragma unroll
                         for (int j = 0; j < kQ; ++j) {
-                            lo |= (k8[r] >> j & 1u) << (8 * j);
-                            hi |= (k8[r] >> (j + kQ) & 1u) << (8 * j);
+                            lo |= (ck8[r] >> j & 1u) << (8 * j);
+                            hi |= (ck8[r] >> (j + kQ) & 1u) << (8 * j);
                         }
                         reinterpret_cast<unsigned *>(sm.d.mrow[wid][0])[lane] = lo;
                         reinterpret_cast<unsigned *>(sm.d.mrow[wid][1])[lane] = hi;
                     }
                     __syncwarp();
                     for (int rr = 0; rr < 2; ++rr) {
-                        const int qrow = 2 * (t0 + r) + rr;
+                        const int qrow = 2 * t + rr;
                         if (qrow >= nout) break;
                         const long long rowoff = V.out_off + (long long)(y0 + qrow) * V.w + xg;
                         float *out = a.E + rowoff;
@@ -1269,16 +1304,23 @@ __global__ void __launch_bounds__(WNT, kWalkBlocksPerSM) edge_walk_kernel(const 
                         const uint8_t *mst = sm.d.mrow[wid][rr];
 #pragma unroll
                         for (int k = 0; k < kQ; ++k) {
-                            const int c = 32 * k + lane - kQ;  // output column xg + c, staged at c + kQ
-                            if (c >= 0 && c < kItemCols && xg + c < V.w) {
-                                out[c] = st[c + kQ];
-                                if (mout) mout[c] = mst[c + kQ];
+                            const int cc = 32 * k + lane - kQ;  // output column xg + cc, staged at cc + kQ
+                            if (cc >= 0 && cc < kItemCols && xg + cc < V.w) {
+                                out[cc] = st[cc + kQ];
+                                if (mout) mout[cc] = mst[cc + kQ];
                             }
                         }
                     }
                     __syncwarp();
                 }
                 run += ctot;
+                ctot = xtot;
+#pragma unroll
+                for (int r = 0; r < kDPairs; ++r) {
+                    ck8[r] = xk8[r];
+                    cex[r] = xex[r];
+                    cof[r] = xof[r];
+                }
             }
         }
     }
