@@ -208,6 +208,13 @@ typedef struct gsp_render_opts {
                               edge score (and every screen-space gradient) is then complete,
                               while the chain to the parameters still runs.  A caller can start
                               the selection on another stream from it. */
+    int64_t list_prefix;   /* read by gsp_render_fwd: entries of each tile's list (in depth order)
+                              written before the compositing, <= 0: 1024.  A tile whose pixels
+                              have not all stopped within them (T would drop below 1e-4) gets
+                              the rest of its list afterwards and is composited again over all
+                              of it, so the results do not depend on this value, only the speed
+                              does.  Ignored (whole lists) when gsp_render_fwd accumulates a
+                              score. */
 } gsp_render_opts;
 
 /* Compositing variants (pixels per thread, Gaussians staged per shared-memory batch,
@@ -246,10 +253,12 @@ gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *cams, int32_
                           const gsp_render_opts *opts, void *workspace, size_t workspace_bytes,
                           int32_t *dev_status, gsp_stream_t stream);
 
-/* Statistics of the last gsp_render_fwd on this workspace (device int64[2] inside
+/* Statistics of the last gsp_render_fwd on this workspace (device int64[3] inside
  * the workspace; valid after that call completes; no counterpart in the paper):
  * [0] tile-Gaussian pairs (exact, also when they exceeded pair_capacity),
- * [1] composited (pixel, Gaussian) pairs, i.e. the terms of the sums for C. */
+ * [1] composited (pixel, Gaussian) pairs, i.e. the terms of the sums for C,
+ * [2] tiles composited a second time, over their whole list, because the
+ *     written prefix (gsp_render_opts.list_prefix) did not suffice. */
 const int64_t *gsp_render_pair_count_ptr(const void *workspace, int64_t capacity,
                                          int32_t sh_degree, const gsp_camera *cams,
                                          int32_t num_views, const gsp_render_opts *opts);
@@ -373,8 +382,8 @@ gsp_status gsp_select_mask(const float *scores, const int32_t *count, int64_t ca
  * - capacity must be <= GSP_TOPK_STATIC_MAX_CAPACITY, else GSP_ERR_INVALID_ARG
  *   is returned and nothing is enqueued.
  * - The first call on a device (that device current) looks up the array's
- *   device address on it (cudaGetSymbolAddress); make that first call before
- *   any stream capture.
+ *   device address on it with cudaGetSymbolAddress, a host-side runtime call;
+ *   later calls on that device reuse the address.
  * - All calls share the one array and the kernels re-initialise what must
  *   start at zero; calls that overlap on the GPU (other streams, other host
  *   threads) race on it and must be serialised by the caller.

@@ -45,7 +45,7 @@ class RenderOpts(ctypes.Structure):
     _fields_ = [("pair_capacity", c_i64), ("fwd_variant", c_i32), ("bwd_variant", c_i32),
                 ("pos_grad_sum", ctypes.c_void_p), ("pos_grad_count", ctypes.c_void_p),
                 ("loss_pixels", c_i64), ("spin_limit", c_i64), ("test_expire", c_i32),
-                ("score_event", ctypes.c_void_p)]
+                ("score_event", ctypes.c_void_p), ("list_prefix", c_i64)]
 
 
 class LrSchedule(ctypes.Structure):

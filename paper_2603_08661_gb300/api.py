@@ -200,6 +200,9 @@ class Renderer:
         # the failure-injection hook (tests); 0 in normal use
         self.spin_limit = 0
         self.test_expire = 0
+        # gsp_render_opts.list_prefix: tile-list entries written before the forward
+        # compositing (0: the library's default; results do not depend on it)
+        self.list_prefix = 0
         # pixels of the whole L1 loss when it spans views rendered elsewhere (0: these views)
         self.loss_pixels = 0
         self.ws_bytes = lib().gsp_render_workspace_size(gs.capacity, gs.sh_degree, self.cams, self.nv,
@@ -221,11 +224,12 @@ class Renderer:
         self.opts.fwd_variant, self.opts.bwd_variant = int(v[0]), int(v[1])
 
     def stats(self) -> torch.Tensor:
-        """Device int64[2] of the last forward: tile-Gaussian pairs, composited pairs."""
+        """Device int64[3] of the last forward: tile-Gaussian pairs, composited pairs,
+        tiles composited again over their whole list."""
         p = lib().gsp_render_pair_count_ptr(_ptr(self.ws), self.gs.capacity, self.gs.sh_degree, self.cams,
                                             self.nv, ctypes.byref(self.opts))
         off = int(p) - self.ws.data_ptr()
-        return self.ws[off:off + 16].view(torch.int64)
+        return self.ws[off:off + 24].view(torch.int64)
 
     def pair_count(self) -> torch.Tensor:
         return self.stats()[0:1]
@@ -244,7 +248,7 @@ class Renderer:
                             _ptr(pos_grad[0]).value if pos_grad is not None else None,
                             _ptr(pos_grad[1]).value if pos_grad is not None else None,
                             int(self.loss_pixels), int(self.spin_limit), int(self.test_expire),
-                            _event_handle(score_event))
+                            _event_handle(score_event), int(self.list_prefix))
 
     def forward(self, targets=None, edge=None, score=None, want_loss: bool = True, status=None, stream=None,
                 out=None):

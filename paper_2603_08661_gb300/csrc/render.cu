@@ -93,8 +93,14 @@ struct State {
     int32_t *id1;             // [pair_cap] supertile lists of Gaussian ids
     unsigned long long *mask1;  // [pair_cap] tile mask of each supertile entry
     unsigned *count2;         // [chunk2_cap][64] level-2 chunk counts, then offsets
+    int32_t *chunk_super;     // [chunk2_cap] supertile of each level-2 chunk
     unsigned *tile_len;       // [total_tiles] list length of each tile
     unsigned *tile_start;     // [total_tiles] first position of each tile's list in ids
+    unsigned *tile_avail;     // [total_tiles] entries of each tile's list written to ids (a prefix)
+    unsigned *tile_redo;      // [total_tiles] 1: the tile needed more than its prefix (forward)
+    unsigned *super_redo;     // [total_super] 1: a tile of the supertile needed more than its prefix
+    unsigned *redo_count;     // [1] tiles in redo_list
+    int32_t *redo_list;       // [total_tiles] tiles composited again over their whole list
     int32_t *ids;             // [pair_cap] Gaussian ids, tile lists one after another
     int32_t *order_fwd;       // [total_tiles] tiles by descending list length
     int32_t *order_bwd;       // [total_tiles] tiles by descending last contributor
@@ -108,6 +114,7 @@ struct State {
     const int32_t *n_dev;     // the caller's device count of live Gaussians
     int nb_max;               // depth-sort blocks for cap
     int nch1_max;             // level-1 chunks for cap
+    unsigned prefix = 0xffffffffu;  // tile-list entries written before the forward compositing
     long long pair_cap;
 };
 
@@ -794,7 +801,13 @@ __global__ void __launch_bounds__(kRsThreads) ds_pass(const uint32_t *kin, const
 //   l2_scan     one block per supertile: chunk offsets per tile, list lengths
 //   tile_scan   one block: list starts of all tiles
 //   l2_scatter  per chunk: for each tile and round, a ballot gives every lane
-//               its slot; each store writes a contiguous run of the list
+//               its slot; each store writes a contiguous run of the list.
+//               Only the first st.prefix positions of each list are written
+//               (a chunk that lies wholly past them is skipped): the forward
+//               compositing stops once every pixel of a tile has saturated,
+//               which on dense tiles happens within a few hundred entries.
+//               Tiles that need more are marked by the compositing; a second
+//               pass (rest = 1) then writes the remainder of their lists.
 
 constexpr int kSuper = 8;                 // supertile edge, in tiles
 constexpr int kL1Ranks = 128;             // ranks per level-1 warp chunk
@@ -1125,6 +1138,7 @@ __global__ void __launch_bounds__(kBinThreads) l2_count(const __grid_constant__ 
     const unsigned nchunk = st.chunk2_base[vs.total_super];
     for (unsigned c = blockIdx.x * kBinWarps + wid; c < nchunk; c += gridDim.x * kBinWarps) {
         const int gs = l2_super(st, vs.total_super, c);
+        if (lane == 0) st.chunk_super[c] = gs;  // for l2_scatter
         const int v = find_view_super(vs, gs);
         const ViewP &V = vs.v[v];
         const int s = gs - V.super_base;
@@ -1247,7 +1261,8 @@ __device__ void order_tiles_desc(const unsigned *work, int total_tiles, int32_t 
 
 // Exclusive scan of the tile list lengths into list starts (one block of
 // kScanThreads, the last of l2_scan); the total is checked against the pair
-// capacity once more before any id is written.
+// capacity once more before any id is written.  Each tile's list is then
+// written up to its first st.prefix entries (tile_avail).
 __device__ void tile_scan(int total_tiles, State st, int32_t *status)
 {
     __shared__ unsigned long long wsum[32];
@@ -1273,7 +1288,10 @@ __device__ void tile_scan(int total_tiles, State st, int32_t *status)
         }
         const unsigned long long c0 = carry;
         __syncthreads();
-        if (i < total_tiles) st.tile_start[i] = unsigned(c0 + wb + inc - x);
+        if (i < total_tiles) {
+            st.tile_start[i] = unsigned(c0 + wb + inc - x);
+            st.tile_avail[i] = unsigned(min(x, (unsigned long long)st.prefix));
+        }
         if (threadIdx.x == 0) carry = c0 + all;
         __syncthreads();
     }
@@ -1290,60 +1308,81 @@ __global__ void __launch_bounds__(1024) tile_order_bwd(int total_tiles, State st
     order_tiles_desc(st.tile_work, total_tiles, st.order_bwd);
 }
 
-__global__ void __launch_bounds__(kBinThreads) l2_scatter(const __grid_constant__ Views vs, State st)
+// rest = 0: every tile's entries at list positions below its prefix
+// (tile_avail); rest = 1 (after the forward compositing): the remaining
+// entries of the tiles the forward marked for a redo, nothing when it marked
+// none.  A work item is one chunk and one group of kScatterTiles of its
+// supertile's tiles (lane t: tile t of the group), so that the few chunks with
+// positions to write (the first of each supertile list) spread over many
+// warps; an item whose tiles need nothing from its chunk is skipped before
+// the chunk's entries are read.
+constexpr int kScatterTiles = 16;
+constexpr int kScatterGroups = 64 / kScatterTiles;
+
+__global__ void __launch_bounds__(kBinThreads) l2_scatter(const __grid_constant__ Views vs, State st, int rest)
 {
     if (*st.overflow) return;
+    if (rest && __ldcg(st.redo_count) == 0) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    const unsigned nchunk = st.chunk2_base[vs.total_super];
-    for (unsigned c = blockIdx.x * kBinWarps + wid; c < nchunk; c += gridDim.x * kBinWarps) {
-        const int gs = l2_super(st, vs.total_super, c);
+    const unsigned nitem = st.chunk2_base[vs.total_super] * kScatterGroups;
+    for (unsigned it = blockIdx.x * kBinWarps + wid; it < nitem; it += gridDim.x * kBinWarps) {
+        const unsigned c = it / kScatterGroups;
+        const int grp = int(it % kScatterGroups);
+        const int gs = st.chunk_super[c];
+        if (!GSP_BOUND(gs, vs.total_super, st.status)) continue;
+        if (rest && __ldcg(st.super_redo + gs) == 0) continue;
         const int v = find_view_super(vs, gs);
         const ViewP &V = vs.v[v];
         const int s = gs - V.super_base;
         const int sy = s / V.sx, sx = s - sy * V.sx;
+        // lane t < kScatterTiles: tile t of the group, the chunk's first list
+        // position in it and the window [lo, hi) of positions this pass writes
+        const int gt = lane < kScatterTiles ? super_tile(V, sx, sy, grp * kScatterTiles + lane) : -1;
+        unsigned cur = 0, lo = 0, hi = 0;
+        if (gt >= 0) {
+            const unsigned ts = st.tile_start[gt];
+            cur = ts + st.count2[(size_t)c * 64 + grp * kScatterTiles + lane];
+            if (!rest) {
+                lo = ts;
+                hi = ts + st.tile_avail[gt];
+            } else if (__ldcg(st.tile_redo + gt)) {
+                lo = ts + st.tile_avail[gt];
+                hi = ts + st.tile_len[gt];
+            }
+        }
+        const unsigned want = __ballot_sync(0xffffffffu, cur < hi);
+        if (want == 0) continue;
         const unsigned e0 = st.list1_start[gs] + (c - st.chunk2_base[gs]) * kBinRanks;
         const unsigned e1 = st.list1_start[gs] + st.len1[gs];
         int g[kBinRounds];
-        unsigned long long m[kBinRounds];
-        unsigned long long any = 0;
+        unsigned mh[kBinRounds];
+        unsigned any = 0;
 #pragma unroll
         for (int k = 0; k < kBinRounds; ++k) {
             const unsigned e = e0 + 32 * k + lane;
             g[k] = 0;
-            m[k] = 0;
+            mh[k] = 0;
             if (e < e1 && GSP_BOUND(e, st.pair_cap, st.status)) {
                 g[k] = st.id1[e];
-                m[k] = st.mask1[e];
+                mh[k] = unsigned(st.mask1[e] >> (grp * kScatterTiles)) & ((1u << kScatterTiles) - 1u);
             }
-            any |= m[k];
+            any |= mh[k];
         }
-        const unsigned any_lo = __reduce_or_sync(0xffffffffu, unsigned(any));
-        const unsigned any_hi = __reduce_or_sync(0xffffffffu, unsigned(any >> 32));
-        const int gt0 = super_tile(V, sx, sy, lane), gt1 = super_tile(V, sx, sy, lane + 32);
-        const unsigned cur0 = gt0 >= 0 ? st.tile_start[gt0] + st.count2[(size_t)c * 64 + lane] : 0u;
-        const unsigned cur1 = gt1 >= 0 ? st.tile_start[gt1] + st.count2[(size_t)c * 64 + 32 + lane] : 0u;
-        // two halves of 32 tiles: the masks' 32-bit halves are shifted once per tile
-        // (a rolled loop: unrolling all 64 tiles overflows the instruction cache)
+        unsigned present = __reduce_or_sync(0xffffffffu, any) & want;
+        while (present) {
+            const int b = __ffs(present) - 1;
+            present &= present - 1;
+            unsigned base = __shfl_sync(0xffffffffu, cur, b);
+            const unsigned wlo = __shfl_sync(0xffffffffu, lo, b), whi = __shfl_sync(0xffffffffu, hi, b);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            unsigned mh[kBinRounds];
-#pragma unroll
-            for (int k = 0; k < kBinRounds; ++k) mh[k] = half ? unsigned(m[k] >> 32) : unsigned(m[k]);
-            unsigned present = half ? any_hi : any_lo;
-            const unsigned cur = half ? cur1 : cur0;
-            while (present) {
-                const int b = __ffs(present) - 1;
-                present &= present - 1;
-                unsigned base = __shfl_sync(0xffffffffu, cur, b);
-#pragma unroll
-                for (int k = 0; k < kBinRounds; ++k) {
-                    const bool bit = (mh[k] >> b) & 1u;
-                    const unsigned bal = __ballot_sync(0xffffffffu, bit);
-                    if (bit && GSP_BOUND(base + __popc(bal & lt), st.pair_cap, st.status))
-                        st.ids[base + __popc(bal & lt)] = g[k];
-                    base += __popc(bal);
-                }
+            for (int k = 0; k < kBinRounds; ++k) {
+                const bool bit = (mh[k] >> b) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, bit);
+                const unsigned pos = base + __popc(bal & lt);
+                if (bit && pos >= wlo && pos < whi && GSP_BOUND(pos, st.pair_cap, st.status)) st.ids[pos] = g[k];
+                base += __popc(bal);
+                if (base >= whi) break;  // warp-uniform: the window is full
             }
         }
     }
@@ -1405,8 +1444,13 @@ __device__ __forceinline__ float target_value(const ViewP &V, int x, int y, int 
 // Forward compositing: one block per 16x16 tile, each thread a vertical run
 // of PPT pixels.  The tile's list is staged through shared memory in batches
 // of BATCH Gaussians; the block leaves when every pixel has stopped.
+// Only a prefix of each list has been written (tile_avail: the first
+// st.prefix entries); a tile that reaches its end with a pixel still running
+// writes nothing, is marked for a redo and leaves.  redo_pass = 1: the blocks
+// composite the marked tiles over their whole lists (written meanwhile by
+// l2_scatter with rest = 1), block b the tiles b, b + grid, ...
 
-template <int PPT, int BATCH, bool CULL>
+template <int PPT, int BATCH, bool CULL, bool REDO>
 __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_constant__ Views vs, State st,
                                                                 long long cap, const float *edge, float *rgb_out,
                                                                 float *T_out, int32_t *last_out, float *score)
@@ -1420,139 +1464,168 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
     __shared__ unsigned s_maxlast;
     __shared__ unsigned long long s_contrib;
     if (*st.overflow) return;
-    const int gt = st.order_fwd[blockIdx.x];
-    const int v = find_view(vs, gt);
-    const ViewP &V = vs.v[v];
-    const int lt = gt - V.tile_base;
-    const int tyy = lt / V.tiles_x, txx = lt - tyy * V.tiles_x;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const WarpBlock<PPT> wb(txx, tyy, tid);
-    const int x = wb.x, y0 = wb.y0;
-    const float wcx = wb.wcx, wcy = wb.wcy, whw = wb.whw, whh = wb.whh;
-    const float px = x + 0.5f;
-    const int len = int(st.tile_len[gt]);
-    const int32_t *list = st.ids + st.tile_start[gt];
-    const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
-    const float2 *mlo = st.mlo + (size_t)v * cap;
-    if (tid == 0) {
-        s_maxlast = 0;
-        s_contrib = 0;
-    }
-    __syncthreads();
-    unsigned ncontrib = 0;
+    // first pass: block b composites tile order_fwd[b]; redo pass: a smaller
+    // grid loops over the marked tiles
+    for (int item = blockIdx.x;; item += gridDim.x) {
+        int gt;
+        if constexpr (REDO) {
+            if (item >= int(__ldcg(st.redo_count))) return;
+            gt = __ldcg(st.redo_list + item);
+            __syncthreads();  // the previous tile's shared state is no longer read
+        } else {
+            gt = st.order_fwd[item];
+        }
+        const int v = find_view(vs, gt);
+        const ViewP &V = vs.v[v];
+        const int lt = gt - V.tile_base;
+        const int tyy = lt / V.tiles_x, txx = lt - tyy * V.tiles_x;
+        const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+        const WarpBlock<PPT> wb(txx, tyy, tid);
+        const int x = wb.x, y0 = wb.y0;
+        const float wcx = wb.wcx, wcy = wb.wcy, whw = wb.whw, whh = wb.whh;
+        const float px = x + 0.5f;
+        const int len_full = int(st.tile_len[gt]);
+        const int len = REDO ? len_full : int(st.tile_avail[gt]);
+        const int32_t *list = st.ids + st.tile_start[gt];
+        const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
+        const float2 *mlo = st.mlo + (size_t)v * cap;
+        if (tid == 0) {
+            s_maxlast = 0;
+            s_contrib = 0;
+            if (REDO) st.tile_avail[gt] = unsigned(len_full);  // the adjoint may read all of it
+        }
+        __syncthreads();
+        unsigned ncontrib = 0;
 
-    float T[PPT], C0[PPT], C1[PPT], C2[PPT], E[PPT];
-    int last[PPT];
-    bool done[PPT];
+        float T[PPT], C0[PPT], C1[PPT], C2[PPT], E[PPT];
+        int last[PPT];
+        bool done[PPT];
 #pragma unroll
-    for (int m = 0; m < PPT; ++m) {
-        const int y = y0 + m;
-        const bool inside = x < V.w && y < V.h;
-        T[m] = 1.f; C0[m] = C1[m] = C2[m] = 0.f; last[m] = 0;
-        done[m] = !inside;
-        E[m] = (edge && inside) ? edge[V.pix_off + (long long)y * V.w + x] : 0.f;
-    }
-    for (int b = 0; b < len; b += BATCH) {
-        bool all = true;
-#pragma unroll
-        for (int m = 0; m < PPT; ++m) all = all && done[m];
-        if (__syncthreads_count(all) == NT) break;
-        for (int q = tid; q < BATCH; q += NT) {
-            const int k = b + q;
-            if (k < len) {
-                int id = 0;
-                if (GSP_BOUND((long long)st.tile_start[gt] + k, st.pair_cap, st.status)) id = list[k];
-                if (!GSP_BOUND(id, cap, st.status)) id = 0;
-                s_id[q] = id;
-                s_xyo[q] = xyo[id];
-                s_mlo[q] = mlo[id];
-                s_con[q] = con[id];
-                s_col[q] = col[id];
-            }
-            if (score) s_score[q] = 0.f;
+        for (int m = 0; m < PPT; ++m) {
+            const int y = y0 + m;
+            const bool inside = x < V.w && y < V.h;
+            T[m] = 1.f; C0[m] = C1[m] = C2[m] = 0.f; last[m] = 0;
+            done[m] = !inside;
+            E[m] = (edge && inside) ? edge[V.pix_off + (long long)y * V.w + x] : 0.f;
         }
-        __syncthreads();
-        const int cnt = min(BATCH, len - b);
-        for (int j = 0; j < cnt; ++j) {
-            const float4 gx = s_xyo[j], gc = s_con[j];
-            // the footprint's bounding box misses every pixel of the warp (warp-uniform)
-            if (CULL && (fabsf(gx.x - wcx) > gx.w + whw || fabsf(gx.y - wcy) > gc.w + whh)) continue;
-            float sv = 0.f;
+        for (int b = 0; b < len; b += BATCH) {
+            bool all = true;
 #pragma unroll
-            for (int m = 0; m < PPT; ++m) {
-                if (done[m]) continue;
-                const Alpha a = eval_alpha(gx, s_mlo[j], gc, px, y0 + m + 0.5f);
-                if (!a.pass) continue;
-                const float Tn = __fmul_rn(T[m], __fsub_rn(1.f, a.alpha));
-                if (Tn < kTMin) {
-                    done[m] = true;
-                    continue;
+            for (int m = 0; m < PPT; ++m) all = all && done[m];
+            if (__syncthreads_count(all) == NT) break;
+            for (int q = tid; q < BATCH; q += NT) {
+                const int k = b + q;
+                if (k < len) {
+                    int id = 0;
+                    if (GSP_BOUND((long long)st.tile_start[gt] + k, st.pair_cap, st.status)) id = list[k];
+                    if (!GSP_BOUND(id, cap, st.status)) id = 0;
+                    s_id[q] = id;
+                    s_xyo[q] = xyo[id];
+                    s_mlo[q] = mlo[id];
+                    s_con[q] = con[id];
+                    s_col[q] = col[id];
                 }
-                ++ncontrib;
-                const float w = __fmul_rn(a.alpha, T[m]);
-                const float4 c = s_col[j];
-                C0[m] = __fmaf_rn(c.x, w, C0[m]);
-                C1[m] = __fmaf_rn(c.y, w, C1[m]);
-                C2[m] = __fmaf_rn(c.z, w, C2[m]);
-                T[m] = Tn;
-                last[m] = b + j + 1;
-                sv = __fmaf_rn(w, E[m], sv);
+                if (score) s_score[q] = 0.f;
             }
-            if (score && __any_sync(0xffffffffu, sv != 0.f)) {
+            __syncthreads();
+            const int cnt = min(BATCH, len - b);
+            for (int j = 0; j < cnt; ++j) {
+                const float4 gx = s_xyo[j], gc = s_con[j];
+                // the footprint's bounding box misses every pixel of the warp (warp-uniform)
+                if (CULL && (fabsf(gx.x - wcx) > gx.w + whw || fabsf(gx.y - wcy) > gc.w + whh)) continue;
+                float sv = 0.f;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-                if (lane == 0) atomicAdd(&s_score[j], sv);
+                for (int m = 0; m < PPT; ++m) {
+                    if (done[m]) continue;
+                    const Alpha a = eval_alpha(gx, s_mlo[j], gc, px, y0 + m + 0.5f);
+                    if (!a.pass) continue;
+                    const float Tn = __fmul_rn(T[m], __fsub_rn(1.f, a.alpha));
+                    if (Tn < kTMin) {
+                        done[m] = true;
+                        continue;
+                    }
+                    ++ncontrib;
+                    const float w = __fmul_rn(a.alpha, T[m]);
+                    const float4 c = s_col[j];
+                    C0[m] = __fmaf_rn(c.x, w, C0[m]);
+                    C1[m] = __fmaf_rn(c.y, w, C1[m]);
+                    C2[m] = __fmaf_rn(c.z, w, C2[m]);
+                    T[m] = Tn;
+                    last[m] = b + j + 1;
+                    sv = __fmaf_rn(w, E[m], sv);
+                }
+                if (score && __any_sync(0xffffffffu, sv != 0.f)) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+                    if (lane == 0) atomicAdd(&s_score[j], sv);
+                }
+            }
+            __syncthreads();
+            if (score)
+                for (int q = tid; q < cnt; q += NT)
+                    if (s_score[q] != 0.f) atomicAdd(&score[s_id[q]], s_score[q]);
+        }
+        if (!REDO && len < len_full) {
+            // the written prefix ran out with a pixel still running (never the case
+            // with a score: the whole lists are written then)
+            bool all = true;
+#pragma unroll
+            for (int m = 0; m < PPT; ++m) all = all && done[m];
+            if (__syncthreads_count(all) != NT) {
+                if (tid == 0) {
+                    st.tile_redo[gt] = 1u;
+                    atomicExch(st.super_redo + V.super_base + (tyy / kSuper) * V.sx + txx / kSuper, 1u);
+                    st.redo_list[atomicAdd(st.redo_count, 1u)] = gt;
+                }
+                return;  // (first pass: one tile per block)
             }
         }
-        __syncthreads();
-        if (score)
-            for (int q = tid; q < cnt; q += NT)
-                if (s_score[q] != 0.f) atomicAdd(&score[s_id[q]], s_score[q]);
-    }
-    {
-        // per-tile statistics: largest last position (orders the adjoint's tiles)
-        // and the number of composited pairs
-        unsigned ml = 0;
+        {
+            // per-tile statistics: largest last position (orders the adjoint's tiles)
+            // and the number of composited pairs
+            unsigned ml = 0;
 #pragma unroll
-        for (int m = 0; m < PPT; ++m) ml = max(ml, unsigned(last[m]));
-        ml = __reduce_max_sync(0xffffffffu, ml);
-        const unsigned nc = __reduce_add_sync(0xffffffffu, ncontrib);
-        if (lane == 0) {
-            atomicMax(&s_maxlast, ml);
-            atomicAdd(&s_contrib, (unsigned long long)nc);
+            for (int m = 0; m < PPT; ++m) ml = max(ml, unsigned(last[m]));
+            ml = __reduce_max_sync(0xffffffffu, ml);
+            const unsigned nc = __reduce_add_sync(0xffffffffu, ncontrib);
+            if (lane == 0) {
+                atomicMax(&s_maxlast, ml);
+                atomicAdd(&s_contrib, (unsigned long long)nc);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                st.tile_work[gt] = s_maxlast;
+                atomicAdd(reinterpret_cast<unsigned long long *>(st.contrib), s_contrib);
+            }
         }
-        __syncthreads();
-        if (tid == 0) {
-            st.tile_work[gt] = s_maxlast;
-            atomicAdd(reinterpret_cast<unsigned long long *>(st.contrib), s_contrib);
-        }
-    }
-    float l = 0.f;
+        float l = 0.f;
 #pragma unroll
-    for (int m = 0; m < PPT; ++m) {
-        const int y = y0 + m;
-        if (x < V.w && y < V.h) {
-            const long long pid = V.pix_off + (long long)y * V.w + x;
-            rgb_out[3 * pid + 0] = C0[m];
-            rgb_out[3 * pid + 1] = C1[m];
-            rgb_out[3 * pid + 2] = C2[m];
-            T_out[pid] = T[m];
-            last_out[pid] = last[m];
-            if (V.tgt)
-                l += fabsf(C0[m] - target_value(V, x, y, 0)) + fabsf(C1[m] - target_value(V, x, y, 1)) +
-                     fabsf(C2[m] - target_value(V, x, y, 2));
+        for (int m = 0; m < PPT; ++m) {
+            const int y = y0 + m;
+            if (x < V.w && y < V.h) {
+                const long long pid = V.pix_off + (long long)y * V.w + x;
+                rgb_out[3 * pid + 0] = C0[m];
+                rgb_out[3 * pid + 1] = C1[m];
+                rgb_out[3 * pid + 2] = C2[m];
+                T_out[pid] = T[m];
+                last_out[pid] = last[m];
+                if (V.tgt)
+                    l += fabsf(C0[m] - target_value(V, x, y, 0)) + fabsf(C1[m] - target_value(V, x, y, 1)) +
+                         fabsf(C2[m] - target_value(V, x, y, 2));
+            }
         }
-    }
-    if (V.tgt) {
+        if (V.tgt) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-        if (lane == 0) s_red[wid] = l;
-        __syncthreads();
-        if (tid == 0) {
-            double sum = 0.0;
-            for (int w = 0; w < NT / 32; ++w) sum += s_red[w];
-            atomicAdd(st.loss_acc, sum);
+            for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+            if (lane == 0) s_red[wid] = l;
+            __syncthreads();
+            if (tid == 0) {
+                double sum = 0.0;
+                for (int w = 0; w < NT / 32; ++w) sum += s_red[w];
+                atomicAdd(st.loss_acc, sum);
+            }
         }
+        if constexpr (!REDO) return;  // one tile per block
     }
 }
 
@@ -1645,7 +1718,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 2 ? 6 : 2048 / (kTilePi
     const WarpBlock<PPT> wb(txx, tyy, tid);
     const int x = wb.x, y0 = wb.y0;
     const float px = x + 0.5f;
-    const int list_len = int(st.tile_len[gt]);
+    const int list_len = int(st.tile_avail[gt]);  // the written prefix of the tile's list
     const int32_t *list = st.ids + st.tile_start[gt];
     const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
     const float2 *mlo = st.mlo + (size_t)v * cap;
@@ -1974,15 +2047,38 @@ constexpr Variant kFwdVariants[] = {{1, 256, true}, {2, 256, true}, {1, 128, tru
 constexpr Variant kBwdVariants[] = {{2, 256, true}, {1, 256, true}, {4, 256, true}, {2, 128, true},
                                     {2, 128, false}, {4, 128, true}};
 constexpr int kNumFwdVariants = sizeof(kFwdVariants) / sizeof(Variant);
+// Tile-list entries written before the forward compositing when the caller
+// sets none: dense tiles stop within a few hundred entries (their pixels
+// saturate), the others get the rest of their list afterwards.
+constexpr unsigned kDefaultListPrefix = 1024;
 constexpr int kNumBwdVariants = sizeof(kBwdVariants) / sizeof(Variant);
 
 template <int V>
 void launch_fwd(const Views &vs, const State &S, long long cap, const float *edge, float *rgb, float *T, int32_t *last,
-                float *score, cudaStream_t s)
+                float *score, int redo_pass, cudaStream_t s)
 {
     constexpr Variant var = kFwdVariants[V];
-    composite_fwd<var.ppt, var.batch, var.cull>
-        <<<vs.total_tiles, kTilePix / var.ppt, 0, s>>>(vs, S, cap, edge, rgb, T, last, score);
+    // the redo pass: a few blocks per SM loop over the marked tiles (usually none)
+    if (redo_pass)
+        composite_fwd<var.ppt, var.batch, var.cull, true>
+            <<<std::min(vs.total_tiles, 4 * num_sms()), kTilePix / var.ppt, 0, s>>>(vs, S, cap, edge, rgb, T, last,
+                                                                                    score);
+    else
+        composite_fwd<var.ppt, var.batch, var.cull, false>
+            <<<vs.total_tiles, kTilePix / var.ppt, 0, s>>>(vs, S, cap, edge, rgb, T, last, score);
+}
+
+void launch_fwd_variant(int variant, const Views &vs, const State &S, long long cap, const float *edge, float *rgb,
+                        float *T, int32_t *last, float *score, int redo_pass, cudaStream_t s)
+{
+    switch (variant) {
+    case 1: launch_fwd<1>(vs, S, cap, edge, rgb, T, last, score, redo_pass, s); break;
+    case 2: launch_fwd<2>(vs, S, cap, edge, rgb, T, last, score, redo_pass, s); break;
+    case 3: launch_fwd<3>(vs, S, cap, edge, rgb, T, last, score, redo_pass, s); break;
+    case 4: launch_fwd<4>(vs, S, cap, edge, rgb, T, last, score, redo_pass, s); break;
+    case 5: launch_fwd<5>(vs, S, cap, edge, rgb, T, last, score, redo_pass, s); break;
+    default: launch_fwd<0>(vs, S, cap, edge, rgb, T, last, score, redo_pass, s); break;
+    }
 }
 
 template <int V>
@@ -1996,7 +2092,7 @@ void launch_bwd(const Views &vs, const State &S, long long cap, const float *dL,
 
 // ------------------------------------------------------------------- host
 
-constexpr int kCounters = 4;
+constexpr int kCounters = 5;
 
 struct Layout {
     State st;
@@ -2031,26 +2127,33 @@ Layout render_layout(void *ws, long long cap, const Views &vs, long long pair_ca
     s.id1 = c.take<int32_t>((size_t)pair_cap);
     s.mask1 = c.take<unsigned long long>((size_t)pair_cap);
     // level-2 chunks: at most one partial chunk per supertile beyond pair_cap / 256 full ones
-    s.count2 = c.take<unsigned>(((size_t)pair_cap / kBinRanks + total_super + 1) * 64);
+    const size_t chunk2_cap = (size_t)pair_cap / kBinRanks + total_super + 1;
+    s.count2 = c.take<unsigned>(chunk2_cap * 64);
+    s.chunk_super = c.take<int32_t>(chunk2_cap);
     s.tile_len = c.take<unsigned>(total_tiles);
     s.tile_start = c.take<unsigned>(total_tiles);
+    s.tile_avail = c.take<unsigned>(total_tiles);
+    s.redo_list = c.take<int32_t>(total_tiles);
     s.ids = c.take<int32_t>((size_t)pair_cap);
     s.order_fwd = c.take<int32_t>(total_tiles);
     s.order_bwd = c.take<int32_t>(total_tiles);
     s.tile_work = c.take<unsigned>(total_tiles);
     s.g2d = c.take<float4>(vc * 3);
     // cleared by one memset per forward pass (from pairs_total to clear_end):
-    // pair total, composited pairs, loss sum, overflow flag; the depth sort's
-    // digit counts and tickets, the binning scans' tickets
+    // pair total, composited pairs, redone tiles, loss sum, overflow flag; the depth sort's
+    // digit counts and tickets, the binning scans' tickets; the redo flags and count
     const size_t clear0 = c.size();  // where the counters start
     long long *ctr = c.take<long long>(kCounters);
     s.pairs_total = ctr;
     s.contrib = ctr + 1;
-    s.loss_acc = reinterpret_cast<double *>(ctr + 2);
-    s.overflow = reinterpret_cast<int32_t *>(ctr + 3);
+    s.redo_count = reinterpret_cast<unsigned *>(ctr + 2);  // the low word of an int64 statistic
+    s.loss_acc = reinterpret_cast<double *>(ctr + 3);
+    s.overflow = reinterpret_cast<int32_t *>(ctr + 4);
     s.sort_ghist = c.take<unsigned>((size_t)vs.n * 4 * 256);
     s.sort_ticket = c.take<unsigned>((size_t)vs.n * 4);
     s.scan_ticket = c.take<unsigned>(2);
+    s.tile_redo = c.take<unsigned>(total_tiles);
+    s.super_redo = c.take<unsigned>(total_super);
     L.clear_bytes = c.size() - clear0;
     s.pair_cap = pair_cap;
     L.bytes = c.size();
@@ -2177,6 +2280,11 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     State S = L.st;
     S.n_dev = g->count;
     S.status = dev_status;
+    // tile-list entries written before the compositing (all of them when a
+    // score is accumulated: the forward must not composite any tile twice then)
+    S.prefix = (score || opts->list_prefix >= 0xffffffffLL) ? 0xffffffffu
+               : opts->list_prefix > 0                      ? unsigned(opts->list_prefix)
+                                                            : kDefaultListPrefix;
     Params P = make_params(g);
     P.status = dev_status;
     P.sh_bulk = (reinterpret_cast<uintptr_t>(g->sh) & 15) == 0;
@@ -2224,22 +2332,20 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
         l1_scatter<<<l1_blocks, kBinThreads, smem, s>>>(vs, S, cap);
         l2_count<<<16 * nsm, kBinThreads, 0, s>>>(vs, S, cap);
         l2_scan<<<vs.total_super, kScanThreads, 0, s>>>(vs, S, dev_status);
-        l2_scatter<<<16 * nsm, kBinThreads, 0, s>>>(vs, S);
+        l2_scatter<<<16 * nsm, kBinThreads, 0, s>>>(vs, S, 0);
     }
     stage_end("bin", s);
     GSP_LAUNCH_CHECK();
     stage_begin("composite_fwd", s);
-    switch (opts->fwd_variant) {
-    case 1: launch_fwd<1>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
-    case 2: launch_fwd<2>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
-    case 3: launch_fwd<3>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
-    case 4: launch_fwd<4>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
-    case 5: launch_fwd<5>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
-    default: launch_fwd<0>(vs, S, cap, edge, rgb_out, T_final, last_idx, score, s); break;
-    }
+    // over the written prefixes; then the rest of the lists of the tiles that
+    // needed more, and those tiles again (both launches leave at once when no
+    // tile did)
+    launch_fwd_variant(opts->fwd_variant, vs, S, cap, edge, rgb_out, T_final, last_idx, score, 0, s);
+    l2_scatter<<<4 * num_sms(), kBinThreads, 0, s>>>(vs, S, 1);
+    launch_fwd_variant(opts->fwd_variant, vs, S, cap, edge, rgb_out, T_final, last_idx, score, 1, s);
     stage_end("composite_fwd", s);
     GSP_LAUNCH_CHECK();
-    note_launches(2 + 5 + 6 + 1);
+    note_launches(2 + 5 + 6 + 3);
     if (loss_out) {
         loss_finalise<<<1, 1, 0, s>>>(S, opts->loss_pixels > 0 ? opts->loss_pixels : vs.total_pix, loss_out);
         note_launches(1);

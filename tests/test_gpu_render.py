@@ -31,11 +31,12 @@ def _flat_edge(edges):
 
 
 def gpu_render(gsp, g, cams, targets=None, edges=None, dL=None, pair_capacity=1 << 22, score_in="fwd",
-               capacity=None):
+               capacity=None, list_prefix=0):
     import torch
     dev = torch.device("cuda")
     gs = gsp.GaussianSet.from_arrays(g, capacity=capacity, device=dev)
     r = gsp.Renderer(gs, cams, pair_capacity, device=dev)
+    r.list_prefix = list_prefix
     E = torch.from_numpy(_flat_edge(edges)).to(dev) if edges is not None else None
     score = torch.zeros(gs.capacity, device=dev) if E is not None else None
     tg = [torch.from_numpy(t).to(dev) for t in targets] if targets is not None else None
@@ -48,7 +49,7 @@ def gpu_render(gsp, g, cams, targets=None, edges=None, dL=None, pair_capacity=1 
     torch.cuda.synchronize()
     res = {"status": int(out["status"].item()), "rgb": out["rgb"].cpu().numpy(), "T": out["T"].cpu().numpy(),
            "last": out["last"].cpu().numpy(), "pairs": int(r.pair_count().item()),
-           "contrib": int(r.stats()[1].item()),
+           "contrib": int(r.stats()[1].item()), "redone": int(r.stats()[2].item()),
            "score": score.cpu().numpy() if score is not None else None,
            "loss": float(out["loss"].item()) if out["loss"] is not None else None}
     if grads is not None:
@@ -388,3 +389,62 @@ def test_degenerate_view_shapes_in_one_batch(gsp_lib):
         off += h * w
     check_scores(res["score"], sum(r["score"] for r in refs), skip)
     check_grads(res["grads"], gr, gm, n, skip)
+
+
+@pytest.mark.parametrize("prefix", [1, 7, 64])
+def test_tile_list_prefix_and_redo_leave_results_unchanged(gsp_lib, prefix):
+    """Only the first list_prefix entries of each tile list are written before
+    the forward compositing; tiles that need more are marked, get the rest of
+    their list and are composited again.  The forward's outputs are bitwise
+    those of whole lists, the gradients (score in the adjoint) still match
+    the oracle, and the redone tiles are counted."""
+    g = synth.gaussians(800, 3, seed=8)
+    g["log_scales"] += np.float32(0.7)
+    g["opacity_logits"] -= np.float32(2.0)  # few pixels saturate: many tiles need their whole list
+    sizes = [(80, 60), (128, 128), (194, 102)]
+    cams = [synth.camera_ring(k, 3, resolutions=sizes) for k in range(3)]
+    rng = np.random.default_rng(3)
+    edges = [rng.uniform(0, 2, (c["height"], c["width"])) for c in cams]
+    npix = sum(c["width"] * c["height"] for c in cams)
+    dL = rng.normal(size=(npix, 3)) / npix
+    whole = gpu_render(gsp_lib, g, cams, edges=edges, dL=dL, score_in="bwd", list_prefix=1 << 40)
+    part = gpu_render(gsp_lib, g, cams, edges=edges, dL=dL, score_in="bwd", list_prefix=prefix)
+    assert whole["status"] == 0 and part["status"] == 0
+    assert whole["redone"] == 0 and part["redone"] > 0
+    for k in ("rgb", "T", "last"):
+        assert np.array_equal(part[k], whole[k]), k
+    assert part["contrib"] == whole["contrib"] and part["pairs"] == whole["pairs"]
+    refs = oracle_views(g, cams, edges)
+    check_image(part, refs, cams)
+    skip = set()
+    for c, r in zip(cams, refs):
+        skip |= exempt_gaussians(g, c, r)
+    check_scores(part["score"], sum(r["score"] for r in refs), skip)
+    off = 0
+    gr, gm = {}, {}
+    for c in cams:
+        n_c = c["width"] * c["height"]
+        d = dL[off:off + n_c].reshape(c["height"], c["width"], 3)
+        a = orc.render_bwd(g, c, d)
+        b = orc.render_bwd(g, c, d, magnitude=True)
+        for k in a:
+            gr[k] = gr.get(k, 0) + a[k]
+            gm[k] = gm.get(k, 0) + b[k]
+        off += n_c
+    check_grads(part["grads"], gr, gm, 800, skip)
+
+
+def test_score_in_forward_writes_whole_lists(gsp_lib):
+    """A forward that accumulates the score composites every tile once: it
+    writes whole lists whatever list_prefix says (no tile is redone)."""
+    g = synth.gaussians(800, 3, seed=8)
+    g["opacity_logits"] -= np.float32(2.0)
+    cam = synth.camera_front(128, 96)
+    e = np.random.default_rng(4).uniform(0, 2, (96, 128))
+    a = gpu_render(gsp_lib, g, [cam], edges=[e], score_in="fwd", list_prefix=1)
+    b = gpu_render(gsp_lib, g, [cam], edges=[e], score_in="fwd", list_prefix=1 << 40)
+    assert a["redone"] == 0
+    for k in ("rgb", "T", "last"):
+        assert np.array_equal(a[k], b[k]), k
+    # floating-point atomics: equal up to the order of the additions
+    assert np.allclose(a["score"], b["score"], rtol=1e-5, atol=1e-6 * float(np.abs(b["score"]).max()))
