@@ -350,6 +350,7 @@ def run_gsp(args, rank, world):
     # data-dependent work counts of the workload (the scene is identical every step)
     stats = rends[0].stats().cpu()
     contrib = int(stats[1])
+    redone = int(stats[2])
     evals = int(fwd_bufs["last"].to(torch.int64).sum().item())
 
     # capture one graph per copy; the dominant stage is bracketed by library events
@@ -556,7 +557,7 @@ def run_gsp(args, rank, world):
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clk.summary(), "plain": plain,
         "stages": stages_roof,
-        "work_counts": {"pairs": pairs, "evaluations": evals, "composited": contrib},
+        "work_counts": {"pairs": pairs, "evaluations": evals, "composited": contrib, "redone_tiles": redone},
         "next_rows": next_rows,
     }
     return line
@@ -722,6 +723,7 @@ def run_multiview(steps=5, warmup=3):
         ms, cnt = timer.read()
         stages[stg] = round(ms / max(cnt, 1), 3)
     gsp.StageTimer.disarm()
+    redone = int(r.stats()[2].item())  # tiles whose list prefix did not suffice
     # plain path: one single-view call per view and pass, default variants, eager
     del r
     torch.cuda.empty_cache()
@@ -754,7 +756,7 @@ def run_multiview(steps=5, warmup=3):
     return {"workload": "3M Gaussians SH3, 8 ring views 640x480..1920x1080 (8.76 Mpix): fwd + L1 + bwd + edge score",
             "pairs": pairs, "variants": list(variants), "ms_per_iter_batched_graph": round(ms_graph, 3),
             "ms_per_iter_plain_per_view": round(ms_plain, 3), "mpix_per_s_batched": round(npix / ms_graph / 1e3, 1),
-            "steps": steps, "stages_ms": stages}
+            "steps": steps, "stages_ms": stages, "redone_tiles": redone}
 
 
 def run_multiview_sharded(rank, world, steps=5, warmup=3):

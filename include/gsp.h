@@ -209,12 +209,11 @@ typedef struct gsp_render_opts {
                               while the chain to the parameters still runs.  A caller can start
                               the selection on another stream from it. */
     int64_t list_prefix;   /* read by gsp_render_fwd: entries of each tile's list (in depth order)
-                              written before the compositing, <= 0: 1024.  A tile whose pixels
+                              written before the compositing, <= 0: 2048.  A tile whose pixels
                               have not all stopped within them (T would drop below 1e-4) gets
-                              the rest of its list afterwards and is composited again over all
-                              of it, so the results do not depend on this value, only the speed
-                              does.  Ignored (whole lists) when gsp_render_fwd accumulates a
-                              score. */
+                              the rest of its list afterwards and its compositing resumes from
+                              where the prefix ended, so the results do not depend on this
+                              value, only the speed does. */
 } gsp_render_opts;
 
 /* Compositing variants (pixels per thread, Gaussians staged per shared-memory batch,
@@ -257,8 +256,8 @@ gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *cams, int32_
  * the workspace; valid after that call completes; no counterpart in the paper):
  * [0] tile-Gaussian pairs (exact, also when they exceeded pair_capacity),
  * [1] composited (pixel, Gaussian) pairs, i.e. the terms of the sums for C,
- * [2] tiles composited a second time, over their whole list, because the
- *     written prefix (gsp_render_opts.list_prefix) did not suffice. */
+ * [2] tiles whose compositing went on past the written prefix of their list
+ *     (gsp_render_opts.list_prefix) once the rest of the list was written. */
 const int64_t *gsp_render_pair_count_ptr(const void *workspace, int64_t capacity,
                                          int32_t sh_degree, const gsp_camera *cams,
                                          int32_t num_views, const gsp_render_opts *opts);

@@ -225,7 +225,7 @@ class Renderer:
 
     def stats(self) -> torch.Tensor:
         """Device int64[3] of the last forward: tile-Gaussian pairs, composited pairs,
-        tiles composited again over their whole list."""
+        tiles whose compositing went on past their list prefix."""
         p = lib().gsp_render_pair_count_ptr(_ptr(self.ws), self.gs.capacity, self.gs.sh_degree, self.cams,
                                             self.nv, ctypes.byref(self.opts))
         off = int(p) - self.ws.data_ptr()

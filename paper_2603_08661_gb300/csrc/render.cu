@@ -100,7 +100,7 @@ struct State {
     unsigned *tile_redo;      // [total_tiles] 1: the tile needed more than its prefix (forward)
     unsigned *super_redo;     // [total_super] 1: a tile of the supertile needed more than its prefix
     unsigned *redo_count;     // [1] tiles in redo_list
-    int32_t *redo_list;       // [total_tiles] tiles composited again over their whole list
+    int32_t *redo_list;       // [total_tiles] tiles whose compositing resumes past their prefix
     int32_t *ids;             // [pair_cap] Gaussian ids, tile lists one after another
     int32_t *order_fwd;       // [total_tiles] tiles by descending list length
     int32_t *order_bwd;       // [total_tiles] tiles by descending last contributor
@@ -1446,9 +1446,12 @@ __device__ __forceinline__ float target_value(const ViewP &V, int x, int y, int 
 // of BATCH Gaussians; the block leaves when every pixel has stopped.
 // Only a prefix of each list has been written (tile_avail: the first
 // st.prefix entries); a tile that reaches its end with a pixel still running
-// writes nothing, is marked for a redo and leaves.  redo_pass = 1: the blocks
-// composite the marked tiles over their whole lists (written meanwhile by
-// l2_scatter with rest = 1), block b the tiles b, b + grid, ...
+// saves every pixel's state (colour, T, last, stopped) in the outputs, is
+// marked and leaves.  REDO: the blocks resume the marked tiles from their
+// saved state over the rest of their lists (written meanwhile by l2_scatter
+// with rest = 1), block b the tiles b, b + grid, ...  Every pixel thus sees
+// the same Gaussians in the same order with the same arithmetic as over
+// the whole list.
 
 template <int PPT, int BATCH, bool CULL, bool REDO>
 __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_constant__ Views vs, State st,
@@ -1485,14 +1488,14 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
         const float wcx = wb.wcx, wcy = wb.wcy, whw = wb.whw, whh = wb.whh;
         const float px = x + 0.5f;
         const int len_full = int(st.tile_len[gt]);
-        const int len = REDO ? len_full : int(st.tile_avail[gt]);
+        const int avail = int(st.tile_avail[gt]);
+        const int len = REDO ? len_full : avail;
         const int32_t *list = st.ids + st.tile_start[gt];
         const float4 *xyo = st.xyo + (size_t)v * cap, *con = st.con + (size_t)v * cap, *col = st.col + (size_t)v * cap;
         const float2 *mlo = st.mlo + (size_t)v * cap;
         if (tid == 0) {
             s_maxlast = 0;
             s_contrib = 0;
-            if (REDO) st.tile_avail[gt] = unsigned(len_full);  // the adjoint may read all of it
         }
         __syncthreads();
         unsigned ncontrib = 0;
@@ -1507,8 +1510,18 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
             T[m] = 1.f; C0[m] = C1[m] = C2[m] = 0.f; last[m] = 0;
             done[m] = !inside;
             E[m] = (edge && inside) ? edge[V.pix_off + (long long)y * V.w + x] : 0.f;
+            if (REDO && inside) {  // the state the first pass saved at the end of the prefix
+                const long long pid = V.pix_off + (long long)y * V.w + x;
+                C0[m] = rgb_out[3 * pid];
+                C1[m] = rgb_out[3 * pid + 1];
+                C2[m] = rgb_out[3 * pid + 2];
+                T[m] = T_out[pid];
+                const int l = last_out[pid];
+                last[m] = l & 0x7fffffff;
+                done[m] = l < 0;
+            }
         }
-        for (int b = 0; b < len; b += BATCH) {
+        for (int b = REDO ? avail : 0; b < len; b += BATCH) {
             bool all = true;
 #pragma unroll
             for (int m = 0; m < PPT; ++m) all = all && done[m];
@@ -1566,12 +1579,25 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
                     if (s_score[q] != 0.f) atomicAdd(&score[s_id[q]], s_score[q]);
         }
         if (!REDO && len < len_full) {
-            // the written prefix ran out with a pixel still running (never the case
-            // with a score: the whole lists are written then)
+            // the written prefix ran out with a pixel still running
             bool all = true;
 #pragma unroll
             for (int m = 0; m < PPT; ++m) all = all && done[m];
             if (__syncthreads_count(all) != NT) {
+#pragma unroll
+                for (int m = 0; m < PPT; ++m) {
+                    const int y = y0 + m;
+                    if (x < V.w && y < V.h) {
+                        const long long pid = V.pix_off + (long long)y * V.w + x;
+                        rgb_out[3 * pid] = C0[m];
+                        rgb_out[3 * pid + 1] = C1[m];
+                        rgb_out[3 * pid + 2] = C2[m];
+                        T_out[pid] = T[m];
+                        last_out[pid] = int(unsigned(last[m]) | (done[m] ? 0x80000000u : 0u));
+                    }
+                }
+                const unsigned nc = __reduce_add_sync(0xffffffffu, ncontrib);
+                if (lane == 0 && nc) atomicAdd(reinterpret_cast<unsigned long long *>(st.contrib), (unsigned long long)nc);
                 if (tid == 0) {
                     st.tile_redo[gt] = 1u;
                     atomicExch(st.super_redo + V.super_base + (tyy / kSuper) * V.sx + txx / kSuper, 1u);
@@ -1596,6 +1622,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) composite_fwd(const __grid_con
             if (tid == 0) {
                 st.tile_work[gt] = s_maxlast;
                 atomicAdd(reinterpret_cast<unsigned long long *>(st.contrib), s_contrib);
+                if (REDO) st.tile_avail[gt] = unsigned(len_full);  // the adjoint may read all of it
             }
         }
         float l = 0.f;
@@ -2049,8 +2076,10 @@ constexpr Variant kBwdVariants[] = {{2, 256, true}, {1, 256, true}, {4, 256, tru
 constexpr int kNumFwdVariants = sizeof(kFwdVariants) / sizeof(Variant);
 // Tile-list entries written before the forward compositing when the caller
 // sets none: dense tiles stop within a few hundred entries (their pixels
-// saturate), the others get the rest of their list afterwards.
-constexpr unsigned kDefaultListPrefix = 1024;
+// saturate), the others get the rest of their list afterwards.  (1M
+// Gaussians on one 1237x822 view: the same step time with 1024 or 2048;
+// 3M on eight ring views: 1,179 resumed tiles with 1024, 4 with 2048.)
+constexpr unsigned kDefaultListPrefix = 2048;
 constexpr int kNumBwdVariants = sizeof(kBwdVariants) / sizeof(Variant);
 
 template <int V>
@@ -2061,7 +2090,7 @@ void launch_fwd(const Views &vs, const State &S, long long cap, const float *edg
     // the redo pass: a few blocks per SM loop over the marked tiles (usually none)
     if (redo_pass)
         composite_fwd<var.ppt, var.batch, var.cull, true>
-            <<<std::min(vs.total_tiles, 4 * num_sms()), kTilePix / var.ppt, 0, s>>>(vs, S, cap, edge, rgb, T, last,
+            <<<std::min(vs.total_tiles, 8 * num_sms()), kTilePix / var.ppt, 0, s>>>(vs, S, cap, edge, rgb, T, last,
                                                                                     score);
     else
         composite_fwd<var.ppt, var.batch, var.cull, false>
@@ -2280,11 +2309,10 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     State S = L.st;
     S.n_dev = g->count;
     S.status = dev_status;
-    // tile-list entries written before the compositing (all of them when a
-    // score is accumulated: the forward must not composite any tile twice then)
-    S.prefix = (score || opts->list_prefix >= 0xffffffffLL) ? 0xffffffffu
-               : opts->list_prefix > 0                      ? unsigned(opts->list_prefix)
-                                                            : kDefaultListPrefix;
+    // tile-list entries written before the compositing
+    S.prefix = opts->list_prefix >= 0xffffffffLL ? 0xffffffffu
+               : opts->list_prefix > 0           ? unsigned(opts->list_prefix)
+                                                 : kDefaultListPrefix;
     Params P = make_params(g);
     P.status = dev_status;
     P.sh_bulk = (reinterpret_cast<uintptr_t>(g->sh) & 15) == 0;
@@ -2341,7 +2369,7 @@ extern "C" gsp_status gsp_render_fwd(const gsp_gaussians *g, const gsp_camera *c
     // needed more, and those tiles again (both launches leave at once when no
     // tile did)
     launch_fwd_variant(opts->fwd_variant, vs, S, cap, edge, rgb_out, T_final, last_idx, score, 0, s);
-    l2_scatter<<<4 * num_sms(), kBinThreads, 0, s>>>(vs, S, 1);
+    l2_scatter<<<16 * num_sms(), kBinThreads, 0, s>>>(vs, S, 1);
     launch_fwd_variant(opts->fwd_variant, vs, S, cap, edge, rgb_out, T_final, last_idx, score, 1, s);
     stage_end("composite_fwd", s);
     GSP_LAUNCH_CHECK();

@@ -394,10 +394,10 @@ def test_degenerate_view_shapes_in_one_batch(gsp_lib):
 @pytest.mark.parametrize("prefix", [1, 7, 64])
 def test_tile_list_prefix_and_redo_leave_results_unchanged(gsp_lib, prefix):
     """Only the first list_prefix entries of each tile list are written before
-    the forward compositing; tiles that need more are marked, get the rest of
-    their list and are composited again.  The forward's outputs are bitwise
+    the forward compositing; tiles that need more save their pixels' state,
+    get the rest of their list and resume.  The forward's outputs are bitwise
     those of whole lists, the gradients (score in the adjoint) still match
-    the oracle, and the redone tiles are counted."""
+    the oracle, and the resumed tiles are counted."""
     g = synth.gaussians(800, 3, seed=8)
     g["log_scales"] += np.float32(0.7)
     g["opacity_logits"] -= np.float32(2.0)  # few pixels saturate: many tiles need their whole list
@@ -434,17 +434,20 @@ def test_tile_list_prefix_and_redo_leave_results_unchanged(gsp_lib, prefix):
     check_grads(part["grads"], gr, gm, 800, skip)
 
 
-def test_score_in_forward_writes_whole_lists(gsp_lib):
-    """A forward that accumulates the score composites every tile once: it
-    writes whole lists whatever list_prefix says (no tile is redone)."""
+def test_score_in_forward_with_resumed_tiles(gsp_lib):
+    """The forward's edge score over resumed tiles: each (pixel, Gaussian)
+    term is added once, before or after the resume."""
     g = synth.gaussians(800, 3, seed=8)
     g["opacity_logits"] -= np.float32(2.0)
     cam = synth.camera_front(128, 96)
     e = np.random.default_rng(4).uniform(0, 2, (96, 128))
-    a = gpu_render(gsp_lib, g, [cam], edges=[e], score_in="fwd", list_prefix=1)
+    a = gpu_render(gsp_lib, g, [cam], edges=[e], score_in="fwd", list_prefix=5)
     b = gpu_render(gsp_lib, g, [cam], edges=[e], score_in="fwd", list_prefix=1 << 40)
-    assert a["redone"] == 0
+    assert a["redone"] > 0 and b["redone"] == 0
     for k in ("rgb", "T", "last"):
         assert np.array_equal(a[k], b[k]), k
     # floating-point atomics: equal up to the order of the additions
     assert np.allclose(a["score"], b["score"], rtol=1e-5, atol=1e-6 * float(np.abs(b["score"]).max()))
+    ref = orc.render(g, cam, edge=e)
+    check_image(a, [ref], [cam])
+    check_scores(a["score"], ref["score"], exempt_gaussians(g, cam, ref))
