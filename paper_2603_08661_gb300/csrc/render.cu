@@ -971,14 +971,27 @@ __global__ void __launch_bounds__(kScanThreads) l1_scan(const __grid_constant__ 
         unsigned *row = st.count1 + (size_t)gs * st.nch1_max;
         const int q = (nch + kScanThreads - 1) / kScanThreads;
         const int c0 = threadIdx.x * q, c1 = min(c0 + q, nch);
+        // (8 loads in flight per step: a running sum over dependent loads
+        // would wait for each one)
         unsigned long long sum = 0;
-        for (int c = c0; c < c1; ++c) sum += row[c];
+        for (int c = c0; c < c1; c += 8) {
+            unsigned x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = c + u < c1 ? row[c + u] : 0u;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sum += x[u];
+        }
         unsigned long long total;
         unsigned long long run = block_excl_scan<kScanThreads>(sum, wsum, &total);
-        for (int c = c0; c < c1; ++c) {
-            const unsigned x = row[c];
-            row[c] = unsigned(run);
-            run += x;
+        for (int c = c0; c < c1; c += 8) {
+            unsigned x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = c + u < c1 ? row[c + u] : 0u;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (c + u < c1) row[c + u] = unsigned(run);
+                run += x[u];
+            }
         }
         if (threadIdx.x == 0) st.len1[gs] = unsigned(total);
     }
@@ -1196,16 +1209,28 @@ __global__ void __launch_bounds__(kScanThreads) l2_scan(const __grid_constant__ 
     const unsigned cb0 = over ? 0u : st.chunk2_base[gs], cb1 = over ? 0u : st.chunk2_base[gs + 1];
     const unsigned nch = cb1 - cb0, q = (nch + kGroups - 1) / kGroups;
     const unsigned c0 = cb0 + grp * q, c1 = min(c0 + q, cb1);
+    // (8 loads in flight per step, as in l1_scan)
     unsigned sum = 0;
-    for (unsigned c = c0; c < c1; ++c) sum += st.count2[(size_t)c * 64 + b];
+    for (unsigned c = c0; c < c1; c += 8) {
+        unsigned x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = c + u < c1 ? st.count2[(size_t)(c + u) * 64 + b] : 0u;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sum += x[u];
+    }
     part[grp][b] = sum;
     __syncthreads();
     unsigned run = 0;
     for (int g2 = 0; g2 < grp; ++g2) run += part[g2][b];
-    for (unsigned c = c0; c < c1; ++c) {
-        const unsigned x = st.count2[(size_t)c * 64 + b];
-        st.count2[(size_t)c * 64 + b] = run;
-        run += x;
+    for (unsigned c = c0; c < c1; c += 8) {
+        unsigned x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = c + u < c1 ? st.count2[(size_t)(c + u) * 64 + b] : 0u;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (c + u < c1) st.count2[(size_t)(c + u) * 64 + b] = run;
+            run += x[u];
+        }
     }
     if (grp == kGroups - 1) {
         const int gt = super_tile(V, sx, sy, b);
