@@ -213,6 +213,22 @@ def issue_roofline(stage, variants, n_sm, sm_mhz, avg_ms):
             "source": "ncu sm__inst_executed.sum; 4 schedulers x SMs x max SM clock"}
 
 
+# Warp instructions per launch of the edge map's walk kernel (32 views of
+# 1237x822, fused mode) from one ncu capture (sm__inst_executed.sum), valid
+# while the walk kernel's source is the one that was captured.
+NCU_INST_EDGE = (193_025_188, "e2b2eee3cd110565")
+
+
+def edge_walk_source_hash():
+    """Hash of the walk kernel's source and the helpers before the tile kernel."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2603_08661_gb300", "csrc", "edge.cu")).read()
+    a = src.index("// ================================================================ tile kernel")
+    b = src.index("// ================================================================ walk kernel")
+    c = src.index("// ------------------------------------------------------------ plain path")
+    return hashlib.sha256((src[:a] + src[b:c]).encode()).hexdigest()[:16]
+
+
 def alu_peak_tflops(n_sm, sm_max_mhz):
     """FP32 peak from unit counts and clock: SMs x 128 lanes x 2 flops (FMA) x clock."""
     return n_sm * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
@@ -643,9 +659,12 @@ def measure_gating(gsp, r, target, E, k, reps=10):
             "note": "eager launches incl. host overhead; statistic fused into the adjoint's parameter pass"}
 
 
-def run_edge_batched(steps=10, warmup=3):
+def run_edge_batched(steps=10, warmup=3, sm_max_mhz=None):
     """32 views of 1237x822: the fused edge map (every stage of every view in one
-    cooperative launch) against the plain path (one launch per stage and view)."""
+    cooperative launch) against the plain path (one launch per stage and view).
+    `issue`: the walk kernel's instruction-issue bound (its ncu warp
+    instructions at one per cycle on 4 schedulers x SMs x max SM clock) against
+    the measured launch time, while its source is the captured one."""
     import torch
 
     import paper_2603_08661_gb300 as gsp
@@ -667,10 +686,19 @@ def run_edge_batched(steps=10, warmup=3):
     gsp.raise_on_device_status(status, "edge batched")
     algo = npix * (3 + 4)
     hbm, _ = peaks()
+    issue = None
+    if NCU_INST_EDGE is not None and NCU_INST_EDGE[1] == edge_walk_source_hash():
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+        peak = 4 * n_sm * (sm_max_mhz or 2070) * 1e6
+        min_ms = NCU_INST_EDGE[0] / peak * 1e3
+        issue = {"warp_inst_per_launch": NCU_INST_EDGE[0], "min_ms": round(min_ms, 4),
+                 "frac": round(min_ms / res["fused"], 4),
+                 "source": "ncu sm__inst_executed.sum; 4 schedulers x SMs x max SM clock"}
     return {"workload": "32 views 1237x822 uint8 RGB -> fp32 E", "ms_fused_batched": round(res["fused"], 4),
             "ms_plain_per_view_per_stage": round(res["plain"], 4),
             "fused_achieved_gbs": round(algo / (res["fused"] * 1e-3) / 1e9, 1),
             "fused_frac_of_hbm": round(algo / (res["fused"] * 1e-3) / 1e9 / hbm, 4),
+            "issue": issue,
             "algorithmic_bytes": algo, "l2": "inputs 98 MB + outputs 130 MB per launch (larger than L2)"}
 
 
@@ -1104,7 +1132,10 @@ def main():
                                   ("loop", "densify_loop", run_densify_loop)):
                 if name in legs:
                     torch.cuda.empty_cache()
-                    line[key] = fn()
+                    if name == "edge":
+                        line[key] = fn(sm_max_mhz=(line.get("clocks") or {}).get("sm_max_mhz"))
+                    else:
+                        line[key] = fn()
         elif world > 1 and not args.no_extra and "multiview" in legs:
             # N > 1: the multi-view workload runs view-sharded (one all-reduce per iteration)
             import torch
