@@ -80,3 +80,47 @@ def test_argument_errors_are_returned_before_any_launch(lib):
     assert L.gsp_edge_map(d, 0, 1, 1, None, None, None, 0, 1, None) == _lib.GSP_ERR_INVALID_ARG
     g = _lib.Gaussians()
     assert L.gsp_las_split(ctypes.byref(g), None, None, 0, None, None, 0, None, None) == _lib.GSP_ERR_INVALID_ARG
+
+
+STRUCTS = {"ImageDesc": "gsp_image_desc", "EdgeOpts": "gsp_edge_opts", "Gaussians": "gsp_gaussians",
+           "Camera": "gsp_camera", "RenderOpts": "gsp_render_opts", "LrSchedule": "gsp_lr_schedule",
+           "SelectOpts": "gsp_select_opts", "LasParams": "gsp_las_params"}
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes mirror of a gsp.h struct has the C struct's size and, field
+    by field, its names and offsets (a C program compiled against the header
+    prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2603_08661_gb300 import _lib as L
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gsp.h"', "int main(void) {"]
+    for py, c in STRUCTS.items():
+        lines.append(f'printf("{py} size %zu\\n", sizeof({c}));')
+        for name, _ in getattr(L, py)._fields_:
+            lines.append(f'printf("{py} {name} %zu\\n", offsetof({c}, {name}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for py in STRUCTS:
+        cls = getattr(L, py)
+        assert c_layout[(py, "size")] == ctypes.sizeof(cls), py
+        for name, _ in cls._fields_:
+            assert c_layout[(py, name)] == getattr(cls, name).offset, (py, name)
+    # every field of every C struct is mirrored (the header's member names)
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    for py, c in STRUCTS.items():
+        body = re.search(r"typedef struct " + c + r"\s*\{(.*?)\}\s*" + c + ";", text, flags=re.S).group(1)
+        members = []
+        for decl in body.split(";"):
+            decl = re.sub(r"\[[^\]]*\]", "", decl).strip()
+            if decl:  # "type a, b" declares a and b: the last identifier of each declarator
+                members += [re.findall(r"[A-Za-z_]\w*", d)[-1] for d in decl.split(",")]
+        assert members == [n for n, _ in getattr(L, py)._fields_], (c, members)
