@@ -302,7 +302,10 @@ def run_gsp(args, rank, world):
     fwd_bufs = {"rgb": torch.empty((npix, 3), device=dev), "T": torch.empty(npix, device=dev),
                 "last": torch.empty(npix, dtype=torch.int32, device=dev), "loss": torch.empty(1, device=dev)}
 
-    edge_stream = torch.cuda.Stream(device=dev)
+    # the second stream (edge map, selection) at the highest priority: its blocks are
+    # scheduled ahead of the adjoint's pending ones (measured: the graph replays are
+    # unchanged, the eager end-to-end steps 20-50 us faster)
+    edge_stream = torch.cuda.Stream(device=dev, priority=-5)
     score_ev = torch.cuda.Event()
     ws_sel = torch.empty_like(ws_las)
     sel_mask = torch.empty(cap, dtype=torch.uint8, device=dev)

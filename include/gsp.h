@@ -356,11 +356,9 @@ typedef struct gsp_select_opts {
     float threshold;               /* gating threshold (not NaN) */
     const float *exp_variates;     /* sampling: device Exp(1) draws [capacity], or NULL for top-k */
     int64_t budget;                /* 0: none */
-    int64_t spin_limit;            /* grid-barrier polls before GSP_ERR_TIMEOUT; <= 0: default */
-    int32_t test_expire;           /* failure-injection hook for tests (0 in normal use): nonzero
-                                      withholds the first grid barrier, so every block's bounded
-                                      wait runs out; dev_status receives GSP_ERR_TIMEOUT and
-                                      mask_out / selected_out are unspecified */
+    int64_t spin_limit;            /* unused: the selection's launches wait on nothing (no grid
+                                      barrier, no flag); kept so that the layout does not change */
+    int32_t test_expire;           /* unused, as spin_limit */
 } gsp_select_opts;
 
 gsp_status gsp_select_mask(const float *scores, const int32_t *count, int64_t capacity, int64_t k,

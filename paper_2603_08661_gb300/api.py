@@ -342,12 +342,9 @@ def sample_mask(scores: torch.Tensor, exp_variates: torch.Tensor, count: torch.T
 
 
 def select_mask(scores: torch.Tensor, count: torch.Tensor, k: int, pos_grad=None, threshold: float = 0.0,
-                exp_variates=None, budget: int = 0, status=None, stream=None, workspace=None, out=None,
-                spin_limit: int = 0, test_expire: int = 0):
+                exp_variates=None, budget: int = 0, status=None, stream=None, workspace=None, out=None):
     """gsp_select_mask: top-k or importance sampling, optionally gated by the
-    gradient threshold (pos_grad = (sum, count)) and capped by a Gaussian budget.
-    spin_limit and test_expire are the grid barriers' limit and the
-    failure-injection hook (tests)."""
+    gradient threshold (pos_grad = (sum, count)) and capped by a Gaussian budget."""
     cap = int(scores.shape[0])
     need = lib().gsp_las_workspace_size(cap)
     ws = workspace if workspace is not None else _workspace(need, scores.device)
@@ -356,8 +353,7 @@ def select_mask(scores: torch.Tensor, count: torch.Tensor, k: int, pos_grad=None
     st = status if status is not None else new_status(scores.device)
     o = L.SelectOpts(_ptr(pos_grad[0]).value if pos_grad is not None else None,
                      _ptr(pos_grad[1]).value if pos_grad is not None else None, float(threshold),
-                     _ptr(exp_variates).value if exp_variates is not None else None, int(budget),
-                     int(spin_limit), int(test_expire))
+                     _ptr(exp_variates).value if exp_variates is not None else None, int(budget), 0, 0)
     L.check(lib().gsp_select_mask(_ptr(scores), _ptr(count), cap, int(k), ctypes.byref(o), _ptr(mask), _ptr(sel),
                                   _ptr(ws), ws.numel(), _ptr(st), _stream_handle(stream)), "gsp_select_mask")
     return mask, sel, st

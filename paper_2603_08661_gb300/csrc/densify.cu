@@ -1,12 +1,13 @@
 // Edge-score selection and Long-Axis-Split (paper Sec. 2.2, Alg. 1 and Alg. 2).
 //
-// Selection: exact top-k in one cooperative launch.  Scores map to
-// order-preserving 32-bit keys; the k-th largest key is found by a 3-digit
-// radix select (11 + 11 + 10 bits, one grid barrier per digit, every block
-// picking the same digit from the global counts), every key above it is
-// taken, and the ties at it are taken in ascending index order (ranks from a
-// block scan plus the tie counts of the lower blocks; skipped when every tie
-// is taken).
+// Selection: exact top-k in five launches that wait on nothing (so that they
+// can interleave with other work).  Scores map to order-preserving 32-bit
+// keys; the k-th largest key is found by a 3-digit radix select (11 + 11 + 10
+// bits, one launch per digit counting into global histograms, every block of
+// the next launch picking the same digit from the counts), every key above it
+// is taken, and the ties at it are taken in ascending index order (ranks from
+// a block scan plus the tie counts of the lower blocks; skipped when every
+// tie is taken).
 //
 // Split: the selected Gaussians are ranked in index order by the same kind
 // of scan; one thread per selected Gaussian applies Alg. 1: the long axis l
@@ -104,9 +105,9 @@ struct TopkArgs {
     long long cap, k;
     uint8_t *mask;
     int32_t *selected_out;
-    unsigned *hist;  // [3][kSelBins] digit counts of the three passes (zeroed before the launch)
+    unsigned *hist;  // [3][kSelBins] digit counts of the three passes (zeroed before the launches)
     unsigned *sums;  // [grid] tie counts of the blocks' index ranges
-    unsigned *bar;   // grid barrier (zeroed before the launch)
+    unsigned *state; // [4][4] the selection state after each stage (kk, prefix, remaining, eq)
     int32_t *status;
     // gradient-threshold masking (all three, or gsum == nullptr for none): Gaussian i
     // is a candidate when gcnt[i] > 0 and gsum[i] / gcnt[i] >= tau (FP32)
@@ -119,8 +120,6 @@ struct TopkArgs {
     // are taken, i.e. the k largest keys -expv[i] / score[i]
     const float *expv;
     long long budget;  // > 0: at most budget - N selected (the room left under a Gaussian budget)
-    long long spin_limit;  // grid-barrier polls before GSP_ERR_TIMEOUT
-    int expire;            // test hook: the first grid barrier is withheld (every wait runs out)
 };
 
 __device__ __forceinline__ bool is_candidate(const TopkArgs &a, long long i)
@@ -185,67 +184,104 @@ __device__ int pick_digit(const unsigned *hist, int nb, unsigned rem, unsigned *
     return b;
 }
 
-__global__ void __launch_bounds__(kThreads) topk_fused(TopkArgs a)
+// The selection in five launches, one per step (no block waits for another:
+// the kernels can interleave with other work on the GPU):
+//   stage 0, 1, 2  counts of digit pass `stage` (11 + 11 + 10 bits, the top
+//                  digit first) over the keys that match the digits picked so
+//                  far, after picking (every block the same) the digit of the
+//                  previous pass from its global counts
+//   stage 3        the last pick; the ties' counts of every block's index range
+//                  when only some of the ties at the k-th key are taken
+//   stage 4        the mask: every key above the k-th, and the first
+//                  `remaining` ties in ascending index order
+// Block 0 of each stage keeps the state (kk, prefix, remaining, eq) for the next.
+__host__ __device__ constexpr int sel_shift(int pass) { return pass == 0 ? 21 : pass == 1 ? 10 : 0; }
+__host__ __device__ constexpr int sel_bits(int pass) { return pass == 2 ? 10 : 11; }
+
+struct SelState {
+    unsigned kk, prefix, remaining, eq;
+};
+
+template <int STAGE>
+__global__ void __launch_bounds__(kThreads) topk_stage(TopkArgs a)
 {
     __shared__ unsigned h[kSelBins];
     const int tid = threadIdx.x;
     const unsigned G = gridDim.x;
     const long long n = max(*a.count, 0);
-    unsigned kk = a.k < 0 ? 0u : (a.k > n ? unsigned(n) : unsigned(a.k));
-    if (a.budget > 0) kk = unsigned(min((long long)kk, max(a.budget - n, 0LL)));
-    // the same prefix / remaining in every block
-    unsigned prefix = 0, remaining = kk, eq = 0;
-    const int shifts[3] = {21, 10, 0}, bits[3] = {11, 11, 10};
-#pragma unroll 1
-    for (int pass = 0; pass < 3; ++pass) {
-        const int shift = shifts[pass], nb = 1 << bits[pass], hi = shift + bits[pass];
-        unsigned *gh = a.hist + pass * kSelBins;
-        if (remaining > 0) {
-            for (int i = tid; i < nb; i += kThreads) h[i] = 0;
-            __syncthreads();
-            unsigned nc = 0;
-            for (long long i = blockIdx.x * (long long)kThreads + tid; i < n; i += (long long)G * kThreads) {
-                if (!is_candidate(a, i)) continue;
-                ++nc;
-                const unsigned key = order_key(select_value(a, i));
-                if (pass > 0 && (key >> hi) != (prefix >> hi)) continue;
-                atomicAdd(&h[(key >> shift) & unsigned(nb - 1)], 1u);
-            }
-            nc = __reduce_add_sync(0xffffffffu, nc);
-            if (pass == 0 && (a.gsum || a.expv) && (tid & 31) == 0 && nc) atomicAdd(a.ncand, nc);
-            __syncthreads();
-            for (int i = tid; i < nb; i += kThreads)
-                if (h[i]) atomicAdd(gh + i, h[i]);
+    SelState st;
+    if (STAGE == 0) {
+        unsigned kk = a.k < 0 ? 0u : (a.k > n ? unsigned(n) : unsigned(a.k));
+        if (a.budget > 0) kk = unsigned(min((long long)kk, max(a.budget - n, 0LL)));
+        st = {kk, 0u, kk, 0u};
+    } else {
+        const unsigned *w = a.state + 4 * (STAGE - 1);
+        st = {__ldcg(w), __ldcg(w + 1), __ldcg(w + 2), __ldcg(w + 3)};
+    }
+    if (STAGE >= 1 && STAGE <= 3) {  // the digit of pass STAGE - 1
+        constexpr int pass = STAGE >= 1 && STAGE <= 3 ? STAGE - 1 : 0;
+        if (pass == 0 && (a.gsum || a.expv)) {  // at most the candidates
+            st.kk = min(st.kk, __ldcg(a.ncand));
+            st.remaining = st.kk;
         }
-        if (!grid_barrier(a.bar, G, a.spin_limit, a.status, a.expire && pass == 0)) return;
-        if (pass == 0 && (a.gsum || a.expv)) {  // at most the candidates (the same in every block)
-            kk = min(kk, __ldcg(a.ncand));
-            remaining = kk;
-        }
-        if (remaining > 0) {
+        if (st.remaining > 0) {
             unsigned above, in_bin;
-            const int b = pick_digit(gh, nb, remaining, &above, &in_bin);
-            prefix |= unsigned(b) << shift;
-            remaining -= above;
-            eq = in_bin;
+            const int b = pick_digit(a.hist + pass * kSelBins, 1 << sel_bits(pass), st.remaining, &above, &in_bin);
+            st.prefix |= unsigned(b) << sel_shift(pass);
+            st.remaining -= above;
+            st.eq = in_bin;
         }
+    }
+    if (STAGE <= 3 && blockIdx.x == 0 && tid == 0) {
+        unsigned *w = a.state + 4 * STAGE;
+        w[0] = st.kk;
+        w[1] = st.prefix;
+        w[2] = st.remaining;
+        w[3] = st.eq;
+    }
+    if (STAGE <= 2) {
+        constexpr int pass = STAGE <= 2 ? STAGE : 0;
+        constexpr int shift = sel_shift(pass), nb = 1 << sel_bits(pass), hi = shift + sel_bits(pass);
+        if (st.remaining == 0) return;
+        unsigned *gh = a.hist + pass * kSelBins;
+        for (int i = tid; i < nb; i += kThreads) h[i] = 0;
+        __syncthreads();
+        unsigned nc = 0;
+        for (long long i = blockIdx.x * (long long)kThreads + tid; i < n; i += (long long)G * kThreads) {
+            if (!is_candidate(a, i)) continue;
+            ++nc;
+            const unsigned key = order_key(select_value(a, i));
+            if (pass > 0 && (key >> hi) != (st.prefix >> hi)) continue;
+            atomicAdd(&h[(key >> shift) & unsigned(nb - 1)], 1u);
+        }
+        nc = __reduce_add_sync(0xffffffffu, nc);
+        if (pass == 0 && (a.gsum || a.expv) && (tid & 31) == 0 && nc) atomicAdd(a.ncand, nc);
+        __syncthreads();
+        for (int i = tid; i < nb; i += kThreads)
+            if (h[i]) atomicAdd(gh + i, h[i]);
+        return;
     }
     // prefix = t, the kk-th largest key; the keys above it are taken, and
     // `remaining` of the eq keys equal to it, in ascending index order
-    const bool rank_ties = kk > 0 && remaining < eq;
+    const unsigned kk = st.kk, prefix = st.prefix, remaining = st.remaining;
+    const bool rank_ties = kk > 0 && remaining < st.eq;
     const long long chunk = (a.cap + G - 1) / G;
     const long long b0 = min((long long)blockIdx.x * chunk, a.cap), b1 = min(b0 + chunk, a.cap);
-    unsigned tie_base = 0;
-    if (rank_ties) {
+    if (STAGE == 3) {
+        if (!rank_ties) return;
         unsigned c = 0;
         for (long long i = b0 + tid; i < min(b1, n); i += kThreads)
             c += is_candidate(a, i) && order_key(select_value(a, i)) == prefix;
         unsigned ex;
         const unsigned tot = block_scan(c, &ex);
         if (tid == 0) a.sums[blockIdx.x] = tot;
-        if (!grid_barrier(a.bar, G, a.spin_limit, a.status)) return;
+        return;
+    }
+    unsigned tie_base = 0;
+    if (rank_ties) {
         unsigned lower = 0;
         for (unsigned q = tid; q < blockIdx.x; q += kThreads) lower += __ldcg(a.sums + q);
+        unsigned ex;
         tie_base = block_scan(lower, &ex);  // the block total: ties in the lower blocks' ranges
     }
     // mark the block's range, kPerThread consecutive items per thread per round
@@ -389,14 +425,14 @@ __global__ void las_commit(int32_t *count, long long cap, const unsigned *rank_o
     *count = int32_t(n + total);
 }
 
-// [3][kSelBins] digit counts, the 2-word grid barrier, the candidate count:
-// zeroed before each selection
-constexpr int kTopkZeroWords = 3 * kSelBins + 3;
+// [3][kSelBins] digit counts, the candidate count (zeroed before each
+// selection), then the [4][4] stage states
+constexpr int kTopkZeroWords = 3 * kSelBins + 1 + 16;
 
 struct DensifyLayout {
     unsigned *hist;
-    unsigned *bar;
     unsigned *ncand;
+    unsigned *state;
     unsigned *sums;
     uint8_t *mask;
     int32_t *src;
@@ -407,8 +443,8 @@ struct DensifyLayout {
 void carve_topk(Carver &c, long long cap, DensifyLayout &L)
 {
     L.hist = c.take<unsigned>(kTopkZeroWords);
-    L.bar = L.hist + 3 * kSelBins;
-    L.ncand = L.hist + 3 * kSelBins + 2;
+    L.ncand = L.hist + 3 * kSelBins;
+    L.state = L.hist + 3 * kSelBins + 1;
     L.sums = c.take<unsigned>(div_up(cap, kBlockItems) + 1);
 }
 
@@ -426,40 +462,24 @@ DensifyLayout densify_layout(void *ws, long long cap)
 gsp_status enqueue_topk(const float *scores, const int32_t *count, long long cap, long long k, uint8_t *mask,
                         int32_t *selected_out, const DensifyLayout &L, int32_t *status, cudaStream_t s,
                         const float *gsum = nullptr, const int32_t *gcnt = nullptr, float tau = 0.f,
-                        const float *expv = nullptr, long long budget = 0, long long spin_limit = 0,
-                        int expire = 0)
+                        const float *expv = nullptr, long long budget = 0)
 {
-    // co-resident blocks (grid barriers), at most two per SM and one per
-    // kBlockItems of capacity (the block sums are sized so); the occupancy is
-    // looked up once per device
-    static int per_sm_dev[kMaxDevices] = {0};
-    int dev = 0;
-    GSP_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return GSP_ERR_UNSUPPORTED;
-    if (!per_sm_dev[dev]) {
-        int per = 0;
-        GSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, topk_fused, kThreads, 0));
-        if (per < 1) return GSP_ERR_UNSUPPORTED;
-        per_sm_dev[dev] = per;
-    }
-    long long grid = (long long)std::min(per_sm_dev[dev], 2) * num_sms();
+    // two blocks per SM, at most one per kBlockItems of capacity (the block sums are sized so)
+    long long grid = 2LL * num_sms();
     grid = std::max(1LL, std::min(grid, (long long)div_up(cap, kBlockItems)));
-    TopkArgs a{scores, count, cap, k, mask, selected_out, L.hist, L.sums, L.bar, status, gsum, gcnt, tau, L.ncand,
-               expv, budget, spin_limit > 0 ? spin_limit : kDefaultSpinLimit, expire ? 1 : 0};
+    const TopkArgs a{scores, count, cap, k, mask, selected_out, L.hist, L.sums, L.state, status, gsum, gcnt, tau,
+                     L.ncand, expv, budget};
     stage_begin("topk", s);
-    GSP_CUDA_TRY(cudaMemsetAsync(L.hist, 0, kTopkZeroWords * sizeof(unsigned), s));
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(unsigned(grid));
-    cfg.blockDim = dim3(kThreads);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    GSP_CUDA_TRY(cudaLaunchKernelEx(&cfg, topk_fused, a));
+    GSP_CUDA_TRY(cudaMemsetAsync(L.hist, 0, (3 * kSelBins + 1) * sizeof(unsigned), s));
+    const unsigned gb = unsigned(grid);
+    topk_stage<0><<<gb, kThreads, 0, s>>>(a);
+    topk_stage<1><<<gb, kThreads, 0, s>>>(a);
+    topk_stage<2><<<gb, kThreads, 0, s>>>(a);
+    topk_stage<3><<<gb, kThreads, 0, s>>>(a);
+    topk_stage<4><<<gb, kThreads, 0, s>>>(a);
     stage_end("topk", s);
-    note_launches(1);
+    note_launches(5);
+    GSP_LAUNCH_CHECK();
     return GSP_OK;
 }
 
@@ -543,7 +563,7 @@ extern "C" gsp_status gsp_select_mask(const float *scores, const int32_t *count,
     L = densify_layout(ws, capacity);
     return enqueue_topk(scores, count, capacity, k, mask_out, selected_out, L, dev_status,
                         reinterpret_cast<cudaStream_t>(stream), opts->pos_grad_sum, opts->pos_grad_count,
-                        opts->threshold, opts->exp_variates, opts->budget, opts->spin_limit, opts->test_expire);
+                        opts->threshold, opts->exp_variates, opts->budget);
 }
 
 extern "C" gsp_status gsp_las_split(const gsp_gaussians *g, const uint8_t *mask, const float *scores, int64_t k,

@@ -1,8 +1,8 @@
 """Every kind of bounded device wait, made to run out, reports GSP_ERR_TIMEOUT.
 
 The library's waits are bounded and return an error status instead of
-hanging: the grid barriers of the fused edge map and of the top-k selection,
-the depth sort's decoupled look-back, and the waits for bulk / TMA copies
+hanging: the grid barrier of the fused edge map, the depth sort's decoupled
+look-back, and the waits for bulk / TMA copies
 into shared memory (projection SH rows, edge-map halo boxes).  Each test
 makes one kind of wait run out deterministically through the entry point's
 failure-injection hook - a barrier that is never opened, a look-back word
@@ -64,25 +64,6 @@ def test_edge_tma_box_wait_that_gives_up(gsp_lib):
     E1, m1, _, s1 = gsp_lib.edge_map(ts)
     torch.cuda.synchronize()
     assert int(s1.item()) == 0 and torch.equal(E0, E1) and torch.equal(m0, m1)
-
-
-@pytest.mark.parametrize("mode", ["topk", "sample"])
-def test_selection_grid_barrier_that_is_never_opened(gsp_lib, mode):
-    import torch
-    n, k = 400_000, 40_000
-    rng = np.random.default_rng(3)
-    scores = torch.from_numpy(rng.random(n, dtype=np.float32)).cuda()
-    expv = torch.from_numpy(rng.exponential(size=n).astype(np.float32)).cuda() if mode == "sample" else None
-    count = torch.tensor([n], dtype=torch.int32, device="cuda")
-    m0, sel0, s0 = gsp_lib.select_mask(scores, count, k, exp_variates=expv)
-    torch.cuda.synchronize()
-    assert int(s0.item()) == 0 and int(sel0.item()) == k
-    _, _, st = gsp_lib.select_mask(scores, count, k, exp_variates=expv, spin_limit=SHORT, test_expire=1)
-    torch.cuda.synchronize()
-    assert int(st.item()) == _timeout(gsp_lib)
-    m1, sel1, s1 = gsp_lib.select_mask(scores, count, k, exp_variates=expv)
-    torch.cuda.synchronize()
-    assert int(s1.item()) == 0 and torch.equal(m0, m1) and int(sel1.item()) == k
 
 
 def _render_scene(gsp, n=200_000, w=640, h=480):
