@@ -399,17 +399,39 @@ __global__ void __launch_bounds__(256) las_copy_sh(LasArgs a, int vec4)
     const int row = 3 * a.K;
     const int chunks = vec4 ? row / 4 : row;
     const long long work = total * chunks;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < work;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long c = t / chunks;
-        const int q = int(t - c * chunks);
-        const long long src = a.src[c], dst = n + c;
-        if (!GSP_BOUND(src, n, a.status)) continue;
-        if (vec4)
-            reinterpret_cast<float4 *>(a.sh + (size_t)dst * row)[q] =
-                reinterpret_cast<const float4 *>(a.sh + (size_t)src * row)[q];
-        else
-            a.sh[(size_t)dst * row + q] = a.sh[(size_t)src * row + q];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // four copies per thread and step, their parent indices and then their
+    // source chunks loaded before any store (each copy is two dependent loads)
+    constexpr int U = 4;
+    for (long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; t0 < work; t0 += U * stride) {
+        long long c[U], src[U];
+        int q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long t = t0 + u * stride;
+            c[u] = t < work ? t / chunks : -1;
+            q[u] = t < work ? int(t - c[u] * chunks) : 0;
+            src[u] = c[u] >= 0 ? (long long)a.src[c[u]] : -1;
+        }
+        if (vec4) {
+            float4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (c[u] >= 0 && GSP_BOUND(src[u], n, a.status))
+                    v[u] = reinterpret_cast<const float4 *>(a.sh + (size_t)src[u] * row)[q[u]];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (c[u] >= 0 && src[u] >= 0 && src[u] < n)
+                    reinterpret_cast<float4 *>(a.sh + (size_t)(n + c[u]) * row)[q[u]] = v[u];
+        } else {
+            float v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (c[u] >= 0 && GSP_BOUND(src[u], n, a.status)) v[u] = a.sh[(size_t)src[u] * row + q[u]];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (c[u] >= 0 && src[u] >= 0 && src[u] < n) a.sh[(size_t)(n + c[u]) * row + q[u]] = v[u];
+        }
     }
 }
 
