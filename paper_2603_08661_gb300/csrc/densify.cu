@@ -137,19 +137,25 @@ __device__ __forceinline__ float select_value(const TopkArgs &a, long long i)
 }
 
 // Block-wide pick of the digit that holds the rem-th largest key, from the
-// counts hist[0 .. nb) (the top digit first): thread t owns the nb / kThreads
-// digits [nb - (t+1) per, nb - t per); a scan of the owners' sums finds the
-// owner, which walks its digits.  Returns the digit; *above = keys in higher
-// digits, *in_bin = keys in the digit.
-__device__ int pick_digit(const unsigned *hist, int nb, unsigned rem, unsigned *above, unsigned *in_bin)
+// counts hist[0 .. NB) (the top digit first): thread t owns the NB / kThreads
+// digits [NB - (t+1) per, NB - t per), loaded at once and kept in registers;
+// a scan of the owners' sums finds the owner, which walks its digits.
+// Returns the digit; *above = keys in higher digits, *in_bin = keys in it.
+template <int NB>
+__device__ int pick_digit(const unsigned *hist, unsigned rem, unsigned *above, unsigned *in_bin)
 {
+    constexpr int per = NB / kThreads;
     __shared__ unsigned wsum[kThreads / 32];
     __shared__ int s_bin;
     __shared__ unsigned s_above, s_in;
-    const int per = nb / kThreads;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned cnt[per];
     unsigned seg = 0;
-    for (int q = 0; q < per; ++q) seg += __ldcg(hist + nb - 1 - (threadIdx.x * per + q));
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+        cnt[q] = __ldcg(hist + NB - 1 - (threadIdx.x * per + q));
+        seg += cnt[q];
+    }
     unsigned inc = seg;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -164,16 +170,15 @@ __device__ int pick_digit(const unsigned *hist, int nb, unsigned rem, unsigned *
     const unsigned before = base + inc - seg;
     if (before < rem && rem <= before + seg) {
         unsigned acc = before;
+#pragma unroll
         for (int q = 0; q < per; ++q) {
-            const int b = nb - 1 - (threadIdx.x * per + q);
-            const unsigned c = __ldcg(hist + b);
-            if (acc + c >= rem) {
-                s_bin = b;
+            if (acc + cnt[q] >= rem) {
+                s_bin = NB - 1 - (threadIdx.x * per + q);
                 s_above = acc;
-                s_in = c;
+                s_in = cnt[q];
                 break;
             }
-            acc += c;
+            acc += cnt[q];
         }
     }
     __syncthreads();
@@ -226,7 +231,7 @@ __global__ void __launch_bounds__(kThreads) topk_stage(TopkArgs a)
         }
         if (st.remaining > 0) {
             unsigned above, in_bin;
-            const int b = pick_digit(a.hist + pass * kSelBins, 1 << sel_bits(pass), st.remaining, &above, &in_bin);
+            const int b = pick_digit<1 << sel_bits(pass)>(a.hist + pass * kSelBins, st.remaining, &above, &in_bin);
             st.prefix |= unsigned(b) << sel_shift(pass);
             st.remaining -= above;
             st.eq = in_bin;
@@ -246,13 +251,26 @@ __global__ void __launch_bounds__(kThreads) topk_stage(TopkArgs a)
         unsigned *gh = a.hist + pass * kSelBins;
         for (int i = tid; i < nb; i += kThreads) h[i] = 0;
         __syncthreads();
+        // (four keys per thread and step, loaded before any is counted)
         unsigned nc = 0;
-        for (long long i = blockIdx.x * (long long)kThreads + tid; i < n; i += (long long)G * kThreads) {
-            if (!is_candidate(a, i)) continue;
-            ++nc;
-            const unsigned key = order_key(select_value(a, i));
-            if (pass > 0 && (key >> hi) != (st.prefix >> hi)) continue;
-            atomicAdd(&h[(key >> shift) & unsigned(nb - 1)], 1u);
+        const long long stride = (long long)G * kThreads;
+        for (long long i0 = blockIdx.x * (long long)kThreads + tid; i0 < n; i0 += 4 * stride) {
+            bool cand[4];
+            float val[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long i = i0 + u * stride;
+                cand[u] = i < n && is_candidate(a, i);
+                val[u] = cand[u] ? select_value(a, i) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!cand[u]) continue;
+                ++nc;
+                const unsigned key = order_key(val[u]);
+                if (pass > 0 && (key >> hi) != (st.prefix >> hi)) continue;
+                atomicAdd(&h[(key >> shift) & unsigned(nb - 1)], 1u);
+            }
         }
         nc = __reduce_add_sync(0xffffffffu, nc);
         if (pass == 0 && (a.gsum || a.expv) && (tid & 31) == 0 && nc) atomicAdd(a.ncand, nc);
@@ -270,8 +288,17 @@ __global__ void __launch_bounds__(kThreads) topk_stage(TopkArgs a)
     if (STAGE == 3) {
         if (!rank_ties) return;
         unsigned c = 0;
-        for (long long i = b0 + tid; i < min(b1, n); i += kThreads)
-            c += is_candidate(a, i) && order_key(select_value(a, i)) == prefix;
+        const long long e = min(b1, n);
+        for (long long i0 = b0 + tid; i0 < e; i0 += 4 * kThreads) {
+            bool t[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long i = i0 + u * kThreads;
+                t[u] = i < e && is_candidate(a, i) && order_key(select_value(a, i)) == prefix;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) c += t[u];
+        }
         unsigned ex;
         const unsigned tot = block_scan(c, &ex);
         if (tid == 0) a.sums[blockIdx.x] = tot;
